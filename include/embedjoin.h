@@ -1,0 +1,218 @@
+/*
+ * embedjoin.h -- C ABI of the GB300-native EmbedJoin hot path.
+ *
+ * Computes the edit-similarity self-join of Section 1 of Zhang & Zhang,
+ * "EmbedJoin: Efficient Edit Similarity Joins via Embeddings" (arXiv 1702.00093):
+ *     { (s_i, s_j) : i != j, ED(s_i, s_j) <= K }
+ * with the randomised method of Algorithms 1-3: CGK embedding (Alg. 1),
+ * bit-sampling LSH with AND/OR amplification (Section 3.2, Thm. 1), bucketing of
+ * equal signatures with the length filter of Alg. 3, and Ukkonen-banded
+ * verification (Section 3.3). All work runs in hand-written CUDA kernels on one
+ * GPU (sm_103a). Output has 100% precision; recall depends on r, m, z, L.
+ *
+ * Naming: r = CGK embeddings per string, m = LSH functions per embedding,
+ * z = sampled positions per function. (Table 1 of the paper calls the number of
+ * functions z and the signature length m: the letters are swapped here.)
+ *
+ * Conventions for every entry point
+ *  - Return value: an ej_status (0 = EJ_OK). No exception crosses the ABI.
+ *    ej_last_error(ctx) gives a one-line description of the last failure.
+ *  - Pointers: every array argument may be device memory or host memory
+ *    (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host arrays through its own device
+ *    buffers. Parameter structs and scalar out-pointers (n_pairs, n_out,
+ *    info, stats) are always host memory.
+ *  - Ownership: the caller owns every input and output array. The context
+ *    owns its scratch memory and reuses it across calls; scratch grows on
+ *    demand and is released by ej_destroy.
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    Kernels are enqueued on it. Entry points that return a count (ej_plan,
+ *    ej_lsh_candidates, ej_verify, ej_join) synchronise that stream before
+ *    returning, so the count and the output are valid on return. ej_embed and
+ *    ej_sign are asynchronous when all their arrays are device memory.
+ *  - One context must not be used by two host threads at once.
+ *  - Strings: a packed byte buffer plus n+1 int64 offsets (offsets[0] = 0,
+ *    non-decreasing); string i is bytes[offsets[i] .. offsets[i+1]).
+ *    n < 2^31, every string shorter than 2^31 bytes, and every byte must be
+ *    one of params->alphabet (else EJ_ERR_INVALID_ARG).
+ *  - Pairs: uint64 (i << 32) | j with 0 <= i < j < n in input order; every
+ *    list of pairs this library returns is sorted ascending and unique.
+ */
+#ifndef EMBEDJOIN_H
+#define EMBEDJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ej_ctx ej_ctx;
+
+typedef enum {
+    EJ_OK = 0,
+    EJ_ERR_INVALID_ARG = 1,  /* bad parameter, offsets or symbol outside the alphabet */
+    EJ_ERR_OOM = 2,          /* device or host allocation failed */
+    EJ_ERR_CAPACITY = 3,     /* output larger than the given capacity; the needed
+                                count is written to the count out-pointer */
+    EJ_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    EJ_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    EJ_ERR_UNSUPPORTED = 6   /* valid request outside what the kernels support
+                                (e.g. a band wider than the verifier's limit) */
+} ej_status;
+
+/* Method parameters (Table 1; Alg. 2 and Alg. 3 inputs). */
+typedef struct {
+    uint32_t r;              /* CGK embeddings per string, 1..255 */
+    uint32_t m;              /* LSH functions per embedding, 1..65535 */
+    uint32_t z;              /* sampled positions per function, >= 1, with
+                                (alphabet_size+1)^z < 2^64 (exact 64-bit keys) */
+    uint32_t L;              /* truncation (Section 4.1): positions are drawn from
+                                [0, L); 0 => out_len */
+    uint32_t out_len;        /* embedding length; 0 => 3N, N = longest string
+                                (Alg. 1). Must be >= L. */
+    int32_t K;               /* edit distance threshold, inclusive, >= 0 */
+    uint64_t seed;           /* seeds the random strings R^l and the positions */
+    const uint8_t *alphabet; /* host pointer: alphabet_size distinct raw bytes; the
+                                index of a byte here is its symbol code */
+    uint32_t alphabet_size;  /* 1..255; the padding symbol (bottom) gets code
+                                alphabet_size */
+} ej_params;
+
+typedef struct {
+    const uint8_t *bytes;    /* packed string bytes (device or host) */
+    const int64_t *offsets;  /* n+1 offsets (device or host) */
+    int64_t n;               /* number of strings */
+} ej_strings;
+
+/* Sizes derived from the strings and parameters (filled by ej_plan). */
+typedef struct {
+    int64_t n;               /* strings */
+    int64_t max_len;         /* N, the longest string */
+    int64_t total_bytes;     /* offsets[n] */
+    uint32_t out_len;        /* effective embedding length */
+    uint32_t L;              /* effective sampling range */
+    uint32_t planes;         /* bit planes per embedded symbol: ceil(log2(alphabet_size)), >= 1 */
+    uint32_t blocks32;       /* ceil(n / 32): string blocks of the embedding layout */
+    uint64_t embedding_bytes;/* bytes of the ej_embed output */
+    uint64_t walk_end_count; /* r * n int32 entries of walk_end */
+    uint64_t key_count;      /* r * m * n uint64 entries of ej_sign output */
+} ej_plan_info;
+
+/* Counters of one join (filled by ej_join when stats != NULL). */
+typedef struct {
+    int64_t n_raw_pairs;     /* bucket pairs passing the length filter, before dedup */
+    int64_t n_candidates;    /* unique candidate pairs (verified) */
+    int64_t n_out;           /* output pairs */
+    int64_t max_bucket;      /* largest bucket (run of equal keys in one table) */
+    float ms_embed;          /* stage times, CUDA events on `stream` (only with */
+    float ms_sign;           /* ej_set_timing(ctx, 1); else 0)                  */
+    float ms_candidates;
+    float ms_verify;
+    float ms_total;
+} ej_join_stats;
+
+/* Create a context bound to CUDA device `device`. *ctx is NULL on failure. */
+int ej_create(ej_ctx **ctx, int device);
+
+/* Release the context and all its scratch memory. NULL is ignored. */
+void ej_destroy(ej_ctx *ctx);
+
+/* Static description of a status code; never NULL. */
+const char *ej_status_string(int status);
+
+/* Description of the last error on this context ("" if none). Valid until the
+ * next call on the context. */
+const char *ej_last_error(ej_ctx *ctx);
+
+/* Turn per-stage CUDA-event timing of ej_join on (1) or off (0). */
+int ej_set_timing(ej_ctx *ctx, int enable);
+
+/*
+ * Validate the strings against the parameters and report the derived sizes
+ * (N, out_len = 3N or params->out_len, L, the embedding layout). Checks
+ * offsets (start at 0, non-decreasing), lengths (< 2^31), symbols (all in the
+ * alphabet) and parameters (Section 4 constraints listed on ej_params).
+ * Synchronises `stream`.
+ */
+int ej_plan(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, ej_plan_info *info,
+            void *stream);
+
+/*
+ * CGK embedding (Algorithm 1) of every string, r times.
+ * Walk of string x under embedding l: i = 0; for step j = 0 .. out_len-1:
+ * if i < |x| emit x[i] and advance i by pi_j^l(x[i]), else emit bottom.
+ * pi_j^l(sigma) is the top bit of splitmix64(splitmix64(seed) ^ (1<<56 | l<<48 |
+ * j<<8 | sigma)) with sigma the raw byte (the library's reading of the random
+ * string R^l of Alg. 1; splitmix64 as published by Steele, Lea and Flood 2014).
+ *
+ * emb (device or host, info.embedding_bytes bytes), bit-sliced layout:
+ *   uint32 word emb[((l * blocks32 + B) * out_len + j) * planes + k]
+ *   bit t of that word = bit k of the code of t^l_{32B+t}[j] (0 for strings
+ *   >= n and for steps at or after walk_end).
+ * walk_end (int32, r*n, [l][i]): the first step whose output is bottom
+ *   (out_len if the walk does not finish; 0 for an empty string).
+ */
+int ej_embed(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, void *emb,
+             int32_t *walk_end, void *stream);
+
+/*
+ * Bit-sampling LSH signatures (Theorem 1 with AND amplification, Section 3.2):
+ * for table t = l*m + f and string i,
+ *   keys[t * n + i] = sum_{q<z} c_q * (alphabet_size+1)^q
+ * where c_q is the code of t^l_i[P[l][f][q]] (alphabet_size if that step is at
+ * or after walk_end) and P[l][f][q] = mulhi64(splitmix64(splitmix64(seed) ^
+ * (2<<56 | l<<48 | f<<32 | q)), L) -- positions drawn with replacement from
+ * [0, L). emb/walk_end are ej_embed's outputs for the same strings and params.
+ */
+int ej_sign(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, const void *emb,
+            const int32_t *walk_end, uint64_t *keys, void *stream);
+
+/*
+ * Candidate pairs (Algorithm 3, filtering stage): all i < j such that some
+ * table t has keys[t*n+i] == keys[t*n+j] and ||s_i| - |s_j|| <= K (the
+ * length filter of Alg. 3), deduplicated (Alg. 3 removes duplicate pairs).
+ * keys is ej_sign's output. Writes up to `capacity` pairs to `pairs`; on
+ * overflow returns EJ_ERR_CAPACITY with the needed count in *n_pairs.
+ * If stats_max_bucket != NULL it receives the largest bucket size.
+ */
+int ej_lsh_candidates(ej_ctx *ctx, const ej_strings *strings, const ej_params *params,
+                      const uint64_t *keys, uint64_t *pairs, int64_t capacity, int64_t *n_pairs,
+                      int64_t *stats_max_bucket, void *stream);
+
+/*
+ * Verification (Section 3.3; last loop of Alg. 3): keeps the pairs with
+ * ED(s_i, s_j) <= params->K (only K and the alphabet of params are used).
+ * Pairs need not be sorted or unique; i and j must be < n. Output keeps the
+ * input order; `out` must hold n_pairs entries. Exact: the result equals a full
+ * Ukkonen band DP. Supports K up to 4095.
+ */
+int ej_verify(ej_ctx *ctx, const ej_strings *strings, const ej_params *params,
+              const uint64_t *pairs, int64_t n_pairs, uint64_t *out, int64_t *n_out, void *stream);
+
+/*
+ * The whole method (Algorithm 3 with Algorithm 2's preprocessing):
+ * embed -> sign -> candidates -> verify. Writes up to `capacity` output pairs
+ * (sorted ascending); on overflow returns EJ_ERR_CAPACITY with the needed count
+ * in *n_out. n < 2 gives 0 pairs. stats may be NULL.
+ */
+int ej_join(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, uint64_t *out,
+            int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream);
+
+/*
+ * Test hook for the running example of Section 4 (Tables 2-4): replace the
+ * random bits and positions with explicit tables (host pointers, copied).
+ *   pi: [r][steps][alphabet_size] bytes in {0,1}, code-indexed; steps at or
+ *       beyond `steps` read 0.
+ *   positions: [r][m][z] uint32, each < L.
+ * Either pointer may be NULL to keep the random source for that part.
+ * ej_set_test_tables(ctx, NULL, 0, 0, 0, NULL, 0, 0) restores both.
+ */
+int ej_set_test_tables(ej_ctx *ctx, const uint8_t *pi, uint32_t r, uint32_t steps,
+                       uint32_t alphabet_size, const uint32_t *positions, uint32_t m, uint32_t z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMBEDJOIN_H */

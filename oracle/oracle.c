@@ -451,7 +451,8 @@ int or_join(const uint8_t *data, const int64_t *offsets, int64_t n, const or_par
     int64_t N = 0;
     for (int64_t s = 0; s < n; s++)
         if (offsets[s + 1] - offsets[s] > N) N = offsets[s + 1] - offsets[s];
-    int64_t out_len = p->out_len ? p->out_len : 3 * N;
+    /* Alg. 1 pads to 3N; a set of empty strings still gets one (bottom) step */
+    int64_t out_len = p->out_len ? p->out_len : (N > 0 ? 3 * N : 1);
     uint32_t L = p->L ? p->L : (uint32_t)out_len;
     st->out_len = out_len; st->L = L;
     if (n < 2) return OR_OK;

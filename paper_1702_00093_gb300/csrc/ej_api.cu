@@ -1,0 +1,719 @@
+// C ABI of the EmbedJoin hot path: argument checks, the context's scratch
+// arena, host/device pointer staging and the stage orchestration of ej_join.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ej_internal.cuh"
+
+namespace ej {
+cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uint8_t *code_map,
+                                  uint32_t *err, cudaStream_t s);
+}
+
+using namespace ej;
+
+namespace {
+
+enum BufId {
+    B_BYTES, B_OFFSETS, B_LENS, B_DERR, B_CODEMAP, B_ALPHABET, B_TABLE, B_POS, B_PI, B_POSINJ,
+    B_EMB, B_WALK, B_KEYS, B_PAIRS_IN, B_OUT_STAGE,
+    B_LKEYS, B_LKEYS_ALT, B_PERM, B_PERM_ALT, B_RK, B_RK_ALT, B_RID, B_RID_ALT,
+    B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
+    B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
+    B_NUM
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct Staged {
+    const uint8_t *bytes = nullptr;
+    const int64_t *offsets = nullptr;
+    int64_t n = 0;
+    int64_t total = 0;
+};
+
+}  // namespace
+
+struct ej_ctx {
+    int device = 0;
+    std::string err;
+    bool timing = false;
+    Buf bufs[B_NUM];
+    // test tables
+    std::vector<uint8_t> pi;
+    uint32_t pi_r = 0, pi_steps = 0, pi_alpha = 0;
+    std::vector<uint32_t> posinj;
+    uint32_t pos_m = 0, pos_z = 0, pos_r = 0;
+    // pinned host counters
+    int64_t *h_cnt = nullptr;
+    cudaEvent_t ev[6] = {};
+    // cached alphabet
+    uint8_t alpha_cache[256];
+    uint32_t alpha_cache_n = 0;
+};
+
+namespace {
+
+int fail(ej_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? EJ_ERR_OOM : EJ_ERR_CUDA,       \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+    } while (0)
+
+#define CKS(expr)                     \
+    do {                              \
+        int s_ = (expr);              \
+        if (s_ != EJ_OK) return s_;   \
+    } while (0)
+
+int ensure(ej_ctx *ctx, BufId id, size_t bytes, void **out) {
+    Buf &b = ctx->bufs[id];
+    if (bytes == 0) bytes = 16;
+    if (b.cap < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        size_t cap = bytes + bytes / 8 + 256;
+        cudaError_t e = cudaMalloc(&b.p, cap);
+        if (e != cudaSuccess) {
+            b.p = nullptr;
+            cudaGetLastError();
+            return fail(ctx, EJ_ERR_OOM, "cudaMalloc(%zu) failed: %s", cap, cudaGetErrorString(e));
+        }
+        b.cap = cap;
+    }
+    *out = b.p;
+    return EJ_OK;
+}
+
+template <typename T>
+int ensure_t(ej_ctx *ctx, BufId id, size_t count, T **out) {
+    void *p = nullptr;
+    int s = ensure(ctx, id, count * sizeof(T), &p);
+    *out = (T *)p;
+    return s;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Input array -> device pointer (copies host arrays into a context buffer).
+int stage_in(ej_ctx *ctx, BufId id, const void *p, size_t bytes, const void **dev, cudaStream_t s) {
+    if (bytes == 0 || is_device_ptr(p)) {
+        *dev = p;
+        return EJ_OK;
+    }
+    void *d = nullptr;
+    CKS(ensure(ctx, id, bytes, &d));
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s));
+    *dev = d;
+    return EJ_OK;
+}
+
+int check_params(ej_ctx *ctx, const ej_params *p, bool need_lsh) {
+    if (!p) return fail(ctx, EJ_ERR_INVALID_ARG, "params is NULL");
+    if (p->K < 0) return fail(ctx, EJ_ERR_INVALID_ARG, "K must be >= 0 (got %d)", p->K);
+    if (p->alphabet_size < 1 || p->alphabet_size > 255 || !p->alphabet)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "alphabet_size must be 1..255 with a non-NULL alphabet");
+    bool seen[256] = {false};
+    for (uint32_t c = 0; c < p->alphabet_size; c++) {
+        if (seen[p->alphabet[c]]) return fail(ctx, EJ_ERR_INVALID_ARG, "alphabet byte %u repeated", p->alphabet[c]);
+        seen[p->alphabet[c]] = true;
+    }
+    if (!need_lsh) return EJ_OK;
+    if (p->r < 1 || p->r > 255) return fail(ctx, EJ_ERR_INVALID_ARG, "r must be 1..255 (got %u)", p->r);
+    if (p->m < 1 || p->m > 65535) return fail(ctx, EJ_ERR_INVALID_ARG, "m must be 1..65535 (got %u)", p->m);
+    if ((uint64_t)p->r * p->m > 65535)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "r*m must be <= 65535 (got %llu)", (unsigned long long)p->r * p->m);
+    if (p->z < 1) return fail(ctx, EJ_ERR_INVALID_ARG, "z must be >= 1");
+    // (alpha+1)^z < 2^64
+    unsigned __int128 v = 1;
+    for (uint32_t q = 0; q < p->z; q++) {
+        v *= (unsigned __int128)(p->alphabet_size + 1);
+        if (v > (unsigned __int128)UINT64_MAX)
+            return fail(ctx, EJ_ERR_INVALID_ARG, "(alphabet_size+1)^z must be < 2^64 (z=%u too large)", p->z);
+    }
+    return EJ_OK;
+}
+
+// Upload the alphabet and the raw-byte -> code map (cached per context).
+int upload_alphabet(ej_ctx *ctx, const ej_params *p, cudaStream_t s) {
+    uint8_t *d_map = nullptr, *d_alpha = nullptr;
+    CKS(ensure_t(ctx, B_CODEMAP, 256, &d_map));
+    CKS(ensure_t(ctx, B_ALPHABET, 256, &d_alpha));
+    if (ctx->alpha_cache_n == p->alphabet_size && !memcmp(ctx->alpha_cache, p->alphabet, p->alphabet_size))
+        return EJ_OK;
+    uint8_t *h = (uint8_t *)ctx->h_cnt + 256;  // pinned scratch beyond the counters
+    memset(h, 255, 256);
+    for (uint32_t c = 0; c < p->alphabet_size; c++) h[p->alphabet[c]] = (uint8_t)c;
+    memcpy(h + 256, p->alphabet, p->alphabet_size);
+    CK(cudaMemcpyAsync(d_map, h, 256, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_alpha, h + 256, p->alphabet_size, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(ctx->alpha_cache, p->alphabet, p->alphabet_size);
+    ctx->alpha_cache_n = p->alphabet_size;
+    return EJ_OK;
+}
+
+struct Plan {
+    Staged st;
+    int32_t *lens = nullptr;
+    int64_t max_len = 0;
+    uint32_t out_len = 0, L = 0, planes = 1;
+    int64_t nb32 = 0;
+};
+
+// Stage strings, validate, compute lengths and derived sizes (synchronises s).
+int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_lsh, Plan *pl, cudaStream_t s) {
+    if (!S) return fail(ctx, EJ_ERR_INVALID_ARG, "strings is NULL");
+    CKS(check_params(ctx, p, need_lsh));
+    if (S->n < 0 || S->n >= (1ll << 31)) return fail(ctx, EJ_ERR_INVALID_ARG, "n must be in [0, 2^31) (got %lld)", (long long)S->n);
+    if (S->n > 0 && (!S->offsets || !S->bytes)) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL bytes/offsets");
+    const int64_t n = S->n;
+    pl->st.n = n;
+    CKS(upload_alphabet(ctx, p, s));
+    // offsets
+    const void *d_off = nullptr;
+    int64_t total = 0;
+    if (n > 0) {
+        CKS(stage_in(ctx, B_OFFSETS, S->offsets, (size_t)(n + 1) * sizeof(int64_t), &d_off, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, (const int64_t *)d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        total = ctx->h_cnt[0];
+        if (total < 0) return fail(ctx, EJ_ERR_INVALID_ARG, "offsets[n] = %lld < 0", (long long)total);
+    }
+    pl->st.offsets = (const int64_t *)d_off;
+    pl->st.total = total;
+    const void *d_bytes = S->bytes;
+    if (total > 0) CKS(stage_in(ctx, B_BYTES, S->bytes, (size_t)total, &d_bytes, s));
+    pl->st.bytes = (const uint8_t *)d_bytes;
+    uint32_t *derr = nullptr;
+    CKS(ensure_t(ctx, B_DERR, 8, &derr));
+    CK(cudaMemsetAsync(derr, 0, 4 * sizeof(uint32_t), s));
+    CKS(ensure_t(ctx, B_LENS, (size_t)(n > 0 ? n : 1), &pl->lens));
+    unsigned long long *dmax = (unsigned long long *)(derr + 2);
+    CK(launch_validate(pl->st.bytes, pl->st.offsets, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->lens,
+                       derr, dmax, s));
+    CK(launch_validate_bytes(pl->st.bytes, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, derr, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt, derr, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t e = (uint32_t)(ctx->h_cnt[0] & 0xffffffffu);
+    if (e & DERR_OFFSETS) return fail(ctx, EJ_ERR_INVALID_ARG, "offsets must start at 0 and be non-decreasing, lengths < 2^31");
+    if (e & DERR_SYMBOL) return fail(ctx, EJ_ERR_INVALID_ARG, "a string byte is not in the alphabet");
+    pl->max_len = (int64_t)((unsigned long long)ctx->h_cnt[1]);
+    if (need_lsh) {
+        uint64_t ol = p->out_len ? p->out_len : (uint64_t)(3 * pl->max_len);
+        if (ol == 0) ol = 1;
+        if (ol > 0x7fffffffull) return fail(ctx, EJ_ERR_INVALID_ARG, "out_len too large");
+        if (ol >= (1ull << 40)) return fail(ctx, EJ_ERR_INVALID_ARG, "out_len too large for the step counter");
+        pl->out_len = (uint32_t)ol;
+        pl->L = p->L ? p->L : pl->out_len;
+        if (pl->L > pl->out_len) return fail(ctx, EJ_ERR_INVALID_ARG, "L (%u) must be <= out_len (%u)", pl->L, pl->out_len);
+        pl->planes = planes_for(p->alphabet_size);
+        pl->nb32 = (n + 31) / 32;
+        if (ctx->pi.size() && (ctx->pi_r != p->r || ctx->pi_alpha != p->alphabet_size))
+            return fail(ctx, EJ_ERR_INVALID_ARG, "injected pi table does not match r/alphabet_size");
+        if (ctx->posinj.size() && (ctx->pos_r != p->r || ctx->pos_m != p->m || ctx->pos_z != p->z))
+            return fail(ctx, EJ_ERR_INVALID_ARG, "injected positions do not match r/m/z");
+        for (uint32_t v : ctx->posinj)
+            if (v >= pl->L) return fail(ctx, EJ_ERR_INVALID_ARG, "injected position %u >= L", v);
+    }
+    return EJ_OK;
+}
+
+uint64_t emb_bytes(const Plan &pl, uint32_t r) {
+    return (uint64_t)r * pl.nb32 * pl.out_len * pl.planes * sizeof(uint32_t);
+}
+
+// Random-bit table and positions into context buffers.
+int make_tables(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint32_t **table, uint32_t **pos, cudaStream_t s) {
+    const uint32_t words = table_words_for(pl.planes);
+    CKS(ensure_t(ctx, B_TABLE, (size_t)p->r * pl.out_len * words, table));
+    CKS(ensure_t(ctx, B_POS, (size_t)p->r * p->m * p->z, pos));
+    const uint8_t *pi_dev = nullptr;
+    if (ctx->pi.size()) {
+        uint8_t *d = nullptr;
+        CKS(ensure_t(ctx, B_PI, ctx->pi.size(), &d));
+        CK(cudaMemcpyAsync(d, ctx->pi.data(), ctx->pi.size(), cudaMemcpyHostToDevice, s));
+        pi_dev = d;
+    }
+    const uint32_t *pos_dev = nullptr;
+    if (ctx->posinj.size()) {
+        uint32_t *d = nullptr;
+        CKS(ensure_t(ctx, B_POSINJ, ctx->posinj.size(), &d));
+        CK(cudaMemcpyAsync(d, ctx->posinj.data(), ctx->posinj.size() * 4, cudaMemcpyHostToDevice, s));
+        pos_dev = d;
+    }
+    CK(launch_bit_table(p->seed, p->r, pl.out_len, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,
+                        words, pi_dev, ctx->pi_steps, *table, s));
+    CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_dev, *pos, s));
+    if (pi_dev || pos_dev) CK(cudaStreamSynchronize(s));  // host vectors may change after return
+    return EJ_OK;
+}
+
+int key_bits(const ej_params *p) {
+    unsigned __int128 v = 1;
+    for (uint32_t q = 0; q < p->z; q++) v *= (unsigned __int128)(p->alphabet_size + 1);
+    uint64_t maxkey = (uint64_t)(v - 1);
+    int b = 0;
+    while (b < 64 && (maxkey >> b)) b++;
+    return b;
+}
+
+int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b)) b++;
+    return b;
+}
+
+// Candidates from keys [T][n] on the device. Result: sorted unique pairs in
+// *cand (context buffer B_CAND), count in *ncand.
+int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t **cand,
+                   int64_t *ncand, int64_t *nraw, int64_t *maxb, cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+    *ncand = 0; *nraw = 0; *maxb = 0;
+    *cand = nullptr;
+    if (n < 2) return EJ_OK;
+    // scratch for radix + scans
+    const size_t rs_len = radix_counts_len(n, T) > radix_counts_len(n, 1) ? radix_counts_len(n, T) : radix_counts_len(n, 1);
+    uint32_t *rs_counts = nullptr;
+    uint64_t *rs_offs = nullptr;
+    void *scan_tmp = nullptr;
+    CKS(ensure_t(ctx, B_RS_COUNTS, rs_len, &rs_counts));
+    CKS(ensure_t(ctx, B_RS_OFFS, rs_len, &rs_offs));
+    CKS(ensure(ctx, B_SCAN_TMP, scan_temp_bytes((int64_t)rs_len), &scan_tmp));
+    RadixTemp rt{rs_counts, rs_offs, scan_tmp};
+    // 1. length order (stable by id)
+    uint64_t *lk = nullptr, *lk2 = nullptr;
+    uint32_t *perm = nullptr, *perm2 = nullptr;
+    CKS(ensure_t(ctx, B_LKEYS, (size_t)n, &lk));
+    CKS(ensure_t(ctx, B_LKEYS_ALT, (size_t)n, &lk2));
+    CKS(ensure_t(ctx, B_PERM, (size_t)n, &perm));
+    CKS(ensure_t(ctx, B_PERM_ALT, (size_t)n, &perm2));
+    CK(launch_len_keys(pl.lens, n, lk, s));
+    CK(launch_iota_u32(perm, n, s));
+    int shifts[16];
+    int np = 0;
+    for (int b = 0; b < bits_for((uint64_t)pl.max_len); b += 8) shifts[np++] = b;
+    bool alt = false;
+    CK(radix_sort_segmented(lk, perm, lk2, perm2, n, 1, shifts, np, rt, &alt, s));
+    const uint32_t *order = alt ? perm2 : perm;
+    // 2. gather into (key, id) records per table, length order
+    uint64_t *rk = nullptr, *rk2 = nullptr;
+    uint32_t *rid = nullptr, *rid2 = nullptr;
+    CKS(ensure_t(ctx, B_RK, (size_t)(n * T), &rk));
+    CKS(ensure_t(ctx, B_RK_ALT, (size_t)(n * T), &rk2));
+    CKS(ensure_t(ctx, B_RID, (size_t)(n * T), &rid));
+    CKS(ensure_t(ctx, B_RID_ALT, (size_t)(n * T), &rid2));
+    CK(launch_len_order_gather(keys, order, n, T, rk, rid, s));
+    // 3. stable sort by key within each table
+    np = 0;
+    for (int b = 0; b < key_bits(p); b += 8) shifts[np++] = b;
+    CK(radix_sort_segmented(rk, rid, rk2, rid2, n, T, shifts, np, rt, &alt, s));
+    const uint64_t *srk = alt ? rk2 : rk;
+    const uint32_t *srid = alt ? rid2 : rid;
+    // 4. count partners per record, scan
+    uint32_t *counts = nullptr;
+    uint64_t *offs = nullptr;
+    CKS(ensure_t(ctx, B_COUNTS, (size_t)(n * T), &counts));
+    CKS(ensure_t(ctx, B_OFFS, (size_t)(n * T) + 1, &offs));
+    uint64_t *dcnt = nullptr;
+    CKS(ensure_t(ctx, B_COUNTERS, 8, &dcnt));
+    CK(cudaMemsetAsync(dcnt, 0, 8 * sizeof(uint64_t), s));
+    CK(launch_bucket_count(srk, srid, pl.lens, n, T, p->K, counts, (unsigned long long *)(dcnt + 1), s));
+    void *scan_tmp2 = nullptr;
+    CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(n * T), &scan_tmp2));
+    CK(exclusive_scan_u32(counts, offs, n * T, dcnt, scan_tmp2, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt, dcnt, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t raw = ctx->h_cnt[0];
+    *nraw = raw;
+    *maxb = ctx->h_cnt[1];
+    if (raw == 0) return EJ_OK;
+    // 5. emit, sort, unique
+    uint64_t *pr = nullptr, *pr2 = nullptr;
+    CKS(ensure_t(ctx, B_RAW, (size_t)raw, &pr));
+    CKS(ensure_t(ctx, B_RAW_ALT, (size_t)raw, &pr2));
+    CK(launch_bucket_emit(srk, srid, pl.lens, n, T, p->K, offs, pr, s));
+    const int nb = bits_for((uint64_t)(n - 1));
+    np = 0;
+    for (int b = 0; b < nb; b += 8) shifts[np++] = b;
+    for (int b = 0; b < nb; b += 8) shifts[np++] = 32 + b;
+    const size_t rs2 = radix_counts_len(raw, 1);
+    uint32_t *c2 = nullptr;
+    uint64_t *o2 = nullptr;
+    if (rs2 > rs_len) {
+        CKS(ensure_t(ctx, B_RS_COUNTS, rs2, &c2));
+        CKS(ensure_t(ctx, B_RS_OFFS, rs2, &o2));
+        CKS(ensure(ctx, B_SCAN_TMP, scan_temp_bytes((int64_t)rs2), &scan_tmp));
+        rt = RadixTemp{c2, o2, scan_tmp};
+    }
+    CK(radix_sort_segmented(pr, nullptr, pr2, nullptr, raw, 1, shifts, np, rt, &alt, s));
+    const uint64_t *sp = alt ? pr2 : pr;
+    uint8_t *fl = nullptr;
+    uint64_t *fo = nullptr;
+    CKS(ensure_t(ctx, B_FLAGS, (size_t)raw, &fl));
+    CKS(ensure_t(ctx, B_FLAG_OFFS, (size_t)raw, &fo));
+    CK(launch_unique_flags(sp, raw, fl, s));
+    CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(raw), &scan_tmp2));
+    CK(exclusive_scan_u8(fl, fo, raw, dcnt + 2, scan_tmp2, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt, dcnt + 2, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t nc = ctx->h_cnt[0];
+    uint64_t *cd = nullptr;
+    CKS(ensure_t(ctx, B_CAND, (size_t)nc, &cd));
+    CK(launch_compact_u64(sp, fl, fo, raw, cd, s));
+    *cand = cd;
+    *ncand = nc;
+    return EJ_OK;
+}
+
+// Verify device pairs; passing pairs (input order) into `out_dev` if it has
+// room (capacity), count in *n_out. If out_dev is null only counts.
+int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *pairs, int64_t np,
+               uint64_t *out_dev, int64_t capacity, int64_t *n_out, cudaStream_t s) {
+    *n_out = 0;
+    if (np == 0) return EJ_OK;
+    VerifyConfig vc = verify_pick(p->K, p->alphabet_size, pl.max_len);
+    if (vc.G == 0)
+        return fail(ctx, EJ_ERR_UNSUPPORTED, "no verifier configuration for K=%d, alphabet %u, max length %lld",
+                    p->K, p->alphabet_size, (long long)pl.max_len);
+    uint8_t *fl = nullptr;
+    uint64_t *fo = nullptr;
+    CKS(ensure_t(ctx, B_FLAGS, (size_t)np, &fl));
+    CKS(ensure_t(ctx, B_FLAG_OFFS, (size_t)np, &fo));
+    uint32_t *derr = (uint32_t *)ctx->bufs[B_DERR].p;
+    uint64_t *dcnt = nullptr;
+    CKS(ensure_t(ctx, B_COUNTERS, 8, &dcnt));
+    CK(cudaMemsetAsync(derr, 0, 4, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
+    CK(launch_verify(vc, pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, (const uint8_t *)ctx->bufs[B_CODEMAP].p,
+                     p->alphabet_size, pairs, np, p->K, pl.max_len, fl, derr, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
+    void *tmp = nullptr;
+    CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(np), &tmp));
+    CK(exclusive_scan_u8(fl, fo, np, dcnt + 3, tmp, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt, dcnt + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt + 1, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if ((uint32_t)ctx->h_cnt[1] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "pair index >= n");
+    const int64_t cnt = ctx->h_cnt[0];
+    *n_out = cnt;
+    if (!out_dev) return EJ_OK;
+    if (cnt > capacity) return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt, (long long)capacity);
+    CK(launch_compact_u64(pairs, fl, fo, np, out_dev, s));
+    return EJ_OK;
+}
+
+// Output array: device pointer or a staging buffer to copy to host after.
+int out_target(ej_ctx *ctx, BufId id, void *user, size_t bytes, void **dev, bool *is_host) {
+    if (is_device_ptr(user)) {
+        *dev = user;
+        *is_host = false;
+        return EJ_OK;
+    }
+    *is_host = true;
+    return ensure(ctx, id, bytes, dev);
+}
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *ej_status_string(int status) {
+    switch (status) {
+        case EJ_OK: return "ok";
+        case EJ_ERR_INVALID_ARG: return "invalid argument";
+        case EJ_ERR_OOM: return "out of memory";
+        case EJ_ERR_CAPACITY: return "output capacity exceeded";
+        case EJ_ERR_CUDA: return "CUDA error";
+        case EJ_ERR_TIMEOUT: return "device wait timed out";
+        case EJ_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+int ej_create(ej_ctx **out, int device) {
+    if (!out) return EJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return EJ_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return EJ_ERR_CUDA;
+    ej_ctx *c = new (std::nothrow) ej_ctx();
+    if (!c) return EJ_ERR_OOM;
+    c->device = device;
+    if (cudaMallocHost((void **)&c->h_cnt, 4096) != cudaSuccess) {
+        delete c;
+        return EJ_ERR_OOM;
+    }
+    for (auto &e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            ej_destroy(c);
+            return EJ_ERR_CUDA;
+        }
+    *out = c;
+    return EJ_OK;
+}
+
+void ej_destroy(ej_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (auto &b : c->bufs)
+        if (b.p) cudaFree(b.p);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    delete c;
+}
+
+const char *ej_last_error(ej_ctx *c) { return c ? c->err.c_str() : ""; }
+
+int ej_set_timing(ej_ctx *c, int enable) {
+    if (!c) return EJ_ERR_INVALID_ARG;
+    c->timing = enable != 0;
+    return EJ_OK;
+}
+
+int ej_set_test_tables(ej_ctx *ctx, const uint8_t *pi, uint32_t r, uint32_t steps, uint32_t alphabet_size,
+                       const uint32_t *positions, uint32_t m, uint32_t z) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    ctx->pi.clear();
+    ctx->posinj.clear();
+    if (pi) {
+        if (r == 0 || steps == 0 || alphabet_size == 0)
+            return fail(ctx, EJ_ERR_INVALID_ARG, "pi table needs r, steps, alphabet_size > 0");
+        ctx->pi.assign(pi, pi + (size_t)r * steps * alphabet_size);
+        ctx->pi_r = r;
+        ctx->pi_steps = steps;
+        ctx->pi_alpha = alphabet_size;
+    }
+    if (positions) {
+        if (r == 0 || m == 0 || z == 0) return fail(ctx, EJ_ERR_INVALID_ARG, "positions need r, m, z > 0");
+        ctx->posinj.assign(positions, positions + (size_t)r * m * z);
+        ctx->pos_r = r;
+        ctx->pos_m = m;
+        ctx->pos_z = z;
+    }
+    return EJ_OK;
+}
+
+int ej_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, ej_plan_info *info, void *stream) {
+    if (!ctx || !info) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/info");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    info->n = pl.st.n;
+    info->max_len = pl.max_len;
+    info->total_bytes = pl.st.total;
+    info->out_len = pl.out_len;
+    info->L = pl.L;
+    info->planes = pl.planes;
+    info->blocks32 = (uint32_t)pl.nb32;
+    info->embedding_bytes = emb_bytes(pl, p->r);
+    info->walk_end_count = (uint64_t)p->r * pl.st.n;
+    info->key_count = (uint64_t)p->r * p->m * pl.st.n;
+    return EJ_OK;
+}
+
+int ej_embed(ej_ctx *ctx, const ej_strings *S, const ej_params *p, void *emb, int32_t *walk_end, void *stream) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    if (pl.st.n == 0) return EJ_OK;
+    if (!emb || !walk_end) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL emb/walk_end");
+    uint32_t *table = nullptr, *pos = nullptr;
+    CKS(make_tables(ctx, p, pl, &table, &pos, s));
+    const size_t eb = emb_bytes(pl, p->r), wb = (size_t)p->r * pl.st.n * sizeof(int32_t);
+    void *d_emb = nullptr, *d_we = nullptr;
+    bool h_emb = false, h_we = false;
+    CKS(out_target(ctx, B_EMB, emb, eb, &d_emb, &h_emb));
+    CKS(out_target(ctx, B_WALK, walk_end, wb, &d_we, &h_we));
+    CK(launch_embed(pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, p->r, table,
+                    (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.out_len, pl.planes, (uint32_t *)d_emb,
+                    (int32_t *)d_we, s));
+    if (h_emb) CK(cudaMemcpyAsync(emb, d_emb, eb, cudaMemcpyDeviceToHost, s));
+    if (h_we) CK(cudaMemcpyAsync(walk_end, d_we, wb, cudaMemcpyDeviceToHost, s));
+    if (h_emb || h_we) CK(cudaStreamSynchronize(s));
+    return EJ_OK;
+}
+
+int ej_sign(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const void *emb, const int32_t *walk_end,
+            uint64_t *keys, void *stream) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    if (pl.st.n == 0) return EJ_OK;
+    if (!emb || !walk_end || !keys) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL emb/walk_end/keys");
+    uint32_t *table = nullptr, *pos = nullptr;
+    CKS(make_tables(ctx, p, pl, &table, &pos, s));
+    const size_t eb = emb_bytes(pl, p->r), wb = (size_t)p->r * pl.st.n * sizeof(int32_t);
+    const void *d_emb = nullptr, *d_we = nullptr;
+    CKS(stage_in(ctx, B_EMB, emb, eb, &d_emb, s));
+    CKS(stage_in(ctx, B_WALK, walk_end, wb, &d_we, s));
+    const size_t kb = (size_t)p->r * p->m * pl.st.n * sizeof(uint64_t);
+    void *d_keys = nullptr;
+    bool h_keys = false;
+    CKS(out_target(ctx, B_KEYS, keys, kb, &d_keys, &h_keys));
+    CK(launch_sign((const uint32_t *)d_emb, (const int32_t *)d_we, pl.st.n, p->r, p->m, p->z, pl.out_len,
+                   pl.planes, p->alphabet_size, pos, (uint64_t *)d_keys, s));
+    if (h_keys) {
+        CK(cudaMemcpyAsync(keys, d_keys, kb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return EJ_OK;
+}
+
+int ej_lsh_candidates(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const uint64_t *keys,
+                      uint64_t *pairs, int64_t capacity, int64_t *n_pairs, int64_t *stats_max_bucket,
+                      void *stream) {
+    if (!ctx || !n_pairs) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_pairs");
+    *n_pairs = 0;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    if (pl.st.n < 2) return EJ_OK;
+    if (!keys) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL keys");
+    const void *d_keys = nullptr;
+    CKS(stage_in(ctx, B_KEYS, keys, (size_t)p->r * p->m * pl.st.n * sizeof(uint64_t), &d_keys, s));
+    uint64_t *cand = nullptr;
+    int64_t nc = 0, raw = 0, mb = 0;
+    CKS(candidates_dev(ctx, pl, p, (const uint64_t *)d_keys, &cand, &nc, &raw, &mb, s));
+    *n_pairs = nc;
+    if (stats_max_bucket) *stats_max_bucket = mb;
+    if (nc > capacity) return fail(ctx, EJ_ERR_CAPACITY, "needs %lld pairs, capacity %lld", (long long)nc, (long long)capacity);
+    if (nc == 0) return EJ_OK;
+    if (!pairs) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL pairs");
+    CK(cudaMemcpyAsync(pairs, cand, (size_t)nc * sizeof(uint64_t), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return EJ_OK;
+}
+
+int ej_verify(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const uint64_t *pairs, int64_t n_pairs,
+              uint64_t *out, int64_t *n_out, void *stream) {
+    if (!ctx || !n_out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_out");
+    *n_out = 0;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    if (n_pairs < 0) return fail(ctx, EJ_ERR_INVALID_ARG, "n_pairs < 0");
+    Plan pl;
+    CKS(make_plan(ctx, S, p, false, &pl, s));
+    if (n_pairs == 0) return EJ_OK;
+    if (!pairs || !out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL pairs/out");
+    const void *d_pairs = nullptr;
+    CKS(stage_in(ctx, B_PAIRS_IN, pairs, (size_t)n_pairs * sizeof(uint64_t), &d_pairs, s));
+    void *d_out = nullptr;
+    bool h_out = false;
+    CKS(out_target(ctx, B_OUT_STAGE, out, (size_t)n_pairs * sizeof(uint64_t), &d_out, &h_out));
+    int64_t cnt = 0;
+    CKS(verify_dev(ctx, pl, p, (const uint64_t *)d_pairs, n_pairs, (uint64_t *)d_out, n_pairs, &cnt, s));
+    *n_out = cnt;
+    if (h_out && cnt) {
+        CK(cudaMemcpyAsync(out, d_out, (size_t)cnt * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return EJ_OK;
+}
+
+int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out, int64_t capacity,
+            int64_t *n_out, ej_join_stats *stats, void *stream) {
+    if (!ctx || !n_out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_out");
+    *n_out = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    if (pl.st.n < 2) return EJ_OK;
+    uint32_t *table = nullptr, *pos = nullptr;
+    CKS(make_tables(ctx, p, pl, &table, &pos, s));
+    uint32_t *emb = nullptr;
+    int32_t *we = nullptr;
+    uint64_t *keys = nullptr;
+    CKS(ensure_t(ctx, B_EMB, (size_t)(emb_bytes(pl, p->r) / 4), &emb));
+    CKS(ensure_t(ctx, B_WALK, (size_t)p->r * pl.st.n, &we));
+    CKS(ensure_t(ctx, B_KEYS, (size_t)p->r * p->m * pl.st.n, &keys));
+    CK(launch_embed(pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, p->r, table,
+                    (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.out_len, pl.planes, emb, we, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+    CK(launch_sign(emb, we, pl.st.n, p->r, p->m, p->z, pl.out_len, pl.planes, p->alphabet_size, pos, keys, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    uint64_t *cand = nullptr;
+    int64_t nc = 0, raw = 0, mb = 0;
+    CKS(candidates_dev(ctx, pl, p, keys, &cand, &nc, &raw, &mb, s));
+    if (ctx->timing && nc == 0) CK(cudaEventRecord(ctx->ev[3], s));
+    int64_t cnt = 0;
+    void *d_out = nullptr;
+    bool h_out = false;
+    if (nc > 0) {
+        CKS(out_target(ctx, B_OUT_STAGE, out, (size_t)nc * sizeof(uint64_t), &d_out, &h_out));
+        int st = verify_dev(ctx, pl, p, cand, nc, (uint64_t *)d_out, h_out ? nc : capacity, &cnt, s);
+        if (st == EJ_ERR_CAPACITY) *n_out = cnt;
+        CKS(st);
+        if (cnt > capacity) {
+            *n_out = cnt;
+            return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt, (long long)capacity);
+        }
+        if (h_out && cnt) CK(cudaMemcpyAsync(out, d_out, (size_t)cnt * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    }
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[5], s));
+    CK(cudaStreamSynchronize(s));
+    *n_out = cnt;
+    if (stats) {
+        stats->n_raw_pairs = raw;
+        stats->n_candidates = nc;
+        stats->n_out = cnt;
+        stats->max_bucket = mb;
+        if (ctx->timing) {
+            cudaEventElapsedTime(&stats->ms_embed, ctx->ev[0], ctx->ev[1]);
+            cudaEventElapsedTime(&stats->ms_sign, ctx->ev[1], ctx->ev[2]);
+            cudaEventElapsedTime(&stats->ms_candidates, ctx->ev[2], ctx->ev[3]);
+            if (nc > 0) cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[5]);
+        }
+    }
+    return EJ_OK;
+}
+
+}  // extern "C"

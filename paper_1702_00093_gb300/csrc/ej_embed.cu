@@ -1,0 +1,313 @@
+// Validation, random-bit tables, CGK embedding (Algorithm 1) and bit-sampling
+// signatures (Theorem 1 with AND amplification, Section 3.2).
+#include "ej_internal.cuh"
+
+namespace ej {
+
+// ---------------------------------------------------------------------------
+// Validation: offsets, lengths, symbols
+// ---------------------------------------------------------------------------
+
+__global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int64_t n,
+                                        int32_t *__restrict__ lens, uint32_t *__restrict__ err,
+                                        unsigned long long *__restrict__ max_len) {
+    unsigned long long local_max = 0;
+    uint32_t local_err = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = offsets[i], b = offsets[i + 1];
+        int64_t len = b - a;
+        if ((i == 0 && a != 0) || len < 0 || len >= (1ll << 31)) {
+            local_err |= DERR_OFFSETS;
+            len = 0;
+        }
+        lens[i] = (int32_t)len;
+        local_max = len > (int64_t)local_max ? (unsigned long long)len : local_max;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(FULL, local_max, o);
+        local_max = v > local_max ? v : local_max;
+        local_err |= __shfl_xor_sync(FULL, local_err, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (local_max) atomicMax(max_len, local_max);
+        if (local_err) atomicOr(err, local_err);
+    }
+}
+
+__global__ void validate_bytes_kernel(const uint8_t *__restrict__ bytes, int64_t total,
+                                      const uint8_t *__restrict__ code_map, uint32_t *__restrict__ err) {
+    __shared__ uint8_t s_map[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
+    __syncthreads();
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= s_map[bytes[i]] == 255;
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(err, (uint32_t)DERR_SYMBOL);
+}
+
+cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n,
+                            const uint8_t *code_map, int32_t *lens, uint32_t *err,
+                            unsigned long long *max_len, cudaStream_t s) {
+    if (n > 0) {
+        int grid = (int)((n + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        validate_offsets_kernel<<<grid, 256, 0, s>>>(offsets, n, lens, err, max_len);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uint8_t *code_map,
+                                  uint32_t *err, cudaStream_t s) {
+    if (total > 0) {
+        int64_t g = (total + 255) / 256;
+        int grid = (int)(g > 8192 ? 8192 : g);
+        validate_bytes_kernel<<<grid, 256, 0, s>>>(bytes, total, code_map, err);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Random-bit table of Alg. 1 and sampled positions of Thm. 1
+// ---------------------------------------------------------------------------
+
+// table[(l * out_len + j) * words + w], bit (c - 32w) = pi_j^l(alphabet[c]).
+__global__ void bit_table_kernel(uint64_t base, uint32_t r, uint32_t out_len,
+                                 const uint8_t *__restrict__ alphabet, uint32_t alpha, uint32_t words,
+                                 const uint8_t *__restrict__ pi, uint32_t inject_steps,
+                                 uint32_t *__restrict__ table) {
+    const uint64_t total = (uint64_t)r * out_len * words;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(idx % words);
+        const uint64_t lj = idx / words;
+        const uint32_t j = (uint32_t)(lj % out_len);
+        const uint32_t l = (uint32_t)(lj / out_len);
+        uint32_t word = 0;
+        const uint32_t c_end = min(alpha, 32 * w + 32);
+        for (uint32_t c = 32 * w; c < c_end; c++) {
+            uint32_t bit;
+            if (pi) {
+                bit = (j < inject_steps) ? (pi[((uint64_t)l * inject_steps + j) * alpha + c] & 1u) : 0u;
+            } else {
+                bit = (uint32_t)(mix64(base ^ walk_counter(l, j, alphabet[c])) >> 63);
+            }
+            word |= bit << (c - 32 * w);
+        }
+        table[idx] = word;
+    }
+}
+
+cudaError_t launch_bit_table(uint64_t seed, uint32_t r, uint32_t out_len, const uint8_t *alphabet_dev,
+                             uint32_t alpha, uint32_t words, const uint8_t *pi_inject,
+                             uint32_t inject_steps, uint32_t *table, cudaStream_t s) {
+    const uint64_t total = (uint64_t)r * out_len * words;
+    if (total) {
+        uint64_t g = (total + 255) / 256;
+        int grid = (int)(g > 4096 ? 4096 : g);
+        bit_table_kernel<<<grid, 256, 0, s>>>(mix64(seed), r, out_len, alphabet_dev, alpha, words,
+                                              pi_inject, inject_steps, table);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void positions_kernel(uint64_t base, uint32_t r, uint32_t m, uint32_t z, uint32_t L,
+                                 const uint32_t *__restrict__ inject, uint32_t *__restrict__ pos) {
+    const uint64_t total = (uint64_t)r * m * z;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        if (inject) {
+            pos[idx] = inject[idx];
+        } else {
+            const uint32_t q = (uint32_t)(idx % z);
+            const uint32_t f = (uint32_t)((idx / z) % m);
+            const uint32_t l = (uint32_t)(idx / ((uint64_t)z * m));
+            pos[idx] = (uint32_t)__umul64hi(mix64(base ^ position_counter(l, f, q)), (uint64_t)L);
+        }
+    }
+}
+
+cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, uint32_t L,
+                             const uint32_t *pos_inject, uint32_t *pos, cudaStream_t s) {
+    const uint64_t total = (uint64_t)r * m * z;
+    if (total) {
+        int grid = (int)((total + 255) / 256 > 1024 ? 1024 : (total + 255) / 256);
+        positions_kernel<<<grid, 256, 0, s>>>(mix64(seed), r, m, z, L, pos_inject, pos);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CGK embedding (Algorithm 1)
+// ---------------------------------------------------------------------------
+//
+// One lane per (string, embedding) walk; a warp walks 32 consecutive strings
+// under the same embedding l in lockstep over the steps j, so the random-bit
+// row of step j (staged in shared memory) is read by all lanes at once and
+// the emitted symbols of the 32 walks are packed by warp ballots into
+// bit-planes: one uint32 per (step, plane) with bit t for lane t. Every 32
+// steps the warp stores 32 x PLANES words, contiguous in memory.
+// The walk's state per lane: position i in the string, the codes of x[i] and
+// x[i+1], and the raw byte x[i+2] already in flight from global memory.
+
+constexpr int EMBED_WARPS = 4;
+constexpr int EMBED_TILE = 2048;  // steps of the random-bit table staged at a time
+
+template <int PLANES>
+__global__ void __launch_bounds__(EMBED_WARPS * 32)
+embed_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
+             const int32_t *__restrict__ lens, int64_t n, const uint32_t *__restrict__ table,
+             const uint8_t *__restrict__ code_map, uint32_t out_len, uint32_t *__restrict__ emb,
+             int32_t *__restrict__ walk_end, int64_t nblocks32) {
+    constexpr int WS = PLANES <= 5 ? 1 : (1 << (PLANES - 5));
+    __shared__ uint32_t s_table[EMBED_TILE * WS];
+    __shared__ uint8_t s_map[256];
+
+    const uint32_t l = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t B = (int64_t)blockIdx.x * EMBED_WARPS + warp;
+    const int64_t s = B * 32 + lane;
+    const bool valid = (B < nblocks32) && (s < n);
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
+    const int32_t len = valid ? lens[s] : 0;
+    const uint8_t *x = bytes + (valid ? offsets[s] : 0);
+    __syncthreads();
+
+    int32_t pos = 0;
+    uint32_t c0 = len > 0 ? s_map[x[0]] : 0u;
+    uint32_t c1 = len > 1 ? s_map[x[1]] : 0u;
+    uint32_t raw2 = len > 2 ? x[2] : 0u;
+    int32_t wend = (len == 0) ? 0 : (int32_t)out_len;
+    uint32_t acc[PLANES];
+#pragma unroll
+    for (int k = 0; k < PLANES; k++) acc[k] = 0;
+
+    const uint32_t *tab_l = table + (size_t)l * out_len * WS;
+    uint32_t *out_base = emb + ((size_t)l * nblocks32 + (size_t)(B < nblocks32 ? B : 0)) * out_len * PLANES;
+
+    for (uint32_t j0 = 0; j0 < out_len; j0 += EMBED_TILE) {
+        const uint32_t tile = min((uint32_t)EMBED_TILE, out_len - j0);
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < tile * WS; t += blockDim.x)
+            s_table[t] = tab_l[(size_t)j0 * WS + t];
+        __syncthreads();
+        if (B >= nblocks32) continue;  // warp-uniform
+        for (uint32_t jj = 0; jj < tile; jj++) {
+            const uint32_t j = j0 + jj;
+            const bool active = pos < len;
+            const uint32_t code = active ? c0 : 0u;
+#pragma unroll
+            for (int k = 0; k < PLANES; k++) {
+                const uint32_t bal = __ballot_sync(FULL, (code >> k) & 1u);
+                acc[k] = (lane == (int)(j & 31)) ? bal : acc[k];
+            }
+            if ((j & 31) == 31 || j == out_len - 1) {  // warp-uniform
+                const uint32_t jb = j & ~31u;
+                if (jb + lane <= j) {
+                    uint32_t *o = out_base + (size_t)(jb + lane) * PLANES;
+#pragma unroll
+                    for (int k = 0; k < PLANES; k++) o[k] = acc[k];
+                }
+            }
+            uint32_t bit = 0;
+            if (active) {
+                const uint32_t w = (WS == 1) ? s_table[jj] : s_table[jj * WS + (code >> 5)];
+                bit = (w >> (code & 31)) & 1u;
+            }
+            if (bit) {
+                pos++;
+                if (pos == len) wend = (int32_t)(j + 1);
+                c0 = c1;
+                c1 = s_map[raw2];
+                raw2 = (pos + 2 < len) ? (uint32_t)x[pos + 2] : 0u;
+            }
+        }
+    }
+    if (valid) walk_end[(size_t)l * n + s] = wend;
+}
+
+cudaError_t launch_embed(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens,
+                         int64_t n, uint32_t r, const uint32_t *table, const uint8_t *code_map,
+                         uint32_t out_len, uint32_t planes, uint32_t *emb, int32_t *walk_end,
+                         cudaStream_t s) {
+    if (n == 0 || out_len == 0) return cudaGetLastError();
+    const int64_t nb32 = (n + 31) / 32;
+    dim3 grid((unsigned)((nb32 + EMBED_WARPS - 1) / EMBED_WARPS), r);
+    dim3 block(EMBED_WARPS * 32);
+#define EJ_EMB(P) embed_kernel<P><<<grid, block, 0, s>>>(bytes, offsets, lens, n, table, code_map, out_len, emb, walk_end, nb32)
+    switch (planes) {
+        case 1: EJ_EMB(1); break;
+        case 2: EJ_EMB(2); break;
+        case 3: EJ_EMB(3); break;
+        case 4: EJ_EMB(4); break;
+        case 5: EJ_EMB(5); break;
+        case 6: EJ_EMB(6); break;
+        case 7: EJ_EMB(7); break;
+        default: EJ_EMB(8); break;
+    }
+#undef EJ_EMB
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Bit-sampling signatures: key = sum_q c_q (alpha+1)^q
+// ---------------------------------------------------------------------------
+//
+// A warp handles the 32 strings of one embedding block for one table
+// t = l*m + f. The sampled step p is the same for all lanes, so each plane word
+// is one broadcast load and lane t extracts its own bit.
+
+constexpr int SIGN_WARPS = 4;
+
+template <int PLANES>
+__global__ void __launch_bounds__(SIGN_WARPS * 32)
+sign_kernel(const uint32_t *__restrict__ emb, const int32_t *__restrict__ walk_end, int64_t n,
+            uint32_t m, uint32_t z, uint32_t out_len, uint32_t alpha, const uint32_t *__restrict__ pos,
+            uint64_t *__restrict__ keys, int64_t nblocks32) {
+    const uint32_t t = blockIdx.y;
+    const uint32_t l = t / m;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t B = (int64_t)blockIdx.x * SIGN_WARPS + warp;
+    if (B >= nblocks32) return;
+    const int64_t s = B * 32 + lane;
+    const bool valid = s < n;
+    const int32_t we = valid ? walk_end[(size_t)l * n + s] : 0;
+    const uint32_t *eb = emb + ((size_t)l * nblocks32 + B) * out_len * PLANES;
+    const uint32_t *P = pos + (size_t)t * z;
+    const uint64_t R = (uint64_t)alpha + 1;
+    uint64_t key = 0;
+    for (int q = (int)z - 1; q >= 0; q--) {
+        const uint32_t p = P[q];
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < PLANES; k++) c |= ((eb[(size_t)p * PLANES + k] >> lane) & 1u) << k;
+        if ((int32_t)p >= we) c = alpha;  // bottom
+        key = key * R + c;
+    }
+    if (valid) keys[(size_t)t * n + s] = key;
+}
+
+cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n, uint32_t r,
+                        uint32_t m, uint32_t z, uint32_t out_len, uint32_t planes, uint32_t alpha,
+                        const uint32_t *pos, uint64_t *keys, cudaStream_t s) {
+    if (n == 0) return cudaGetLastError();
+    const int64_t nb32 = (n + 31) / 32;
+    dim3 grid((unsigned)((nb32 + SIGN_WARPS - 1) / SIGN_WARPS), r * m);
+    dim3 block(SIGN_WARPS * 32);
+#define EJ_SIGN(P) sign_kernel<P><<<grid, block, 0, s>>>(emb, walk_end, n, m, z, out_len, alpha, pos, keys, nb32)
+    switch (planes) {
+        case 1: EJ_SIGN(1); break;
+        case 2: EJ_SIGN(2); break;
+        case 3: EJ_SIGN(3); break;
+        case 4: EJ_SIGN(4); break;
+        case 5: EJ_SIGN(5); break;
+        case 6: EJ_SIGN(6); break;
+        case 7: EJ_SIGN(7); break;
+        default: EJ_SIGN(8); break;
+    }
+#undef EJ_SIGN
+    return cudaGetLastError();
+}
+
+}  // namespace ej

@@ -1,0 +1,139 @@
+// Internal declarations of the EmbedJoin CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/embedjoin.h"
+
+namespace ej {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// SplitMix64 output function (Steele, Lea, Flood 2014): the counter-based
+// source of the random strings R^l (Alg. 1) and of the sampled positions
+// (Thm. 1). Written for the device here; the CPU oracle has its own copy.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t walk_counter(uint32_t l, uint64_t j, uint32_t sigma) {
+    return (1ull << 56) | ((uint64_t)l << 48) | (j << 8) | (uint64_t)sigma;
+}
+
+__host__ __device__ __forceinline__ uint64_t position_counter(uint32_t l, uint32_t f, uint32_t q) {
+    return (2ull << 56) | ((uint64_t)l << 48) | ((uint64_t)f << 32) | (uint64_t)q;
+}
+
+// Bit planes needed for symbol codes 0..alpha-1.
+inline uint32_t planes_for(uint32_t alpha) {
+    uint32_t b = 1;
+    while ((1u << b) < alpha) b++;
+    return b;
+}
+
+// u32 words per step of the code-indexed random-bit table.
+inline uint32_t table_words_for(uint32_t planes) { return planes <= 5 ? 1u : (1u << (planes - 5)); }
+
+// Device-side error bits.
+enum : uint32_t {
+    DERR_OFFSETS = 1u,     // offsets not starting at 0 / decreasing / too long
+    DERR_SYMBOL = 2u,      // byte outside the alphabet
+    DERR_PAIR = 4u,        // pair index out of range
+    DERR_TIMEOUT = 8u,     // bounded wait gave up
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns cudaGetLastError() of its launch)
+// ---------------------------------------------------------------------------
+
+// Validation + lengths: lens[i] = offsets[i+1]-offsets[i]; err |= DERR_*;
+// stats[0] = max length (int64 via unsigned max), stats[1] = total bytes.
+cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n,
+                            const uint8_t *code_map, int32_t *lens, uint32_t *err,
+                            unsigned long long *max_len, cudaStream_t s);
+
+// Random-bit table [r][out_len][words]: bit c of row (l, j) = pi_j^l(alphabet[c]).
+cudaError_t launch_bit_table(uint64_t seed, uint32_t r, uint32_t out_len, const uint8_t *alphabet_dev,
+                             uint32_t alpha, uint32_t words, const uint8_t *pi_inject,
+                             uint32_t inject_steps, uint32_t *table, cudaStream_t s);
+
+// Positions [r][m][z] in [0, L).
+cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, uint32_t L,
+                             const uint32_t *pos_inject, uint32_t *pos, cudaStream_t s);
+
+cudaError_t launch_embed(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens,
+                         int64_t n, uint32_t r, const uint32_t *table, const uint8_t *code_map,
+                         uint32_t out_len, uint32_t planes, uint32_t *emb, int32_t *walk_end,
+                         cudaStream_t s);
+
+cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n, uint32_t r,
+                        uint32_t m, uint32_t z, uint32_t out_len, uint32_t planes, uint32_t alpha,
+                        const uint32_t *pos, uint64_t *keys, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Scan and sort primitives (ej_sort.cu)
+// ---------------------------------------------------------------------------
+
+// Exclusive prefix sums of n values into out (uint64), total into *total_dev
+// (device pointer, may be null). Input types: u8, u32, u64.
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_u8(const uint8_t *in, uint64_t *out, int64_t n, uint64_t *total_dev,
+                              void *temp, cudaStream_t s);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint64_t *out, int64_t n, uint64_t *total_dev,
+                               void *temp, cudaStream_t s);
+
+// Stable LSD radix sort of `nseg` independent segments of `seg_len` records
+// each (segment k occupies [k*seg_len, (k+1)*seg_len)), by 8-bit digits at the
+// given bit shifts (least significant first). vals may be null.
+// keys/vals hold the input; the result ends in (keys, vals) or (keys_alt,
+// vals_alt): the function returns which through *in_alt.
+struct RadixTemp {
+    uint32_t *counts;   // nseg * 256 * tiles_per_seg
+    uint64_t *offsets;  // same size
+    void *scan_temp;
+};
+size_t radix_counts_len(int64_t seg_len, int64_t nseg);
+cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                                 int64_t seg_len, int64_t nseg, const int *shifts, int npasses,
+                                 RadixTemp tmp, bool *in_alt, cudaStream_t s);
+
+// Candidates: gather keys into length order, per-table bucket windows.
+cudaError_t launch_len_order_gather(const uint64_t *keys, const uint32_t *perm, int64_t n, int64_t T,
+                                    uint64_t *rec_keys, uint32_t *rec_ids, cudaStream_t s);
+cudaError_t launch_iota_u32(uint32_t *v, int64_t n, cudaStream_t s);
+cudaError_t launch_len_keys(const int32_t *lens, int64_t n, uint64_t *k, cudaStream_t s);
+cudaError_t launch_bucket_count(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens,
+                                int64_t n, int64_t T, int32_t K, uint32_t *counts,
+                                unsigned long long *max_bucket, cudaStream_t s);
+cudaError_t launch_bucket_emit(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens,
+                               int64_t n, int64_t T, int32_t K, const uint64_t *offs,
+                               uint64_t *pairs, cudaStream_t s);
+cudaError_t launch_unique_flags(const uint64_t *sorted, int64_t n, uint8_t *flags, cudaStream_t s);
+cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const uint64_t *offs,
+                               int64_t n, uint64_t *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Verification (ej_verify.cu)
+// ---------------------------------------------------------------------------
+
+struct VerifyConfig {
+    int G;          // lanes per pair
+    int V;          // 64-bit words per lane
+    int warps;      // warps per block
+};
+
+// Picks a configuration for threshold K (band 2K+1 bits) and alphabet size.
+VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len);
+// Shared memory per block of a configuration.
+size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_t K);
+
+cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
+                          const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
+                          const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
+                          uint8_t *flags, uint32_t *err, cudaStream_t s);
+
+}  // namespace ej

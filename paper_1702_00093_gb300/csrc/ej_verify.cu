@@ -1,0 +1,395 @@
+// Verification of candidate pairs: ED(x, y) <= K (Section 3.3, the last loop of
+// Algorithm 3), computed exactly with a banded bit-parallel form of the
+// edit-distance DP.
+//
+// Formulation. Rows i = 1..m follow x (the longer string), columns j = 1..n
+// follow y (the shorter). D(i, 0) = i, D(0, j) = j. Only a window of 64*W rows
+// is kept per column: after the shift at column j it holds rows
+// j-K .. j-K+64W-1 (bit b <-> row j-K+b), which covers Ukkonen's band
+// |i - j| <= K because 64W >= 2K+1. The window stores vertical differences
+// D(i,j) - D(i-1,j) as two bit-vectors (Pv: +1, Mv: -1) and the column is
+// advanced with the bit-vector recurrence for unit-cost edit distance (Myers
+// 1999, in the form of Hyyro 2001). Cells the window does not hold are
+// replaced by upper bounds that keep every difference in {-1, 0, +1}:
+//   - the row above the window gains +1 per column (horizontal shift-in 1),
+//   - the row entering at the bottom is one more than the row above it,
+//   - virtual rows above row 0 start at D(i, 0) = -i (vertical -1), never match.
+// With those boundaries every computed value is >= min(D, K+1) and equals D
+// wherever D <= K (an optimal path of cost <= K never leaves the band), so
+// "value(m, n) <= K" decides ED <= K exactly. The value of the cell above the
+// window, T, is tracked explicitly; D(m, n) = T + sum of the differences of
+// rows j-K .. m at the last column.
+//
+// Early exit: every 64 columns the group computes the minimum value in its
+// window; the minimum over the band never decreases from one column to the
+// next (D(i, j+1) >= D(i-1, j)), so once it exceeds K the pair is rejected.
+//
+// Mapping: a group of G lanes verifies one pair; lane g holds V consecutive
+// 64-bit words of the window. The carry of the multi-word addition crosses
+// lanes through two ballots (generate / propagate bits combined with one
+// integer addition), the one-bit shifts cross lanes through shuffles.
+// The pattern bit-masks Peq[c] of x live in shared memory, one region per
+// group, with K zero bits in front so that window bit b at column j is Peq bit
+// j-1+b. All groups of a warp step through columns together (the loop bound is
+// the warp maximum), so every warp collective runs with the full mask.
+#include "ej_internal.cuh"
+
+namespace ej {
+
+constexpr int VERIFY_MAX_THREADS = 256;
+
+__device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t sh) {
+    return sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
+}
+
+template <int G, int V>
+__global__ void __launch_bounds__(VERIFY_MAX_THREADS)
+verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
+              const int32_t *__restrict__ lens, int64_t n_str, const uint8_t *__restrict__ code_map,
+              uint32_t alpha, const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t Lw,
+              uint8_t *__restrict__ flags, uint32_t *__restrict__ err) {
+    constexpr int GPW = 32 / G;
+    extern __shared__ uint64_t smem[];
+    __shared__ uint8_t s_map[256];
+    __shared__ int8_t s_nsum[256];
+    __shared__ int8_t s_nmin[256];
+
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        s_map[t] = code_map[t];
+        // nibble table: index = P nibble | M nibble << 4; sum and minimum prefix
+        const uint32_t P = t & 15u, M = t >> 4;
+        int run = 0, mn = 1 << 20;
+        for (int k = 0; k < 4; k++) {
+            run += (int)((P >> k) & 1u) - (int)((M >> k) & 1u);
+            mn = run < mn ? run : mn;
+        }
+        s_nsum[t] = (int8_t)run;
+        s_nmin[t] = (int8_t)mn;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    const int warps_per_block = blockDim.x >> 5;
+    uint64_t *peq = smem + (size_t)(warp * GPW + g) * alpha * Lw;
+    const int64_t warps_total = (int64_t)gridDim.x * warps_per_block;
+
+    for (int64_t wb = (int64_t)blockIdx.x * warps_per_block + warp; wb * GPW < np; wb += warps_total) {
+        const int64_t p = wb * GPW + g;
+        bool valid = p < np;
+        int32_t la = 0, lb = 0;
+        int64_t a = 0, b = 0;
+        if (valid) {
+            const uint64_t pr = pairs[p];
+            a = (int64_t)(pr >> 32);
+            b = (int64_t)(pr & 0xFFFFFFFFull);
+            if (a >= n_str || b >= n_str) {
+                if (gl == 0) atomicOr(err, (uint32_t)DERR_PAIR);
+                valid = false;
+            } else {
+                la = lens[a];
+                lb = lens[b];
+            }
+        }
+        const bool a_long = la >= lb;
+        const uint8_t *xs = bytes + offsets[valid ? (a_long ? a : b) : 0];
+        const uint8_t *ys = bytes + offsets[valid ? (a_long ? b : a) : 0];
+        const int32_t mlen = a_long ? la : lb;
+        const int32_t nlen = a_long ? lb : la;
+        bool decided = !valid;
+        bool pass = false;
+        if (valid && mlen - nlen > K) {
+            decided = true;
+        } else if (valid && nlen == 0) {
+            decided = true;
+            pass = mlen <= K;
+        }
+        int32_t ncols = decided ? 0 : nlen;
+        const int32_t mrows = decided ? 0 : mlen;
+
+        // Peq[c]: bit K+i set iff code(x[i]) == c
+        const int32_t mmax = __reduce_max_sync(FULL, mrows);
+        if (mmax > 0) {
+            for (int i = gl; i < (int)alpha * Lw; i += G) peq[i] = 0ull;
+            __syncwarp();
+            for (int32_t i = gl; i < mmax; i += G) {
+                const uint32_t c = (i < mrows) ? (uint32_t)s_map[xs[i]] : 255u;
+                if (c < alpha) {
+                    const uint32_t q = (uint32_t)K + (uint32_t)i;
+                    atomicOr((unsigned long long *)&peq[c * Lw + (q >> 6)], 1ull << (q & 63u));
+                }
+            }
+            __syncwarp();
+        }
+
+        // column 0: rows -K..0 have difference -1, rows >= 1 have +1; T = K+1
+        uint64_t Pv[V], Mv[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const int lo = 64 * (gl * V + v);
+            if (K >= lo + 63) {
+                Mv[v] = ~0ull; Pv[v] = 0ull;
+            } else if (K < lo) {
+                Mv[v] = 0ull; Pv[v] = ~0ull;
+            } else {
+                const int nb = K - lo + 1;
+                Mv[v] = (1ull << nb) - 1ull;
+                Pv[v] = ~Mv[v];
+            }
+        }
+        int32_t T = K + 1;
+
+        int32_t nmax = __reduce_max_sync(FULL, ncols);
+        uint32_t cnext = (ncols > 0) ? (uint32_t)s_map[ys[0]] : 0u;
+        for (int32_t j = 1; j <= nmax; j++) {
+            const bool act = j <= ncols;
+            const uint32_t c = cnext;
+            if (j < ncols) cnext = s_map[ys[j]];
+
+            // T := value of the row above the shifted window
+            if (gl == 0 && act) T += (int32_t)(Pv[0] & 1ull) - (int32_t)(Mv[0] & 1ull) + 1;
+
+            // shift the window down one row; the new bottom row has difference +1
+            uint32_t low = (uint32_t)(Pv[0] & 1ull) | ((uint32_t)(Mv[0] & 1ull) << 1);
+            uint32_t nxt = (G > 1) ? __shfl_down_sync(FULL, low, 1, G) : low;
+            if (gl == G - 1) nxt = 1u;
+            uint64_t nP[V], nM[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const uint64_t upP = (v + 1 < V) ? Pv[v + 1 < V ? v + 1 : v] : (uint64_t)(nxt & 1u);
+                const uint64_t upM = (v + 1 < V) ? Mv[v + 1 < V ? v + 1 : v] : (uint64_t)(nxt >> 1);
+                nP[v] = (Pv[v] >> 1) | (upP << 63);
+                nM[v] = (Mv[v] >> 1) | (upM << 63);
+            }
+
+            // match masks of the window rows against y[j-1]
+            const bool cval = act && c < alpha;  // a symbol outside the alphabet matches nothing
+            const uint64_t *row = peq + (size_t)(cval ? c : 0u) * Lw;
+            const uint32_t q0 = (uint32_t)(j - 1) + 64u * (uint32_t)(gl * V);
+            const uint32_t sh = q0 & 63u;
+            const uint32_t i0 = q0 >> 6;
+            uint64_t Eq[V];
+            {
+                uint64_t w_lo = cval ? row[i0] : 0ull;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const uint64_t w_hi = cval ? row[i0 + v + 1] : 0ull;
+                    Eq[v] = funnel64(w_lo, w_hi, sh);
+                    w_lo = w_hi;
+                }
+            }
+
+            // bit-vector step (Myers/Hyyro): Xh = (((Eq & Pv) + Pv) ^ Pv) | Eq
+            uint64_t S[V];
+            uint32_t cy = 0;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const uint64_t x1 = Eq[v] & nP[v];
+                const uint64_t t1 = x1 + nP[v];
+                const uint32_t c1 = t1 < x1;
+                const uint64_t s1 = t1 + cy;
+                const uint32_t c2 = s1 < t1;
+                S[v] = s1;
+                cy = c1 | c2;
+            }
+            if (G > 1) {
+                bool prop = true;
+#pragma unroll
+                for (int v = 0; v < V; v++) prop = prop && (S[v] == ~0ull);
+                const unsigned gb = __ballot_sync(FULL, cy != 0u);
+                const unsigned pb = __ballot_sync(FULL, prop);
+                const unsigned sel = (G == 32) ? FULL : ((1u << G) - 1u);
+                const unsigned gG = (gb >> (g * G)) & sel;
+                const unsigned gP = (pb >> (g * G)) & sel;
+                const unsigned A = gG | gP;
+                const unsigned carries = (A + gG) ^ A ^ gG;  // carry into each lane
+                uint32_t cin = (carries >> gl) & 1u;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const uint64_t s2 = S[v] + cin;
+                    cin = cin & (s2 == 0ull ? 1u : 0u);
+                    S[v] = s2;
+                }
+            }
+            uint64_t Ph[V], Mh[V], X[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                X[v] = Eq[v] | nM[v];
+                const uint64_t Xh = (S[v] ^ nP[v]) | Eq[v];
+                Ph[v] = nM[v] | ~(Xh | nP[v]);
+                Mh[v] = nP[v] & Xh;
+            }
+            // shift the horizontal differences down one row; the row above the
+            // window contributes +1 (Ph shift-in 1, Mh shift-in 0)
+            const uint32_t top = (uint32_t)(Ph[V - 1] >> 63) | ((uint32_t)(Mh[V - 1] >> 63) << 1);
+            uint32_t prv = (G > 1) ? __shfl_up_sync(FULL, top, 1, G) : top;
+            if (gl == 0) prv = 1u;
+#pragma unroll
+            for (int v = V - 1; v >= 0; v--) {
+                const uint64_t inP = (v > 0) ? (Ph[v > 0 ? v - 1 : 0] >> 63) : (uint64_t)(prv & 1u);
+                const uint64_t inM = (v > 0) ? (Mh[v > 0 ? v - 1 : 0] >> 63) : (uint64_t)(prv >> 1);
+                Ph[v] = (Ph[v] << 1) | inP;
+                Mh[v] = (Mh[v] << 1) | inM;
+            }
+            if (act) {
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    Pv[v] = Mh[v] | ~(X[v] | Ph[v]);
+                    Mv[v] = Ph[v] & X[v];
+                }
+            }
+
+            // early exit: minimum of the window exceeds K
+            if ((j & 63) == 0 && j < nmax) {
+                int32_t run = 0, mn = 1 << 30;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+#pragma unroll
+                    for (int k = 0; k < 16; k++) {
+                        const uint32_t idx = (uint32_t)((Pv[v] >> (4 * k)) & 15u) |
+                                             ((uint32_t)((Mv[v] >> (4 * k)) & 15u) << 4);
+                        const int32_t cand = run + s_nmin[idx];
+                        mn = cand < mn ? cand : mn;
+                        run += s_nsum[idx];
+                    }
+                }
+                // prefix of run over the group's lanes (in lane order)
+                int32_t inc = run;
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    const int32_t t = __shfl_up_sync(FULL, inc, o, G);
+                    if (gl >= o) inc += t;
+                }
+                int32_t gmin = mn + (inc - run);
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    const int32_t t = __shfl_xor_sync(FULL, gmin, o, G);
+                    gmin = t < gmin ? t : gmin;
+                }
+                const int32_t T0 = (G > 1) ? __shfl_sync(FULL, T, 0, G) : T;
+                if (act && T0 + gmin > K) {
+                    decided = true;
+                    pass = false;
+                    ncols = 0;
+                }
+                nmax = __reduce_max_sync(FULL, ncols);
+            }
+        }
+
+        {
+            // D(m, n) = T + sum of differences of window bits 0 .. m - n + K
+            // (computed by every lane so that the collectives stay converged)
+            const int32_t bmax = (mrows - ncols) + K;
+            int32_t cnt = 0;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const int lo = 64 * (gl * V + v);
+                uint64_t mask;
+                if (lo > bmax) mask = 0ull;
+                else if (lo + 63 <= bmax) mask = ~0ull;
+                else mask = (1ull << (bmax - lo + 1)) - 1ull;
+                cnt += __popcll(Pv[v] & mask) - __popcll(Mv[v] & mask);
+            }
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) cnt += __shfl_xor_sync(FULL, cnt, o, G);
+            const int32_t T0 = (G > 1) ? __shfl_sync(FULL, T, 0, G) : T;
+            if (!decided) pass = (T0 + cnt) <= K;
+        }
+        if (valid && gl == 0) flags[p] = pass ? 1 : 0;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Configuration
+// ---------------------------------------------------------------------------
+
+static int words_needed(int32_t K) { return (2 * K + 1 + 63) / 64; }
+
+static int32_t peq_words(int64_t max_len, int32_t K, int W) {
+    return (int32_t)(((max_len + (int64_t)K + 64ll * W) >> 6) + 2);
+}
+
+size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_t K) {
+    const int W = c.G * c.V;
+    return (size_t)c.warps * (32 / c.G) * alpha * (size_t)peq_words(max_len, K, W) * sizeof(uint64_t);
+}
+
+VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
+    const int W = words_needed(K);
+    // For each words-per-lane V take the fewest lanes G (a power of two) that
+    // cover the band; keep the smallest window, preferring configurations whose
+    // shared memory allows >= 8 resident warps per SM, then larger V (fewer
+    // cross-lane collectives per word).
+    VerifyConfig best{0, 0, 0};
+    int best_words = 1 << 30;
+    bool best_fit = false;
+    for (int V = 4; V >= 1; V--) {
+        int G = 1;
+        while (G * V < W && G < 32) G <<= 1;
+        if (G * V < W) continue;
+        VerifyConfig c{G, V, 1};
+        const size_t per_warp = verify_smem_bytes(c, alpha, max_len, K);
+        if (per_warp > 200 * 1024) continue;
+        const bool fit = per_warp <= 28 * 1024;
+        const int words = G * V;
+        if ((fit && !best_fit) || (fit == best_fit && words < best_words)) {
+            best = c;
+            best_words = words;
+            best_fit = fit;
+        }
+    }
+    if (best.G == 0) return best;
+    const size_t per_warp = verify_smem_bytes(best, alpha, max_len, K);
+    int warps = (int)((96 * 1024) / (per_warp ? per_warp : 1));
+    if (warps > VERIFY_MAX_THREADS / 32) warps = VERIFY_MAX_THREADS / 32;
+    if (warps < 1) warps = 1;
+    best.warps = warps;
+    return best;
+}
+
+template <int G, int V>
+static cudaError_t launch_gv(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
+                             const uint8_t *code_map, uint32_t alpha, const uint64_t *pairs, int64_t np,
+                             int32_t K, int64_t max_len, int warps, uint8_t *flags, uint32_t *err,
+                             cudaStream_t s) {
+    const int32_t Lw = peq_words(max_len, K, G * V);
+    const size_t smem = (size_t)warps * (32 / G) * alpha * Lw * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(verify_kernel<G, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_kernel<G, V>, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t warp_batches = (np + (32 / G) - 1) / (32 / G);
+    int64_t blocks = (warp_batches + warps - 1) / warps;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    verify_kernel<G, V><<<(unsigned)blocks, warps * 32, smem, s>>>(bytes, offsets, lens, n, code_map, alpha,
+                                                                  pairs, np, K, Lw, flags, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
+                          const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
+                          const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
+                          uint8_t *flags, uint32_t *err, cudaStream_t s) {
+    if (np == 0) return cudaGetLastError();
+#define EJ_V(GG, VV)                                                                                    \
+    if (c.G == GG && c.V == VV)                                                                         \
+        return launch_gv<GG, VV>(bytes, offsets, lens, n, code_map, alpha, pairs, np, K, max_len, c.warps, \
+                                 flags, err, s);
+    EJ_V(1, 1) EJ_V(1, 2) EJ_V(1, 3) EJ_V(1, 4)
+    EJ_V(2, 1) EJ_V(2, 2) EJ_V(2, 3) EJ_V(2, 4)
+    EJ_V(4, 1) EJ_V(4, 2) EJ_V(4, 3) EJ_V(4, 4)
+    EJ_V(8, 1) EJ_V(8, 2) EJ_V(8, 3) EJ_V(8, 4)
+    EJ_V(16, 1) EJ_V(16, 2) EJ_V(16, 3) EJ_V(16, 4)
+    EJ_V(32, 1) EJ_V(32, 2) EJ_V(32, 3) EJ_V(32, 4)
+#undef EJ_V
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ej

@@ -1,0 +1,298 @@
+"""Python binding of the EmbedJoin C-ABI library (argument marshalling only).
+
+Every step of the join runs in the CUDA kernels of ``libembedjoin.so``; this
+module only passes pointers, sizes and streams. Arrays may be torch tensors
+(device or host) or numpy arrays (host). PyTorch is used for device memory and
+streams. Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libembedjoin.so")
+
+EJ_OK = 0
+EJ_ERR_INVALID_ARG = 1
+EJ_ERR_OOM = 2
+EJ_ERR_CAPACITY = 3
+EJ_ERR_CUDA = 4
+EJ_ERR_TIMEOUT = 5
+EJ_ERR_UNSUPPORTED = 6
+
+EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
+            "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
+            "ej_set_test_tables"]
+
+
+class EJError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("r", C.c_uint32), ("m", C.c_uint32), ("z", C.c_uint32), ("L", C.c_uint32),
+                ("out_len", C.c_uint32), ("K", C.c_int32), ("seed", C.c_uint64),
+                ("alphabet", C.c_void_p), ("alphabet_size", C.c_uint32)]
+
+
+class _Strings(C.Structure):
+    _fields_ = [("bytes", C.c_void_p), ("offsets", C.c_void_p), ("n", C.c_int64)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("max_len", C.c_int64), ("total_bytes", C.c_int64),
+                ("out_len", C.c_uint32), ("L", C.c_uint32), ("planes", C.c_uint32),
+                ("blocks32", C.c_uint32), ("embedding_bytes", C.c_uint64),
+                ("walk_end_count", C.c_uint64), ("key_count", C.c_uint64)]
+
+
+class JoinStats(C.Structure):
+    _fields_ = [("n_raw_pairs", C.c_int64), ("n_candidates", C.c_int64), ("n_out", C.c_int64),
+                ("max_bucket", C.c_int64), ("ms_embed", C.c_float), ("ms_sign", C.c_float),
+                ("ms_candidates", C.c_float), ("ms_verify", C.c_float), ("ms_total", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libembedjoin.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libembedjoin.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.ej_create.argtypes = [C.POINTER(vp), C.c_int]
+        L.ej_create.restype = C.c_int
+        L.ej_destroy.argtypes = [vp]
+        L.ej_destroy.restype = None
+        L.ej_status_string.argtypes = [C.c_int]
+        L.ej_status_string.restype = C.c_char_p
+        L.ej_last_error.argtypes = [vp]
+        L.ej_last_error.restype = C.c_char_p
+        L.ej_set_timing.argtypes = [vp, C.c_int]
+        L.ej_set_timing.restype = C.c_int
+        L.ej_plan.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), C.POINTER(PlanInfo), vp]
+        L.ej_plan.restype = C.c_int
+        L.ej_embed.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, vp, vp]
+        L.ej_embed.restype = C.c_int
+        L.ej_sign.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, vp, vp, vp]
+        L.ej_sign.restype = C.c_int
+        L.ej_lsh_candidates.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, vp, i64,
+                                        C.POINTER(i64), C.POINTER(i64), vp]
+        L.ej_lsh_candidates.restype = C.c_int
+        L.ej_verify.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, i64, vp,
+                                C.POINTER(i64), vp]
+        L.ej_verify.restype = C.c_int
+        L.ej_join.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, i64, C.POINTER(i64),
+                              C.POINTER(JoinStats), vp]
+        L.ej_join.restype = C.c_int
+        L.ej_set_test_tables.argtypes = [vp, vp, C.c_uint32, C.c_uint32, C.c_uint32, vp,
+                                         C.c_uint32, C.c_uint32]
+        L.ej_set_test_tables.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data if a.size else None
+    assert a.is_contiguous()
+    return a.data_ptr() if a.numel() else None
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class Params:
+    """Method parameters: r embeddings, m LSH functions of z positions each,
+    sampling range L (0 = out_len), out_len (0 = 3N), threshold K, seed."""
+    K: int
+    r: int
+    m: int
+    z: int
+    seed: int = 1
+    L: int = 0
+    out_len: int = 0
+    alphabet: bytes = b"ACGT"
+
+    def _c(self):
+        buf = C.create_string_buffer(bytes(self.alphabet), len(self.alphabet))
+        p = _Params(self.r, self.m, self.z, self.L, self.out_len, self.K, self.seed & (2**64 - 1),
+                    C.cast(buf, C.c_void_p), len(self.alphabet))
+        return p, buf
+
+
+class Strings:
+    """Packed strings: uint8 bytes + int64 offsets (n+1), torch tensors or numpy."""
+
+    def __init__(self, data, offsets):
+        self.data = data
+        self.offsets = offsets
+        self.n = int(offsets.shape[0]) - 1
+
+    def _c(self):
+        return _Strings(_ptr(self.data), _ptr(self.offsets), self.n)
+
+    @staticmethod
+    def from_set(ss, device=None):
+        """From a ``synth.StringSet``; device=None keeps host numpy arrays."""
+        if device is None:
+            return Strings(ss.data, ss.offsets)
+        import torch
+        d = torch.from_numpy(ss.data if ss.data.size else np.zeros(1, np.uint8)).to(device)
+        o = torch.from_numpy(ss.offsets).to(device)
+        return Strings(d, o)
+
+
+class Context:
+    """An ej_ctx bound to one CUDA device (owns scratch memory)."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        st = lib().ej_create(C.byref(self._h), device)
+        if st != EJ_OK:
+            raise EJError(st, f"ej_create failed: {lib().ej_status_string(st).decode()}")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().ej_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != EJ_OK:
+            detail = lib().ej_last_error(self._h).decode()
+            raise EJError(st, f"{what}: {lib().ej_status_string(st).decode()}: {detail}")
+
+    def set_timing(self, on: bool = True):
+        self._check(lib().ej_set_timing(self._h, 1 if on else 0), "ej_set_timing")
+
+    def plan(self, s: Strings, p: Params, stream=None) -> PlanInfo:
+        info = PlanInfo()
+        cs, (cp, _keep) = s._c(), p._c()
+        self._check(lib().ej_plan(self._h, C.byref(cs), C.byref(cp), C.byref(info), _stream(stream)),
+                    "ej_plan")
+        return info
+
+    def embed(self, s: Strings, p: Params, emb, walk_end, stream=None):
+        cs, (cp, _keep) = s._c(), p._c()
+        self._check(lib().ej_embed(self._h, C.byref(cs), C.byref(cp), _ptr(emb), _ptr(walk_end),
+                                   _stream(stream)), "ej_embed")
+
+    def sign(self, s: Strings, p: Params, emb, walk_end, keys, stream=None):
+        cs, (cp, _keep) = s._c(), p._c()
+        self._check(lib().ej_sign(self._h, C.byref(cs), C.byref(cp), _ptr(emb), _ptr(walk_end),
+                                  _ptr(keys), _stream(stream)), "ej_sign")
+
+    def lsh_candidates(self, s: Strings, p: Params, keys, pairs, stream=None) -> tuple[int, int]:
+        """Returns (count, max_bucket). Raises EJError(EJ_ERR_CAPACITY) with
+        .needed set when `pairs` is too small."""
+        cs, (cp, _keep) = s._c(), p._c()
+        n = C.c_int64(0)
+        mb = C.c_int64(0)
+        cap = 0 if pairs is None else int(pairs.shape[0])
+        st = lib().ej_lsh_candidates(self._h, C.byref(cs), C.byref(cp), _ptr(keys), _ptr(pairs), cap,
+                                     C.byref(n), C.byref(mb), _stream(stream))
+        if st == EJ_ERR_CAPACITY:
+            e = EJError(st, "ej_lsh_candidates: capacity")
+            e.needed = n.value
+            raise e
+        self._check(st, "ej_lsh_candidates")
+        return n.value, mb.value
+
+    def verify(self, s: Strings, p: Params, pairs, out, stream=None) -> int:
+        cs, (cp, _keep) = s._c(), p._c()
+        n = C.c_int64(0)
+        self._check(lib().ej_verify(self._h, C.byref(cs), C.byref(cp), _ptr(pairs), int(pairs.shape[0]),
+                                    _ptr(out), C.byref(n), _stream(stream)), "ej_verify")
+        return n.value
+
+    def join_into(self, s: Strings, p: Params, out, stream=None) -> tuple[int, JoinStats]:
+        """ej_join into a caller buffer. Raises EJError with .needed on overflow."""
+        cs, (cp, _keep) = s._c(), p._c()
+        n = C.c_int64(0)
+        stats = JoinStats()
+        cap = 0 if out is None else int(out.shape[0])
+        st = lib().ej_join(self._h, C.byref(cs), C.byref(cp), _ptr(out), cap, C.byref(n),
+                           C.byref(stats), _stream(stream))
+        if st == EJ_ERR_CAPACITY:
+            e = EJError(st, "ej_join: capacity")
+            e.needed = n.value
+            raise e
+        self._check(st, "ej_join")
+        return n.value, stats
+
+    def join(self, s: Strings, p: Params, device=None, capacity: int = 1 << 16, stream=None):
+        """Convenience: returns (pairs, stats) with pairs a uint64 tensor on `device`
+        (or a numpy array if device is None), growing the buffer on overflow."""
+        while True:
+            if device is None:
+                out = np.zeros(max(capacity, 1), dtype=np.uint64)
+            else:
+                import torch
+                out = torch.empty(max(capacity, 1), dtype=torch.int64, device=device)
+            try:
+                n, stats = self.join_into(s, p, out, stream)
+                return out[:n], stats
+            except EJError as e:
+                if e.status != EJ_ERR_CAPACITY:
+                    raise
+                capacity = e.needed
+
+    def set_test_tables(self, pi=None, positions=None):
+        """Inject explicit pi tables [r][steps][alphabet] (0/1) and/or positions
+        [r][m][z] (the running example's Tables 2-3). No arguments restores RNG."""
+        pi_a = None if pi is None else np.ascontiguousarray(pi, dtype=np.uint8)
+        pos_a = None if positions is None else np.ascontiguousarray(positions, dtype=np.uint32)
+        r = pi_a.shape[0] if pi_a is not None else (pos_a.shape[0] if pos_a is not None else 0)
+        st = lib().ej_set_test_tables(
+            self._h, _ptr(pi_a), r, 0 if pi_a is None else pi_a.shape[1],
+            0 if pi_a is None else pi_a.shape[2], _ptr(pos_a),
+            0 if pos_a is None else pos_a.shape[1], 0 if pos_a is None else pos_a.shape[2])
+        self._check(st, "ej_set_test_tables")
+
+
+def decode_embedding(emb_words: np.ndarray, walk_end: np.ndarray, r: int, n: int, out_len: int,
+                     planes: int, alphabet_size: int) -> np.ndarray:
+    """Bit-sliced ej_embed output -> codes [r][n][out_len] (bottom = alphabet_size).
+    Host-side inspection helper (numpy), not part of the join."""
+    nb32 = (n + 31) // 32
+    w = np.asarray(emb_words, dtype=np.uint32).reshape(r, nb32, out_len, planes)
+    bits = ((w[..., None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.uint8)  # r,B,j,k,t
+    codes = np.zeros((r, nb32, 32, out_len), dtype=np.uint8)
+    for k in range(planes):
+        codes |= (bits[:, :, :, k, :].transpose(0, 1, 3, 2) << k).astype(np.uint8)
+    codes = codes.reshape(r, nb32 * 32, out_len)[:, :n]
+    steps = np.arange(out_len)[None, None, :]
+    codes = np.where(steps >= np.asarray(walk_end)[:, :, None], alphabet_size, codes).astype(np.uint8)
+    return codes

@@ -1,0 +1,293 @@
+"""GPU parity: every stage of the CUDA path (called through the C ABI) against
+the CPU oracle on the same seeded inputs. All of this is integer work, so the
+bar is bit-identical output: embeddings, walk ends, keys, candidate sets and
+output pair sets."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00093_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ej():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_00093_gb300 import build
+    build.build()
+    oracle.build()
+    from paper_1702_00093_gb300 import embedjoin
+    return embedjoin
+
+
+@pytest.fixture(scope="module")
+def ctx(ej):
+    c = ej.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def _np_u64(t):
+    return t.cpu().numpy().view(np.uint64) if t.dtype == torch.int64 else t.cpu().numpy().astype(np.uint64)
+
+
+def gpu_embed(ej, ctx, ss, params):
+    s = ej.Strings.from_set(ss, DEV)
+    info = ctx.plan(s, params)
+    emb = torch.zeros(max(info.embedding_bytes // 4, 1), dtype=torch.int32, device=DEV)
+    we = torch.zeros(max(params.r * ss.n, 1), dtype=torch.int32, device=DEV)
+    ctx.embed(s, params, emb, we)
+    torch.cuda.synchronize()
+    codes = ej.decode_embedding(emb.cpu().numpy().view(np.uint32)[: info.embedding_bytes // 4],
+                                we.cpu().numpy()[: params.r * ss.n].reshape(params.r, ss.n),
+                                params.r, ss.n, info.out_len, info.planes, len(ss.alphabet))
+    return s, info, emb, we, codes
+
+
+def gpu_keys(ej, ctx, s, params, emb, we, n):
+    keys = torch.zeros(params.r * params.m * n, dtype=torch.int64, device=DEV)
+    ctx.sign(s, params, emb, we, keys)
+    torch.cuda.synchronize()
+    return _np_u64(keys).reshape(params.r * params.m, n)
+
+
+def gpu_candidates(ej, ctx, s, params, keys_np):
+    keys = torch.from_numpy(keys_np.view(np.int64).ravel().copy()).to(DEV)
+    try:
+        n, mb = ctx.lsh_candidates(s, params, keys, torch.empty(1, dtype=torch.int64, device=DEV))
+        out = torch.empty(max(n, 1), dtype=torch.int64, device=DEV)
+    except ej.EJError as e:
+        assert e.status == ej.EJ_ERR_CAPACITY
+        out = torch.empty(e.needed, dtype=torch.int64, device=DEV)
+    n, mb = ctx.lsh_candidates(s, params, keys, out)
+    return _np_u64(out[:n])
+
+
+def check_all_stages(ej, ctx, ss, params, check_join=True):
+    s, info, emb, we, codes = gpu_embed(ej, ctx, ss, params)
+    ref_emb, ref_we = oracle.embed(ss.data, ss.offsets, ss.alphabet, params.r, info.out_len, params.seed)
+    assert np.array_equal(we.cpu().numpy()[: params.r * ss.n].reshape(params.r, ss.n), ref_we)
+    assert np.array_equal(codes, ref_emb)
+    pos = oracle.positions(params.seed, params.r, params.m, params.z, info.L)
+    ref_keys = oracle.sign(ref_emb, ref_we, pos, len(ss.alphabet))
+    keys = gpu_keys(ej, ctx, s, params, emb, we, ss.n)
+    assert np.array_equal(keys, ref_keys)
+    cand = gpu_candidates(ej, ctx, s, params, keys)
+    ref_cand = oracle.candidates(ss.data, ss.offsets, ref_keys, params.K)
+    assert np.array_equal(cand, ref_cand)
+    if len(cand):
+        pt = torch.from_numpy(cand.view(np.int64).copy()).to(DEV)
+        out = torch.empty_like(pt)
+        k = ctx.verify(s, params, pt, out)
+        flags = oracle.verify(ss.data, ss.offsets, cand, params.K)
+        assert np.array_equal(_np_u64(out[:k]), cand[flags == 1])
+    if check_join:
+        pairs, stats = ctx.join(s, params, device=DEV)
+        ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=params.K, r=params.r, m=params.m,
+                          z=params.z, seed=params.seed, L=params.L, out_len=params.out_len)
+        assert stats.n_candidates == ref.n_candidates
+        assert np.array_equal(_np_u64(pairs), ref.pairs)
+    return cand
+
+
+# ---------------------------------------------------------------------------
+# The paper's running example (Section 4, Tables 2-4) through the injection hook
+# ---------------------------------------------------------------------------
+
+def test_running_example_on_gpu(ej, ctx, golden):
+    g = golden("running_example_sec4.json")
+    ss = synth.pack([x.encode() for x in g["strings"]], b"ACGT")
+    pi = np.zeros((2, 10, 4), dtype=np.uint8)
+    for l, name in enumerate(["R1", "R2"]):
+        for c, ch in enumerate("ACGT"):
+            pi[l, :, c] = g["pi_steps_1_to_10"][name][ch]
+    f = g["functions_1based_positions"]
+    pos = np.array([[f["f1^1"], f["f2^1"]], [f["f1^2"], f["f2^2"]]], dtype=np.uint32) - 1
+    params = ej.Params(K=3, r=2, m=2, z=2, seed=0, L=10, out_len=10, alphabet=b"ACGT")
+    ctx.set_test_tables(pi, pos)
+    try:
+        s, info, emb, we, codes = gpu_embed(ej, ctx, ss, params)
+        for i in range(4):
+            for l in range(2):
+                assert "".join("ACGT"[c] for c in codes[l, i]) == g["embedded_prefixes"][f"t{i + 1}^{l + 1}"]
+        keys = gpu_keys(ej, ctx, s, params, emb, we, 4)
+        for i in range(4):
+            for col in range(4):
+                sig = g["signatures"][str(i + 1)][col]
+                assert int(keys[col, i]) == "ACGT".index(sig[0]) + 5 * "ACGT".index(sig[1])
+        cand = gpu_candidates(ej, ctx, s, params, keys)
+        assert [(int(p >> 32) + 1, int(p & 0xFFFFFFFF) + 1) for p in cand] == [tuple(x) for x in g["candidates_1based"]]
+        pairs, _ = ctx.join(s, params, device=DEV)
+        got = [(int(p >> 32) + 1, int(p & 0xFFFFFFFF) + 1) for p in _np_u64(pairs)]
+        assert got == [tuple(x) for x in g["output_1based"]]
+    finally:
+        ctx.set_test_tables()
+
+
+def test_worked_example_on_gpu(ej, ctx, golden):
+    g = golden("worked_example_sec1.json")
+    ss = synth.pack([x.encode() for x in g["strings"]], b"ACGT")
+    s = ej.Strings.from_set(ss, DEV)
+    params = ej.Params(K=2, r=7, m=16, z=2, seed=5, alphabet=b"ACGT")
+    pairs, _ = ctx.join(s, params, device=DEV)
+    got = [(int(p >> 32), int(p & 0xFFFFFFFF)) for p in _np_u64(pairs)]
+    assert got == [tuple(x) for x in g["expected_pairs_0based"]]
+    # verification alone on all pairs equals the definition
+    allp = np.array([(i << 32) | j for i, j in itertools.combinations(range(5), 2)], dtype=np.uint64)
+    pt = torch.from_numpy(allp.view(np.int64).copy()).to(DEV)
+    out = torch.empty_like(pt)
+    k = ctx.verify(s, params, pt, out)
+    assert [(int(p >> 32), int(p & 0xFFFFFFFF)) for p in _np_u64(out[:k])] == got
+
+
+# ---------------------------------------------------------------------------
+# Stage-by-stage parity on the workload shapes
+# ---------------------------------------------------------------------------
+
+def test_small_dna_full_config(ej, ctx):
+    """n=1000 DNA, 100 clusters of 10, K=6, r=3, m=10, z=12 (L = 3N)."""
+    ss = synth.small_dna()
+    p = synth.SMALL_DNA_PARAMS
+    params = ej.Params(K=p["K"], r=p["r"], m=p["m"], z=p["z"], seed=p["seed"], alphabet=ss.alphabet)
+    cand = check_all_stages(ej, ctx, ss, params)
+    assert len(cand) > 1000
+
+
+@pytest.mark.parametrize("K", [50, 150, 250])
+def test_long_dna_shape(ej, ctx, K):
+    """Strings shaped like the long-DNA workload (length ~5000, 1-8% edits)."""
+    ss = synth.long_dna(n_clusters=4, seed=77)
+    p = synth.long_dna_params(K)
+    params = ej.Params(K=K, r=p["r"], m=p["m"], z=p["z"], seed=p["seed"], L=p["L"], alphabet=ss.alphabet)
+    check_all_stages(ej, ctx, ss, params)
+
+
+@pytest.mark.parametrize("maker,K,z", [
+    (lambda: synth.protein_like(5, 300, median=120, lo=20, hi=400), 12, 8),
+    (lambda: synth.text_like(6, 300, len_lo=50, len_hi=300, rate_lo=0.01, rate_hi=0.1), 20, 6),
+])
+def test_large_alphabets(ej, ctx, maker, K, z):
+    ss = maker()
+    L = int(2 * ss.lengths().mean())
+    params = ej.Params(K=K, r=4, m=6, z=z, seed=3, L=L, alphabet=ss.alphabet)
+    check_all_stages(ej, ctx, ss, params)
+
+
+def test_ragged_and_degenerate_strings(ej, ctx):
+    """Empty strings, identical strings (one big bucket), n not a multiple of 32."""
+    rng = np.random.default_rng(8)
+    strs = [b"", b"", b"A", b"AC", b"ACGT" * 10, b"ACGT" * 10, b"ACGA" * 10]
+    strs += [bytes(rng.choice(list(b"ACGT"), size=int(rng.integers(0, 90))).astype(np.uint8)) for _ in range(70)]
+    strs += [b"GATTACA" * 5] * 12
+    ss = synth.pack(strs, b"ACGT")
+    for K in (0, 1, 3, 40):
+        params = ej.Params(K=K, r=3, m=5, z=3, seed=11, alphabet=b"ACGT")
+        check_all_stages(ej, ctx, ss, params)
+
+
+def test_tiny_inputs(ej, ctx):
+    params = ej.Params(K=2, r=2, m=2, z=2, seed=1, alphabet=b"ACGT")
+    for strs in ([], [b"ACGT"], [b"", b""], [b"A", b"C"]):
+        ss = synth.pack(strs, b"ACGT")
+        s = ej.Strings.from_set(ss, DEV) if strs else ej.Strings(
+            torch.zeros(1, dtype=torch.uint8, device=DEV), torch.zeros(1, dtype=torch.int64, device=DEV))
+        pairs, _ = ctx.join(s, params, device=DEV)
+        want = oracle.join_bruteforce(ss.data, ss.offsets, 2) if strs else np.zeros(0, np.uint64)
+        assert np.array_equal(_np_u64(pairs), want)
+
+
+# ---------------------------------------------------------------------------
+# Verification kernel: many thresholds, lengths and band widths
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("K", [0, 1, 5, 31, 32, 63, 64, 100, 200, 300, 500, 1000])
+def test_verify_random_pairs(ej, ctx, K):
+    rng = np.random.default_rng(K + 1)
+    base = [rng.integers(0, 4, size=int(rng.integers(0, 1500))).astype(np.uint8) for _ in range(40)]
+    strs = []
+    for b in base:
+        strs.append(b)
+        strs.append(synth.mutate(rng, b, int(rng.integers(0, max(2, 2 * K + 5))), 4))
+    strs = [np.frombuffer(b"ACGT", np.uint8)[s].tobytes() for s in strs]
+    ss = synth.pack(strs, b"ACGT")
+    n = ss.n
+    pairs = sorted({(min(a, b), max(a, b)) for a, b in rng.integers(0, n, size=(600, 2)) if a != b}
+                   | {(2 * i, 2 * i + 1) for i in range(len(base))})
+    arr = np.array([(a << 32) | b for a, b in pairs], dtype=np.uint64)
+    s = ej.Strings.from_set(ss, DEV)
+    params = ej.Params(K=K, r=1, m=1, z=1, alphabet=b"ACGT")
+    pt = torch.from_numpy(arr.view(np.int64).copy()).to(DEV)
+    out = torch.empty_like(pt)
+    k = ctx.verify(s, params, pt, out)
+    flags = oracle.verify(ss.data, ss.offsets, arr, K)
+    assert np.array_equal(_np_u64(out[:k]), arr[flags == 1])
+    assert flags.sum() > 0
+
+
+def test_verify_host_buffers_and_unsorted_pairs(ej, ctx):
+    """Host (numpy) inputs and outputs through the same entry point; order kept."""
+    rng = np.random.default_rng(3)
+    ss = synth.dna_clusters(4, 10, 5, 50, 80, edits_mean=3.0)
+    s = ej.Strings.from_set(ss, None)
+    pairs = np.array([(int(a) << 32) | int(b) for a, b in rng.integers(0, ss.n, size=(300, 2)) if a != b],
+                     dtype=np.uint64)
+    out = np.zeros_like(pairs)
+    params = ej.Params(K=4, r=1, m=1, z=1, alphabet=b"ACGT")
+    k = ctx.verify(s, params, pairs, out)
+    flags = oracle.verify(ss.data, ss.offsets, pairs, 4)
+    assert np.array_equal(out[:k], pairs[flags == 1])
+
+
+def test_join_host_buffers_equal_device(ej, ctx):
+    ss = synth.small_dna(scale=0.2)
+    p = synth.SMALL_DNA_PARAMS
+    params = ej.Params(K=p["K"], r=p["r"], m=p["m"], z=p["z"], seed=p["seed"], alphabet=ss.alphabet)
+    host_pairs, _ = ctx.join(ej.Strings.from_set(ss, None), params, device=None)
+    dev_pairs, _ = ctx.join(ej.Strings.from_set(ss, DEV), params, device=DEV)
+    assert np.array_equal(host_pairs, _np_u64(dev_pairs))
+
+
+# ---------------------------------------------------------------------------
+# Errors are reported, not faulted
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_are_rejected(ej, ctx):
+    ss = synth.pack([b"ACGT", b"ACGN"], b"ACGT")
+    params = ej.Params(K=1, r=1, m=1, z=1, alphabet=b"ACGT")
+    with pytest.raises(ej.EJError) as e:
+        ctx.join(ej.Strings.from_set(ss, DEV), params, device=DEV)
+    assert e.value.status == ej.EJ_ERR_INVALID_ARG
+    bad = ej.Strings(torch.zeros(8, dtype=torch.uint8, device=DEV) + 65,
+                     torch.tensor([0, 5, 3], dtype=torch.int64, device=DEV))
+    with pytest.raises(ej.EJError) as e:
+        ctx.join(bad, ej.Params(K=1, r=1, m=1, z=1, alphabet=b"A"), device=DEV)
+    assert e.value.status == ej.EJ_ERR_INVALID_ARG
+    with pytest.raises(ej.EJError) as e:
+        ctx.join(ej.Strings.from_set(synth.pack([b"A", b"A"], b"A"), DEV),
+                 ej.Params(K=1, r=1, m=1, z=100, alphabet=b"A"), device=DEV)
+    assert e.value.status == ej.EJ_ERR_INVALID_ARG
+    pairs = torch.tensor([(0 << 32) | 7], dtype=torch.int64, device=DEV)
+    with pytest.raises(ej.EJError) as e:
+        ctx.verify(ej.Strings.from_set(synth.pack([b"A", b"A"], b"A"), DEV),
+                   ej.Params(K=1, r=1, m=1, z=1, alphabet=b"A"), pairs, torch.empty_like(pairs))
+    assert e.value.status == ej.EJ_ERR_INVALID_ARG
+    # the context still works afterwards
+    test_tiny_inputs(ej, ctx)
+
+
+def test_capacity_reports_needed_count(ej, ctx):
+    ss = synth.pack([b"ACGT"] * 10, b"ACGT")
+    params = ej.Params(K=0, r=1, m=1, z=2, alphabet=b"ACGT")
+    s = ej.Strings.from_set(ss, DEV)
+    with pytest.raises(ej.EJError) as e:
+        ctx.join_into(s, params, torch.empty(3, dtype=torch.int64, device=DEV))
+    assert e.value.status == ej.EJ_ERR_CAPACITY and e.value.needed == 45
