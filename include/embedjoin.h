@@ -111,6 +111,13 @@ typedef struct {
     float ms_candidates;
     float ms_verify;
     float ms_total;
+    uint64_t band_cells;     /* sum over candidates of the Ukkonen band size
+                                |{(a,b): a<|x|, b<|y|, |a-b|<=K}| (work of the
+                                verification, counted algorithmically) */
+    uint64_t verify_word_columns; /* 64-bit band words times columns the verifier
+                                actually advanced (ceil((2K+1)/64) words per
+                                column, early exit included) */
+    int64_t kernel_launches; /* CUDA kernels this call launched */
 } ej_join_stats;
 
 /* Create a context bound to CUDA device `device`. *ctx is NULL on failure. */

@@ -15,6 +15,13 @@ cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uin
 
 using namespace ej;
 
+#include <atomic>
+namespace ej {
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace ej
+
 namespace {
 
 enum BufId {
@@ -397,7 +404,8 @@ int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
 // Verify device pairs; passing pairs (input order) into `out_dev` if it has
 // room (capacity), count in *n_out. If out_dev is null only counts.
 int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *pairs, int64_t np,
-               uint64_t *out_dev, int64_t capacity, int64_t *n_out, cudaStream_t s) {
+               uint64_t *out_dev, int64_t capacity, int64_t *n_out, cudaStream_t s,
+               uint64_t *work_out = nullptr) {
     *n_out = 0;
     if (np == 0) return EJ_OK;
     VerifyConfig vc = verify_pick(p->K, p->alphabet_size, pl.max_len);
@@ -412,16 +420,23 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     uint64_t *dcnt = nullptr;
     CKS(ensure_t(ctx, B_COUNTERS, 8, &dcnt));
     CK(cudaMemsetAsync(derr, 0, 4, s));
+    CK(cudaMemsetAsync(dcnt + 4, 0, 2 * sizeof(uint64_t), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
     CK(launch_verify(vc, pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, (const uint8_t *)ctx->bufs[B_CODEMAP].p,
-                     p->alphabet_size, pairs, np, p->K, pl.max_len, fl, derr, s));
+                     p->alphabet_size, pairs, np, p->K, pl.max_len, fl, derr,
+                     (unsigned long long *)(dcnt + 4), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
     void *tmp = nullptr;
     CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(np), &tmp));
     CK(exclusive_scan_u8(fl, fo, np, dcnt + 3, tmp, s));
     CK(cudaMemcpyAsync(ctx->h_cnt, dcnt + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_cnt + 1, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt + 2, dcnt + 4, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (work_out) {
+        work_out[0] = (uint64_t)ctx->h_cnt[2];
+        work_out[1] = (uint64_t)ctx->h_cnt[3];
+    }
     if ((uint32_t)ctx->h_cnt[1] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "pair index >= n");
     const int64_t cnt = ctx->h_cnt[0];
     *n_out = cnt;
@@ -660,6 +675,8 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     if (!ctx || !n_out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_out");
     *n_out = 0;
     if (stats) memset(stats, 0, sizeof *stats);
+    const int64_t launches0 = launches_so_far();
+    uint64_t work[2] = {0, 0};
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
@@ -688,7 +705,7 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     bool h_out = false;
     if (nc > 0) {
         CKS(out_target(ctx, B_OUT_STAGE, out, (size_t)nc * sizeof(uint64_t), &d_out, &h_out));
-        int st = verify_dev(ctx, pl, p, cand, nc, (uint64_t *)d_out, h_out ? nc : capacity, &cnt, s);
+        int st = verify_dev(ctx, pl, p, cand, nc, (uint64_t *)d_out, h_out ? nc : capacity, &cnt, s, work);
         if (st == EJ_ERR_CAPACITY) *n_out = cnt;
         CKS(st);
         if (cnt > capacity) {
@@ -705,6 +722,9 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
         stats->n_candidates = nc;
         stats->n_out = cnt;
         stats->max_bucket = mb;
+        stats->band_cells = work[0];
+        stats->verify_word_columns = work[1];
+        stats->kernel_launches = launches_so_far() - launches0;
         if (ctx->timing) {
             cudaEventElapsedTime(&stats->ms_embed, ctx->ev[0], ctx->ev[1]);
             cudaEventElapsedTime(&stats->ms_sign, ctx->ev[1], ctx->ev[2]);

@@ -54,6 +54,7 @@ cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_
         int grid = (int)((n + 255) / 256);
         if (grid > 4096) grid = 4096;
         validate_offsets_kernel<<<grid, 256, 0, s>>>(offsets, n, lens, err, max_len);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -64,6 +65,7 @@ cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uin
         int64_t g = (total + 255) / 256;
         int grid = (int)(g > 8192 ? 8192 : g);
         validate_bytes_kernel<<<grid, 256, 0, s>>>(bytes, total, code_map, err);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -108,6 +110,7 @@ cudaError_t launch_bit_table(uint64_t seed, uint32_t r, uint32_t out_len, const 
         int grid = (int)(g > 4096 ? 4096 : g);
         bit_table_kernel<<<grid, 256, 0, s>>>(mix64(seed), r, out_len, alphabet_dev, alpha, words,
                                               pi_inject, inject_steps, table);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -134,6 +137,7 @@ cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, 
     if (total) {
         int grid = (int)((total + 255) / 256 > 1024 ? 1024 : (total + 255) / 256);
         positions_kernel<<<grid, 256, 0, s>>>(mix64(seed), r, m, z, L, pos_inject, pos);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -246,6 +250,7 @@ cudaError_t launch_embed(const uint8_t *bytes, const int64_t *offsets, const int
         case 7: EJ_EMB(7); break;
         default: EJ_EMB(8); break;
     }
+    note_launches(1);
 #undef EJ_EMB
     return cudaGetLastError();
 }
@@ -306,6 +311,7 @@ cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n,
         case 7: EJ_SIGN(7); break;
         default: EJ_SIGN(8); break;
     }
+    note_launches(1);
 #undef EJ_SIGN
     return cudaGetLastError();
 }

@@ -38,6 +38,11 @@ inline uint32_t planes_for(uint32_t alpha) {
 // u32 words per step of the code-indexed random-bit table.
 inline uint32_t table_words_for(uint32_t planes) { return planes <= 5 ? 1u : (1u << (planes - 5)); }
 
+// Number of kernels launched by this library (all threads); a launcher adds
+// the kernels it enqueued.
+void note_launches(int k);
+int64_t launches_so_far();
+
 // Device-side error bits.
 enum : uint32_t {
     DERR_OFFSETS = 1u,     // offsets not starting at 0 / decreasing / too long
@@ -134,6 +139,6 @@ size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_
 cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
                           const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
-                          uint8_t *flags, uint32_t *err, cudaStream_t s);
+                          uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s);
 
 }  // namespace ej

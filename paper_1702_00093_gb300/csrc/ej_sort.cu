@@ -126,6 +126,7 @@ static cudaError_t exclusive_scan(const T *in, uint64_t *out, int64_t n, uint64_
     if (nb > 0) scan_reduce_kernel<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
     scan_sums_kernel<<<1, SCAN_THREADS, 0, s>>>(sums, nb, total_dev);
     if (nb > 0) scan_apply_kernel<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    note_launches(nb > 0 ? 3 : 1);
     return cudaGetLastError();
 }
 
@@ -254,6 +255,7 @@ cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_
         if (e != cudaSuccess) return e;
         radix_scatter_kernel<<<grid, RS_THREADS, 0, s>>>(ki, vi, ko, vo, seg_len, tps, shifts[p],
                                                          tmp.offsets);
+        note_launches(2);
         uint64_t *kt = ki; ki = ko; ko = kt;
         uint32_t *vt = vi; vi = vo; vo = vt;
         *in_alt = !*in_alt;
@@ -276,6 +278,7 @@ __global__ void iota_kernel(uint32_t *v, int64_t n) {
 }
 cudaError_t launch_iota_u32(uint32_t *v, int64_t n, cudaStream_t s) {
     if (n > 0) iota_kernel<<<grid_for(n, 4096), 256, 0, s>>>(v, n);
+    if (n > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -285,6 +288,7 @@ __global__ void len_keys_kernel(const int32_t *lens, int64_t n, uint64_t *k) {
 }
 cudaError_t launch_len_keys(const int32_t *lens, int64_t n, uint64_t *k, cudaStream_t s) {
     if (n > 0) len_keys_kernel<<<grid_for(n, 4096), 256, 0, s>>>(lens, n, k);
+    if (n > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -308,6 +312,7 @@ cudaError_t launch_len_order_gather(const uint64_t *keys, const uint32_t *perm, 
     if (total > 0)
         len_order_gather_kernel<<<grid_for(total, 16384), 256, 0, s>>>(
             keys, perm, n, T, rec_keys, rec_ids);
+    if (total > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -383,6 +388,7 @@ cudaError_t launch_bucket_count(const uint64_t *rec_keys, const uint32_t *rec_id
     if (total > 0)
         bucket_count_kernel<<<grid_for(total, 16384), 256, 0, s>>>(
             rec_keys, rec_ids, lens, n, T, K, counts, max_bucket);
+    if (total > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -413,6 +419,7 @@ cudaError_t launch_bucket_emit(const uint64_t *rec_keys, const uint32_t *rec_ids
     if (total > 0)
         bucket_emit_kernel<<<grid_for(total, 16384), 256, 0, s>>>(
             rec_keys, rec_ids, lens, n, T, K, offs, pairs);
+    if (total > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -422,6 +429,7 @@ __global__ void unique_flags_kernel(const uint64_t *__restrict__ a, int64_t n, u
 }
 cudaError_t launch_unique_flags(const uint64_t *sorted, int64_t n, uint8_t *flags, cudaStream_t s) {
     if (n > 0) unique_flags_kernel<<<grid_for(n, 16384), 256, 0, s>>>(sorted, n, flags);
+    if (n > 0) note_launches(1);
     return cudaGetLastError();
 }
 
@@ -433,6 +441,7 @@ __global__ void compact_kernel(const uint64_t *__restrict__ in, const uint8_t *_
 cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const uint64_t *offs,
                                int64_t n, uint64_t *out, cudaStream_t s) {
     if (n > 0) compact_kernel<<<grid_for(n, 16384), 256, 0, s>>>(in, flags, offs, n, out);
+    if (n > 0) note_launches(1);
     return cudaGetLastError();
 }
 

@@ -42,13 +42,26 @@ __device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t 
     return sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
 }
 
+// |{(a, b): 0 <= a < lx, 0 <= b < ly, |a - b| <= K}|, Ukkonen's band size.
+__device__ __forceinline__ unsigned long long band_cells(int64_t lx, int64_t ly, int64_t K) {
+    if (lx <= 0 || ly <= 0) return 0ull;
+    const int64_t amax = min(lx - 1, ly - 1 + K);   // rows whose band range is non-empty
+    if (amax < 0) return 0ull;
+    const int64_t t = min(amax + 1, max((int64_t)0, ly - K));  // rows whose range ends at a+K
+    const int64_t s1 = t * (t - 1) / 2 + t * (K + 1) + (amax + 1 - t) * ly;
+    const int64_t u = max((int64_t)0, amax - K);
+    return (unsigned long long)(s1 - u * (u + 1) / 2);
+}
+
 template <int G, int V>
 __global__ void __launch_bounds__(VERIFY_MAX_THREADS)
 verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
               const int32_t *__restrict__ lens, int64_t n_str, const uint8_t *__restrict__ code_map,
               uint32_t alpha, const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t Lw,
-              uint8_t *__restrict__ flags, uint32_t *__restrict__ err) {
+              uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
+              unsigned long long *__restrict__ work) {
     constexpr int GPW = 32 / G;
+    const int32_t w_min = (2 * K + 1 + 63) / 64;
     extern __shared__ uint64_t smem[];
     __shared__ uint8_t s_map[256];
     __shared__ int8_t s_nsum[256];
@@ -106,6 +119,7 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
         }
         int32_t ncols = decided ? 0 : nlen;
         const int32_t mrows = decided ? 0 : mlen;
+        int32_t cols_run = ncols;  // columns actually advanced (early exit shortens it)
 
         // Peq[c]: bit K+i set iff code(x[i]) == c
         const int32_t mmax = __reduce_max_sync(FULL, mrows);
@@ -271,6 +285,7 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
                     decided = true;
                     pass = false;
                     ncols = 0;
+                    cols_run = j;
                 }
                 nmax = __reduce_max_sync(FULL, ncols);
             }
@@ -295,7 +310,13 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
             const int32_t T0 = (G > 1) ? __shfl_sync(FULL, T, 0, G) : T;
             if (!decided) pass = (T0 + cnt) <= K;
         }
-        if (valid && gl == 0) flags[p] = pass ? 1 : 0;
+        if (valid && gl == 0) {
+            flags[p] = pass ? 1 : 0;
+            if (work) {
+                atomicAdd(&work[0], band_cells(mlen, nlen, K));
+                atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+            }
+        }
         __syncwarp();
     }
 }
@@ -352,7 +373,7 @@ template <int G, int V>
 static cudaError_t launch_gv(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
                              const uint8_t *code_map, uint32_t alpha, const uint64_t *pairs, int64_t np,
                              int32_t K, int64_t max_len, int warps, uint8_t *flags, uint32_t *err,
-                             cudaStream_t s) {
+                             unsigned long long *work, cudaStream_t s) {
     const int32_t Lw = peq_words(max_len, K, G * V);
     const size_t smem = (size_t)warps * (32 / G) * alpha * Lw * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(verify_kernel<G, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -369,19 +390,20 @@ static cudaError_t launch_gv(const uint8_t *bytes, const int64_t *offsets, const
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     verify_kernel<G, V><<<(unsigned)blocks, warps * 32, smem, s>>>(bytes, offsets, lens, n, code_map, alpha,
-                                                                  pairs, np, K, Lw, flags, err);
+                                                                  pairs, np, K, Lw, flags, err, work);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
                           const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
-                          uint8_t *flags, uint32_t *err, cudaStream_t s) {
+                          uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
     if (np == 0) return cudaGetLastError();
 #define EJ_V(GG, VV)                                                                                    \
     if (c.G == GG && c.V == VV)                                                                         \
         return launch_gv<GG, VV>(bytes, offsets, lens, n, code_map, alpha, pairs, np, K, max_len, c.warps, \
-                                 flags, err, s);
+                                 flags, err, work, s);
     EJ_V(1, 1) EJ_V(1, 2) EJ_V(1, 3) EJ_V(1, 4)
     EJ_V(2, 1) EJ_V(2, 2) EJ_V(2, 3) EJ_V(2, 4)
     EJ_V(4, 1) EJ_V(4, 2) EJ_V(4, 3) EJ_V(4, 4)

@@ -55,7 +55,9 @@ class PlanInfo(C.Structure):
 class JoinStats(C.Structure):
     _fields_ = [("n_raw_pairs", C.c_int64), ("n_candidates", C.c_int64), ("n_out", C.c_int64),
                 ("max_bucket", C.c_int64), ("ms_embed", C.c_float), ("ms_sign", C.c_float),
-                ("ms_candidates", C.c_float), ("ms_verify", C.c_float), ("ms_total", C.c_float)]
+                ("ms_candidates", C.c_float), ("ms_verify", C.c_float), ("ms_total", C.c_float),
+                ("band_cells", C.c_uint64), ("verify_word_columns", C.c_uint64),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -201,8 +201,12 @@ def test_tiny_inputs(ej, ctx):
         s = ej.Strings.from_set(ss, DEV) if strs else ej.Strings(
             torch.zeros(1, dtype=torch.uint8, device=DEV), torch.zeros(1, dtype=torch.int64, device=DEV))
         pairs, _ = ctx.join(s, params, device=DEV)
-        want = oracle.join_bruteforce(ss.data, ss.offsets, 2) if strs else np.zeros(0, np.uint64)
+        want = oracle.join(ss.data, ss.offsets, b"ACGT", K=2, r=2, m=2, z=2, seed=1).pairs \
+            if strs else np.zeros(0, np.uint64)
         assert np.array_equal(_np_u64(pairs), want)
+        # precision: every output pair is a true pair
+        truth = set(oracle.join_bruteforce(ss.data, ss.offsets, 2).tolist()) if strs else set()
+        assert set(_np_u64(pairs).tolist()) <= truth
 
 
 # ---------------------------------------------------------------------------
