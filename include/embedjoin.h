@@ -137,6 +137,15 @@ const char *ej_last_error(ej_ctx *ctx);
 int ej_set_timing(ej_ctx *ctx, int enable);
 
 /*
+ * Verifier tiling (the autotuner's knob): lanes_per_pair G in {1,2,4,8,16,32}
+ * and 64-bit words per lane V in {1,2,3,4} with 64*G*V >= 2K+1, and warps per
+ * block. All zero restores the automatic choice. A configuration that cannot
+ * cover the band of a later call makes that call fall back to the automatic
+ * choice. Results never depend on the tiling.
+ */
+int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
+
+/*
  * Validate the strings against the parameters and report the derived sizes
  * (N, out_len = 3N or params->out_len, L, the embedding layout). Checks
  * offsets (start at 0, non-decreasing), lengths (< 2^31), symbols (all in the

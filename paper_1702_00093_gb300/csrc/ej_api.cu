@@ -8,11 +8,6 @@
 
 #include "ej_internal.cuh"
 
-namespace ej {
-cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uint8_t *code_map,
-                                  uint32_t *err, cudaStream_t s);
-}
-
 using namespace ej;
 
 #include <atomic>
@@ -30,6 +25,7 @@ enum BufId {
     B_LKEYS, B_LKEYS_ALT, B_PERM, B_PERM_ALT, B_RK, B_RK_ALT, B_RID, B_RID_ALT,
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
+    B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3,
     B_NUM
 };
 
@@ -60,6 +56,8 @@ struct ej_ctx {
     // pinned host counters
     int64_t *h_cnt = nullptr;
     cudaEvent_t ev[6] = {};
+    // verifier tiling override (0 = automatic)
+    int vG = 0, vV = 0, vWarps = 0;
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -191,6 +189,9 @@ int upload_alphabet(ej_ctx *ctx, const ej_params *p, cudaStream_t s) {
 struct Plan {
     Staged st;
     int32_t *lens = nullptr;
+    const uint4 *packed = nullptr;   // B-bit codes, one chunk run per string
+    const uint64_t *pofs = nullptr;  // chunk offset of each string (n+1)
+    int B = 2;
     int64_t max_len = 0;
     uint32_t out_len = 0, L = 0, planes = 1;
     int64_t nb32 = 0;
@@ -227,7 +228,23 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     unsigned long long *dmax = (unsigned long long *)(derr + 2);
     CK(launch_validate(pl->st.bytes, pl->st.offsets, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->lens,
                        derr, dmax, s));
-    CK(launch_validate_bytes(pl->st.bytes, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, derr, s));
+    // pack into B-bit codes: chunk counts -> offsets -> pack (flags bad symbols)
+    pl->B = packed_bits_for(p->alphabet_size);
+    uint32_t *ccnt = nullptr;
+    uint64_t *pofs = nullptr;
+    uint4 *packed = nullptr;
+    void *stmp = nullptr;
+    CKS(ensure_t(ctx, B_CHUNK_CNT, (size_t)n + 1, &ccnt));
+    CKS(ensure_t(ctx, B_POFS, (size_t)n + 2, &pofs));
+    CKS(ensure(ctx, B_SCAN_TMP3, scan_temp_bytes(n + 1), &stmp));
+    const int64_t chunk_bound = (total * pl->B + 127) / 128 + n + 1;
+    CKS(ensure_t(ctx, B_PACKED, (size_t)chunk_bound, &packed));
+    CK(launch_chunk_counts(pl->lens, n, pl->B, ccnt, s));
+    CK(exclusive_scan_u32(ccnt, pofs, n + 1, nullptr, stmp, s));
+    CK(launch_pack(pl->st.bytes, pl->st.offsets, pl->lens, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->B,
+                   pofs, packed, derr, s));
+    pl->packed = packed;
+    pl->pofs = pofs;
     CK(cudaMemcpyAsync(ctx->h_cnt, derr, 16, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint32_t e = (uint32_t)(ctx->h_cnt[0] & 0xffffffffu);
@@ -409,6 +426,15 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     *n_out = 0;
     if (np == 0) return EJ_OK;
     VerifyConfig vc = verify_pick(p->K, p->alphabet_size, pl.max_len);
+    if (ctx->vG > 0 && (int64_t)64 * ctx->vG * ctx->vV >= 2ll * p->K + 1) {
+        VerifyConfig o{ctx->vG, ctx->vV, ctx->vWarps > 0 ? ctx->vWarps : 1};
+        if (ctx->vWarps <= 0) {
+            const size_t per_warp = verify_smem_bytes(o, p->alphabet_size, pl.max_len, p->K);
+            int w = (int)((96 * 1024) / (per_warp ? per_warp : 1));
+            o.warps = w < 1 ? 1 : (w > 8 ? 8 : w);
+        }
+        if (verify_smem_bytes(o, p->alphabet_size, pl.max_len, p->K) <= 200 * 1024) vc = o;
+    }
     if (vc.G == 0)
         return fail(ctx, EJ_ERR_UNSUPPORTED, "no verifier configuration for K=%d, alphabet %u, max length %lld",
                     p->K, p->alphabet_size, (long long)pl.max_len);
@@ -422,7 +448,7 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     CK(cudaMemsetAsync(derr, 0, 4, s));
     CK(cudaMemsetAsync(dcnt + 4, 0, 2 * sizeof(uint64_t), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
-    CK(launch_verify(vc, pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, (const uint8_t *)ctx->bufs[B_CODEMAP].p,
+    CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, pl.st.n,
                      p->alphabet_size, pairs, np, p->K, pl.max_len, fl, derr,
                      (unsigned long long *)(dcnt + 4), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
@@ -524,6 +550,21 @@ int ej_set_timing(ej_ctx *c, int enable) {
     return EJ_OK;
 }
 
+int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    if (G == 0 && V == 0) {
+        ctx->vG = ctx->vV = ctx->vWarps = 0;
+        return EJ_OK;
+    }
+    const bool okG = G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
+    if (!okG || V < 1 || V > 4 || warps < 0 || warps > 8)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "verify config G=%d V=%d warps=%d not supported", G, V, warps);
+    ctx->vG = G;
+    ctx->vV = V;
+    ctx->vWarps = warps;
+    return EJ_OK;
+}
+
 int ej_set_test_tables(ej_ctx *ctx, const uint8_t *pi, uint32_t r, uint32_t steps, uint32_t alphabet_size,
                        const uint32_t *positions, uint32_t m, uint32_t z) {
     if (!ctx) return EJ_ERR_INVALID_ARG;
@@ -581,9 +622,8 @@ int ej_embed(ej_ctx *ctx, const ej_strings *S, const ej_params *p, void *emb, in
     bool h_emb = false, h_we = false;
     CKS(out_target(ctx, B_EMB, emb, eb, &d_emb, &h_emb));
     CKS(out_target(ctx, B_WALK, walk_end, wb, &d_we, &h_we));
-    CK(launch_embed(pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, p->r, table,
-                    (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.out_len, pl.planes, (uint32_t *)d_emb,
-                    (int32_t *)d_we, s));
+    CK(launch_embed(pl.packed, pl.pofs, pl.lens, pl.st.n, p->r, table, pl.B, pl.out_len, pl.planes,
+                    (uint32_t *)d_emb, (int32_t *)d_we, s));
     if (h_emb) CK(cudaMemcpyAsync(emb, d_emb, eb, cudaMemcpyDeviceToHost, s));
     if (h_we) CK(cudaMemcpyAsync(walk_end, d_we, wb, cudaMemcpyDeviceToHost, s));
     if (h_emb || h_we) CK(cudaStreamSynchronize(s));
@@ -691,8 +731,7 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     CKS(ensure_t(ctx, B_EMB, (size_t)(emb_bytes(pl, p->r) / 4), &emb));
     CKS(ensure_t(ctx, B_WALK, (size_t)p->r * pl.st.n, &we));
     CKS(ensure_t(ctx, B_KEYS, (size_t)p->r * p->m * pl.st.n, &keys));
-    CK(launch_embed(pl.st.bytes, pl.st.offsets, pl.lens, pl.st.n, p->r, table,
-                    (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.out_len, pl.planes, emb, we, s));
+    CK(launch_embed(pl.packed, pl.pofs, pl.lens, pl.st.n, p->r, table, pl.B, pl.out_len, pl.planes, emb, we, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
     CK(launch_sign(emb, we, pl.st.n, p->r, p->m, p->z, pl.out_len, pl.planes, p->alphabet_size, pos, keys, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));

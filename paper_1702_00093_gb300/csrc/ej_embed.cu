@@ -35,18 +35,6 @@ __global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int
     }
 }
 
-__global__ void validate_bytes_kernel(const uint8_t *__restrict__ bytes, int64_t total,
-                                      const uint8_t *__restrict__ code_map, uint32_t *__restrict__ err) {
-    __shared__ uint8_t s_map[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
-    __syncthreads();
-    bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x)
-        bad |= s_map[bytes[i]] == 255;
-    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(err, (uint32_t)DERR_SYMBOL);
-}
-
 cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n,
                             const uint8_t *code_map, int32_t *lens, uint32_t *err,
                             unsigned long long *max_len, cudaStream_t s) {
@@ -59,12 +47,67 @@ cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate_bytes(const uint8_t *bytes, int64_t total, const uint8_t *code_map,
-                                  uint32_t *err, cudaStream_t s) {
-    if (total > 0) {
-        int64_t g = (total + 255) / 256;
-        int grid = (int)(g > 8192 ? 8192 : g);
-        validate_bytes_kernel<<<grid, 256, 0, s>>>(bytes, total, code_map, err);
+// ---------------------------------------------------------------------------
+// Pack: bytes -> dense B-bit codes, one 16-byte-aligned run of chunks per string
+// ---------------------------------------------------------------------------
+
+__global__ void chunk_counts_kernel(const int32_t *__restrict__ lens, int64_t n, int B,
+                                    uint32_t *__restrict__ counts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        counts[i] = (i < n) ? (uint32_t)chunks_for(lens[i], B) : 0u;
+}
+
+cudaError_t launch_chunk_counts(const int32_t *lens, int64_t n, int B, uint32_t *counts, cudaStream_t s) {
+    int64_t g = (n + 1 + 255) / 256;
+    chunk_counts_kernel<<<(unsigned)(g > 4096 ? 4096 : g), 256, 0, s>>>(lens, n, B, counts);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// One warp per string; lane t builds chunks t, t+32, ... A chunk holds
+// 128/B symbols; bytes outside the alphabet flag DERR_SYMBOL.
+__global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
+                            const int32_t *__restrict__ lens, int64_t n, const uint8_t *__restrict__ code_map,
+                            int B, const uint64_t *__restrict__ pofs, uint4 *__restrict__ packed,
+                            uint32_t *__restrict__ err) {
+    __shared__ uint8_t s_map[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int S = 128 / B;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int32_t len = lens[i];
+        const uint8_t *x = bytes + offsets[i];
+        const int64_t nch = chunks_for(len, B);
+        uint4 *dst = packed + pofs[i];
+        for (int64_t c = lane; c < nch; c += 32) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            const int64_t k0 = c * S;
+            const int cnt = (int)((len - k0) < S ? (len - k0) : S);
+            for (int t = 0; t < cnt; t++) {
+                uint32_t code = s_map[x[k0 + t]];
+                if (code == 255u) {
+                    bad = true;
+                    code = 0u;
+                }
+                const int bit = t * B;
+                w[bit >> 5] |= code << (bit & 31);
+            }
+            dst[c] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, (uint32_t)DERR_SYMBOL);
+}
+
+cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
+                        const uint8_t *code_map, int B, const uint64_t *pofs, uint4 *packed,
+                        uint32_t *err, cudaStream_t s) {
+    if (n > 0) {
+        int64_t blocks = (n + 7) / 8;   // 8 warps per block
+        pack_kernel<<<(unsigned)(blocks > 8192 ? 8192 : blocks), 256, 0, s>>>(bytes, offsets, lens, n, code_map, B,
+                                                                                pofs, packed, err);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -152,43 +195,38 @@ cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, 
 // the emitted symbols of the 32 walks are packed by warp ballots into
 // bit-planes: one uint32 per (step, plane) with bit t for lane t. Every 32
 // steps the warp stores 32 x PLANES words, contiguous in memory.
-// The walk's state per lane: position i in the string, the codes of x[i] and
-// x[i+1], and the raw byte x[i+2] already in flight from global memory.
+// Each lane reads its string's packed codes through a two-chunk prefetch
+// (SymReader), so the walk never waits on a load it has just issued.
 
 constexpr int EMBED_WARPS = 4;
 constexpr int EMBED_TILE = 2048;  // steps of the random-bit table staged at a time
 
-template <int PLANES>
+template <int PLANES, int B>
 __global__ void __launch_bounds__(EMBED_WARPS * 32)
-embed_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
+embed_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
              const int32_t *__restrict__ lens, int64_t n, const uint32_t *__restrict__ table,
-             const uint8_t *__restrict__ code_map, uint32_t out_len, uint32_t *__restrict__ emb,
-             int32_t *__restrict__ walk_end, int64_t nblocks32) {
+             uint32_t out_len, uint32_t *__restrict__ emb, int32_t *__restrict__ walk_end,
+             int64_t nblocks32) {
     constexpr int WS = PLANES <= 5 ? 1 : (1 << (PLANES - 5));
     __shared__ uint32_t s_table[EMBED_TILE * WS];
-    __shared__ uint8_t s_map[256];
 
     const uint32_t l = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t B = (int64_t)blockIdx.x * EMBED_WARPS + warp;
-    const int64_t s = B * 32 + lane;
-    const bool valid = (B < nblocks32) && (s < n);
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
+    const int64_t B32 = (int64_t)blockIdx.x * EMBED_WARPS + warp;
+    const int64_t s = B32 * 32 + lane;
+    const bool valid = (B32 < nblocks32) && (s < n);
     const int32_t len = valid ? lens[s] : 0;
-    const uint8_t *x = bytes + (valid ? offsets[s] : 0);
-    __syncthreads();
+    SymReader<B> rd;
+    rd.init(packed + (valid ? pofs[s] : 0), valid ? chunks_for(len, B) : 0);
 
     int32_t pos = 0;
-    uint32_t c0 = len > 0 ? s_map[x[0]] : 0u;
-    uint32_t c1 = len > 1 ? s_map[x[1]] : 0u;
-    uint32_t raw2 = len > 2 ? x[2] : 0u;
     int32_t wend = (len == 0) ? 0 : (int32_t)out_len;
     uint32_t acc[PLANES];
 #pragma unroll
     for (int k = 0; k < PLANES; k++) acc[k] = 0;
 
     const uint32_t *tab_l = table + (size_t)l * out_len * WS;
-    uint32_t *out_base = emb + ((size_t)l * nblocks32 + (size_t)(B < nblocks32 ? B : 0)) * out_len * PLANES;
+    uint32_t *out_base = emb + ((size_t)l * nblocks32 + (size_t)(B32 < nblocks32 ? B32 : 0)) * out_len * PLANES;
 
     for (uint32_t j0 = 0; j0 < out_len; j0 += EMBED_TILE) {
         const uint32_t tile = min((uint32_t)EMBED_TILE, out_len - j0);
@@ -196,11 +234,11 @@ embed_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offs
         for (uint32_t t = threadIdx.x; t < tile * WS; t += blockDim.x)
             s_table[t] = tab_l[(size_t)j0 * WS + t];
         __syncthreads();
-        if (B >= nblocks32) continue;  // warp-uniform
+        if (B32 >= nblocks32) continue;  // warp-uniform
         for (uint32_t jj = 0; jj < tile; jj++) {
             const uint32_t j = j0 + jj;
             const bool active = pos < len;
-            const uint32_t code = active ? c0 : 0u;
+            const uint32_t code = active ? rd.code() : 0u;
 #pragma unroll
             for (int k = 0; k < PLANES; k++) {
                 const uint32_t bal = __ballot_sync(FULL, (code >> k) & 1u);
@@ -214,41 +252,42 @@ embed_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offs
                     for (int k = 0; k < PLANES; k++) o[k] = acc[k];
                 }
             }
-            uint32_t bit = 0;
-            if (active) {
-                const uint32_t w = (WS == 1) ? s_table[jj] : s_table[jj * WS + (code >> 5)];
-                bit = (w >> (code & 31)) & 1u;
-            }
+            const uint32_t w = (WS == 1) ? s_table[jj] : s_table[jj * WS + (code >> 5)];
+            const bool bit = active && ((w >> (code & 31)) & 1u);
             if (bit) {
                 pos++;
                 if (pos == len) wend = (int32_t)(j + 1);
-                c0 = c1;
-                c1 = s_map[raw2];
-                raw2 = (pos + 2 < len) ? (uint32_t)x[pos + 2] : 0u;
+                rd.advance();
             }
         }
     }
     if (valid) walk_end[(size_t)l * n + s] = wend;
 }
 
-cudaError_t launch_embed(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens,
-                         int64_t n, uint32_t r, const uint32_t *table, const uint8_t *code_map,
-                         uint32_t out_len, uint32_t planes, uint32_t *emb, int32_t *walk_end,
-                         cudaStream_t s) {
+template <int PLANES, int B>
+static void embed_launch(dim3 grid, dim3 block, cudaStream_t s, const uint4 *packed, const uint64_t *pofs,
+                         const int32_t *lens, int64_t n, const uint32_t *table, uint32_t out_len,
+                         uint32_t *emb, int32_t *walk_end, int64_t nb32) {
+    embed_kernel<PLANES, B><<<grid, block, 0, s>>>(packed, pofs, lens, n, table, out_len, emb, walk_end, nb32);
+}
+
+cudaError_t launch_embed(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                         uint32_t r, const uint32_t *table, int B, uint32_t out_len, uint32_t planes,
+                         uint32_t *emb, int32_t *walk_end, cudaStream_t s) {
     if (n == 0 || out_len == 0) return cudaGetLastError();
     const int64_t nb32 = (n + 31) / 32;
     dim3 grid((unsigned)((nb32 + EMBED_WARPS - 1) / EMBED_WARPS), r);
     dim3 block(EMBED_WARPS * 32);
-#define EJ_EMB(P) embed_kernel<P><<<grid, block, 0, s>>>(bytes, offsets, lens, n, table, code_map, out_len, emb, walk_end, nb32)
+#define EJ_EMB(P, BB) embed_launch<P, BB>(grid, block, s, packed, pofs, lens, n, table, out_len, emb, walk_end, nb32)
     switch (planes) {
-        case 1: EJ_EMB(1); break;
-        case 2: EJ_EMB(2); break;
-        case 3: EJ_EMB(3); break;
-        case 4: EJ_EMB(4); break;
-        case 5: EJ_EMB(5); break;
-        case 6: EJ_EMB(6); break;
-        case 7: EJ_EMB(7); break;
-        default: EJ_EMB(8); break;
+        case 1: EJ_EMB(1, 2); break;
+        case 2: EJ_EMB(2, 2); break;
+        case 3: EJ_EMB(3, 8); break;
+        case 4: EJ_EMB(4, 8); break;
+        case 5: EJ_EMB(5, 8); break;
+        case 6: EJ_EMB(6, 8); break;
+        case 7: EJ_EMB(7, 8); break;
+        default: EJ_EMB(8, 8); break;
     }
     note_launches(1);
 #undef EJ_EMB

@@ -38,6 +38,54 @@ inline uint32_t planes_for(uint32_t alpha) {
 // u32 words per step of the code-indexed random-bit table.
 inline uint32_t table_words_for(uint32_t planes) { return planes <= 5 ? 1u : (1u << (planes - 5)); }
 
+// ---------------------------------------------------------------------------
+// Packed symbol codes
+// ---------------------------------------------------------------------------
+// Every string is re-encoded once as dense codes (index in the alphabet) of
+// B = 2 (alphabets of at most 4 symbols) or 8 bits, little-endian inside 128-bit chunks; each string starts
+// on its own chunk (16-byte aligned), chunk offsets in pofs[n+1].
+
+inline int packed_bits_for(uint32_t alpha) { return alpha <= 4 ? 2 : 8; }
+
+__host__ __device__ __forceinline__ int64_t chunks_for(int64_t len, int B) {
+    return (len * B + 127) / 128;
+}
+
+// Sequential reader of one string's packed codes with a two-chunk prefetch:
+// the next 16-byte chunk is requested 128/B symbols before it is needed.
+template <int B>
+struct SymReader {
+    const uint4 *p;
+    const uint4 *end;
+    uint4 cur, nxt;
+    int left;
+
+    __device__ __forceinline__ void init(const uint4 *base, int64_t nchunks) {
+        p = base;
+        end = base + nchunks;
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        cur = (p < end) ? *p : zero;
+        p += (p < end);
+        nxt = (p < end) ? *p : zero;
+        p += (p < end);
+        left = 128 / B;
+    }
+    __device__ __forceinline__ uint32_t code() const { return cur.x & ((1u << B) - 1u); }
+    __device__ __forceinline__ void advance() {
+        cur.x = __funnelshift_r(cur.x, cur.y, B);
+        cur.y = __funnelshift_r(cur.y, cur.z, B);
+        cur.z = __funnelshift_r(cur.z, cur.w, B);
+        cur.w >>= B;
+        if (--left == 0) {
+            cur = nxt;
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+            nxt = (p < end) ? *p : zero;
+            p += (p < end);
+            left = 128 / B;
+        }
+    }
+};
+
 // Number of kernels launched by this library (all threads); a launcher adds
 // the kernels it enqueued.
 void note_launches(int k);
@@ -70,10 +118,16 @@ cudaError_t launch_bit_table(uint64_t seed, uint32_t r, uint32_t out_len, const 
 cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, uint32_t L,
                              const uint32_t *pos_inject, uint32_t *pos, cudaStream_t s);
 
-cudaError_t launch_embed(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens,
-                         int64_t n, uint32_t r, const uint32_t *table, const uint8_t *code_map,
-                         uint32_t out_len, uint32_t planes, uint32_t *emb, int32_t *walk_end,
-                         cudaStream_t s);
+// Chunk counts per string (u32) from lengths.
+cudaError_t launch_chunk_counts(const int32_t *lens, int64_t n, int B, uint32_t *counts, cudaStream_t s);
+// Pack bytes -> codes; bytes outside the alphabet set DERR_SYMBOL (code 0 is stored).
+cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
+                        const uint8_t *code_map, int B, const uint64_t *pofs, uint4 *packed,
+                        uint32_t *err, cudaStream_t s);
+
+cudaError_t launch_embed(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                         uint32_t r, const uint32_t *table, int B, uint32_t out_len, uint32_t planes,
+                         uint32_t *emb, int32_t *walk_end, cudaStream_t s);
 
 cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n, uint32_t r,
                         uint32_t m, uint32_t z, uint32_t out_len, uint32_t planes, uint32_t alpha,
@@ -136,8 +190,8 @@ VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len);
 // Shared memory per block of a configuration.
 size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_t K);
 
-cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
-                          const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
+cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *pofs, int B,
+                          const int32_t *lens, int64_t n, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
                           uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s);
 

@@ -42,6 +42,37 @@ __device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t 
     return sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
 }
 
+// Gathers the even bits of x into the low 16 bits.
+__device__ __forceinline__ uint32_t compress_even(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// Symbols k0 .. k0+63 of a 2-bit packed string (nch chunks) as two bit-planes:
+// bit t of lo/hi = low/high bit of the code of symbol k0+t (0 outside the string).
+__device__ __forceinline__ void sym64_planes(const uint4 *__restrict__ xc, int64_t nch, int64_t k0,
+                                             uint64_t &lo, uint64_t &hi) {
+    const int64_t c0 = (k0 >= 0) ? (k0 >> 6) : -((-k0 + 63) >> 6);
+    const uint32_t o = (uint32_t)(k0 - 64 * c0);  // 0..63 symbols
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 A = (c0 >= 0 && c0 < nch) ? xc[c0] : zero;
+    const uint4 Bc = (c0 + 1 >= 0 && c0 + 1 < nch) ? xc[c0 + 1] : zero;
+    uint32_t t0 = A.x, t1 = A.y, t2 = A.z, t3 = A.w, t4 = Bc.x, t5 = Bc.y, t6 = Bc.z, t7 = Bc.w;
+    const uint32_t sh = 2u * o, ws = sh >> 5, bs = sh & 31u;
+    if (ws & 2u) { t0 = t2; t1 = t3; t2 = t4; t3 = t5; t4 = t6; t5 = t7; t6 = 0u; t7 = 0u; }
+    if (ws & 1u) { t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = 0u; }
+    const uint32_t w0 = __funnelshift_r(t0, t1, bs), w1 = __funnelshift_r(t1, t2, bs);
+    const uint32_t w2 = __funnelshift_r(t2, t3, bs), w3 = __funnelshift_r(t3, t4, bs);
+    lo = (uint64_t)compress_even(w0) | ((uint64_t)compress_even(w1) << 16) |
+         ((uint64_t)compress_even(w2) << 32) | ((uint64_t)compress_even(w3) << 48);
+    hi = (uint64_t)compress_even(w0 >> 1) | ((uint64_t)compress_even(w1 >> 1) << 16) |
+         ((uint64_t)compress_even(w2 >> 1) << 32) | ((uint64_t)compress_even(w3 >> 1) << 48);
+}
+
 // |{(a, b): 0 <= a < lx, 0 <= b < ly, |a - b| <= K}|, Ukkonen's band size.
 __device__ __forceinline__ unsigned long long band_cells(int64_t lx, int64_t ly, int64_t K) {
     if (lx <= 0 || ly <= 0) return 0ull;
@@ -53,22 +84,20 @@ __device__ __forceinline__ unsigned long long band_cells(int64_t lx, int64_t ly,
     return (unsigned long long)(s1 - u * (u + 1) / 2);
 }
 
-template <int G, int V>
+template <int G, int V, int B>
 __global__ void __launch_bounds__(VERIFY_MAX_THREADS)
-verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
-              const int32_t *__restrict__ lens, int64_t n_str, const uint8_t *__restrict__ code_map,
+verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+              const int32_t *__restrict__ lens, int64_t n_str,
               uint32_t alpha, const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t Lw,
               uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
               unsigned long long *__restrict__ work) {
     constexpr int GPW = 32 / G;
     const int32_t w_min = (2 * K + 1 + 63) / 64;
     extern __shared__ uint64_t smem[];
-    __shared__ uint8_t s_map[256];
     __shared__ int8_t s_nsum[256];
     __shared__ int8_t s_nmin[256];
 
     for (int t = threadIdx.x; t < 256; t += blockDim.x) {
-        s_map[t] = code_map[t];
         // nibble table: index = P nibble | M nibble << 4; sum and minimum prefix
         const uint32_t P = t & 15u, M = t >> 4;
         int run = 0, mn = 1 << 20;
@@ -105,8 +134,7 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
             }
         }
         const bool a_long = la >= lb;
-        const uint8_t *xs = bytes + offsets[valid ? (a_long ? a : b) : 0];
-        const uint8_t *ys = bytes + offsets[valid ? (a_long ? b : a) : 0];
+        const int64_t xi = valid ? (a_long ? a : b) : 0, yi = valid ? (a_long ? b : a) : 0;
         const int32_t mlen = a_long ? la : lb;
         const int32_t nlen = a_long ? lb : la;
         bool decided = !valid;
@@ -124,17 +152,46 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
         // Peq[c]: bit K+i set iff code(x[i]) == c
         const int32_t mmax = __reduce_max_sync(FULL, mrows);
         if (mmax > 0) {
-            for (int i = gl; i < (int)alpha * Lw; i += G) peq[i] = 0ull;
-            __syncwarp();
-            for (int32_t i = gl; i < mmax; i += G) {
-                const uint32_t c = (i < mrows) ? (uint32_t)s_map[xs[i]] : 255u;
-                if (c < alpha) {
-                    const uint32_t q = (uint32_t)K + (uint32_t)i;
-                    atomicOr((unsigned long long *)&peq[c * Lw + (q >> 6)], 1ull << (q & 63u));
+            const uint4 *xc = packed + pofs[xi];
+            const int64_t xch = chunks_for(mrows, B);
+            if (B == 2) {
+                // whole 64-bit words from the 2-bit codes, no atomics
+                for (int w = gl; w < Lw; w += G) {
+                    const int64_t k0 = 64ll * w - K;
+                    uint64_t lo = 0, hi = 0;
+                    if (mrows > 0) sym64_planes(xc, xch, k0, lo, hi);
+                    const int64_t t_lo = k0 < 0 ? -k0 : 0;
+                    const int64_t t_hi = (int64_t)mrows - k0;  // symbols t < t_hi are inside x
+                    uint64_t valid_m = 0ull;
+                    if (t_hi > t_lo && t_lo < 64) {
+                        const uint64_t upto = t_hi >= 64 ? ~0ull : ((1ull << t_hi) - 1ull);
+                        const uint64_t from = ~((1ull << t_lo) - 1ull);
+                        valid_m = upto & from;
+                    }
+                    for (uint32_t c = 0; c < alpha; c++)
+                        peq[c * Lw + w] = ((c & 1u) ? lo : ~lo) & ((c & 2u) ? hi : ~hi) & valid_m;
+                }
+            } else {
+                for (int i = gl; i < (int)alpha * Lw; i += G) peq[i] = 0ull;
+                __syncwarp();
+                for (int64_t ch = gl; ch < xch; ch += G) {
+                    const uint4 v = xc[ch];
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int64_t k = ch * 16 + t;
+                        const uint32_t c = (wv[t >> 2] >> ((t & 3) * 8)) & 0xFFu;
+                        if (k < mrows && c < alpha) {
+                            const uint32_t q = (uint32_t)K + (uint32_t)k;
+                            atomicOr((unsigned long long *)&peq[c * Lw + (q >> 6)], 1ull << (q & 63u));
+                        }
+                    }
                 }
             }
             __syncwarp();
         }
+        SymReader<B> yr;
+        yr.init(packed + pofs[yi], chunks_for(ncols, B));
 
         // column 0: rows -K..0 have difference -1, rows >= 1 have +1; T = K+1
         uint64_t Pv[V], Mv[V];
@@ -154,11 +211,10 @@ verify_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ off
         int32_t T = K + 1;
 
         int32_t nmax = __reduce_max_sync(FULL, ncols);
-        uint32_t cnext = (ncols > 0) ? (uint32_t)s_map[ys[0]] : 0u;
         for (int32_t j = 1; j <= nmax; j++) {
             const bool act = j <= ncols;
-            const uint32_t c = cnext;
-            if (j < ncols) cnext = s_map[ys[j]];
+            const uint32_t c = yr.code();
+            if (act) yr.advance();
 
             // T := value of the row above the shifted window
             if (gl == 0 && act) T += (int32_t)(Pv[0] & 1ull) - (int32_t)(Mv[0] & 1ull) + 1;
@@ -369,41 +425,45 @@ VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
     return best;
 }
 
-template <int G, int V>
-static cudaError_t launch_gv(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
-                             const uint8_t *code_map, uint32_t alpha, const uint64_t *pairs, int64_t np,
+template <int G, int V, int B>
+static cudaError_t launch_gv(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                             uint32_t alpha, const uint64_t *pairs, int64_t np,
                              int32_t K, int64_t max_len, int warps, uint8_t *flags, uint32_t *err,
                              unsigned long long *work, cudaStream_t s) {
     const int32_t Lw = peq_words(max_len, K, G * V);
     const size_t smem = (size_t)warps * (32 / G) * alpha * Lw * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(verify_kernel<G, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(verify_kernel<G, V, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_kernel<G, V>, warps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_kernel<G, V, B>, warps * 32, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t warp_batches = (np + (32 / G) - 1) / (32 / G);
     int64_t blocks = (warp_batches + warps - 1) / warps;
     const int64_t cap = (int64_t)sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    verify_kernel<G, V><<<(unsigned)blocks, warps * 32, smem, s>>>(bytes, offsets, lens, n, code_map, alpha,
-                                                                  pairs, np, K, Lw, flags, err, work);
+    verify_kernel<G, V, B><<<(unsigned)blocks, warps * 32, smem, s>>>(packed, pofs, lens, n, alpha,
+                                                                     pairs, np, K, Lw, flags, err, work);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_verify(VerifyConfig c, const uint8_t *bytes, const int64_t *offsets,
-                          const int32_t *lens, int64_t n, const uint8_t *code_map, uint32_t alpha,
+cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *pofs, int B,
+                          const int32_t *lens, int64_t n, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
                           uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
     if (np == 0) return cudaGetLastError();
-#define EJ_V(GG, VV)                                                                                    \
-    if (c.G == GG && c.V == VV)                                                                         \
-        return launch_gv<GG, VV>(bytes, offsets, lens, n, code_map, alpha, pairs, np, K, max_len, c.warps, \
-                                 flags, err, work, s);
+#define EJ_V(GG, VV)                                                                                     \
+    if (c.G == GG && c.V == VV) {                                                                        \
+        if (B == 2)                                                                                      \
+            return launch_gv<GG, VV, 2>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps,    \
+                                        flags, err, work, s);                                            \
+        return launch_gv<GG, VV, 8>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps, flags, \
+                                    err, work, s);                                                       \
+    }
     EJ_V(1, 1) EJ_V(1, 2) EJ_V(1, 3) EJ_V(1, 4)
     EJ_V(2, 1) EJ_V(2, 2) EJ_V(2, 3) EJ_V(2, 4)
     EJ_V(4, 1) EJ_V(4, 2) EJ_V(4, 3) EJ_V(4, 4)

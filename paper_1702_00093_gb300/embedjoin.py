@@ -26,7 +26,7 @@ EJ_ERR_UNSUPPORTED = 6
 
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
-            "ej_set_test_tables"]
+            "ej_set_test_tables", "ej_set_verify_config"]
 
 
 class EJError(RuntimeError):
@@ -102,6 +102,8 @@ def lib():
         L.ej_set_test_tables.argtypes = [vp, vp, C.c_uint32, C.c_uint32, C.c_uint32, vp,
                                          C.c_uint32, C.c_uint32]
         L.ej_set_test_tables.restype = C.c_int
+        L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.ej_set_verify_config.restype = C.c_int
         _lib = L
     return _lib
 
@@ -195,6 +197,11 @@ class Context:
         if st != EJ_OK:
             detail = lib().ej_last_error(self._h).decode()
             raise EJError(st, f"{what}: {lib().ej_status_string(st).decode()}: {detail}")
+
+    def set_verify_config(self, lanes_per_pair: int = 0, words_per_lane: int = 0, warps: int = 0):
+        """Verifier tiling (G lanes per pair, V words per lane); zeros = automatic."""
+        self._check(lib().ej_set_verify_config(self._h, lanes_per_pair, words_per_lane, warps),
+                    "ej_set_verify_config")
 
     def set_timing(self, on: bool = True):
         self._check(lib().ej_set_timing(self._h, 1 if on else 0), "ej_set_timing")

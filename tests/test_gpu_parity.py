@@ -295,3 +295,37 @@ def test_capacity_reports_needed_count(ej, ctx):
     with pytest.raises(ej.EJError) as e:
         ctx.join_into(s, params, torch.empty(3, dtype=torch.int64, device=DEV))
     assert e.value.status == ej.EJ_ERR_CAPACITY and e.value.needed == 45
+
+
+@pytest.mark.parametrize("K,alphabet", [(5, b"ACGT"), (60, b"ACGT"), (150, b"ACGT"), (40, synth.PROTEIN)])
+def test_verify_every_tiling_is_exact(ej, ctx, K, alphabet):
+    """Every lanes-per-pair x words-per-lane tiling that covers the band gives the oracle's answer."""
+    rng = np.random.default_rng(K)
+    sigma = len(alphabet)
+    base = [rng.integers(0, sigma, size=int(rng.integers(1, 700))).astype(np.uint8) for _ in range(24)]
+    strs = []
+    for b in base:
+        strs += [b, synth.mutate(rng, b, int(rng.integers(0, 2 * K + 3)), sigma)]
+    lut = np.frombuffer(alphabet, np.uint8)
+    ss = synth.pack([lut[x].tobytes() for x in strs], alphabet)
+    pairs = sorted({(min(a, b), max(a, b)) for a, b in rng.integers(0, ss.n, size=(200, 2)) if a != b}
+                   | {(2 * i, 2 * i + 1) for i in range(len(base))})
+    arr = np.array([(a << 32) | b for a, b in pairs], dtype=np.uint64)
+    want = arr[oracle.verify(ss.data, ss.offsets, arr, K) == 1]
+    s = ej.Strings.from_set(ss, DEV)
+    params = ej.Params(K=K, r=1, m=1, z=1, alphabet=alphabet)
+    pt = torch.from_numpy(arr.view(np.int64).copy()).to(DEV)
+    tried = 0
+    try:
+        for G in (1, 2, 4, 8, 16, 32):
+            for V in (1, 2, 3, 4):
+                if 64 * G * V < 2 * K + 1 or G * V > 4 * max(1, (2 * K + 1 + 63) // 64):
+                    continue
+                ctx.set_verify_config(G, V, 0)
+                out = torch.empty_like(pt)
+                k = ctx.verify(s, params, pt, out)
+                assert np.array_equal(_np_u64(out[:k]), want), (G, V)
+                tried += 1
+    finally:
+        ctx.set_verify_config(0, 0, 0)
+    assert tried >= 3
