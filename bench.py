@@ -282,8 +282,8 @@ def main():
         rows = [s for k, _, s in stats if k == K]
         per_k[str(K)] = {
             "join_ms": statistics.mean(s["ms_total"] for s in rows),
-            "embed_ms": statistics.mean(s["ms_embed"] for s in rows),
-            "sign_ms": statistics.mean(s["ms_sign"] for s in rows),
+            "prepare_ms": statistics.mean(s["ms_prepare"] for s in rows),
+            "embed_sign_ms": statistics.mean(s["ms_embed_sign"] for s in rows),
             "candidates_ms": statistics.mean(s["ms_candidates"] for s in rows),
             "verify_ms": statistics.mean(s["ms_verify"] for s in rows),
             "candidates": rows[0]["n_candidates"], "raw_pairs": rows[0]["n_raw_pairs"],

@@ -106,11 +106,12 @@ typedef struct {
     int64_t n_candidates;    /* unique candidate pairs (verified) */
     int64_t n_out;           /* output pairs */
     int64_t max_bucket;      /* largest bucket (run of equal keys in one table) */
-    float ms_embed;          /* stage times, CUDA events on `stream` (only with */
-    float ms_sign;           /* ej_set_timing(ctx, 1); else 0)                  */
-    float ms_candidates;
-    float ms_verify;
-    float ms_total;
+    /* stage times in ms from CUDA events on `stream` (only with ej_set_timing(ctx, 1)) */
+    float ms_prepare;        /* validation, packing, random tables, positions */
+    float ms_embed_sign;     /* CGK walks and signature keys */
+    float ms_candidates;     /* sort, bucket windows, pair sort, dedup */
+    float ms_verify;         /* the verification kernel alone */
+    float ms_total;          /* the whole call */
     uint64_t band_cells;     /* sum over candidates of the Ukkonen band size
                                 |{(a,b): a<|x|, b<|y|, |a-b|<=K}| (work of the
                                 verification, counted algorithmically) */
@@ -138,8 +139,8 @@ int ej_set_timing(ej_ctx *ctx, int enable);
 
 /*
  * Verifier tiling (the autotuner's knob): lanes_per_pair G in {1,2,4,8,16,32}
- * and 64-bit words per lane V in {1,2,3,4} with 64*G*V >= 2K+1, and warps per
- * block. All zero restores the automatic choice. A configuration that cannot
+ * and 64-bit words per lane V (1..8 when G = 1, else 1..4) with 64*G*V >= 2K+1,
+ * and warps per block (0 = automatic; at most 4 when G = 1). All zero restores the automatic choice. A configuration that cannot
  * cover the band of a later call makes that call fall back to the automatic
  * choice. Results never depend on the tiling.
  */
@@ -184,6 +185,16 @@ int ej_embed(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, vo
  */
 int ej_sign(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, const void *emb,
             const int32_t *walk_end, uint64_t *keys, void *stream);
+
+/*
+ * ej_embed followed by ej_sign without materialising the embedding: the same
+ * keys (bit-identical), computed by walking each string once per embedding and
+ * reading only the m*z sampled steps (the "only compute the sampled bits"
+ * remark of Section 4). keys: [r*m][n] uint64 as for ej_sign. This is the path
+ * ej_join uses.
+ */
+int ej_embed_sign(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, uint64_t *keys,
+                  void *stream);
 
 /*
  * Candidate pairs (Algorithm 3, filtering stage): all i < j such that some

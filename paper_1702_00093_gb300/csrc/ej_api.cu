@@ -25,7 +25,7 @@ enum BufId {
     B_LKEYS, B_LKEYS_ALT, B_PERM, B_PERM_ALT, B_RK, B_RK_ALT, B_RID, B_RID_ALT,
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
-    B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3,
+    B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
     B_NUM
 };
 
@@ -301,6 +301,61 @@ int make_tables(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint32_t **tabl
     return EJ_OK;
 }
 
+// Keys [r*m][n] for the plan's strings into `keys` (device): the fused walk
+// when its tables fit in shared memory, else embed (prefix of length L) + sign.
+int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cudaStream_t s) {
+    const int64_t n = pl.st.n;
+    if (n == 0) return EJ_OK;
+    uint32_t *pos = nullptr;
+    CKS(ensure_t(ctx, B_POS, (size_t)p->r * p->m * p->z, &pos));
+    const uint8_t *pi_dev = nullptr;
+    if (ctx->pi.size()) {
+        uint8_t *d = nullptr;
+        CKS(ensure_t(ctx, B_PI, ctx->pi.size(), &d));
+        CK(cudaMemcpyAsync(d, ctx->pi.data(), ctx->pi.size(), cudaMemcpyHostToDevice, s));
+        pi_dev = d;
+    }
+    const uint32_t *pos_inj = nullptr;
+    if (ctx->posinj.size()) {
+        uint32_t *d = nullptr;
+        CKS(ensure_t(ctx, B_POSINJ, ctx->posinj.size(), &d));
+        CK(cudaMemcpyAsync(d, ctx->posinj.data(), ctx->posinj.size() * 4, cudaMemcpyHostToDevice, s));
+        pos_inj = d;
+    }
+    CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_inj, pos, s));
+    if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z) > 0) {
+        uint32_t *tsym = nullptr, *spos = nullptr, *stag = nullptr;
+        CKS(ensure_t(ctx, B_TSYM, (size_t)p->r * p->alphabet_size * (pl.L / 32 + 1), &tsym));
+        CKS(ensure_t(ctx, B_SPOS, (size_t)p->r * p->m * p->z, &spos));
+        CKS(ensure_t(ctx, B_STAG, (size_t)p->r * p->m * p->z, &stag));
+        CK(launch_symbol_table(p->seed, p->r, pl.L, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,
+                               pi_dev, ctx->pi_steps, tsym, s));
+        CK(launch_sort_samples(pos, p->r, p->m, p->z, spos, stag, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+        CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
+                             tsym, spos, stag, keys, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    } else {
+        // materialise only the prefix [0, L) of every embedding
+        Plan pl2 = pl;
+        pl2.out_len = pl.L;
+        const uint32_t words = table_words_for(pl.planes);
+        uint32_t *table = nullptr, *emb = nullptr;
+        int32_t *we = nullptr;
+        CKS(ensure_t(ctx, B_TABLE, (size_t)p->r * pl2.out_len * words, &table));
+        CKS(ensure_t(ctx, B_EMB, (size_t)(emb_bytes(pl2, p->r) / 4), &emb));
+        CKS(ensure_t(ctx, B_WALK, (size_t)p->r * n, &we));
+        CK(launch_bit_table(p->seed, p->r, pl2.out_len, (const uint8_t *)ctx->bufs[B_ALPHABET].p,
+                            p->alphabet_size, words, pi_dev, ctx->pi_steps, table, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+        CK(launch_embed(pl.packed, pl.pofs, pl.lens, n, p->r, table, pl.B, pl2.out_len, pl.planes, emb, we, s));
+        CK(launch_sign(emb, we, n, p->r, p->m, p->z, pl2.out_len, pl.planes, p->alphabet_size, pos, keys, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    }
+    if (pi_dev || pos_inj) CK(cudaStreamSynchronize(s));
+    return EJ_OK;
+}
+
 int key_bits(const ej_params *p) {
     unsigned __int128 v = 1;
     for (uint32_t q = 0; q < p->z; q++) v *= (unsigned __int128)(p->alphabet_size + 1);
@@ -429,10 +484,13 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     if (ctx->vG > 0 && (int64_t)64 * ctx->vG * ctx->vV >= 2ll * p->K + 1) {
         VerifyConfig o{ctx->vG, ctx->vV, ctx->vWarps > 0 ? ctx->vWarps : 1};
         if (ctx->vWarps <= 0) {
-            const size_t per_warp = verify_smem_bytes(o, p->alphabet_size, pl.max_len, p->K);
+            VerifyConfig one{o.G, o.V, 1};
+            const size_t per_warp = verify_smem_bytes(one, p->alphabet_size, pl.max_len, p->K);
             int w = (int)((96 * 1024) / (per_warp ? per_warp : 1));
-            o.warps = w < 1 ? 1 : (w > 8 ? 8 : w);
+            const int wmax = o.G == 1 ? 4 : 8;
+            o.warps = w < 1 ? 1 : (w > wmax ? wmax : w);
         }
+        if (o.G == 1 && o.warps > 4) o.warps = 4;
         if (verify_smem_bytes(o, p->alphabet_size, pl.max_len, p->K) <= 200 * 1024) vc = o;
     }
     if (vc.G == 0)
@@ -557,7 +615,7 @@ int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
         return EJ_OK;
     }
     const bool okG = G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
-    if (!okG || V < 1 || V > 4 || warps < 0 || warps > 8)
+    if (!okG || V < 1 || V > (G == 1 ? 8 : 4) || warps < 0 || warps > 8)
         return fail(ctx, EJ_ERR_INVALID_ARG, "verify config G=%d V=%d warps=%d not supported", G, V, warps);
     ctx->vG = G;
     ctx->vV = V;
@@ -658,6 +716,26 @@ int ej_sign(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const void *em
     return EJ_OK;
 }
 
+int ej_embed_sign(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *keys, void *stream) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    if (pl.st.n == 0) return EJ_OK;
+    if (!keys) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL keys");
+    const size_t kb = (size_t)p->r * p->m * pl.st.n * sizeof(uint64_t);
+    void *d_keys = nullptr;
+    bool h_keys = false;
+    CKS(out_target(ctx, B_KEYS, keys, kb, &d_keys, &h_keys));
+    CKS(keys_dev(ctx, p, pl, (uint64_t *)d_keys, s));
+    if (h_keys) {
+        CK(cudaMemcpyAsync(keys, d_keys, kb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return EJ_OK;
+}
+
 int ej_lsh_candidates(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const uint64_t *keys,
                       uint64_t *pairs, int64_t capacity, int64_t *n_pairs, int64_t *stats_max_bucket,
                       void *stream) {
@@ -723,18 +801,9 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     Plan pl;
     CKS(make_plan(ctx, S, p, true, &pl, s));
     if (pl.st.n < 2) return EJ_OK;
-    uint32_t *table = nullptr, *pos = nullptr;
-    CKS(make_tables(ctx, p, pl, &table, &pos, s));
-    uint32_t *emb = nullptr;
-    int32_t *we = nullptr;
     uint64_t *keys = nullptr;
-    CKS(ensure_t(ctx, B_EMB, (size_t)(emb_bytes(pl, p->r) / 4), &emb));
-    CKS(ensure_t(ctx, B_WALK, (size_t)p->r * pl.st.n, &we));
     CKS(ensure_t(ctx, B_KEYS, (size_t)p->r * p->m * pl.st.n, &keys));
-    CK(launch_embed(pl.packed, pl.pofs, pl.lens, pl.st.n, p->r, table, pl.B, pl.out_len, pl.planes, emb, we, s));
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
-    CK(launch_sign(emb, we, pl.st.n, p->r, p->m, p->z, pl.out_len, pl.planes, p->alphabet_size, pos, keys, s));
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    CKS(keys_dev(ctx, p, pl, keys, s));
     uint64_t *cand = nullptr;
     int64_t nc = 0, raw = 0, mb = 0;
     CKS(candidates_dev(ctx, pl, p, keys, &cand, &nc, &raw, &mb, s));
@@ -765,8 +834,8 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
         stats->verify_word_columns = work[1];
         stats->kernel_launches = launches_so_far() - launches0;
         if (ctx->timing) {
-            cudaEventElapsedTime(&stats->ms_embed, ctx->ev[0], ctx->ev[1]);
-            cudaEventElapsedTime(&stats->ms_sign, ctx->ev[1], ctx->ev[2]);
+            cudaEventElapsedTime(&stats->ms_prepare, ctx->ev[0], ctx->ev[1]);
+            cudaEventElapsedTime(&stats->ms_embed_sign, ctx->ev[1], ctx->ev[2]);
             cudaEventElapsedTime(&stats->ms_candidates, ctx->ev[2], ctx->ev[3]);
             if (nc > 0) cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
             cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[5]);

@@ -355,4 +355,168 @@ cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fused embed + sign: only the sampled steps of each walk are produced
+// ---------------------------------------------------------------------------
+//
+// Algorithm 1 emits x[i] from the step a_i at which the walk arrives at i up to
+// and including the first step j >= a_i with pi_j(x[i]) = 1; so
+// a_{i+1} = next1_{x[i]}(a_i) + 1. With one step bitmap per symbol, next1 is a
+// find-first-set, one per input character instead of work per step. The m*z
+// sampled steps of embedding l (Thm. 1 with AND amplification) are visited in
+// step order; a sample at step p < a_{i+1} reads x[i], a sample at or after the
+// end of the walk reads bottom. Each sample adds c * (alpha+1)^q to the key of
+// its function f, kept in shared memory per thread, so the embedded string is
+// never written.
+
+__global__ void symbol_table_kernel(uint64_t base, uint32_t r, uint32_t L, const uint8_t *__restrict__ alphabet,
+                                    uint32_t alpha, const uint8_t *__restrict__ pi, uint32_t inject_steps,
+                                    uint32_t *__restrict__ tsym) {
+    const uint32_t LW = L / 32 + 1;
+    const uint64_t total = (uint64_t)r * alpha * LW;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(idx % LW);
+        const uint32_t c = (uint32_t)((idx / LW) % alpha);
+        const uint32_t l = (uint32_t)(idx / ((uint64_t)LW * alpha));
+        uint32_t word = 0;
+        for (uint32_t b = 0; b < 32; b++) {
+            const uint32_t j = 32 * w + b;
+            uint32_t bit;
+            if (j >= L) bit = 1u;  // sentinel: the search never runs past the table
+            else if (pi) bit = (j < inject_steps) ? (pi[((uint64_t)l * inject_steps + j) * alpha + c] & 1u) : 0u;
+            else bit = (uint32_t)(mix64(base ^ walk_counter(l, j, alphabet[c])) >> 63);
+            word |= bit << b;
+        }
+        tsym[idx] = word;
+    }
+}
+
+cudaError_t launch_symbol_table(uint64_t seed, uint32_t r, uint32_t L, const uint8_t *alphabet_dev,
+                                uint32_t alpha, const uint8_t *pi_inject, uint32_t inject_steps,
+                                uint32_t *tsym, cudaStream_t s) {
+    const uint64_t total = (uint64_t)r * alpha * (L / 32 + 1);
+    uint64_t g = (total + 255) / 256;
+    symbol_table_kernel<<<(unsigned)(g > 4096 ? 4096 : (g ? g : 1)), 256, 0, s>>>(
+        mix64(seed), r, L, alphabet_dev, alpha, pi_inject, inject_steps, tsym);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// One block per embedding: rank every sample by (step, index).
+__global__ void sort_samples_kernel(const uint32_t *__restrict__ pos, uint32_t m, uint32_t z,
+                                    uint32_t *__restrict__ spos, uint32_t *__restrict__ stag) {
+    const uint32_t l = blockIdx.x, M = m * z;
+    const uint32_t *P = pos + (size_t)l * M;
+    for (uint32_t i = threadIdx.x; i < M; i += blockDim.x) {
+        const uint32_t pi_ = P[i];
+        uint32_t rank = 0;
+        for (uint32_t k = 0; k < M; k++) {
+            const uint32_t pk = P[k];
+            rank += (pk < pi_) || (pk == pi_ && k < i);
+        }
+        spos[(size_t)l * M + rank] = pi_;
+        stag[(size_t)l * M + rank] = ((i / z) << 16) | (i % z);
+    }
+}
+
+cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uint32_t z, uint32_t *spos,
+                                uint32_t *stag, cudaStream_t s) {
+    sort_samples_kernel<<<r, 256, 0, s>>>(pos, m, z, spos, stag);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+constexpr int ES_THREADS = 128;
+
+size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
+    const size_t M = (size_t)m * z;
+    if (M > 16384 || z > 65535 || m > 65535) return 0;
+    const size_t bytes = (size_t)alpha * (L / 32 + 1) * 4 + M * 8 + (size_t)z * 8 + (size_t)m * ES_THREADS * 8;
+    return bytes <= 200 * 1024 ? bytes : 0;
+}
+
+template <int B>
+__global__ void __launch_bounds__(ES_THREADS)
+embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+                  const int32_t *__restrict__ lens, int64_t n, uint32_t m, uint32_t z, uint32_t L,
+                  uint32_t alpha, const uint32_t *__restrict__ tsym, const uint32_t *__restrict__ spos,
+                  const uint32_t *__restrict__ stag, uint64_t *__restrict__ keys) {
+    extern __shared__ uint64_t es_smem[];
+    const uint32_t l = blockIdx.y, M = m * z, LW = L / 32 + 1;
+    uint64_t *s_key = es_smem;                              // [m][ES_THREADS]
+    uint64_t *s_pow = s_key + (size_t)m * ES_THREADS;        // [z]
+    uint32_t *s_pos = (uint32_t *)(s_pow + z);               // [M]
+    uint32_t *s_tag = s_pos + M;                             // [M]
+    uint32_t *s_tab = s_tag + M;                             // [alpha][LW]
+    for (uint32_t i = threadIdx.x; i < M; i += blockDim.x) {
+        s_pos[i] = spos[(size_t)l * M + i];
+        s_tag[i] = stag[(size_t)l * M + i];
+    }
+    for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
+    if (threadIdx.x == 0) {
+        uint64_t p = 1;
+        for (uint32_t q = 0; q < z; q++) {
+            s_pow[q] = p;
+            p *= (uint64_t)alpha + 1;
+        }
+    }
+    for (uint32_t f = 0; f < m; f++) s_key[(size_t)f * ES_THREADS + threadIdx.x] = 0ull;
+    __syncthreads();
+
+    const int64_t s = (int64_t)blockIdx.x * ES_THREADS + threadIdx.x;
+    const int32_t len = s < n ? lens[s] : 0;
+    SymReader<B> rd;
+    rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
+    uint64_t *my = s_key + threadIdx.x;
+    uint32_t k = 0;          // next sample (in step order)
+    uint32_t a = 0;          // step at which the walk arrives at x[i]
+    int32_t i = 0;
+    while (k < M && i < len) {
+        const uint32_t c = rd.code();
+        const uint32_t *row = s_tab + c * LW;
+        uint32_t aa = a;
+        uint32_t w = row[aa >> 5] >> (aa & 31u);
+        while (w == 0u) {    // ends at the sentinel bits (steps >= L)
+            aa = (aa | 31u) + 1u;
+            w = row[aa >> 5];
+        }
+        const uint32_t a_next = aa + (uint32_t)__ffs((int)w);   // next1 + 1
+        while (k < M && s_pos[k] < a_next) {
+            const uint32_t tag = s_tag[k];
+            my[(size_t)(tag >> 16) * ES_THREADS] += (uint64_t)c * s_pow[tag & 0xFFFFu];
+            k++;
+        }
+        a = a_next;
+        i++;
+        rd.advance();
+    }
+    // walk finished before the last sample: the rest read bottom
+    for (; k < M; k++) {
+        const uint32_t tag = s_tag[k];
+        my[(size_t)(tag >> 16) * ES_THREADS] += (uint64_t)alpha * s_pow[tag & 0xFFFFu];
+    }
+    if (s < n)
+        for (uint32_t f = 0; f < m; f++) keys[((size_t)l * m + f) * n + s] = my[(size_t)f * ES_THREADS];
+}
+
+cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                              uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
+                              const uint32_t *tsym, const uint32_t *spos, const uint32_t *stag,
+                              uint64_t *keys, cudaStream_t s) {
+    if (n == 0) return cudaGetLastError();
+    const size_t smem = embed_sign_smem(alpha, L, m, z);
+    if (smem == 0) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((n + ES_THREADS - 1) / ES_THREADS), r);
+    if (B == 2) {
+        cudaFuncSetAttribute(embed_sign_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        embed_sign_kernel<2><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym, spos, stag, keys);
+    } else {
+        cudaFuncSetAttribute(embed_sign_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        embed_sign_kernel<8><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym, spos, stag, keys);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace ej

@@ -133,6 +133,22 @@ cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n,
                         uint32_t m, uint32_t z, uint32_t out_len, uint32_t planes, uint32_t alpha,
                         const uint32_t *pos, uint64_t *keys, cudaStream_t s);
 
+// Fused embed + sign (arrival form of Alg. 1 restricted to the sampled steps).
+// Per-symbol step bitmaps [r][alpha][LW]: bit b of word w = pi_{32w+b}(alphabet[c])
+// for steps < L, 1 for steps >= L (sentinel); LW = L/32 + 1.
+cudaError_t launch_symbol_table(uint64_t seed, uint32_t r, uint32_t L, const uint8_t *alphabet_dev,
+                                uint32_t alpha, const uint8_t *pi_inject, uint32_t inject_steps,
+                                uint32_t *tsym, cudaStream_t s);
+// Sampled steps of every embedding sorted by step: spos/stag [r][m*z], tag = f<<16 | q.
+cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uint32_t z, uint32_t *spos,
+                                uint32_t *stag, cudaStream_t s);
+// Shared memory the fused kernel needs (0 if it does not fit: use embed + sign).
+size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z);
+cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                              uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
+                              const uint32_t *tsym, const uint32_t *spos, const uint32_t *stag,
+                              uint64_t *keys, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Scan and sort primitives (ej_sort.cu)
 // ---------------------------------------------------------------------------

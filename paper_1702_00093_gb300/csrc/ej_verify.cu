@@ -73,6 +73,64 @@ __device__ __forceinline__ void sym64_planes(const uint4 *__restrict__ xc, int64
          ((uint64_t)compress_even(w2 >> 1) << 32) | ((uint64_t)compress_even(w3 >> 1) << 48);
 }
 
+// S = A + Bv as one (64*W)-bit addition; the carry runs through the hardware
+// carry flag inside a single asm block.
+template <int W>
+__device__ __forceinline__ void add_chain(uint64_t (&S)[W], const uint64_t (&A)[W], const uint64_t (&Bv)[W]);
+template <>
+__device__ __forceinline__ void add_chain<1>(uint64_t (&S)[1], const uint64_t (&A)[1], const uint64_t (&Bv)[1]) {
+    S[0] = A[0] + Bv[0];
+}
+
+template <>
+__device__ __forceinline__ void add_chain<2>(uint64_t (&S)[2], const uint64_t (&A)[2], const uint64_t (&Bv)[2]) {
+    asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+        : "=l"(S[0]), "=l"(S[1])
+        : "l"(A[0]), "l"(A[1]), "l"(Bv[0]), "l"(Bv[1]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<3>(uint64_t (&S)[3], const uint64_t (&A)[3], const uint64_t (&Bv)[3]) {
+    asm("add.cc.u64 %0, %3, %6;\n\taddc.cc.u64 %1, %4, %7;\n\taddc.u64 %2, %5, %8;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<4>(uint64_t (&S)[4], const uint64_t (&A)[4], const uint64_t (&Bv)[4]) {
+    asm("add.cc.u64 %0, %4, %8;\n\taddc.cc.u64 %1, %5, %9;\n\taddc.cc.u64 %2, %6, %10;\n\taddc.u64 %3, %7, %11;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<5>(uint64_t (&S)[5], const uint64_t (&A)[5], const uint64_t (&Bv)[5]) {
+    asm("add.cc.u64 %0, %5, %10;\n\taddc.cc.u64 %1, %6, %11;\n\taddc.cc.u64 %2, %7, %12;\n\taddc.cc.u64 %3, %8, %13;\n\taddc.u64 %4, %9, %14;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<6>(uint64_t (&S)[6], const uint64_t (&A)[6], const uint64_t (&Bv)[6]) {
+    asm("add.cc.u64 %0, %6, %12;\n\taddc.cc.u64 %1, %7, %13;\n\taddc.cc.u64 %2, %8, %14;\n\taddc.cc.u64 %3, %9, %15;\n\taddc.cc.u64 %4, %10, %16;\n\taddc.u64 %5, %11, %17;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<7>(uint64_t (&S)[7], const uint64_t (&A)[7], const uint64_t (&Bv)[7]) {
+    asm("add.cc.u64 %0, %7, %14;\n\taddc.cc.u64 %1, %8, %15;\n\taddc.cc.u64 %2, %9, %16;\n\taddc.cc.u64 %3, %10, %17;\n\taddc.cc.u64 %4, %11, %18;\n\taddc.cc.u64 %5, %12, %19;\n\taddc.u64 %6, %13, %20;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<8>(uint64_t (&S)[8], const uint64_t (&A)[8], const uint64_t (&Bv)[8]) {
+    asm("add.cc.u64 %0, %8, %16;\n\taddc.cc.u64 %1, %9, %17;\n\taddc.cc.u64 %2, %10, %18;\n\taddc.cc.u64 %3, %11, %19;\n\taddc.cc.u64 %4, %12, %20;\n\taddc.cc.u64 %5, %13, %21;\n\taddc.cc.u64 %6, %14, %22;\n\taddc.u64 %7, %15, %23;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6]), "=l"(S[7])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]));
+}
+
 // |{(a, b): 0 <= a < lx, 0 <= b < ly, |a - b| <= K}|, Ukkonen's band size.
 __device__ __forceinline__ unsigned long long band_cells(int64_t lx, int64_t ly, int64_t K) {
     if (lx <= 0 || ly <= 0) return 0ull;
@@ -377,6 +435,241 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// One lane per pair: the whole window of W <= 8 words lives in one thread
+// ---------------------------------------------------------------------------
+//
+// Same recurrence and boundaries as verify_kernel, without cross-lane traffic.
+// The match masks are not stored for all of x: a ring of R = W+2 words per
+// symbol holds Peq words i0 .. i0+W (i0 = (j-1)/64) and one new word is built
+// every 64 columns, so shared memory per pair is alpha*(W+2) words instead of
+// alpha*|x|/64.
+
+constexpr int VG1_MAX_THREADS = 128;
+
+template <int W, int B>
+__global__ void __launch_bounds__(VG1_MAX_THREADS)
+verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+                 const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
+                 const uint64_t *__restrict__ pairs, int64_t np, int32_t K,
+                 uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
+                 unsigned long long *__restrict__ work) {
+    constexpr int R = W + 2;
+    extern __shared__ uint64_t smem[];
+    __shared__ int8_t s_nsum[256];
+    __shared__ int8_t s_nmin[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        const uint32_t P = t & 15u, M = t >> 4;
+        int run = 0, mn = 1 << 20;
+        for (int k = 0; k < 4; k++) {
+            run += (int)((P >> k) & 1u) - (int)((M >> k) & 1u);
+            mn = run < mn ? run : mn;
+        }
+        s_nsum[t] = (int8_t)run;
+        s_nmin[t] = (int8_t)mn;
+    }
+    __syncthreads();
+    const int T_ = blockDim.x;
+    // ring word (c, slot) of this thread: smem[(c * R + slot) * T_ + tid]
+    uint64_t *ring = smem + threadIdx.x;
+    const int32_t w_min = (2 * K + 1 + 63) / 64;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        const uint64_t pr = pairs[p];
+        const int64_t a = (int64_t)(pr >> 32), b = (int64_t)(pr & 0xFFFFFFFFull);
+        if (a >= n_str || b >= n_str) {
+            atomicOr(err, (uint32_t)DERR_PAIR);
+            continue;
+        }
+        const int32_t la = lens[a], lb = lens[b];
+        const bool a_long = la >= lb;
+        const int64_t xi = a_long ? a : b, yi = a_long ? b : a;
+        const int32_t mrows = a_long ? la : lb, ncols = a_long ? lb : la;
+        bool pass;
+        int32_t cols_run = 0;
+        if (mrows - ncols > K) {
+            pass = false;
+        } else if (ncols == 0) {
+            pass = mrows <= K;
+        } else {
+            const uint4 *xc = packed + pofs[xi];
+            const int64_t xch = chunks_for(mrows, B);
+            // Peq word wi (bits <-> x symbols 64*wi-K .. +63) into ring slot `slot`
+            auto build = [&](int64_t wi, int slot) {
+                const int64_t k0 = 64ll * wi - K;
+                const int64_t t_lo = k0 < 0 ? -k0 : 0;
+                const int64_t t_hi = (int64_t)mrows - k0;
+                uint64_t valid_m = 0ull;
+                if (t_hi > t_lo && t_lo < 64) {
+                    const uint64_t upto = t_hi >= 64 ? ~0ull : ((1ull << t_hi) - 1ull);
+                    valid_m = upto & ~((1ull << t_lo) - 1ull);
+                }
+                if (B == 2) {
+                    uint64_t lo = 0, hi = 0;
+                    if (valid_m) sym64_planes(xc, xch, k0, lo, hi);
+                    for (uint32_t c = 0; c < alpha; c++)
+                        ring[(size_t)(c * R + slot) * T_] = ((c & 1u) ? lo : ~lo) & ((c & 2u) ? hi : ~hi) & valid_m;
+                } else {
+                    for (uint32_t c = 0; c < alpha; c++) ring[(size_t)(c * R + slot) * T_] = 0ull;
+                    if (valid_m) {
+                        const int64_t ks = k0 + t_lo, ke = k0 + (t_hi < 64 ? t_hi : 64);
+                        for (int64_t k = ks; k < ke; k++) {
+                            const uint4 v = xc[k >> 4];
+                            const uint32_t sel = (uint32_t)(k & 15);
+                            const uint32_t wv = (sel < 8) ? ((sel < 4) ? v.x : v.y) : ((sel < 12) ? v.z : v.w);
+                            const uint32_t c = (wv >> ((sel & 3u) * 8u)) & 0xFFu;
+                            if (c < alpha) ring[(size_t)(c * R + slot) * T_] |= 1ull << (uint32_t)(k - k0);
+                        }
+                    }
+                }
+            };
+#pragma unroll 1
+            for (int wi = 0; wi <= W; wi++) build(wi, wi);
+            int base = 0;  // ring slot of word i0
+
+            uint64_t Pv[W], Mv[W];
+#pragma unroll
+            for (int v = 0; v < W; v++) {
+                const int lo = 64 * v;
+                if (K >= lo + 63) { Mv[v] = ~0ull; Pv[v] = 0ull; }
+                else if (K < lo) { Mv[v] = 0ull; Pv[v] = ~0ull; }
+                else { Mv[v] = (1ull << (K - lo + 1)) - 1ull; Pv[v] = ~Mv[v]; }
+            }
+            int32_t T = K + 1;
+            SymReader<B> yr;
+            yr.init(packed + pofs[yi], chunks_for(ncols, B));
+            bool rejected = false;
+            int32_t j = 1;
+            for (; j <= ncols; j++) {
+                const uint32_t jm = (uint32_t)(j - 1);
+                if ((jm & 63u) == 0u && j > 1) {
+                    // window start moved to word i0: word wi lives in slot wi mod R, so
+                    // word i0+W takes the slot of word i0-2 (R = W+2), no longer read
+                    const int64_t i0 = jm >> 6;
+                    base = (base + 1 == R) ? 0 : base + 1;
+                    int slot = base + W;
+                    if (slot >= R) slot -= R;
+                    build(i0 + W, slot);
+                    // early exit: the minimum of the window exceeds K
+                    int32_t run = 0, mn = 1 << 30;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            const uint32_t idx = (uint32_t)((Pv[v] >> (4 * k)) & 15u) |
+                                                 ((uint32_t)((Mv[v] >> (4 * k)) & 15u) << 4);
+                            const int32_t cand = run + s_nmin[idx];
+                            mn = cand < mn ? cand : mn;
+                            run += s_nsum[idx];
+                        }
+                    }
+                    if (T + mn > K) {
+                        rejected = true;
+                        break;
+                    }
+                }
+                const uint32_t c = yr.code();
+                yr.advance();
+                T += (int32_t)(Pv[0] & 1ull) - (int32_t)(Mv[0] & 1ull) + 1;
+                uint64_t nP[W], nM[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    const uint64_t upP = (v + 1 < W) ? Pv[v + 1 < W ? v + 1 : v] : 1ull;
+                    const uint64_t upM = (v + 1 < W) ? Mv[v + 1 < W ? v + 1 : v] : 0ull;
+                    nP[v] = (Pv[v] >> 1) | (upP << 63);
+                    nM[v] = (Mv[v] >> 1) | (upM << 63);
+                }
+                uint64_t Eq[W];
+                {
+                    const uint32_t sh = jm & 63u;
+                    const uint64_t *row = ring + (size_t)(c < alpha ? c : 0u) * R * T_;
+                    int sl = base;
+                    uint64_t w_lo = (c < alpha) ? row[(size_t)sl * T_] : 0ull;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        sl = (sl + 1 == R) ? 0 : sl + 1;
+                        const uint64_t w_hi = (c < alpha) ? row[(size_t)sl * T_] : 0ull;
+                        Eq[v] = funnel64(w_lo, w_hi, sh);
+                        w_lo = w_hi;
+                    }
+                }
+                uint64_t A[W], S[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) A[v] = Eq[v] & nP[v];
+                add_chain<W>(S, A, nP);
+                uint64_t Ph[W], Mh[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    const uint64_t Xh = (S[v] ^ nP[v]) | Eq[v];
+                    Ph[v] = nM[v] | ~(Xh | nP[v]);
+                    Mh[v] = nP[v] & Xh;
+                }
+#pragma unroll
+                for (int v = W - 1; v >= 0; v--) {
+                    const uint64_t inP = (v > 0) ? (Ph[v > 0 ? v - 1 : 0] >> 63) : 1ull;
+                    const uint64_t inM = (v > 0) ? (Mh[v > 0 ? v - 1 : 0] >> 63) : 0ull;
+                    Ph[v] = (Ph[v] << 1) | inP;
+                    Mh[v] = (Mh[v] << 1) | inM;
+                }
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    const uint64_t X = Eq[v] | nM[v];
+                    Pv[v] = Mh[v] | ~(X | Ph[v]);
+                    Mv[v] = Ph[v] & X;
+                }
+            }
+            cols_run = rejected ? j - 1 : ncols;
+            if (rejected) {
+                pass = false;
+            } else {
+                const int32_t bmax = (mrows - ncols) + K;
+                int32_t cnt = 0;
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    const int lo = 64 * v;
+                    uint64_t mask;
+                    if (lo > bmax) mask = 0ull;
+                    else if (lo + 63 <= bmax) mask = ~0ull;
+                    else mask = (1ull << (bmax - lo + 1)) - 1ull;
+                    cnt += __popcll(Pv[v] & mask) - __popcll(Mv[v] & mask);
+                }
+                pass = (T + cnt) <= K;
+            }
+        }
+        flags[p] = pass ? 1 : 0;
+        if (work) {
+            atomicAdd(&work[0], band_cells(mrows, ncols, K));
+            atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+        }
+    }
+}
+
+template <int W, int B>
+static cudaError_t launch_g1(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                             uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
+                             uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
+    const int threads = warps * 32;
+    const size_t smem = (size_t)alpha * (W + 2) * sizeof(uint64_t) * threads;
+    cudaError_t e = cudaFuncSetAttribute(verify_g1_kernel<W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_g1_kernel<W, B>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (np + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    verify_g1_kernel<W, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
+                                                                    flags, err, work);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Configuration
 // ---------------------------------------------------------------------------
@@ -388,21 +681,25 @@ static int32_t peq_words(int64_t max_len, int32_t K, int W) {
 }
 
 size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_t K) {
+    if (c.G == 1) return (size_t)c.warps * 32 * alpha * (c.V + 2) * sizeof(uint64_t);
     const int W = c.G * c.V;
     return (size_t)c.warps * (32 / c.G) * alpha * (size_t)peq_words(max_len, K, W) * sizeof(uint64_t);
 }
 
 VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
     const int W = words_needed(K);
-    // For each words-per-lane V take the fewest lanes G (a power of two) that
-    // cover the band; keep the smallest window, preferring configurations whose
-    // shared memory allows >= 8 resident warps per SM, then larger V (fewer
-    // cross-lane collectives per word).
+    if (W <= 8) {
+        // one lane per pair, the window in registers, a Peq ring in shared memory
+        VerifyConfig c{1, W, 4};
+        while (c.warps > 1 && verify_smem_bytes(c, alpha, max_len, K) > 100 * 1024) c.warps >>= 1;
+        if (verify_smem_bytes(c, alpha, max_len, K) <= 200 * 1024) return c;
+    }
+    // wider bands: G lanes per pair (power of two), V words per lane
     VerifyConfig best{0, 0, 0};
     int best_words = 1 << 30;
     bool best_fit = false;
     for (int V = 4; V >= 1; V--) {
-        int G = 1;
+        int G = 2;
         while (G * V < W && G < 32) G <<= 1;
         if (G * V < W) continue;
         VerifyConfig c{G, V, 1};
@@ -464,7 +761,17 @@ cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *p
         return launch_gv<GG, VV, 8>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps, flags, \
                                     err, work, s);                                                       \
     }
-    EJ_V(1, 1) EJ_V(1, 2) EJ_V(1, 3) EJ_V(1, 4)
+    if (c.G == 1) {
+#define EJ_G1(WW)                                                                                         \
+    if (c.V == WW) {                                                                                      \
+        if (B == 2)                                                                                       \
+            return launch_g1<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s); \
+        return launch_g1<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s);     \
+    }
+        EJ_G1(1) EJ_G1(2) EJ_G1(3) EJ_G1(4) EJ_G1(5) EJ_G1(6) EJ_G1(7) EJ_G1(8)
+#undef EJ_G1
+        return cudaErrorInvalidValue;
+    }
     EJ_V(2, 1) EJ_V(2, 2) EJ_V(2, 3) EJ_V(2, 4)
     EJ_V(4, 1) EJ_V(4, 2) EJ_V(4, 3) EJ_V(4, 4)
     EJ_V(8, 1) EJ_V(8, 2) EJ_V(8, 3) EJ_V(8, 4)

@@ -26,7 +26,7 @@ EJ_ERR_UNSUPPORTED = 6
 
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
-            "ej_set_test_tables", "ej_set_verify_config"]
+            "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign"]
 
 
 class EJError(RuntimeError):
@@ -54,7 +54,7 @@ class PlanInfo(C.Structure):
 
 class JoinStats(C.Structure):
     _fields_ = [("n_raw_pairs", C.c_int64), ("n_candidates", C.c_int64), ("n_out", C.c_int64),
-                ("max_bucket", C.c_int64), ("ms_embed", C.c_float), ("ms_sign", C.c_float),
+                ("max_bucket", C.c_int64), ("ms_prepare", C.c_float), ("ms_embed_sign", C.c_float),
                 ("ms_candidates", C.c_float), ("ms_verify", C.c_float), ("ms_total", C.c_float),
                 ("band_cells", C.c_uint64), ("verify_word_columns", C.c_uint64),
                 ("kernel_launches", C.c_int64)]
@@ -102,6 +102,8 @@ def lib():
         L.ej_set_test_tables.argtypes = [vp, vp, C.c_uint32, C.c_uint32, C.c_uint32, vp,
                                          C.c_uint32, C.c_uint32]
         L.ej_set_test_tables.restype = C.c_int
+        L.ej_embed_sign.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, vp]
+        L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
         _lib = L
@@ -222,6 +224,12 @@ class Context:
         cs, (cp, _keep) = s._c(), p._c()
         self._check(lib().ej_sign(self._h, C.byref(cs), C.byref(cp), _ptr(emb), _ptr(walk_end),
                                   _ptr(keys), _stream(stream)), "ej_sign")
+
+    def embed_sign(self, s: Strings, p: Params, keys, stream=None):
+        """Keys [r*m][n] without materialising the embedding (fused walk)."""
+        cs, (cp, _keep) = s._c(), p._c()
+        self._check(lib().ej_embed_sign(self._h, C.byref(cs), C.byref(cp), _ptr(keys), _stream(stream)),
+                    "ej_embed_sign")
 
     def lsh_candidates(self, s: Strings, p: Params, keys, pairs, stream=None) -> tuple[int, int]:
         """Returns (count, max_bucket). Raises EJError(EJ_ERR_CAPACITY) with

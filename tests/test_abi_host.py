@@ -78,7 +78,7 @@ int main(void) {{
   printf("ej_join_stats %zu\\n", sizeof(ej_join_stats));
   F(ej_params, seed) F(ej_params, alphabet) F(ej_params, alphabet_size) F(ej_params, K)
   F(ej_plan_info, embedding_bytes) F(ej_plan_info, key_count)
-  F(ej_join_stats, ms_embed) F(ej_join_stats, ms_total)
+  F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total)
   return 0;
 }}''')
     exe = tmp_path / "probe"

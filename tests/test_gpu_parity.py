@@ -81,6 +81,9 @@ def check_all_stages(ej, ctx, ss, params, check_join=True):
     ref_keys = oracle.sign(ref_emb, ref_we, pos, len(ss.alphabet))
     keys = gpu_keys(ej, ctx, s, params, emb, we, ss.n)
     assert np.array_equal(keys, ref_keys)
+    fused = torch.zeros(params.r * params.m * ss.n, dtype=torch.int64, device=DEV)
+    ctx.embed_sign(s, params, fused)
+    assert np.array_equal(_np_u64(fused).reshape(params.r * params.m, ss.n), ref_keys)
     cand = gpu_candidates(ej, ctx, s, params, keys)
     ref_cand = oracle.candidates(ss.data, ss.offsets, ref_keys, params.K)
     assert np.array_equal(cand, ref_cand)
@@ -120,6 +123,9 @@ def test_running_example_on_gpu(ej, ctx, golden):
             for l in range(2):
                 assert "".join("ACGT"[c] for c in codes[l, i]) == g["embedded_prefixes"][f"t{i + 1}^{l + 1}"]
         keys = gpu_keys(ej, ctx, s, params, emb, we, 4)
+        fused = torch.zeros(16, dtype=torch.int64, device=DEV)
+        ctx.embed_sign(s, params, fused)
+        assert np.array_equal(_np_u64(fused).reshape(4, 4), keys)
         for i in range(4):
             for col in range(4):
                 sig = g["signatures"][str(i + 1)][col]
@@ -318,7 +324,7 @@ def test_verify_every_tiling_is_exact(ej, ctx, K, alphabet):
     tried = 0
     try:
         for G in (1, 2, 4, 8, 16, 32):
-            for V in (1, 2, 3, 4):
+            for V in ((1, 2, 3, 4, 5, 6, 7, 8) if G == 1 else (1, 2, 3, 4)):
                 if 64 * G * V < 2 * K + 1 or G * V > 4 * max(1, (2 * K + 1 + 63) // 64):
                     continue
                 ctx.set_verify_config(G, V, 0)
