@@ -138,11 +138,14 @@ const char *ej_last_error(ej_ctx *ctx);
 int ej_set_timing(ej_ctx *ctx, int enable);
 
 /*
- * Verifier tiling (the autotuner's knob): lanes_per_pair G in {1,2,4,8,16,32}
- * and 64-bit words per lane V (1..8 when G = 1, else 1..4) with 64*G*V >= 2K+1,
- * and warps per block (0 = automatic; at most 4 when G = 1). All zero restores the automatic choice. A configuration that cannot
- * cover the band of a later call makes that call fall back to the automatic
- * choice. Results never depend on the tiling.
+ * Verifier tiling (the autotuner's knob). lanes_per_pair selects the kernel:
+ *   1: one lane per pair, diagonal window of V = 1..8 words (64V >= 2K+1);
+ *   2: two lanes per pair (forward and backward halves meeting at the middle
+ *      column), block-aligned window of V = 2..12 words (64(V-1) >= 2K+1);
+ *   4, 8, 16, 32: that many lanes per pair, V = 1..4 words each (64GV >= 2K+1).
+ * warps_per_block 0 = automatic (at most 4 for lanes_per_pair <= 2). All zero
+ * restores the automatic choice. A configuration that cannot cover the band of
+ * a later call falls back to the automatic choice. Results never depend on it.
  */
 int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
 

@@ -481,16 +481,17 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     *n_out = 0;
     if (np == 0) return EJ_OK;
     VerifyConfig vc = verify_pick(p->K, p->alphabet_size, pl.max_len);
-    if (ctx->vG > 0 && (int64_t)64 * ctx->vG * ctx->vV >= 2ll * p->K + 1) {
+    const int64_t cover = ctx->vG == 2 ? 64ll * (ctx->vV - 1) : 64ll * ctx->vG * ctx->vV;
+    if (ctx->vG > 0 && cover >= 2ll * p->K + 1) {
         VerifyConfig o{ctx->vG, ctx->vV, ctx->vWarps > 0 ? ctx->vWarps : 1};
         if (ctx->vWarps <= 0) {
             VerifyConfig one{o.G, o.V, 1};
             const size_t per_warp = verify_smem_bytes(one, p->alphabet_size, pl.max_len, p->K);
             int w = (int)((96 * 1024) / (per_warp ? per_warp : 1));
-            const int wmax = o.G == 1 ? 4 : 8;
+            const int wmax = o.G <= 2 ? 4 : 8;
             o.warps = w < 1 ? 1 : (w > wmax ? wmax : w);
         }
-        if (o.G == 1 && o.warps > 4) o.warps = 4;
+        if (o.G <= 2 && o.warps > 4) o.warps = 4;
         if (verify_smem_bytes(o, p->alphabet_size, pl.max_len, p->K) <= 200 * 1024) vc = o;
     }
     if (vc.G == 0)
@@ -615,7 +616,8 @@ int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
         return EJ_OK;
     }
     const bool okG = G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
-    if (!okG || V < 1 || V > (G == 1 ? 8 : 4) || warps < 0 || warps > 8)
+    const int vmax = G == 1 ? 8 : (G == 2 ? 12 : 4);
+    if (!okG || V < (G == 2 ? 2 : 1) || V > vmax || warps < 0 || warps > 8)
         return fail(ctx, EJ_ERR_INVALID_ARG, "verify config G=%d V=%d warps=%d not supported", G, V, warps);
     ctx->vG = G;
     ctx->vV = V;

@@ -131,6 +131,34 @@ __device__ __forceinline__ void add_chain<8>(uint64_t (&S)[8], const uint64_t (&
         : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]));
 }
 
+template <>
+__device__ __forceinline__ void add_chain<9>(uint64_t (&S)[9], const uint64_t (&A)[9], const uint64_t (&Bv)[9]) {
+    asm("add.cc.u64 %0, %9, %18;\n\taddc.cc.u64 %1, %10, %19;\n\taddc.cc.u64 %2, %11, %20;\n\taddc.cc.u64 %3, %12, %21;\n\taddc.cc.u64 %4, %13, %22;\n\taddc.cc.u64 %5, %14, %23;\n\taddc.cc.u64 %6, %15, %24;\n\taddc.cc.u64 %7, %16, %25;\n\taddc.u64 %8, %17, %26;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6]), "=l"(S[7]), "=l"(S[8])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]), "l"(Bv[8]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<10>(uint64_t (&S)[10], const uint64_t (&A)[10], const uint64_t (&Bv)[10]) {
+    asm("add.cc.u64 %0, %10, %20;\n\taddc.cc.u64 %1, %11, %21;\n\taddc.cc.u64 %2, %12, %22;\n\taddc.cc.u64 %3, %13, %23;\n\taddc.cc.u64 %4, %14, %24;\n\taddc.cc.u64 %5, %15, %25;\n\taddc.cc.u64 %6, %16, %26;\n\taddc.cc.u64 %7, %17, %27;\n\taddc.cc.u64 %8, %18, %28;\n\taddc.u64 %9, %19, %29;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6]), "=l"(S[7]), "=l"(S[8]), "=l"(S[9])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]), "l"(Bv[8]), "l"(Bv[9]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<11>(uint64_t (&S)[11], const uint64_t (&A)[11], const uint64_t (&Bv)[11]) {
+    asm("add.cc.u64 %0, %11, %22;\n\taddc.cc.u64 %1, %12, %23;\n\taddc.cc.u64 %2, %13, %24;\n\taddc.cc.u64 %3, %14, %25;\n\taddc.cc.u64 %4, %15, %26;\n\taddc.cc.u64 %5, %16, %27;\n\taddc.cc.u64 %6, %17, %28;\n\taddc.cc.u64 %7, %18, %29;\n\taddc.cc.u64 %8, %19, %30;\n\taddc.cc.u64 %9, %20, %31;\n\taddc.u64 %10, %21, %32;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6]), "=l"(S[7]), "=l"(S[8]), "=l"(S[9]), "=l"(S[10])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]), "l"(A[10]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]), "l"(Bv[8]), "l"(Bv[9]), "l"(Bv[10]));
+}
+
+template <>
+__device__ __forceinline__ void add_chain<12>(uint64_t (&S)[12], const uint64_t (&A)[12], const uint64_t (&Bv)[12]) {
+    asm("add.cc.u64 %0, %12, %24;\n\taddc.cc.u64 %1, %13, %25;\n\taddc.cc.u64 %2, %14, %26;\n\taddc.cc.u64 %3, %15, %27;\n\taddc.cc.u64 %4, %16, %28;\n\taddc.cc.u64 %5, %17, %29;\n\taddc.cc.u64 %6, %18, %30;\n\taddc.cc.u64 %7, %19, %31;\n\taddc.cc.u64 %8, %20, %32;\n\taddc.cc.u64 %9, %21, %33;\n\taddc.cc.u64 %10, %22, %34;\n\taddc.u64 %11, %23, %35;"
+        : "=l"(S[0]), "=l"(S[1]), "=l"(S[2]), "=l"(S[3]), "=l"(S[4]), "=l"(S[5]), "=l"(S[6]), "=l"(S[7]), "=l"(S[8]), "=l"(S[9]), "=l"(S[10]), "=l"(S[11])
+        : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]), "l"(A[10]), "l"(A[11]), "l"(Bv[0]), "l"(Bv[1]), "l"(Bv[2]), "l"(Bv[3]), "l"(Bv[4]), "l"(Bv[5]), "l"(Bv[6]), "l"(Bv[7]), "l"(Bv[8]), "l"(Bv[9]), "l"(Bv[10]), "l"(Bv[11]));
+}
+
 // |{(a, b): 0 <= a < lx, 0 <= b < ly, |a - b| <= K}|, Ukkonen's band size.
 __device__ __forceinline__ unsigned long long band_cells(int64_t lx, int64_t ly, int64_t K) {
     if (lx <= 0 || ly <= 0) return 0ull;
@@ -670,6 +698,366 @@ static cudaError_t launch_g1(const uint4 *packed, const uint64_t *pofs, const in
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Two lanes per pair: forward and backward halves of a block-aligned band
+// ---------------------------------------------------------------------------
+//
+// Block-aligned window. Rows are grouped in fixed 64-row words (word k holds
+// rows 64k+1 .. 64k+64). At column j the thread keeps W1 consecutive words
+// starting at k0 = max(0, floor((j-K-1)/64)); 64*W1 >= 2K+1+64 rows always
+// cover Ukkonen's band [j-K, j+K]. Match masks are then Peq words as they are
+// (no per-column funnel) and the window moves by one whole word every 64
+// columns: the top word's differences are folded into T, the value of row
+// 64*k0 (the row above the window), and a fresh bottom word enters with
+// vertical differences +1. Row 64*k0 lies outside the band (64*k0 < j-K), so
+// it is replaced by the upper bound "+1 per column" (real when k0 = 0: D(0,j)
+// = j), and the same argument as for the diagonal window gives exactness for
+// values <= K.
+//
+// Bidirectional split. With n1 = n/2, ED(x, y) = min_i D(i, n1) + ED(x[i:], y[n1:]).
+// Lane 2t computes D(., n1) forward; lane 2t+1 runs the same recurrence on the
+// reversed strings for n - n1 columns, which gives ED(x[i:], y[n1:]) for the
+// rows of its window. Both halves are exact where their value is <= K and
+// >= min(true, K+1) elsewhere; an optimal path of cost <= K crosses column n1
+// inside both bands, so "min_i F(i) + B(i) <= K" decides ED <= K exactly. The
+// two halves run concurrently, halving the sequential chain of a pair.
+
+constexpr int VBD_THREADS = 128;
+
+// reversed reader: symbols idx, idx-1, ..., 0 of a packed string
+template <int B>
+struct SymReaderRev {
+    const uint4 *base;
+    int64_t ch;   // index of the chunk that `nxt` holds (the one before cur)
+    uint4 cur, nxt;
+    int left;
+    __device__ __forceinline__ void init(const uint4 *b, int64_t len) {
+        constexpr int S = 128 / B;
+        base = b;
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        if (len <= 0) {
+            cur = nxt = zero;
+            left = S;
+            ch = -1;
+            return;
+        }
+        const int64_t last = len - 1;
+        const int64_t c = last / S;
+        const int s = (int)(last - c * S);  // position of the last symbol in its chunk
+        cur = b[c];
+        // shift left so that symbol s occupies the top B bits
+        const uint32_t sh = (uint32_t)((S - 1 - s) * B);  // 0 .. 128-B
+        uint32_t w0 = cur.x, w1 = cur.y, w2 = cur.z, w3 = cur.w;
+        if (sh & 64u) { w3 = w1; w2 = w0; w1 = 0u; w0 = 0u; }
+        if (sh & 32u) { w3 = w2; w2 = w1; w1 = w0; w0 = 0u; }
+        const uint32_t bs = sh & 31u;
+        cur.w = __funnelshift_l(w2, w3, bs);
+        cur.z = __funnelshift_l(w1, w2, bs);
+        cur.y = __funnelshift_l(w0, w1, bs);
+        cur.x = w0 << bs;
+        left = s + 1;
+        ch = c - 1;
+        nxt = (ch >= 0) ? b[ch] : zero;
+    }
+    __device__ __forceinline__ uint32_t code() const { return cur.w >> (32 - B); }
+    __device__ __forceinline__ void advance() {
+        cur.w = __funnelshift_l(cur.z, cur.w, B);
+        cur.z = __funnelshift_l(cur.y, cur.z, B);
+        cur.y = __funnelshift_l(cur.x, cur.y, B);
+        cur.x <<= B;
+        if (--left == 0) {
+            cur = nxt;
+            ch--;
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+            nxt = (ch >= 0) ? base[ch] : zero;
+            left = 128 / B;
+        }
+    }
+};
+
+// Peq word k (rows 64k+1 .. 64k+64) of x, or of reversed x when `rev`, for every
+// symbol c < alpha, into ring slot `slot` (stride T_ between slots).
+template <int B, int R>
+__device__ __forceinline__ void bd_build(uint64_t *ring, int T_, int slot, const uint4 *__restrict__ xc,
+                                         int64_t m, int64_t k, bool rev, uint32_t alpha) {
+    // forward symbols covered: [k0, k0+64) (reversed: x[m-64-64k .. m-1-64k])
+    const int64_t k0 = rev ? (m - 64 - 64 * k) : 64 * k;
+    const int64_t t_lo = k0 < 0 ? -k0 : 0;
+    const int64_t t_hi = m - k0;
+    uint64_t valid_m = 0ull;
+    if (t_hi > t_lo && t_lo < 64) {
+        const uint64_t upto = t_hi >= 64 ? ~0ull : ((1ull << t_hi) - 1ull);
+        valid_m = upto & ~((1ull << t_lo) - 1ull);
+    }
+    const int64_t xch = chunks_for(m, B);
+    if (B == 2) {
+        uint64_t lo = 0, hi = 0;
+        if (valid_m) sym64_planes(xc, xch, k0, lo, hi);
+        if (rev) {
+            lo = __brevll(lo);
+            hi = __brevll(hi);
+            valid_m = __brevll(valid_m);
+        }
+        for (uint32_t c = 0; c < alpha; c++)
+            ring[(size_t)(c * R + slot) * T_] = ((c & 1u) ? lo : ~lo) & ((c & 2u) ? hi : ~hi) & valid_m;
+    } else {
+        for (uint32_t c = 0; c < alpha; c++) ring[(size_t)(c * R + slot) * T_] = 0ull;
+        if (valid_m) {
+            const int64_t ks = k0 + t_lo, ke = k0 + (t_hi < 64 ? t_hi : 64);
+            for (int64_t kk = ks; kk < ke; kk++) {
+                const uint4 v = xc[kk >> 4];
+                const uint32_t sel = (uint32_t)(kk & 15);
+                const uint32_t wv = (sel < 8) ? ((sel < 4) ? v.x : v.y) : ((sel < 12) ? v.z : v.w);
+                const uint32_t c = (wv >> ((sel & 3u) * 8u)) & 0xFFu;
+                const uint32_t bit = rev ? (uint32_t)(63 - (kk - k0)) : (uint32_t)(kk - k0);
+                if (c < alpha) ring[(size_t)(c * R + slot) * T_] |= 1ull << bit;
+            }
+        }
+    }
+}
+
+template <int W1, int B>
+__global__ void __launch_bounds__(VBD_THREADS)
+verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+                 const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
+                 const uint64_t *__restrict__ pairs, int64_t np, int32_t K,
+                 uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
+                 unsigned long long *__restrict__ work) {
+    constexpr int R = W1 + 1;
+    extern __shared__ uint64_t smem[];
+    __shared__ int8_t s_nsum[256];
+    __shared__ int8_t s_nmin[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        const uint32_t P = t & 15u, M = t >> 4;
+        int run = 0, mn = 1 << 20;
+        for (int k = 0; k < 4; k++) {
+            run += (int)((P >> k) & 1u) - (int)((M >> k) & 1u);
+            mn = run < mn ? run : mn;
+        }
+        s_nsum[t] = (int8_t)run;
+        s_nmin[t] = (int8_t)mn;
+    }
+    __syncthreads();
+    const int T_ = blockDim.x;
+    uint64_t *ring = smem + threadIdx.x;  // per thread: (c*R + slot)*T_, reused as a dump area
+    const int lane = threadIdx.x & 31;
+    const bool rev = lane & 1;
+    const unsigned pmask = 3u << (lane & ~1);
+    const int32_t w_min = (2 * K + 1 + 63) / 64;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 1);
+    const int64_t niter = (np + stride - 1) / stride;   // same for both lanes of a pair
+
+    for (int64_t it = 0; it < niter; it++) {
+        const int64_t p = it * stride + (int64_t)blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1);
+        bool valid = p < np;
+        int64_t a = 0, b = 0;
+        if (valid) {
+            const uint64_t pr = pairs[p];
+            a = (int64_t)(pr >> 32);
+            b = (int64_t)(pr & 0xFFFFFFFFull);
+            if (a >= n_str || b >= n_str) {
+                if (!rev) atomicOr(err, (uint32_t)DERR_PAIR);
+                valid = false;
+            }
+        }
+        const int32_t la = valid ? lens[a] : 0, lb = valid ? lens[b] : 0;
+        const bool a_long = la >= lb;
+        const int64_t xi = a_long ? a : b, yi = a_long ? b : a;
+        const int32_t m = a_long ? la : lb, n = a_long ? lb : la;
+        bool decided = !valid, pass = false;
+        if (valid && m - n > K) decided = true;
+        else if (valid && n == 0) { decided = true; pass = m <= K; }
+        const int32_t n1 = n / 2;
+        const int32_t ncols = decided ? 0 : (rev ? n - n1 : n1);
+
+        uint64_t Pv[W1], Mv[W1];
+        int32_t T = 0;
+        int64_t k0 = 0;
+        bool rejected = false;
+        int32_t cols_run = 0;
+        if (!decided) {
+            const uint4 *xc = packed + pofs[xi];
+            for (int wi = 0; wi < W1; wi++) bd_build<B, R>(ring, T_, wi, xc, m, wi, rev, alpha);
+#pragma unroll
+            for (int v = 0; v < W1; v++) { Pv[v] = ~0ull; Mv[v] = 0ull; }
+            int base = 0;  // slot of word k0
+            SymReader<B> yf;
+            SymReaderRev<B> yb;
+            if (rev) yb.init(packed + pofs[yi], n);
+            else yf.init(packed + pofs[yi], chunks_for(n1, B));
+            int32_t j = 1;
+            for (; j <= ncols; j++) {
+                const int64_t jk = (int64_t)j - K - 1;
+                const int64_t knew = jk > 0 ? (jk >> 6) : 0;
+                if (knew > k0) {
+                    // drop the top word into T, shift the window down one word
+                    T += __popcll(Pv[0]) - __popcll(Mv[0]);
+#pragma unroll
+                    for (int v = 0; v + 1 < W1; v++) { Pv[v] = Pv[v + 1]; Mv[v] = Mv[v + 1]; }
+                    Pv[W1 - 1] = ~0ull;
+                    Mv[W1 - 1] = 0ull;
+                    k0 = knew;
+                    const int old = base;
+                    base = (base + 1 == R) ? 0 : base + 1;
+                    (void)old;
+                    int slot = base + W1 - 1;
+                    if (slot >= R) slot -= R;
+                    bd_build<B, R>(ring, T_, slot, xc, m, k0 + W1 - 1, rev, alpha);
+                    // early exit: minimum over the window exceeds K
+                    int32_t run = 0, mn = 1 << 30;
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
+                                                 ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
+                            const int32_t cand = run + s_nmin[idx];
+                            mn = cand < mn ? cand : mn;
+                            run += s_nsum[idx];
+                        }
+                    }
+                    if (T + mn > K) {
+                        rejected = true;
+                        break;
+                    }
+                }
+                uint32_t c;
+                if (rev) { c = yb.code(); yb.advance(); }
+                else { c = yf.code(); yf.advance(); }
+                const bool cv = c < alpha;
+                const uint64_t *row = ring + (size_t)(cv ? c : 0u) * R * T_;
+                uint64_t Eq[W1];
+                {
+                    int sl = base;
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+                        Eq[v] = cv ? row[(size_t)sl * T_] : 0ull;
+                        sl = (sl + 1 == R) ? 0 : sl + 1;
+                    }
+                }
+                uint64_t A[W1], S[W1];
+#pragma unroll
+                for (int v = 0; v < W1; v++) A[v] = Eq[v] & Pv[v];
+                add_chain<W1>(S, A, Pv);
+                uint64_t Ph[W1], Mh[W1];
+#pragma unroll
+                for (int v = 0; v < W1; v++) {
+                    const uint64_t Xh = (S[v] ^ Pv[v]) | Eq[v];
+                    Ph[v] = Mv[v] | ~(Xh | Pv[v]);
+                    Mh[v] = Pv[v] & Xh;
+                }
+#pragma unroll
+                for (int v = W1 - 1; v >= 0; v--) {
+                    const uint64_t inP = (v > 0) ? (Ph[v > 0 ? v - 1 : 0] >> 63) : 1ull;
+                    const uint64_t inM = (v > 0) ? (Mh[v > 0 ? v - 1 : 0] >> 63) : 0ull;
+                    Ph[v] = (Ph[v] << 1) | inP;
+                    Mh[v] = (Mh[v] << 1) | inM;
+                }
+#pragma unroll
+                for (int v = 0; v < W1; v++) {
+                    const uint64_t X = Eq[v] | Mv[v];
+                    Pv[v] = Mh[v] | ~(X | Ph[v]);
+                    Mv[v] = Ph[v] & X;
+                }
+                T += 1;  // the row above the window: +1 per column
+            }
+            cols_run = rejected ? j - 1 : ncols;
+        }
+        // exchange: dump state into this thread's ring area
+#pragma unroll
+        for (int v = 0; v < W1; v++) {
+            ring[(size_t)(2 * v) * T_] = Pv[v];
+            ring[(size_t)(2 * v + 1) * T_] = Mv[v];
+        }
+        ring[(size_t)(2 * W1) * T_] = (uint64_t)(uint32_t)T | ((uint64_t)k0 << 32);
+        ring[(size_t)(2 * W1 + 1) * T_] = rejected ? 1ull : 0ull;
+        __syncwarp(pmask);
+        if (!rev && !decided) {
+            const uint64_t *rb = smem + threadIdx.x + 1;  // partner (backward) dump
+            const bool rej_b = rb[(size_t)(2 * W1 + 1) * T_] != 0ull;
+            if (rejected || rej_b) {
+                pass = false;
+            } else {
+                const uint64_t tb = rb[(size_t)(2 * W1) * T_];
+                const int32_t Tb = (int32_t)(uint32_t)(tb & 0xFFFFFFFFull);
+                const int64_t k0b = (int64_t)(tb >> 32);
+                const int64_t k0f = k0;
+                const uint64_t *rf = ring;
+                // forward rows: [64 k0f, min(m, 64(k0f+W1))]; backward rows i' -> i = m - i'
+                const int64_t f_hi = min((int64_t)m, 64 * (k0f + W1));
+                const int64_t b_hi = min((int64_t)m, 64 * (k0b + W1));
+                const int64_t i_lo = max(64 * k0f, (int64_t)m - b_hi);
+                const int64_t i_hi = min(f_hi, (int64_t)m - 64 * k0b);
+                if (i_lo > i_hi) {
+                    pass = false;
+                } else {
+                    // F(i_lo) = T_f + sum of forward differences of rows 64k0f+1 .. i_lo
+                    auto prefix = [&](const uint64_t *dump, int64_t k0x, int32_t Tx, int64_t row) -> int32_t {
+                        int32_t acc = Tx;
+                        const int64_t nrows = row - 64 * k0x;  // rows 64k0x+1 .. row
+                        for (int v = 0; v < W1; v++) {
+                            const int64_t lo = 64ll * v;
+                            if (lo >= nrows) break;
+                            const uint64_t msk = (nrows - lo >= 64) ? ~0ull : ((1ull << (nrows - lo)) - 1ull);
+                            acc += __popcll(dump[(size_t)(2 * v) * T_] & msk) -
+                                   __popcll(dump[(size_t)(2 * v + 1) * T_] & msk);
+                        }
+                        return acc;
+                    };
+                    int32_t F = prefix(rf, k0f, T, i_lo);
+                    int32_t Bv = prefix(rb, k0b, Tb, (int64_t)m - i_lo);
+                    int32_t best = F + Bv;
+                    for (int64_t i = i_lo; i < i_hi; i++) {
+                        // F(i+1) = F(i) + dv_f(row i+1); B(i+1) = B(i) - dv_b(row m-i)
+                        const int64_t rf_ = i + 1 - 64 * k0f - 1;          // 0-based bit in forward window
+                        const int64_t rb_ = (int64_t)m - i - 64 * k0b - 1;   // 0-based bit in backward window
+                        const uint64_t fp = rf[(size_t)(2 * (rf_ >> 6)) * T_], fm = rf[(size_t)(2 * (rf_ >> 6) + 1) * T_];
+                        const uint64_t bp = rb[(size_t)(2 * (rb_ >> 6)) * T_], bm = rb[(size_t)(2 * (rb_ >> 6) + 1) * T_];
+                        F += (int32_t)((fp >> (rf_ & 63)) & 1ull) - (int32_t)((fm >> (rf_ & 63)) & 1ull);
+                        Bv -= (int32_t)((bp >> (rb_ & 63)) & 1ull) - (int32_t)((bm >> (rb_ & 63)) & 1ull);
+                        best = min(best, F + Bv);
+                    }
+                    pass = best <= K;
+                }
+            }
+        }
+        if (valid && !rev) flags[p] = pass ? 1 : 0;
+        if (valid && work) {
+            if (!rev) atomicAdd(&work[0], band_cells(m, n, K));
+            atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+        }
+        __syncwarp(pmask);
+    }
+}
+
+template <int W1, int B>
+static cudaError_t launch_bd(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
+                             uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
+                             uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
+    const int threads = warps * 32;
+    const int R = W1 + 1;
+    const size_t per_thread = (size_t)(alpha * R > 2 * W1 + 2 ? alpha * R : 2 * W1 + 2) * sizeof(uint64_t);
+    const size_t smem = per_thread * threads;
+    cudaError_t e = cudaFuncSetAttribute(verify_bd_kernel<W1, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_bd_kernel<W1, B>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t pairs_per_block = threads / 2;
+    int64_t blocks = (np + pairs_per_block - 1) / pairs_per_block;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    verify_bd_kernel<W1, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
+                                                                     flags, err, work);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Configuration
 // ---------------------------------------------------------------------------
@@ -682,12 +1070,22 @@ static int32_t peq_words(int64_t max_len, int32_t K, int W) {
 
 size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_t K) {
     if (c.G == 1) return (size_t)c.warps * 32 * alpha * (c.V + 2) * sizeof(uint64_t);
+    if (c.G == 2) {
+        const size_t per = (size_t)(alpha * (c.V + 1) > (uint32_t)(2 * c.V + 2) ? alpha * (c.V + 1) : 2 * c.V + 2);
+        return (size_t)c.warps * 32 * per * sizeof(uint64_t);
+    }
     const int W = c.G * c.V;
     return (size_t)c.warps * (32 / c.G) * alpha * (size_t)peq_words(max_len, K, W) * sizeof(uint64_t);
 }
 
 VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
     const int W = words_needed(K);
+    if (W + 1 <= 12) {
+        // forward/backward halves, block-aligned window of W+1 words per lane
+        VerifyConfig c{2, W + 1, 4};
+        while (c.warps > 1 && verify_smem_bytes(c, alpha, max_len, K) > 100 * 1024) c.warps >>= 1;
+        if (verify_smem_bytes(c, alpha, max_len, K) <= 200 * 1024) return c;
+    }
     if (W <= 8) {
         // one lane per pair, the window in registers, a Peq ring in shared memory
         VerifyConfig c{1, W, 4};
@@ -699,7 +1097,7 @@ VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
     int best_words = 1 << 30;
     bool best_fit = false;
     for (int V = 4; V >= 1; V--) {
-        int G = 2;
+        int G = 4;
         while (G * V < W && G < 32) G <<= 1;
         if (G * V < W) continue;
         VerifyConfig c{G, V, 1};
@@ -772,7 +1170,17 @@ cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *p
 #undef EJ_G1
         return cudaErrorInvalidValue;
     }
-    EJ_V(2, 1) EJ_V(2, 2) EJ_V(2, 3) EJ_V(2, 4)
+    if (c.G == 2) {
+#define EJ_BD(WW)                                                                                          \
+    if (c.V == WW) {                                                                                       \
+        if (B == 2)                                                                                        \
+            return launch_bd<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s); \
+        return launch_bd<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s);     \
+    }
+        EJ_BD(2) EJ_BD(3) EJ_BD(4) EJ_BD(5) EJ_BD(6) EJ_BD(7) EJ_BD(8) EJ_BD(9) EJ_BD(10) EJ_BD(11) EJ_BD(12)
+#undef EJ_BD
+        return cudaErrorInvalidValue;
+    }
     EJ_V(4, 1) EJ_V(4, 2) EJ_V(4, 3) EJ_V(4, 4)
     EJ_V(8, 1) EJ_V(8, 2) EJ_V(8, 3) EJ_V(8, 4)
     EJ_V(16, 1) EJ_V(16, 2) EJ_V(16, 3) EJ_V(16, 4)

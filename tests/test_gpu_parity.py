@@ -323,9 +323,12 @@ def test_verify_every_tiling_is_exact(ej, ctx, K, alphabet):
     pt = torch.from_numpy(arr.view(np.int64).copy()).to(DEV)
     tried = 0
     try:
+        W = (2 * K + 1 + 63) // 64
         for G in (1, 2, 4, 8, 16, 32):
-            for V in ((1, 2, 3, 4, 5, 6, 7, 8) if G == 1 else (1, 2, 3, 4)):
-                if 64 * G * V < 2 * K + 1 or G * V > 4 * max(1, (2 * K + 1 + 63) // 64):
+            Vs = {1: range(1, 9), 2: range(2, 13)}.get(G, range(1, 5))
+            for V in Vs:
+                cover = 64 * (V - 1) if G == 2 else 64 * G * V
+                if cover < 2 * K + 1 or G * V > 4 * max(1, W) + 2:
                     continue
                 ctx.set_verify_config(G, V, 0)
                 out = torch.empty_like(pt)
