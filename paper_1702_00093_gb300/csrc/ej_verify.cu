@@ -904,8 +904,9 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                     int slot = base + W1 - 1;
                     if (slot >= R) slot -= R;
                     bd_build<B, R>(ring, T_, slot, xc, m, k0 + W1 - 1, rev, alpha);
-                    // early exit: minimum over the window exceeds K
-                    int32_t run = 0, mn = 1 << 30;
+                    // early exit: minimum over the window exceeds K. Row 64*k0 (value T)
+                    // is still the top of the band at column j-1, so it takes part.
+                    int32_t run = 0, mn = 0;
 #pragma unroll
                     for (int v = 0; v < W1; v++) {
 #pragma unroll
