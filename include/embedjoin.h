@@ -58,9 +58,14 @@ typedef enum {
                                 count is written to the count out-pointer */
     EJ_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
     EJ_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    EJ_ERR_UNSUPPORTED = 6   /* valid request outside what the kernels support
+    EJ_ERR_UNSUPPORTED = 6,  /* valid request outside what the kernels support
                                 (e.g. a band wider than the verifier's limit) */
+    EJ_ERR_TOO_LARGE = 7     /* the request needs more scratch than the fixed
+                                array of ej_verify_noalloc holds */
 } ej_status;
+
+/* Size of the fixed device scratch array used by ej_verify_noalloc. */
+#define EJ_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
 /* Method parameters (Table 1; Alg. 2 and Alg. 3 inputs). */
 typedef struct {
@@ -220,6 +225,32 @@ int ej_lsh_candidates(ej_ctx *ctx, const ej_strings *strings, const ej_params *p
  */
 int ej_verify(ej_ctx *ctx, const ej_strings *strings, const ej_params *params,
               const uint64_t *pairs, int64_t n_pairs, uint64_t *out, int64_t *n_out, void *stream);
+
+/*
+ * ej_verify without any memory allocation (the paper has no counterpart; this
+ * is a deployment variant of the verification step).
+ *
+ * For callers that cannot let a library allocate: processes whose device memory
+ * is reserved up front by another allocator, and services that must not call
+ * cudaMalloc/cudaFree on their request path (those calls can synchronise the
+ * device). No context is needed; the call never allocates. Its scratch is one
+ * file-scope device array of EJ_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU
+ * which loads the library keeps until the process exits.
+ *  - strings->bytes, strings->offsets, pairs and out must be device memory;
+ *    params supplies K and the alphabet only; out holds n_pairs entries.
+ *  - Output and result are those of ej_verify (passing pairs in input order,
+ *    count in *n_out); the call synchronises `stream` before returning.
+ *  - Scratch needed: about 16 bytes per string, the packed codes (total bytes x
+ *    2/8 for alphabets of at most 4 symbols, else x 1) and 9 bytes per pair;
+ *    beyond EJ_NOALLOC_SCRATCH_BYTES the call returns EJ_ERR_TOO_LARGE.
+ *  - All calls share the array and it keeps the previous call's contents (the
+ *    call clears what must start at zero). Calls whose GPU work overlaps, on
+ *    different streams or host threads, race on it: serialise them.
+ *  - The first call on a device looks the array's address up
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ */
+int ej_verify_noalloc(const ej_strings *strings, const ej_params *params, const uint64_t *pairs,
+                      int64_t n_pairs, uint64_t *out, int64_t *n_out, void *stream);
 
 /*
  * The whole method (Algorithm 3 with Algorithm 2's preprocessing):

@@ -561,6 +561,7 @@ const char *ej_status_string(int status) {
         case EJ_ERR_CUDA: return "CUDA error";
         case EJ_ERR_TIMEOUT: return "device wait timed out";
         case EJ_ERR_UNSUPPORTED: return "unsupported configuration";
+        case EJ_ERR_TOO_LARGE: return "request exceeds the fixed scratch of ej_verify_noalloc";
         default: return "unknown status";
     }
 }

@@ -23,10 +23,12 @@ EJ_ERR_CAPACITY = 3
 EJ_ERR_CUDA = 4
 EJ_ERR_TIMEOUT = 5
 EJ_ERR_UNSUPPORTED = 6
+EJ_ERR_TOO_LARGE = 7
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
-            "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign"]
+            "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc"]
 
 
 class EJError(RuntimeError):
@@ -102,6 +104,9 @@ def lib():
         L.ej_set_test_tables.argtypes = [vp, vp, C.c_uint32, C.c_uint32, C.c_uint32, vp,
                                          C.c_uint32, C.c_uint32]
         L.ej_set_test_tables.restype = C.c_int
+        L.ej_verify_noalloc.argtypes = [C.POINTER(_Strings), C.POINTER(_Params), vp, i64, vp,
+                                        C.POINTER(i64), vp]
+        L.ej_verify_noalloc.restype = C.c_int
         L.ej_embed_sign.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), vp, vp]
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
@@ -297,6 +302,23 @@ class Context:
             0 if pi_a is None else pi_a.shape[2], _ptr(pos_a),
             0 if pos_a is None else pos_a.shape[1], 0 if pos_a is None else pos_a.shape[2])
         self._check(st, "ej_set_test_tables")
+
+
+def verify_noalloc(s: Strings, p: Params, pairs, out, stream=None) -> int:
+    """ej_verify_noalloc: verification that allocates nothing (device arrays only).
+
+    For callers whose device memory is reserved by another allocator or who must
+    not trigger cudaMalloc/cudaFree on their request path. Returns the number of
+    passing pairs written to `out`; raises EJError on failure (EJ_ERR_TOO_LARGE
+    when the request does not fit the library's fixed 64 MiB scratch array).
+    """
+    cs, (cp, _keep) = s._c(), p._c()
+    n = C.c_int64(0)
+    st = lib().ej_verify_noalloc(C.byref(cs), C.byref(cp), _ptr(pairs), int(pairs.shape[0]), _ptr(out),
+                                 C.byref(n), _stream(stream))
+    if st != EJ_OK:
+        raise EJError(st, f"ej_verify_noalloc: {lib().ej_status_string(st).decode()}")
+    return n.value
 
 
 def decode_embedding(emb_words: np.ndarray, walk_end: np.ndarray, r: int, n: int, out_len: int,
