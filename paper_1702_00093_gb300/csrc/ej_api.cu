@@ -325,7 +325,7 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
     CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_inj, pos, s));
     if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z) > 0) {
         uint32_t *tsym = nullptr, *spos = nullptr, *stag = nullptr;
-        CKS(ensure_t(ctx, B_TSYM, (size_t)p->r * p->alphabet_size * (pl.L / 32 + 1), &tsym));
+        CKS(ensure_t(ctx, B_TSYM, symbol_table_words(p->r, p->alphabet_size, pl.L), &tsym));
         CKS(ensure_t(ctx, B_SPOS, (size_t)p->r * p->m * p->z, &spos));
         CKS(ensure_t(ctx, B_STAG, (size_t)p->r * p->m * p->z, &stag));
         CK(launch_symbol_table(p->seed, p->r, pl.L, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,

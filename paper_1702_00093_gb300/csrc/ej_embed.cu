@@ -369,10 +369,12 @@ cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n,
 // its function f, kept in shared memory per thread, so the embedded string is
 // never written.
 
+__host__ __device__ __forceinline__ uint32_t sym_words(uint32_t L) { return L / 32 + 2; }
+
 __global__ void symbol_table_kernel(uint64_t base, uint32_t r, uint32_t L, const uint8_t *__restrict__ alphabet,
                                     uint32_t alpha, const uint8_t *__restrict__ pi, uint32_t inject_steps,
                                     uint32_t *__restrict__ tsym) {
-    const uint32_t LW = L / 32 + 1;
+    const uint32_t LW = sym_words(L);
     const uint64_t total = (uint64_t)r * alpha * LW;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
@@ -395,13 +397,15 @@ __global__ void symbol_table_kernel(uint64_t base, uint32_t r, uint32_t L, const
 cudaError_t launch_symbol_table(uint64_t seed, uint32_t r, uint32_t L, const uint8_t *alphabet_dev,
                                 uint32_t alpha, const uint8_t *pi_inject, uint32_t inject_steps,
                                 uint32_t *tsym, cudaStream_t s) {
-    const uint64_t total = (uint64_t)r * alpha * (L / 32 + 1);
+    const uint64_t total = (uint64_t)r * alpha * sym_words(L);
     uint64_t g = (total + 255) / 256;
     symbol_table_kernel<<<(unsigned)(g > 4096 ? 4096 : (g ? g : 1)), 256, 0, s>>>(
         mix64(seed), r, L, alphabet_dev, alpha, pi_inject, inject_steps, tsym);
     note_launches(1);
     return cudaGetLastError();
 }
+
+size_t symbol_table_words(uint32_t r, uint32_t alpha, uint32_t L) { return (size_t)r * alpha * sym_words(L); }
 
 // One block per embedding: rank every sample by (step, index).
 __global__ void sort_samples_kernel(const uint32_t *__restrict__ pos, uint32_t m, uint32_t z,
@@ -432,9 +436,54 @@ constexpr int ES_THREADS = 128;
 size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
     const size_t M = (size_t)m * z;
     if (M > 16384 || z > 65535 || m > 65535) return 0;
-    const size_t bytes = (size_t)alpha * (L / 32 + 1) * 4 + M * 8 + (size_t)z * 8 + (size_t)m * ES_THREADS * 8;
+    const size_t bytes = (size_t)alpha * sym_words(L) * 4 + (M + 1) * 8 + (size_t)z * 8 +
+                         (size_t)m * ES_THREADS * 8;
     return bytes <= 200 * 1024 ? bytes : 0;
 }
+
+// Codes of one string, 64 bits at a time. Every string starts on a chunk
+// boundary and the walk consumes exactly one symbol per loop iteration, so all
+// lanes of a warp refill at the same iteration.
+template <int B>
+struct WordReader {
+    const uint4 *p;
+    const uint4 *end;
+    uint64_t w;          // current symbol in the low B bits
+    uint4 cur, nxt;
+    int left;
+    bool hi_next;        // the upper half of cur is still to be consumed
+    __device__ __forceinline__ uint4 fetch() {
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 v = (p < end) ? *p : zero;
+        p += (p < end);
+        return v;
+    }
+    __device__ __forceinline__ void init(const uint4 *base, int64_t nchunks) {
+        p = base;
+        end = base + nchunks;
+        cur = fetch();
+        nxt = fetch();
+        w = ((uint64_t)cur.y << 32) | cur.x;
+        hi_next = true;
+        left = 64 / B;
+    }
+    __device__ __forceinline__ uint32_t code() const { return (uint32_t)w & ((1u << B) - 1u); }
+    __device__ __forceinline__ void advance() {
+        w >>= B;
+        if (--left == 0) {
+            left = 64 / B;
+            if (hi_next) {
+                w = ((uint64_t)cur.w << 32) | cur.z;
+                hi_next = false;
+            } else {
+                cur = nxt;
+                nxt = fetch();
+                w = ((uint64_t)cur.y << 32) | cur.x;
+                hi_next = true;
+            }
+        }
+    }
+};
 
 template <int B>
 __global__ void __launch_bounds__(ES_THREADS)
@@ -443,22 +492,22 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                   uint32_t alpha, const uint32_t *__restrict__ tsym, const uint32_t *__restrict__ spos,
                   const uint32_t *__restrict__ stag, uint64_t *__restrict__ keys) {
     extern __shared__ uint64_t es_smem[];
-    const uint32_t l = blockIdx.y, M = m * z, LW = L / 32 + 1;
+    const uint32_t l = blockIdx.y, M = m * z, LW = sym_words(L);
     uint64_t *s_key = es_smem;                              // [m][ES_THREADS]
     uint64_t *s_pow = s_key + (size_t)m * ES_THREADS;        // [z]
-    uint32_t *s_pos = (uint32_t *)(s_pow + z);               // [M]
-    uint32_t *s_tag = s_pos + M;                             // [M]
-    uint32_t *s_tab = s_tag + M;                             // [alpha][LW]
-    for (uint32_t i = threadIdx.x; i < M; i += blockDim.x) {
-        s_pos[i] = spos[(size_t)l * M + i];
-        s_tag[i] = stag[(size_t)l * M + i];
+    uint32_t *s_pos = (uint32_t *)(s_pow + z);               // [M+1], sentinel at M
+    uint32_t *s_tag = s_pos + M + 1;                         // [M+1]
+    uint32_t *s_tab = s_tag + M + 1;                         // [alpha][LW]
+    for (uint32_t i = threadIdx.x; i <= M; i += blockDim.x) {
+        s_pos[i] = i < M ? spos[(size_t)l * M + i] : 0xFFFFFFFFu;
+        s_tag[i] = i < M ? stag[(size_t)l * M + i] : 0u;
     }
     for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
     if (threadIdx.x == 0) {
-        uint64_t p = 1;
+        uint64_t pw = 1;
         for (uint32_t q = 0; q < z; q++) {
-            s_pow[q] = p;
-            p *= (uint64_t)alpha + 1;
+            s_pow[q] = pw;
+            pw *= (uint64_t)alpha + 1;
         }
     }
     for (uint32_t f = 0; f < m; f++) s_key[(size_t)f * ES_THREADS + threadIdx.x] = 0ull;
@@ -466,26 +515,38 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
 
     const int64_t s = (int64_t)blockIdx.x * ES_THREADS + threadIdx.x;
     const int32_t len = s < n ? lens[s] : 0;
-    SymReader<B> rd;
+    WordReader<B> rd;
     rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
     uint64_t *my = s_key + threadIdx.x;
-    uint32_t k = 0;          // next sample (in step order)
-    uint32_t a = 0;          // step at which the walk arrives at x[i]
+    uint32_t k = 0;                          // next sample (in step order)
+    uint32_t ps = s_pos[0], tg = s_tag[0];   // its step and tag (f << 16 | q)
+    uint32_t a = 0;                          // step at which the walk arrives at x[i]
     int32_t i = 0;
-    while (k < M && i < len) {
+    while (i < len && k < M) {
         const uint32_t c = rd.code();
         const uint32_t *row = s_tab + c * LW;
-        uint32_t aa = a;
-        uint32_t w = row[aa >> 5] >> (aa & 31u);
-        while (w == 0u) {    // ends at the sentinel bits (steps >= L)
-            aa = (aa | 31u) + 1u;
-            w = row[aa >> 5];
+        const uint32_t wi = a >> 5;
+        const uint64_t w = (((uint64_t)row[wi + 1] << 32) | row[wi]) >> (a & 31u);
+        uint32_t a_next;
+        if (w != 0ull) {
+            a_next = a + (uint32_t)__ffsll((long long)w);   // first step with pi = 1, plus one
+        } else {                                            // rare: 33+ zero bits in a row
+            uint32_t j2 = wi + 2;
+            uint32_t v = row[j2];
+            while (v == 0u) v = row[++j2];                  // ends at the sentinel word
+            a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
         }
-        const uint32_t a_next = aa + (uint32_t)__ffs((int)w);   // next1 + 1
-        while (k < M && s_pos[k] < a_next) {
-            const uint32_t tag = s_tag[k];
-            my[(size_t)(tag >> 16) * ES_THREADS] += (uint64_t)c * s_pow[tag & 0xFFFFu];
+        // samples inside [a, a_next) read x[i]: one predicated update, a loop for more
+        const bool hit = ps < a_next;
+        my[(size_t)(tg >> 16) * ES_THREADS] += hit ? (uint64_t)c * s_pow[tg & 0xFFFFu] : 0ull;
+        k += hit ? 1u : 0u;
+        ps = s_pos[k];
+        tg = s_tag[k];
+        while (ps < a_next) {
+            my[(size_t)(tg >> 16) * ES_THREADS] += (uint64_t)c * s_pow[tg & 0xFFFFu];
             k++;
+            ps = s_pos[k];
+            tg = s_tag[k];
         }
         a = a_next;
         i++;

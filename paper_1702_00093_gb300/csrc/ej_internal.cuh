@@ -135,10 +135,11 @@ cudaError_t launch_sign(const uint32_t *emb, const int32_t *walk_end, int64_t n,
 
 // Fused embed + sign (arrival form of Alg. 1 restricted to the sampled steps).
 // Per-symbol step bitmaps [r][alpha][LW]: bit b of word w = pi_{32w+b}(alphabet[c])
-// for steps < L, 1 for steps >= L (sentinel); LW = L/32 + 1.
+// for steps < L, 1 for steps >= L (sentinel); LW = L/32 + 2.
 cudaError_t launch_symbol_table(uint64_t seed, uint32_t r, uint32_t L, const uint8_t *alphabet_dev,
                                 uint32_t alpha, const uint8_t *pi_inject, uint32_t inject_steps,
                                 uint32_t *tsym, cudaStream_t s);
+size_t symbol_table_words(uint32_t r, uint32_t alpha, uint32_t L);
 // Sampled steps of every embedding sorted by step: spos/stag [r][m*z], tag = f<<16 | q.
 cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uint32_t z, uint32_t *spos,
                                 uint32_t *stag, cudaStream_t s);
