@@ -26,6 +26,7 @@ enum BufId {
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
+    B_HASH, B_APP, B_JCOUNT,
     B_NUM
 };
 
@@ -56,6 +57,8 @@ struct ej_ctx {
     // pinned host counters
     int64_t *h_cnt = nullptr;
     cudaEvent_t ev[6] = {};
+    // raw-pair capacity remembered from the previous join (grows on overflow)
+    uint64_t raw_cap_hint = 0;
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
     // cached alphabet
@@ -371,16 +374,12 @@ int bits_for(uint64_t maxval) {
     return b;
 }
 
-// Candidates from keys [T][n] on the device. Result: sorted unique pairs in
-// *cand (context buffer B_CAND), count in *ncand.
-int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t **cand,
-                   int64_t *ncand, int64_t *nraw, int64_t *maxb, cudaStream_t s) {
+// Records (key, id) of every table, sorted by key with ties in (length, id)
+// order: the layout both candidate paths start from.
+int sorted_records(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys,
+                   const uint64_t **out_rk, const uint32_t **out_rid, cudaStream_t s) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
-    *ncand = 0; *nraw = 0; *maxb = 0;
-    *cand = nullptr;
-    if (n < 2) return EJ_OK;
-    // scratch for radix + scans
-    const size_t rs_len = radix_counts_len(n, T) > radix_counts_len(n, 1) ? radix_counts_len(n, T) : radix_counts_len(n, 1);
+    const size_t rs_len = radix_counts_len(n, T);
     uint32_t *rs_counts = nullptr;
     uint64_t *rs_offs = nullptr;
     void *scan_tmp = nullptr;
@@ -415,8 +414,28 @@ int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
     np = 0;
     for (int b = 0; b < key_bits(p); b += 8) shifts[np++] = b;
     CK(radix_sort_segmented(rk, rid, rk2, rid2, n, T, shifts, np, rt, &alt, s));
-    const uint64_t *srk = alt ? rk2 : rk;
-    const uint32_t *srid = alt ? rid2 : rid;
+    *out_rk = alt ? rk2 : rk;
+    *out_rid = alt ? rid2 : rid;
+    return EJ_OK;
+}
+
+// Candidates from keys [T][n] on the device (sort-based, sorted unique output).
+// Result: sorted unique pairs in *cand (context buffer B_CAND), count in *ncand.
+int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t **cand,
+                   int64_t *ncand, int64_t *nraw, int64_t *maxb, cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+    *ncand = 0; *nraw = 0; *maxb = 0;
+    *cand = nullptr;
+    if (n < 2) return EJ_OK;
+    const uint64_t *srk = nullptr;
+    const uint32_t *srid = nullptr;
+    CKS(sorted_records(ctx, pl, p, keys, &srk, &srid, s));
+    int shifts[16];
+    int np = 0;
+    bool alt = false;
+    const size_t rs_len = radix_counts_len(n, T);
+    RadixTemp rt{(uint32_t *)ctx->bufs[B_RS_COUNTS].p, (uint64_t *)ctx->bufs[B_RS_OFFS].p, ctx->bufs[B_SCAN_TMP].p};
+    void *scan_tmp = ctx->bufs[B_SCAN_TMP].p;
     // 4. count partners per record, scan
     uint32_t *counts = nullptr;
     uint64_t *offs = nullptr;
@@ -473,13 +492,8 @@ int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
     return EJ_OK;
 }
 
-// Verify device pairs; passing pairs (input order) into `out_dev` if it has
-// room (capacity), count in *n_out. If out_dev is null only counts.
-int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *pairs, int64_t np,
-               uint64_t *out_dev, int64_t capacity, int64_t *n_out, cudaStream_t s,
-               uint64_t *work_out = nullptr) {
-    *n_out = 0;
-    if (np == 0) return EJ_OK;
+// Verifier tiling: the automatic choice, or the context's override if it covers the band.
+int pick_verify(ej_ctx *ctx, const ej_params *p, const Plan &pl, VerifyConfig *out) {
     VerifyConfig vc = verify_pick(p->K, p->alphabet_size, pl.max_len);
     const int64_t cover = ctx->vG == 2 ? 64ll * (ctx->vV - 1) : 64ll * ctx->vG * ctx->vV;
     if (ctx->vG > 0 && cover >= 2ll * p->K + 1) {
@@ -497,6 +511,19 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     if (vc.G == 0)
         return fail(ctx, EJ_ERR_UNSUPPORTED, "no verifier configuration for K=%d, alphabet %u, max length %lld",
                     p->K, p->alphabet_size, (long long)pl.max_len);
+    *out = vc;
+    return EJ_OK;
+}
+
+// Verify device pairs; passing pairs (input order) into `out_dev` if it has
+// room (capacity), count in *n_out. If out_dev is null only counts.
+int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *pairs, int64_t np,
+               uint64_t *out_dev, int64_t capacity, int64_t *n_out, cudaStream_t s,
+               uint64_t *work_out = nullptr) {
+    *n_out = 0;
+    if (np == 0) return EJ_OK;
+    VerifyConfig vc;
+    CKS(pick_verify(ctx, p, pl, &vc));
     uint8_t *fl = nullptr;
     uint64_t *fo = nullptr;
     CKS(ensure_t(ctx, B_FLAGS, (size_t)np, &fl));
@@ -507,9 +534,9 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     CK(cudaMemsetAsync(derr, 0, 4, s));
     CK(cudaMemsetAsync(dcnt + 4, 0, 2 * sizeof(uint64_t), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
-    CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, pl.st.n,
-                     p->alphabet_size, pairs, np, p->K, pl.max_len, fl, derr,
-                     (unsigned long long *)(dcnt + 4), s));
+    VerifyOut vo{fl, nullptr, nullptr, 0, nullptr, derr, (unsigned long long *)(dcnt + 4)};
+    CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, pl.st.n, p->alphabet_size, pairs, np, p->K,
+                     pl.max_len, vo, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
     void *tmp = nullptr;
     CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(np), &tmp));
@@ -528,6 +555,91 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     if (!out_dev) return EJ_OK;
     if (cnt > capacity) return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt, (long long)capacity);
     CK(launch_compact_u64(pairs, fl, fo, np, out_dev, s));
+    return EJ_OK;
+}
+
+// ej_join's back half without host round trips between stages: bucket windows
+// append pairs, a device hash set keeps the first copy of each pair, the
+// verifier reads the candidate count from the device and appends passing pairs,
+// and only the output is sorted. The host reads the counters once, after the
+// verifier; if the raw pairs outgrew the capacity it enlarges it and reruns
+// from the append step (the sorted records are kept).
+int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t *out,
+              int64_t capacity, int64_t *n_out, ej_join_stats *stats, cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+    const uint64_t *srk = nullptr;
+    const uint32_t *srid = nullptr;
+    CKS(sorted_records(ctx, pl, p, keys, &srk, &srid, s));
+    VerifyConfig vc;
+    CKS(pick_verify(ctx, p, pl, &vc));
+    unsigned long long *cnt = nullptr;
+    CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
+    uint32_t *derr = (uint32_t *)ctx->bufs[B_DERR].p;
+    uint64_t cap = ctx->raw_cap_hint ? ctx->raw_cap_hint : (uint64_t)(n * 4 > 65536 ? n * 4 : 65536);
+    uint64_t *raw = nullptr, *cand = nullptr, *table = nullptr, *app = nullptr;
+    unsigned long long hc[8];
+    for (int attempt = 0;; attempt++) {
+        uint64_t hsize = 1;
+        while (hsize < 2 * cap) hsize <<= 1;
+        CKS(ensure_t(ctx, B_RAW, (size_t)cap, &raw));
+        CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
+        CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
+        CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
+        CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(derr, 0, 4, s));
+        CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
+        CK(launch_emit_append(srk, srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
+        CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
+        VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4};
+        CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
+                         pl.max_len, vo, s));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, cnt, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt + 6, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(hc, ctx->h_cnt, sizeof hc);
+        if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+        if (hc[0] <= cap) break;
+        if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
+        cap = hc[0] + hc[0] / 4 + 1024;
+    }
+    ctx->raw_cap_hint = cap;
+    const int64_t cntout = (int64_t)hc[3];
+    if (stats) {
+        stats->n_raw_pairs = (int64_t)hc[0];
+        stats->max_bucket = (int64_t)hc[1];
+        stats->n_candidates = (int64_t)hc[2];
+        stats->n_out = cntout;
+        stats->band_cells = hc[4];
+        stats->verify_word_columns = hc[5];
+    }
+    *n_out = cntout;
+    if (cntout > capacity)
+        return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cntout, (long long)capacity);
+    if (cntout == 0) return EJ_OK;
+    // sort the output pairs
+    const uint64_t *sorted = app;
+    if (cntout <= small_sort_max()) {
+        CK(launch_small_sort(app, cnt + 3, (uint64_t)cntout, s));
+    } else {
+        const int nb = bits_for((uint64_t)(n - 1));
+        int shifts[16], np = 0;
+        for (int b = 0; b < nb; b += 8) shifts[np++] = b;
+        for (int b = 0; b < nb; b += 8) shifts[np++] = 32 + b;
+        const size_t rs2 = radix_counts_len(cntout, 1);
+        uint32_t *c2 = nullptr;
+        uint64_t *o2 = nullptr;
+        void *st2 = nullptr;
+        CKS(ensure_t(ctx, B_RS_COUNTS, rs2 > radix_counts_len(n, T) ? rs2 : radix_counts_len(n, T), &c2));
+        CKS(ensure_t(ctx, B_RS_OFFS, rs2 > radix_counts_len(n, T) ? rs2 : radix_counts_len(n, T), &o2));
+        CKS(ensure(ctx, B_SCAN_TMP, scan_temp_bytes((int64_t)rs2), &st2));
+        RadixTemp rt{c2, o2, st2};
+        bool alt = false;
+        CK(radix_sort_segmented(app, nullptr, raw, nullptr, cntout, 1, shifts, np, rt, &alt, s));
+        sorted = alt ? raw : app;
+    }
+    CK(cudaMemcpyAsync(out, sorted, (size_t)cntout * sizeof(uint64_t), cudaMemcpyDefault, s));
     return EJ_OK;
 }
 
@@ -797,7 +909,6 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     *n_out = 0;
     if (stats) memset(stats, 0, sizeof *stats);
     const int64_t launches0 = launches_so_far();
-    uint64_t work[2] = {0, 0};
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
@@ -807,40 +918,26 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     uint64_t *keys = nullptr;
     CKS(ensure_t(ctx, B_KEYS, (size_t)p->r * p->m * pl.st.n, &keys));
     CKS(keys_dev(ctx, p, pl, keys, s));
-    uint64_t *cand = nullptr;
-    int64_t nc = 0, raw = 0, mb = 0;
-    CKS(candidates_dev(ctx, pl, p, keys, &cand, &nc, &raw, &mb, s));
-    if (ctx->timing && nc == 0) CK(cudaEventRecord(ctx->ev[3], s));
+    if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
+    ej_join_stats st_local;
+    memset(&st_local, 0, sizeof st_local);
     int64_t cnt = 0;
-    void *d_out = nullptr;
-    bool h_out = false;
-    if (nc > 0) {
-        CKS(out_target(ctx, B_OUT_STAGE, out, (size_t)nc * sizeof(uint64_t), &d_out, &h_out));
-        int st = verify_dev(ctx, pl, p, cand, nc, (uint64_t *)d_out, h_out ? nc : capacity, &cnt, s, work);
-        if (st == EJ_ERR_CAPACITY) *n_out = cnt;
-        CKS(st);
-        if (cnt > capacity) {
-            *n_out = cnt;
-            return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt, (long long)capacity);
-        }
-        if (h_out && cnt) CK(cudaMemcpyAsync(out, d_out, (size_t)cnt * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    const int status = join_back(ctx, pl, p, keys, out, capacity, &cnt, &st_local, s);
+    *n_out = cnt;
+    if (status != EJ_OK) {
+        if (stats) *stats = st_local;
+        return status;
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[5], s));
     CK(cudaStreamSynchronize(s));
-    *n_out = cnt;
     if (stats) {
-        stats->n_raw_pairs = raw;
-        stats->n_candidates = nc;
-        stats->n_out = cnt;
-        stats->max_bucket = mb;
-        stats->band_cells = work[0];
-        stats->verify_word_columns = work[1];
+        *stats = st_local;
         stats->kernel_launches = launches_so_far() - launches0;
         if (ctx->timing) {
             cudaEventElapsedTime(&stats->ms_prepare, ctx->ev[0], ctx->ev[1]);
             cudaEventElapsedTime(&stats->ms_embed_sign, ctx->ev[1], ctx->ev[2]);
             cudaEventElapsedTime(&stats->ms_candidates, ctx->ev[2], ctx->ev[3]);
-            if (nc > 0) cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
+            cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
             cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[5]);
         }
     }

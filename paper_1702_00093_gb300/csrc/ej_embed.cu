@@ -436,9 +436,11 @@ constexpr int ES_THREADS = 128;
 size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
     const size_t M = (size_t)m * z;
     if (M > 16384 || z > 65535 || m > 65535) return 0;
-    const size_t bytes = (size_t)alpha * sym_words(L) * 4 + (M + 1) * 8 + (size_t)z * 8 +
-                         (size_t)m * ES_THREADS * 8;
-    return bytes <= 200 * 1024 ? bytes : 0;
+    // table, sorted steps (+ sentinel), rank of (f, q) in step order, powers,
+    // one code byte per sample and thread
+    const size_t bytes = (size_t)alpha * sym_words(L) * 4 + (M + 1) * 4 + M * 4 + (size_t)z * 8 +
+                         M * ES_THREADS;
+    return bytes <= 160 * 1024 ? bytes : 0;
 }
 
 // Codes of one string, 64 bits at a time. Every string starts on a chunk
@@ -493,14 +495,17 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                   const uint32_t *__restrict__ stag, uint64_t *__restrict__ keys) {
     extern __shared__ uint64_t es_smem[];
     const uint32_t l = blockIdx.y, M = m * z, LW = sym_words(L);
-    uint64_t *s_key = es_smem;                              // [m][ES_THREADS]
-    uint64_t *s_pow = s_key + (size_t)m * ES_THREADS;        // [z]
-    uint32_t *s_pos = (uint32_t *)(s_pow + z);               // [M+1], sentinel at M
-    uint32_t *s_tag = s_pos + M + 1;                         // [M+1]
-    uint32_t *s_tab = s_tag + M + 1;                         // [alpha][LW]
+    uint64_t *s_pow = es_smem;                                // [z]
+    uint32_t *s_pos = (uint32_t *)(s_pow + z);                // [M+1], sentinel at M
+    uint32_t *s_rank = s_pos + M + 1;                         // [M]: step-order index of sample f*z+q
+    uint32_t *s_tab = s_rank + M;                             // [alpha][LW]
+    uint8_t *s_code = (uint8_t *)(s_tab + (size_t)alpha * LW); // [M][ES_THREADS]
     for (uint32_t i = threadIdx.x; i <= M; i += blockDim.x) {
         s_pos[i] = i < M ? spos[(size_t)l * M + i] : 0xFFFFFFFFu;
-        s_tag[i] = i < M ? stag[(size_t)l * M + i] : 0u;
+        if (i < M) {
+            const uint32_t tag = stag[(size_t)l * M + i];
+            s_rank[(tag >> 16) * z + (tag & 0xFFFFu)] = i;
+        }
     }
     for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
     if (threadIdx.x == 0) {
@@ -510,55 +515,55 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
             pw *= (uint64_t)alpha + 1;
         }
     }
-    for (uint32_t f = 0; f < m; f++) s_key[(size_t)f * ES_THREADS + threadIdx.x] = 0ull;
     __syncthreads();
 
     const int64_t s = (int64_t)blockIdx.x * ES_THREADS + threadIdx.x;
     const int32_t len = s < n ? lens[s] : 0;
     WordReader<B> rd;
     rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
-    uint64_t *my = s_key + threadIdx.x;
+    uint8_t *my = s_code + threadIdx.x;
     uint32_t k = 0;                          // next sample (in step order)
-    uint32_t ps = s_pos[0], tg = s_tag[0];   // its step and tag (f << 16 | q)
+    uint32_t ps = s_pos[0];                  // its step
     uint32_t a = 0;                          // step at which the walk arrives at x[i]
     int32_t i = 0;
     while (i < len && k < M) {
         const uint32_t c = rd.code();
-        const uint32_t *row = s_tab + c * LW;
-        const uint32_t wi = a >> 5;
-        const uint64_t w = (((uint64_t)row[wi + 1] << 32) | row[wi]) >> (a & 31u);
+        const uint32_t *row = s_tab + c * LW + (a >> 5);
+        const uint32_t sh = a & 31u;
+        const uint32_t lo = __funnelshift_r(row[0], row[1], sh);   // steps a .. a+31
         uint32_t a_next;
-        if (w != 0ull) {
-            a_next = a + (uint32_t)__ffsll((long long)w);   // first step with pi = 1, plus one
-        } else {                                            // rare: 33+ zero bits in a row
-            uint32_t j2 = wi + 2;
-            uint32_t v = row[j2];
-            while (v == 0u) v = row[++j2];                  // ends at the sentinel word
-            a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
+        if (lo != 0u) {
+            a_next = a + (uint32_t)__ffs((int)lo);   // first step with pi = 1, plus one
+        } else {
+            const uint32_t hi = row[1] >> sh;           // steps a+32 .. (word end)
+            if (hi != 0u) {
+                a_next = a + 32u + (uint32_t)__ffs((int)hi);
+            } else {                                    // rare: a longer run of zeros
+                uint32_t j2 = (a >> 5) + 2;
+                uint32_t v = s_tab[c * LW + j2];
+                while (v == 0u) v = s_tab[c * LW + (++j2)];   // ends at the sentinel word
+                a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
+            }
         }
-        // samples inside [a, a_next) read x[i]: one predicated update, a loop for more
-        const bool hit = ps < a_next;
-        my[(size_t)(tg >> 16) * ES_THREADS] += hit ? (uint64_t)c * s_pow[tg & 0xFFFFu] : 0ull;
-        k += hit ? 1u : 0u;
-        ps = s_pos[k];
-        tg = s_tag[k];
+        // samples inside [a, a_next) read x[i]: store its code, one per step in order
         while (ps < a_next) {
-            my[(size_t)(tg >> 16) * ES_THREADS] += (uint64_t)c * s_pow[tg & 0xFFFFu];
-            k++;
-            ps = s_pos[k];
-            tg = s_tag[k];
+            my[(size_t)k * ES_THREADS] = (uint8_t)c;
+            ps = s_pos[++k];
         }
         a = a_next;
         i++;
         rd.advance();
     }
     // walk finished before the last sample: the rest read bottom
-    for (; k < M; k++) {
-        const uint32_t tag = s_tag[k];
-        my[(size_t)(tag >> 16) * ES_THREADS] += (uint64_t)alpha * s_pow[tag & 0xFFFFu];
+    for (; k < M; k++) my[(size_t)k * ES_THREADS] = (uint8_t)alpha;
+    if (s < n) {
+        for (uint32_t f = 0; f < m; f++) {
+            uint64_t key = 0;
+            for (uint32_t q = 0; q < z; q++)
+                key += (uint64_t)my[(size_t)s_rank[f * z + q] * ES_THREADS] * s_pow[q];
+            keys[((size_t)l * m + f) * n + s] = key;
+        }
     }
-    if (s < n)
-        for (uint32_t f = 0; f < m; f++) keys[((size_t)l * m + f) * n + s] = my[(size_t)f * ES_THREADS];
 }
 
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,

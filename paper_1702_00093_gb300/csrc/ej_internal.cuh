@@ -192,9 +192,34 @@ cudaError_t launch_unique_flags(const uint64_t *sorted, int64_t n, uint8_t *flag
 cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const uint64_t *offs,
                                int64_t n, uint64_t *out, cudaStream_t s);
 
+// Pipeline kernels (ej_pipeline.cu). counters: [0] raw pairs, [1] largest
+// bucket, [2] candidates, [3] output pairs, [4..5] verifier work.
+cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens, int64_t n,
+                               int64_t T, int32_t K, uint64_t *raw, uint64_t cap, unsigned long long *counters,
+                               cudaStream_t s);
+cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uint64_t hsize, uint64_t *cand,
+                         unsigned long long *counters, cudaStream_t s);
+int small_sort_max();
+cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Verification (ej_verify.cu)
 // ---------------------------------------------------------------------------
+
+// Where the verifier puts its results. Either flags[p] = pass for every pair
+// (input order), or, when app != nullptr, every passing pair is appended to
+// app[0 .. app_cap) with *app_count counting them (order unspecified).
+// np_dev (optional) holds the number of pairs on the device; the host-side
+// np is then only an upper bound used to size the grid.
+struct VerifyOut {
+    uint8_t *flags;
+    uint64_t *app;
+    unsigned long long *app_count;
+    uint64_t app_cap;
+    const unsigned long long *np_dev;
+    uint32_t *err;
+    unsigned long long *work;
+};
 
 struct VerifyConfig {
     int G;          // lanes per pair
@@ -210,6 +235,6 @@ size_t verify_smem_bytes(VerifyConfig c, uint32_t alpha, int64_t max_len, int32_
 cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *pofs, int B,
                           const int32_t *lens, int64_t n, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
-                          uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s);
+                          VerifyOut vo, cudaStream_t s);
 
 }  // namespace ej

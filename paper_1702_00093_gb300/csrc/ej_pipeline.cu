@@ -1,0 +1,205 @@
+// Back half of ej_join without host round trips: bucket windows append their
+// pairs, a device hash set removes duplicates (Alg. 3's deduplication), and the
+// verified output is sorted at the end. Counts stay on the device; the host
+// reads them once, after verification.
+#include "ej_internal.cuh"
+
+namespace ej {
+
+// Window of record p in its table (records sorted by key, then length): the
+// following records with the same key and length <= len_p + K.
+__device__ __forceinline__ int64_t pl_window_end(const uint64_t *__restrict__ rk, const uint32_t *__restrict__ rid,
+                                                 const int32_t *__restrict__ lens, int64_t p, int64_t n,
+                                                 uint64_t key, int64_t limit) {
+    auto pred = [&](int64_t q) { return rk[q] == key && (int64_t)lens[rid[q]] <= limit; };
+    if (p + 1 >= n || !pred(p + 1)) return p + 1;
+    int64_t good = p + 1, step = 1;
+    while (true) {
+        const int64_t nx = good + step;
+        if (nx < n && pred(nx)) {
+            good = nx;
+            step <<= 1;
+        } else {
+            break;
+        }
+    }
+    int64_t lo = good, hi = min(good + step, n);
+    while (hi - lo > 1) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (pred(mid)) lo = mid; else hi = mid;
+    }
+    return lo + 1;
+}
+
+// counters: [0] raw pairs emitted (may exceed cap), [1] largest bucket
+__global__ void emit_append_kernel(const uint64_t *__restrict__ rec_keys, const uint32_t *__restrict__ rec_ids,
+                                   const int32_t *__restrict__ lens, int64_t n, int64_t T, int32_t K,
+                                   uint64_t *__restrict__ raw, uint64_t cap,
+                                   unsigned long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = n * T;
+    unsigned long long mb = 0;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // every lane runs the same number of iterations so the warp collectives converge
+    const int64_t iters = (total + step - 1) / step;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t i = start + it * step;
+        int64_t cnt = 0, t = 0, p = 0;
+        uint32_t a = 0;
+        if (i < total) {
+            t = i / n;
+            p = i - t * n;
+            const uint64_t *rk = rec_keys + t * n;
+            const uint32_t *rid = rec_ids + t * n;
+            const uint64_t key = rk[p];
+            a = rid[p];
+            cnt = pl_window_end(rk, rid, lens, p, n, key, (int64_t)lens[a] + K) - p - 1;
+            if (cnt > 0 && (p == 0 || rk[p - 1] != key)) {
+                int64_t e = p + 1;
+                while (e < n && rk[e] == key) e++;   // bucket size (stats only, first record of a run)
+                mb = max(mb, (unsigned long long)(e - p));
+            }
+        }
+        // warp-aggregated reservation
+        unsigned long long incl = (unsigned long long)cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+        unsigned long long base = 0;
+        if (wtotal) {
+            if (lane == 31) base = atomicAdd(&counters[0], wtotal);
+            base = __shfl_sync(FULL, base, 31);
+        }
+        if (cnt > 0) {
+            uint64_t o = base + incl - (unsigned long long)cnt;
+            const uint32_t *rid = rec_ids + t * n;
+            for (int64_t q = p + 1; q <= p + cnt; q++, o++) {
+                if (o < cap) {
+                    const uint32_t b = rid[q];
+                    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                    raw[o] = (lo << 32) | hi;
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(FULL, mb, o);
+        mb = v > mb ? v : mb;
+    }
+    if (lane == 0 && mb) atomicMax(&counters[1], mb);
+}
+
+cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens, int64_t n,
+                               int64_t T, int32_t K, uint64_t *raw, uint64_t cap, unsigned long long *counters,
+                               cudaStream_t s) {
+    const int64_t total = n * T;
+    if (total > 0) {
+        int64_t g = (total + 255) / 256;
+        emit_append_kernel<<<(unsigned)(g > 16384 ? 16384 : g), 256, 0, s>>>(rec_keys, rec_ids, lens, n, T, K, raw,
+                                                                               cap, counters);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ uint64_t pair_hash(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Insert raw pairs into an open-addressing set of `hsize` (power of two,
+// >= 2 * count) slots pre-filled with ~0; the first copy of every pair is
+// appended to cand. counters: [0] raw count (read), [2] candidates (written).
+__global__ void dedup_kernel(const uint64_t *__restrict__ raw, uint64_t cap, uint64_t *__restrict__ table,
+                             uint64_t hsize, uint64_t *__restrict__ cand, unsigned long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nraw_all = counters[0];
+    const int64_t nraw = (int64_t)(nraw_all < cap ? nraw_all : cap);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iters = (nraw + step - 1) / step;
+    const uint64_t EMPTY = ~0ull;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t i = start + it * step;
+        bool is_new = false;
+        uint64_t key = 0;
+        if (i < nraw) {
+            key = raw[i];
+            uint64_t h = pair_hash(key) & (hsize - 1);
+            for (uint64_t probe = 0; probe < hsize; probe++) {
+                const unsigned long long old = atomicCAS((unsigned long long *)&table[h], EMPTY, key);
+                if (old == EMPTY) {
+                    is_new = true;
+                    break;
+                }
+                if (old == key) break;
+                h = (h + 1) & (hsize - 1);
+            }
+        }
+        const unsigned mask = __ballot_sync(FULL, is_new);
+        unsigned long long base = 0;
+        if (mask) {
+            if (lane == 0) base = atomicAdd(&counters[2], (unsigned long long)__popc(mask));
+            base = __shfl_sync(FULL, base, 0);
+        }
+        if (is_new) cand[base + __popc(mask & ((1u << lane) - 1u))] = key;
+    }
+}
+
+cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uint64_t hsize, uint64_t *cand,
+                         unsigned long long *counters, cudaStream_t s) {
+    int64_t g = ((int64_t)cap + 255) / 256;
+    dedup_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hsize, cand, counters);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Sorts up to SMALL_SORT_MAX uint64 keys in one block (bitonic network in
+// shared memory); the count comes from the device.
+constexpr int SMALL_SORT_MAX = 8192;
+
+__global__ void __launch_bounds__(1024)
+small_sort_kernel(uint64_t *__restrict__ a, const unsigned long long *__restrict__ count_dev, uint64_t n_cap) {
+    __shared__ uint64_t s[SMALL_SORT_MAX];
+    const unsigned long long c = *count_dev;
+    const int n = (int)(c < n_cap ? c : n_cap);
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < n ? a[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = s[i], y = s[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        s[i] = y;
+                        s[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = s[i];
+}
+
+int small_sort_max() { return SMALL_SORT_MAX; }
+
+cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s) {
+    small_sort_kernel<<<1, 1024, 0, s>>>(a, count_dev, n_cap > (uint64_t)SMALL_SORT_MAX ? SMALL_SORT_MAX : n_cap);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace ej

@@ -38,6 +38,19 @@ namespace ej {
 
 constexpr int VERIFY_MAX_THREADS = 256;
 
+__device__ __forceinline__ void emit_result(const VerifyOut &vo, int64_t p, const uint64_t *__restrict__ pairs,
+                                            bool pass) {
+    if (vo.app) {
+        if (pass) {
+            const unsigned long long idx = atomicAdd(vo.app_count, 1ull);
+            if (idx < vo.app_cap) vo.app[idx] = pairs[p];
+        }
+    } else {
+        vo.flags[p] = pass ? 1 : 0;
+    }
+}
+
+
 __device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t sh) {
     return sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
 }
@@ -175,8 +188,13 @@ __global__ void __launch_bounds__(VERIFY_MAX_THREADS)
 verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
               const int32_t *__restrict__ lens, int64_t n_str,
               uint32_t alpha, const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t Lw,
-              uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
-              unsigned long long *__restrict__ work) {
+              VerifyOut vo) {
+    uint32_t *__restrict__ err = vo.err;
+    unsigned long long *__restrict__ work = vo.work;
+    if (vo.np_dev) {
+        const int64_t dn = (int64_t)*vo.np_dev;
+        np = dn < np ? dn : np;
+    }
     constexpr int GPW = 32 / G;
     const int32_t w_min = (2 * K + 1 + 63) / 64;
     extern __shared__ uint64_t smem[];
@@ -453,7 +471,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
             if (!decided) pass = (T0 + cnt) <= K;
         }
         if (valid && gl == 0) {
-            flags[p] = pass ? 1 : 0;
+            emit_result(vo, p, pairs, pass);
             if (work) {
                 atomicAdd(&work[0], band_cells(mlen, nlen, K));
                 atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
@@ -481,8 +499,13 @@ __global__ void __launch_bounds__(VG1_MAX_THREADS)
 verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
                  const uint64_t *__restrict__ pairs, int64_t np, int32_t K,
-                 uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
-                 unsigned long long *__restrict__ work) {
+                 VerifyOut vo) {
+    uint32_t *__restrict__ err = vo.err;
+    unsigned long long *__restrict__ work = vo.work;
+    if (vo.np_dev) {
+        const int64_t dn = (int64_t)*vo.np_dev;
+        np = dn < np ? dn : np;
+    }
     constexpr int R = W + 2;
     extern __shared__ uint64_t smem[];
     __shared__ int8_t s_nsum[256];
@@ -666,7 +689,7 @@ verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 pass = (T + cnt) <= K;
             }
         }
-        flags[p] = pass ? 1 : 0;
+        emit_result(vo, p, pairs, pass);
         if (work) {
             atomicAdd(&work[0], band_cells(mrows, ncols, K));
             atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
@@ -677,7 +700,7 @@ verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
 template <int W, int B>
 static cudaError_t launch_g1(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                              uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
-                             uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
+                             VerifyOut vo, cudaStream_t s) {
     const int threads = warps * 32;
     const size_t smem = (size_t)alpha * (W + 2) * sizeof(uint64_t) * threads;
     cudaError_t e = cudaFuncSetAttribute(verify_g1_kernel<W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -693,7 +716,7 @@ static cudaError_t launch_g1(const uint4 *packed, const uint64_t *pofs, const in
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     verify_g1_kernel<W, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
-                                                                    flags, err, work);
+                                                                    vo);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -822,8 +845,13 @@ __global__ void __launch_bounds__(VBD_THREADS)
 verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
                  const uint64_t *__restrict__ pairs, int64_t np, int32_t K,
-                 uint8_t *__restrict__ flags, uint32_t *__restrict__ err,
-                 unsigned long long *__restrict__ work) {
+                 VerifyOut vo) {
+    uint32_t *__restrict__ err = vo.err;
+    unsigned long long *__restrict__ work = vo.work;
+    if (vo.np_dev) {
+        const int64_t dn = (int64_t)*vo.np_dev;
+        np = dn < np ? dn : np;
+    }
     constexpr int R = W1 + 1;
     extern __shared__ uint64_t smem[];
     __shared__ int8_t s_nsum[256];
@@ -1023,7 +1051,7 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 }
             }
         }
-        if (valid && !rev) flags[p] = pass ? 1 : 0;
+        if (valid && !rev) emit_result(vo, p, pairs, pass);
         if (valid && work) {
             if (!rev) atomicAdd(&work[0], band_cells(m, n, K));
             atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
@@ -1035,7 +1063,7 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
 template <int W1, int B>
 static cudaError_t launch_bd(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                              uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
-                             uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
+                             VerifyOut vo, cudaStream_t s) {
     const int threads = warps * 32;
     const int R = W1 + 1;
     const size_t per_thread = (size_t)(alpha * R > 2 * W1 + 2 ? alpha * R : 2 * W1 + 2) * sizeof(uint64_t);
@@ -1054,7 +1082,7 @@ static cudaError_t launch_bd(const uint4 *packed, const uint64_t *pofs, const in
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     verify_bd_kernel<W1, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
-                                                                     flags, err, work);
+                                                                     vo);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1124,8 +1152,7 @@ VerifyConfig verify_pick(int32_t K, uint32_t alpha, int64_t max_len) {
 template <int G, int V, int B>
 static cudaError_t launch_gv(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                              uint32_t alpha, const uint64_t *pairs, int64_t np,
-                             int32_t K, int64_t max_len, int warps, uint8_t *flags, uint32_t *err,
-                             unsigned long long *work, cudaStream_t s) {
+                             int32_t K, int64_t max_len, int warps, VerifyOut vo, cudaStream_t s) {
     const int32_t Lw = peq_words(max_len, K, G * V);
     const size_t smem = (size_t)warps * (32 / G) * alpha * Lw * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(verify_kernel<G, V, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1142,7 +1169,7 @@ static cudaError_t launch_gv(const uint4 *packed, const uint64_t *pofs, const in
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     verify_kernel<G, V, B><<<(unsigned)blocks, warps * 32, smem, s>>>(packed, pofs, lens, n, alpha,
-                                                                     pairs, np, K, Lw, flags, err, work);
+                                                                     pairs, np, K, Lw, vo);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1150,22 +1177,21 @@ static cudaError_t launch_gv(const uint4 *packed, const uint64_t *pofs, const in
 cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *pofs, int B,
                           const int32_t *lens, int64_t n, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
-                          uint8_t *flags, uint32_t *err, unsigned long long *work, cudaStream_t s) {
+                          VerifyOut vo, cudaStream_t s) {
     if (np == 0) return cudaGetLastError();
 #define EJ_V(GG, VV)                                                                                     \
     if (c.G == GG && c.V == VV) {                                                                        \
         if (B == 2)                                                                                      \
             return launch_gv<GG, VV, 2>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps,    \
-                                        flags, err, work, s);                                            \
-        return launch_gv<GG, VV, 8>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps, flags, \
-                                    err, work, s);                                                       \
+                                        vo, s);                                            \
+        return launch_gv<GG, VV, 8>(packed, pofs, lens, n, alpha, pairs, np, K, max_len, c.warps, vo, s); \
     }
     if (c.G == 1) {
 #define EJ_G1(WW)                                                                                         \
     if (c.V == WW) {                                                                                      \
         if (B == 2)                                                                                       \
-            return launch_g1<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s); \
-        return launch_g1<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s);     \
+            return launch_g1<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, vo, s); \
+        return launch_g1<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, vo, s);     \
     }
         EJ_G1(1) EJ_G1(2) EJ_G1(3) EJ_G1(4) EJ_G1(5) EJ_G1(6) EJ_G1(7) EJ_G1(8)
 #undef EJ_G1
@@ -1175,8 +1201,8 @@ cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *p
 #define EJ_BD(WW)                                                                                          \
     if (c.V == WW) {                                                                                       \
         if (B == 2)                                                                                        \
-            return launch_bd<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s); \
-        return launch_bd<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, flags, err, work, s);     \
+            return launch_bd<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, vo, s); \
+        return launch_bd<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, c.warps, vo, s);     \
     }
         EJ_BD(2) EJ_BD(3) EJ_BD(4) EJ_BD(5) EJ_BD(6) EJ_BD(7) EJ_BD(8) EJ_BD(9) EJ_BD(10) EJ_BD(11) EJ_BD(12)
 #undef EJ_BD
