@@ -379,6 +379,25 @@ int bits_for(uint64_t maxval) {
 int sorted_records(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys,
                    const uint64_t **out_rk, const uint32_t **out_rid, cudaStream_t s) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+    const int idb = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
+    if (n <= table_sort_max() && idb + key_bits(p) <= 64 && idb + bits_for((uint64_t)pl.max_len) <= 64) {
+        // every table fits one block: length order, then all tables, one block each
+        uint64_t *lk = nullptr, *lsorted = nullptr;
+        uint32_t *perm = nullptr;
+        CKS(ensure_t(ctx, B_LKEYS, (size_t)n, &lk));
+        CKS(ensure_t(ctx, B_LKEYS_ALT, (size_t)n, &lsorted));
+        CKS(ensure_t(ctx, B_PERM, (size_t)n, &perm));
+        CK(launch_len_keys(pl.lens, n, lk, s));
+        CK(launch_table_sort(lk, nullptr, n, 1, idb, bits_for((uint64_t)pl.max_len), lsorted, perm, s));
+        uint64_t *rk = nullptr;
+        uint32_t *rid = nullptr;
+        CKS(ensure_t(ctx, B_RK, (size_t)(n * T), &rk));
+        CKS(ensure_t(ctx, B_RID, (size_t)(n * T), &rid));
+        CK(launch_table_sort(keys, perm, n, T, idb, key_bits(p), rk, rid, s));
+        *out_rk = rk;
+        *out_rid = rid;
+        return EJ_OK;
+    }
     const size_t rs_len = radix_counts_len(n, T);
     uint32_t *rs_counts = nullptr;
     uint64_t *rs_offs = nullptr;
@@ -434,8 +453,13 @@ int candidates_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
     int np = 0;
     bool alt = false;
     const size_t rs_len = radix_counts_len(n, T);
-    RadixTemp rt{(uint32_t *)ctx->bufs[B_RS_COUNTS].p, (uint64_t *)ctx->bufs[B_RS_OFFS].p, ctx->bufs[B_SCAN_TMP].p};
-    void *scan_tmp = ctx->bufs[B_SCAN_TMP].p;
+    uint32_t *rsc = nullptr;
+    uint64_t *rso = nullptr;
+    void *scan_tmp = nullptr;
+    CKS(ensure_t(ctx, B_RS_COUNTS, rs_len, &rsc));
+    CKS(ensure_t(ctx, B_RS_OFFS, rs_len, &rso));
+    CKS(ensure(ctx, B_SCAN_TMP, scan_temp_bytes((int64_t)rs_len), &scan_tmp));
+    RadixTemp rt{rsc, rso, scan_tmp};
     // 4. count partners per record, scan
     uint32_t *counts = nullptr;
     uint64_t *offs = nullptr;

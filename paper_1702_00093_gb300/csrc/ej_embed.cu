@@ -64,8 +64,23 @@ cudaError_t launch_chunk_counts(const int32_t *lens, int64_t n, int B, uint32_t 
     return cudaGetLastError();
 }
 
-// One warp per string; lane t builds chunks t, t+32, ... A chunk holds
-// 128/B symbols; bytes outside the alphabet flag DERR_SYMBOL.
+// Spreads the 32 bits of v to the even bit positions of a 64-bit word.
+__device__ __forceinline__ uint64_t spread_even(uint32_t v) {
+    uint64_t x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+
+// One warp per string. Each load instruction reads 32 consecutive bytes (lane
+// t reads symbol 32g+t). For 2-bit codes two ballots give the low and high bit
+// planes of the 32 symbols, which interleave into one 64-bit word; lane u keeps
+// the word of group g = gbase+u and the warp stores 32 words (256 bytes) at
+// once. 8-bit codes are stored byte for byte. Symbols past the end of a
+// string are written as 0 up to its chunk boundary.
 __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
                             const int32_t *__restrict__ lens, int64_t n, const uint8_t *__restrict__ code_map,
                             int B, const uint64_t *__restrict__ pofs, uint4 *__restrict__ packed,
@@ -75,27 +90,41 @@ __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int S = 128 / B;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const int32_t len = lens[i];
+        const int64_t len = lens[i];
         const uint8_t *x = bytes + offsets[i];
         const int64_t nch = chunks_for(len, B);
-        uint4 *dst = packed + pofs[i];
-        for (int64_t c = lane; c < nch; c += 32) {
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            const int64_t k0 = c * S;
-            const int cnt = (int)((len - k0) < S ? (len - k0) : S);
-            for (int t = 0; t < cnt; t++) {
-                uint32_t code = s_map[x[k0 + t]];
-                if (code == 255u) {
-                    bad = true;
-                    code = 0u;
+        if (B == 2) {
+            uint64_t *dst = (uint64_t *)(packed + pofs[i]);
+            const int64_t nwords = 2 * nch;            // 32 symbols per 64-bit word
+            for (int64_t gbase = 0; gbase < nwords; gbase += 32) {
+                uint64_t mine = 0;
+                const int64_t gend = (nwords - gbase) < 32 ? (nwords - gbase) : 32;
+                for (int u = 0; u < (int)gend; u++) {
+                    const int64_t k = (gbase + u) * 32 + lane;
+                    uint32_t code = 0;
+                    if (k < len) {
+                        code = s_map[x[k]];
+                        if (code == 255u) { bad = true; code = 0u; }
+                    }
+                    const uint32_t p0 = __ballot_sync(FULL, code & 1u);
+                    const uint32_t p1 = __ballot_sync(FULL, (code >> 1) & 1u);
+                    if (lane == u) mine = spread_even(p0) | (spread_even(p1) << 1);
                 }
-                const int bit = t * B;
-                w[bit >> 5] |= code << (bit & 31);
+                if (lane < gend) dst[gbase + lane] = mine;
             }
-            dst[c] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            uint8_t *dst = (uint8_t *)(packed + pofs[i]);
+            const int64_t nbytes = 16 * nch;
+            for (int64_t k = lane; k < nbytes; k += 32) {
+                uint32_t code = 0;
+                if (k < len) {
+                    code = s_map[x[k]];
+                    if (code == 255u) { bad = true; code = 0u; }
+                }
+                dst[k] = (uint8_t)code;
+            }
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, (uint32_t)DERR_SYMBOL);

@@ -177,6 +177,13 @@ cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_
                                  int64_t seg_len, int64_t nseg, const int *shifts, int npasses,
                                  RadixTemp tmp, bool *in_alt, cudaStream_t s);
 
+// One block per table: stable sort of (key, id) records whose key has kb bits and
+// whose ids need idb bits (idb + kb <= 64, n <= table_sort_max()); records start
+// in perm order (perm may be null). Output keys and ids per table.
+int table_sort_max();
+cudaError_t launch_table_sort(const uint64_t *src, const uint32_t *perm, int64_t n, int64_t T, int idb, int kb,
+                              uint64_t *out_keys, uint32_t *out_ids, cudaStream_t s);
+
 // Candidates: gather keys into length order, per-table bucket windows.
 cudaError_t launch_len_order_gather(const uint64_t *keys, const uint32_t *perm, int64_t n, int64_t T,
                                     uint64_t *rec_keys, uint32_t *rec_ids, cudaStream_t s);

@@ -445,4 +445,110 @@ cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const u
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Per-table sort inside one block (tables that fit in shared memory)
+// ---------------------------------------------------------------------------
+//
+// Block t sorts the n records of table t: record p = (src[t*n + id] << idb) | id
+// with id = perm[p] (or p), i.e. the records start in the order of perm. A
+// stable LSD sort on the key bits, one bit per pass: the records sit in
+// registers (R per thread, blocked order), each pass counts the zero bits of a
+// thread's items, a block-wide exclusive scan gives every item its place, the
+// items go through one shared-memory buffer and are read back blocked. Padding
+// items (all ones) sort last. Output: key and id arrays of the table.
+
+constexpr int TS_THREADS = 1024;
+constexpr int TS_ITEMS = 24;   // up to 24576 records per table
+
+int table_sort_max() { return TS_THREADS * TS_ITEMS; }
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *total, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = s_warp[lane];   // TS_THREADS / 32 == 32 warps
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += t;
+        }
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t res = s_warp[warp] + inc - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(TS_THREADS, 1)
+table_sort_kernel(const uint64_t *__restrict__ src, const uint32_t *__restrict__ perm, int n, int idb, int kb,
+                  uint64_t *__restrict__ out_keys, uint32_t *__restrict__ out_ids) {
+    extern __shared__ uint64_t ts_buf[];   // n_pad records
+    __shared__ uint32_t s_warp[33];
+    const int t = blockIdx.x;
+    const uint64_t *sk = src + (size_t)t * n;
+    const uint64_t idmask = (idb >= 64) ? ~0ull : ((1ull << idb) - 1ull);
+    uint64_t r[TS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < TS_ITEMS; k++) {
+        const int p = threadIdx.x * TS_ITEMS + k;
+        if (p < n) {
+            const uint32_t id = perm ? perm[p] : (uint32_t)p;
+            r[k] = (sk[id] << idb) | id;
+        } else {
+            r[k] = ~0ull;
+        }
+    }
+    for (int b = idb; b < idb + kb; b++) {
+        uint32_t z = 0;
+#pragma unroll
+        for (int k = 0; k < TS_ITEMS; k++) z += ((r[k] >> b) & 1ull) ? 0u : 1u;
+        uint32_t zeros_total;
+        const uint32_t zb = block_excl_scan_u32(z, &zeros_total, s_warp);
+        const uint32_t before = threadIdx.x * TS_ITEMS;   // items before this thread
+        uint32_t zi = zb, oi = zeros_total + (before - zb);
+#pragma unroll
+        for (int k = 0; k < TS_ITEMS; k++) {
+            const bool one = (r[k] >> b) & 1ull;
+            const uint32_t dst = one ? oi : zi;
+            ts_buf[dst] = r[k];
+            oi += one ? 1u : 0u;
+            zi += one ? 0u : 1u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TS_ITEMS; k++) r[k] = ts_buf[threadIdx.x * TS_ITEMS + k];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < TS_ITEMS; k++) {
+        const int p = threadIdx.x * TS_ITEMS + k;
+        if (p < n) {
+            out_keys[(size_t)t * n + p] = r[k] >> idb;
+            out_ids[(size_t)t * n + p] = (uint32_t)(r[k] & idmask);
+        }
+    }
+}
+
+cudaError_t launch_table_sort(const uint64_t *src, const uint32_t *perm, int64_t n, int64_t T, int idb, int kb,
+                              uint64_t *out_keys, uint32_t *out_ids, cudaStream_t s) {
+    if (n > table_sort_max() || idb + kb > 64 || T < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)TS_THREADS * TS_ITEMS * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(table_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    table_sort_kernel<<<(unsigned)T, TS_THREADS, smem, s>>>(src, perm, (int)n, idb, kb, out_keys, out_ids);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace ej
