@@ -26,7 +26,7 @@ enum BufId {
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
-    B_HASH, B_APP, B_JCOUNT,
+    B_HASH, B_APP, B_JCOUNT, B_NEXT,
     B_NUM
 };
 
@@ -334,9 +334,14 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         CK(launch_symbol_table(p->seed, p->r, pl.L, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,
                                pi_dev, ctx->pi_steps, tsym, s));
         CK(launch_sort_samples(pos, p->r, p->m, p->z, spos, stag, s));
+        uint16_t *next = nullptr;
+        if (embed_sign_uses_table(p->alphabet_size, pl.L)) {
+            CKS(ensure_t(ctx, B_NEXT, next_table_elems(p->r, p->alphabet_size, pl.L), &next));
+            CK(launch_next_table(tsym, p->r, p->alphabet_size, pl.L, next, s));
+        }
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
         CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
-                             tsym, spos, stag, keys, s));
+                             tsym, next, spos, stag, keys, s));
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
     } else {
         // materialise only the prefix [0, L) of every embedding

@@ -100,17 +100,25 @@ __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__
             const int64_t nwords = 2 * nch;            // 32 symbols per 64-bit word
             for (int64_t gbase = 0; gbase < nwords; gbase += 32) {
                 uint64_t mine = 0;
-                const int64_t gend = (nwords - gbase) < 32 ? (nwords - gbase) : 32;
-                for (int u = 0; u < (int)gend; u++) {
-                    const int64_t k = (gbase + u) * 32 + lane;
-                    uint32_t code = 0;
-                    if (k < len) {
-                        code = s_map[x[k]];
-                        if (code == 255u) { bad = true; code = 0u; }
+                const int gend = (int)((nwords - gbase) < 32 ? (nwords - gbase) : 32);
+                for (int u0 = 0; u0 < gend; u0 += 8) {
+                    uint32_t code[8];
+#pragma unroll
+                    for (int v = 0; v < 8; v++) {   // eight independent loads in flight
+                        const int64_t k = (gbase + u0 + v) * 32 + lane;
+                        code[v] = (u0 + v < gend && k < len) ? (uint32_t)x[k] : 256u;
                     }
-                    const uint32_t p0 = __ballot_sync(FULL, code & 1u);
-                    const uint32_t p1 = __ballot_sync(FULL, (code >> 1) & 1u);
-                    if (lane == u) mine = spread_even(p0) | (spread_even(p1) << 1);
+#pragma unroll
+                    for (int v = 0; v < 8; v++) {
+                        uint32_t c = 0;
+                        if (code[v] < 256u) {
+                            c = s_map[code[v]];
+                            if (c == 255u) { bad = true; c = 0u; }
+                        }
+                        const uint32_t p0 = __ballot_sync(FULL, c & 1u);
+                        const uint32_t p1 = __ballot_sync(FULL, (c >> 1) & 1u);
+                        if (lane == u0 + v) mine = spread_even(p0) | (spread_even(p1) << 1);
+                    }
                 }
                 if (lane < gend) dst[gbase + lane] = mine;
             }
@@ -460,16 +468,65 @@ cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uin
     return cudaGetLastError();
 }
 
-constexpr int ES_THREADS = 128;
+constexpr int ES_THREADS = 256;
+constexpr size_t ES_TABLE_MAX = 48 * 1024;   // next-step table kept in shared memory up to this size
+
+// Per-embedding stride of the next-step table, even so that every table starts
+// on a 4-byte boundary.
+__host__ __device__ __forceinline__ uint64_t next_stride(uint32_t alpha, uint32_t L) {
+    return ((uint64_t)alpha * L + 1) & ~1ull;
+}
+
+// next[l][c][a] = next1_c(a) + 1 for a < L (16-bit), from the step bitmaps.
+__global__ void next_table_kernel(const uint32_t *__restrict__ tsym, uint32_t r, uint32_t alpha, uint32_t L,
+                                  uint16_t *__restrict__ next) {
+    const uint32_t LW = sym_words(L);
+    const uint64_t total = (uint64_t)r * alpha * L;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = (uint32_t)(idx % L);
+        const uint64_t lc = idx / L;   // l * alpha + c
+        const uint64_t l = lc / alpha, c = lc % alpha;
+        const uint32_t *row = tsym + lc * LW;
+        uint32_t wi = a >> 5;
+        uint32_t w = row[wi] >> (a & 31u);
+        uint32_t base = a;
+        while (w == 0u) {               // ends at the sentinel bits (steps >= L)
+            wi++;
+            w = row[wi];
+            base = wi << 5;
+        }
+        next[l * next_stride(alpha, L) + c * L + a] = (uint16_t)(base + (uint32_t)__ffs((int)w));
+    }
+}
+
+cudaError_t launch_next_table(const uint32_t *tsym, uint32_t r, uint32_t alpha, uint32_t L, uint16_t *next,
+                              cudaStream_t s) {
+    const uint64_t total = (uint64_t)r * alpha * L;
+    uint64_t g = (total + 255) / 256;
+    next_table_kernel<<<(unsigned)(g > 4096 ? 4096 : (g ? g : 1)), 256, 0, s>>>(tsym, r, alpha, L, next);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+size_t next_table_elems(uint32_t r, uint32_t alpha, uint32_t L) { return (size_t)r * next_stride(alpha, L); }
+
+bool embed_sign_uses_table(uint32_t alpha, uint32_t L) {
+    return (size_t)alpha * L * 2 <= ES_TABLE_MAX && L < 65535u;
+}
+
+static size_t es_code_words(uint32_t alpha, uint32_t M) {
+    const uint32_t per = alpha <= 4 ? 16u : 4u;   // codes per 32-bit word (2 or 8 bits each)
+    return (M + per - 1) / per;
+}
 
 size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
     const size_t M = (size_t)m * z;
     if (M > 16384 || z > 65535 || m > 65535) return 0;
-    // table, sorted steps (+ sentinel), rank of (f, q) in step order, powers,
-    // one code byte per sample and thread
-    const size_t bytes = (size_t)alpha * sym_words(L) * 4 + (M + 1) * 4 + M * 4 + (size_t)z * 8 +
-                         M * ES_THREADS;
-    return bytes <= 160 * 1024 ? bytes : 0;
+    const size_t table = embed_sign_uses_table(alpha, L) ? (size_t)alpha * L * 2 : (size_t)alpha * sym_words(L) * 4;
+    const size_t bytes = (size_t)z * 8 + (M + 1) * 4 + M * 4 + ((table + 7) & ~(size_t)7) +
+                         es_code_words(alpha, (uint32_t)M) * 4 * ES_THREADS;
+    return bytes <= 200 * 1024 ? bytes : 0;
 }
 
 // Codes of one string, 64 bits at a time. Every string starts on a chunk
@@ -516,19 +573,25 @@ struct WordReader {
     }
 };
 
-template <int B>
+// TABLE: next steps from the 16-bit table (one shared load per character);
+// otherwise a find-first-set over the step bitmaps. CB: bits per stored code.
+template <int B, bool TABLE, int CB>
 __global__ void __launch_bounds__(ES_THREADS)
 embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                   const int32_t *__restrict__ lens, int64_t n, uint32_t m, uint32_t z, uint32_t L,
-                  uint32_t alpha, const uint32_t *__restrict__ tsym, const uint32_t *__restrict__ spos,
-                  const uint32_t *__restrict__ stag, uint64_t *__restrict__ keys) {
+                  uint32_t alpha, const uint32_t *__restrict__ tsym, const uint16_t *__restrict__ next,
+                  const uint32_t *__restrict__ spos, const uint32_t *__restrict__ stag,
+                  uint64_t *__restrict__ keys) {
+    constexpr uint32_t PER = 32 / CB;   // codes per word
     extern __shared__ uint64_t es_smem[];
     const uint32_t l = blockIdx.y, M = m * z, LW = sym_words(L);
-    uint64_t *s_pow = es_smem;                                // [z]
-    uint32_t *s_pos = (uint32_t *)(s_pow + z);                // [M+1], sentinel at M
-    uint32_t *s_rank = s_pos + M + 1;                         // [M]: step-order index of sample f*z+q
-    uint32_t *s_tab = s_rank + M;                             // [alpha][LW]
-    uint8_t *s_code = (uint8_t *)(s_tab + (size_t)alpha * LW); // [M][ES_THREADS]
+    uint64_t *s_pow = es_smem;                                 // [z]
+    uint32_t *s_pos = (uint32_t *)(s_pow + z);                 // [M+1], sentinel at M
+    uint32_t *s_rank = s_pos + M + 1;                          // [M]: step-order index of sample f*z+q
+    uint32_t *s_tab = s_rank + M;                              // bitmaps [alpha][LW] or next table
+    const size_t tab_bytes = TABLE ? (size_t)alpha * L * 2 : (size_t)alpha * LW * 4;
+    uint16_t *s_next = (uint16_t *)s_tab;
+    uint32_t *s_code = (uint32_t *)((char *)s_tab + ((tab_bytes + 7) & ~(size_t)7));  // [words][ES_THREADS]
     for (uint32_t i = threadIdx.x; i <= M; i += blockDim.x) {
         s_pos[i] = i < M ? spos[(size_t)l * M + i] : 0xFFFFFFFFu;
         if (i < M) {
@@ -536,7 +599,14 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
             s_rank[(tag >> 16) * z + (tag & 0xFFFFu)] = i;
         }
     }
-    for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
+    if (TABLE) {
+        const uint32_t *src = (const uint32_t *)(next + (size_t)l * next_stride(alpha, L));
+        uint32_t *dst = (uint32_t *)s_next;
+        const uint32_t nw = (alpha * L + 1) / 2;
+        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    } else {
+        for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
+    }
     if (threadIdx.x == 0) {
         uint64_t pw = 1;
         for (uint32_t q = 0; q < z; q++) {
@@ -550,65 +620,90 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     const int32_t len = s < n ? lens[s] : 0;
     WordReader<B> rd;
     rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
-    uint8_t *my = s_code + threadIdx.x;
+    uint32_t *my = s_code + threadIdx.x;
     uint32_t k = 0;                          // next sample (in step order)
     uint32_t ps = s_pos[0];                  // its step
+    uint32_t acc = 0;                        // codes of samples k & ~(PER-1) .. k-1
     uint32_t a = 0;                          // step at which the walk arrives at x[i]
     int32_t i = 0;
     while (i < len && k < M) {
         const uint32_t c = rd.code();
-        const uint32_t *row = s_tab + c * LW + (a >> 5);
-        const uint32_t sh = a & 31u;
-        const uint32_t lo = __funnelshift_r(row[0], row[1], sh);   // steps a .. a+31
         uint32_t a_next;
-        if (lo != 0u) {
-            a_next = a + (uint32_t)__ffs((int)lo);   // first step with pi = 1, plus one
+        if (TABLE) {
+            a_next = s_next[c * L + a];
         } else {
-            const uint32_t hi = row[1] >> sh;           // steps a+32 .. (word end)
-            if (hi != 0u) {
-                a_next = a + 32u + (uint32_t)__ffs((int)hi);
-            } else {                                    // rare: a longer run of zeros
-                uint32_t j2 = (a >> 5) + 2;
-                uint32_t v = s_tab[c * LW + j2];
-                while (v == 0u) v = s_tab[c * LW + (++j2)];   // ends at the sentinel word
-                a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
+            const uint32_t *row = s_tab + c * LW + (a >> 5);
+            const uint32_t sh = a & 31u;
+            const uint32_t lo = __funnelshift_r(row[0], row[1], sh);
+            if (lo != 0u) {
+                a_next = a + (uint32_t)__ffs((int)lo);
+            } else {
+                const uint32_t hi = row[1] >> sh;
+                if (hi != 0u) {
+                    a_next = a + 32u + (uint32_t)__ffs((int)hi);
+                } else {
+                    uint32_t j2 = (a >> 5) + 2;
+                    uint32_t v = s_tab[c * LW + j2];
+                    while (v == 0u) v = s_tab[c * LW + (++j2)];
+                    a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
+                }
             }
         }
-        // samples inside [a, a_next) read x[i]: store its code, one per step in order
+        // samples inside [a, a_next) read x[i]
         while (ps < a_next) {
-            my[(size_t)k * ES_THREADS] = (uint8_t)c;
+            acc |= c << ((k % PER) * CB);
+            if (k % PER == PER - 1) {
+                my[(size_t)(k / PER) * ES_THREADS] = acc;
+                acc = 0;
+            }
             ps = s_pos[++k];
         }
         a = a_next;
         i++;
         rd.advance();
     }
-    // walk finished before the last sample: the rest read bottom
-    for (; k < M; k++) my[(size_t)k * ES_THREADS] = (uint8_t)alpha;
+    const uint32_t k_end = k;   // samples from k_end on lie after the walk: bottom
+    if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc;
     if (s < n) {
         for (uint32_t f = 0; f < m; f++) {
             uint64_t key = 0;
-            for (uint32_t q = 0; q < z; q++)
-                key += (uint64_t)my[(size_t)s_rank[f * z + q] * ES_THREADS] * s_pow[q];
+            for (uint32_t q = 0; q < z; q++) {
+                const uint32_t rk = s_rank[f * z + q];
+                const uint32_t c = (rk < k_end)
+                                       ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                       : alpha;
+                key += (uint64_t)c * s_pow[q];
+            }
             keys[((size_t)l * m + f) * n + s] = key;
         }
     }
 }
 
+template <int B, bool TABLE, int CB>
+static void es_launch(dim3 grid, size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs,
+                      const int32_t *lens, int64_t n, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha,
+                      const uint32_t *tsym, const uint16_t *next, const uint32_t *spos, const uint32_t *stag,
+                      uint64_t *keys) {
+    cudaFuncSetAttribute(embed_sign_kernel<B, TABLE, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    embed_sign_kernel<B, TABLE, CB><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym,
+                                                                   next, spos, stag, keys);
+}
+
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
-                              const uint32_t *tsym, const uint32_t *spos, const uint32_t *stag,
-                              uint64_t *keys, cudaStream_t s) {
+                              const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
+                              const uint32_t *stag, uint64_t *keys, cudaStream_t s) {
     if (n == 0) return cudaGetLastError();
     const size_t smem = embed_sign_smem(alpha, L, m, z);
     if (smem == 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((n + ES_THREADS - 1) / ES_THREADS), r);
+    const bool table = embed_sign_uses_table(alpha, L) && next != nullptr;
     if (B == 2) {
-        cudaFuncSetAttribute(embed_sign_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        embed_sign_kernel<2><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym, spos, stag, keys);
+        if (table) es_launch<2, true, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
+        else es_launch<2, false, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
     } else {
-        cudaFuncSetAttribute(embed_sign_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        embed_sign_kernel<8><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym, spos, stag, keys);
+        if (table) es_launch<8, true, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
+        else es_launch<8, false, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
     }
     note_launches(1);
     return cudaGetLastError();

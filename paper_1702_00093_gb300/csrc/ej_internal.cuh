@@ -145,10 +145,15 @@ cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uin
                                 uint32_t *stag, cudaStream_t s);
 // Shared memory the fused kernel needs (0 if it does not fit: use embed + sign).
 size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z);
+// next[l][c][a] = next1_c(a) + 1 (16-bit) when embed_sign_uses_table(alpha, L).
+bool embed_sign_uses_table(uint32_t alpha, uint32_t L);
+size_t next_table_elems(uint32_t r, uint32_t alpha, uint32_t L);
+cudaError_t launch_next_table(const uint32_t *tsym, uint32_t r, uint32_t alpha, uint32_t L, uint16_t *next,
+                              cudaStream_t s);
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
-                              const uint32_t *tsym, const uint32_t *spos, const uint32_t *stag,
-                              uint64_t *keys, cudaStream_t s);
+                              const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
+                              const uint32_t *stag, uint64_t *keys, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Scan and sort primitives (ej_sort.cu)
