@@ -99,7 +99,7 @@ __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__
             uint64_t *dst = (uint64_t *)(packed + pofs[i]);
             const int64_t nwords = 2 * nch;            // 32 symbols per 64-bit word
             for (int64_t gbase = 0; gbase < nwords; gbase += 32) {
-                uint64_t mine = 0;
+                uint32_t my0 = 0, my1 = 0;   // bit planes of group gbase+lane
                 const int gend = (int)((nwords - gbase) < 32 ? (nwords - gbase) : 32);
                 for (int u0 = 0; u0 < gend; u0 += 8) {
                     uint32_t code[8];
@@ -117,10 +117,11 @@ __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__
                         }
                         const uint32_t p0 = __ballot_sync(FULL, c & 1u);
                         const uint32_t p1 = __ballot_sync(FULL, (c >> 1) & 1u);
-                        if (lane == u0 + v) mine = spread_even(p0) | (spread_even(p1) << 1);
+                        my0 = (lane == u0 + v) ? p0 : my0;
+                        my1 = (lane == u0 + v) ? p1 : my1;
                     }
                 }
-                if (lane < gend) dst[gbase + lane] = mine;
+                if (lane < gend) dst[gbase + lane] = spread_even(my0) | (spread_even(my1) << 1);
             }
         } else {
             uint8_t *dst = (uint8_t *)(packed + pofs[i]);
@@ -621,48 +622,46 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     WordReader<B> rd;
     rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
     uint32_t *my = s_code + threadIdx.x;
-    uint32_t k = 0;                          // next sample (in step order)
-    uint32_t ps = s_pos[0];                  // its step
-    uint32_t acc = 0;                        // codes of samples k & ~(PER-1) .. k-1
-    uint32_t a = 0;                          // step at which the walk arrives at x[i]
-    int32_t i = 0;
-    while (i < len && k < M) {
-        const uint32_t c = rd.code();
-        uint32_t a_next;
-        if (TABLE) {
-            a_next = s_next[c * L + a];
-        } else {
-            const uint32_t *row = s_tab + c * LW + (a >> 5);
-            const uint32_t sh = a & 31u;
-            const uint32_t lo = __funnelshift_r(row[0], row[1], sh);
-            if (lo != 0u) {
-                a_next = a + (uint32_t)__ffs((int)lo);
-            } else {
-                const uint32_t hi = row[1] >> sh;
-                if (hi != 0u) {
-                    a_next = a + 32u + (uint32_t)__ffs((int)hi);
-                } else {
-                    uint32_t j2 = (a >> 5) + 2;
-                    uint32_t v = s_tab[c * LW + j2];
-                    while (v == 0u) v = s_tab[c * LW + (++j2)];
-                    a_next = (j2 << 5) + (uint32_t)__ffs((int)v);
-                }
-            }
+    // next step after the current character: first step >= a with pi = 1, plus one
+    auto step_after = [&](uint32_t c, uint32_t a) -> uint32_t {
+        if (a >= L) return L + 1;   // past every sample
+        if (TABLE) return s_next[c * L + a];
+        const uint32_t *row = s_tab + c * LW + (a >> 5);
+        const uint32_t sh = a & 31u;
+        const uint32_t lo = __funnelshift_r(row[0], row[1], sh);
+        if (lo != 0u) return a + (uint32_t)__ffs((int)lo);
+        const uint32_t hi = row[1] >> sh;
+        if (hi != 0u) return a + 32u + (uint32_t)__ffs((int)hi);
+        uint32_t j2 = (a >> 5) + 2;
+        uint32_t v = s_tab[c * LW + j2];
+        while (v == 0u) v = s_tab[c * LW + (++j2)];
+        return (j2 << 5) + (uint32_t)__ffs((int)v);
+    };
+    int32_t i = 0;                       // current character
+    uint32_t a = 0;                      // step at which the walk arrived at x[i]
+    uint32_t c = rd.code();
+    uint32_t a_next = len > 0 ? step_after(c, 0) : 0;
+    uint32_t acc = 0;
+    uint32_t k = 0;
+    uint32_t k_end = M;                  // first sample at or after the end of the walk
+    // Samples in step order (the same for every lane): advance the walk until
+    // the current character covers the sample's step, then record it.
+    for (; k < M; k++) {
+        const uint32_t ps = s_pos[k];
+        while (i < len && a_next <= ps) {
+            a = a_next;
+            i++;
+            rd.advance();
+            c = rd.code();
+            a_next = step_after(c, a);
         }
-        // samples inside [a, a_next) read x[i]
-        while (ps < a_next) {
-            acc |= c << ((k % PER) * CB);
-            if (k % PER == PER - 1) {
-                my[(size_t)(k / PER) * ES_THREADS] = acc;
-                acc = 0;
-            }
-            ps = s_pos[++k];
+        if (i >= len && k_end == M) k_end = k;
+        acc |= (i < len ? c : 0u) << ((k % PER) * CB);
+        if (k % PER == PER - 1) {
+            my[(size_t)(k / PER) * ES_THREADS] = acc;
+            acc = 0;
         }
-        a = a_next;
-        i++;
-        rd.advance();
     }
-    const uint32_t k_end = k;   // samples from k_end on lie after the walk: bottom
     if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc;
     if (s < n) {
         for (uint32_t f = 0; f < m; f++) {
