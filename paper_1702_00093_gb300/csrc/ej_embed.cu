@@ -469,7 +469,7 @@ cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uin
     return cudaGetLastError();
 }
 
-constexpr int ES_THREADS = 256;
+constexpr int ES_THREADS = 512;
 constexpr size_t ES_TABLE_MAX = 48 * 1024;   // next-step table kept in shared memory up to this size
 
 // Per-embedding stride of the next-step table, even so that every table starts
@@ -637,31 +637,39 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
         while (v == 0u) v = s_tab[c * LW + (++j2)];
         return (j2 << 5) + (uint32_t)__ffs((int)v);
     };
-    int32_t i = 0;                       // current character
+    // Character-major walk, all lanes one character per iteration. A sample
+    // inside the current character's steps [a, a_next) is recorded without a
+    // branch (at most one per iteration; a second one in the same character
+    // takes a short loop).
+    int32_t i = 0;
     uint32_t a = 0;                      // step at which the walk arrived at x[i]
-    uint32_t c = rd.code();
-    uint32_t a_next = len > 0 ? step_after(c, 0) : 0;
+    uint32_t k = 0;                      // next sample (in step order)
+    uint32_t ps = s_pos[0];              // its step
     uint32_t acc = 0;
-    uint32_t k = 0;
-    uint32_t k_end = M;                  // first sample at or after the end of the walk
-    // Samples in step order (the same for every lane): advance the walk until
-    // the current character covers the sample's step, then record it.
-    for (; k < M; k++) {
-        const uint32_t ps = s_pos[k];
-        while (i < len && a_next <= ps) {
-            a = a_next;
-            i++;
-            rd.advance();
-            c = rd.code();
-            a_next = step_after(c, a);
-        }
-        if (i >= len && k_end == M) k_end = k;
-        acc |= (i < len ? c : 0u) << ((k % PER) * CB);
-        if (k % PER == PER - 1) {
+    while (i < len && k < M) {
+        const uint32_t c = rd.code();
+        const uint32_t a_next = step_after(c, a);
+        const bool hit = ps < a_next;
+        acc |= hit ? (c << ((k % PER) * CB)) : 0u;
+        if (hit && (k % PER == PER - 1)) {
             my[(size_t)(k / PER) * ES_THREADS] = acc;
             acc = 0;
         }
+        k += hit ? 1u : 0u;
+        ps = s_pos[k];
+        while (ps < a_next) {            // rare: another sample in the same character
+            acc |= c << ((k % PER) * CB);
+            if (k % PER == PER - 1) {
+                my[(size_t)(k / PER) * ES_THREADS] = acc;
+                acc = 0;
+            }
+            ps = s_pos[++k];
+        }
+        a = a_next;
+        i++;
+        rd.advance();
     }
+    const uint32_t k_end = k;            // samples from k_end on lie after the walk: bottom
     if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc;
     if (s < n) {
         for (uint32_t f = 0; f < m; f++) {
