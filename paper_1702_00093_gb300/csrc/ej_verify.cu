@@ -867,7 +867,7 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         s_nmin[t] = (int8_t)mn;
     }
     __syncthreads();
-    const int T_ = blockDim.x;
+    constexpr int T_ = VBD_THREADS;      // slot stride (every launch uses VBD_THREADS threads)
     uint64_t *ring = smem + threadIdx.x;  // per thread: (c*R + slot)*T_, reused as a dump area
     const int lane = threadIdx.x & 31;
     const bool rev = lane & 1;
@@ -910,61 +910,62 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
 #pragma unroll
             for (int v = 0; v < W1; v++) { Pv[v] = ~0ull; Mv[v] = 0ull; }
             int base = 0;  // slot of word k0
+            uint32_t soff[W1];   // element offset of the slot of word k0+v
+#pragma unroll
+            for (int v = 0; v < W1; v++) soff[v] = (uint32_t)v * T_;
             SymReader<B> yf;
             SymReaderRev<B> yb;
             if (rev) yb.init(packed + pofs[yi], n);
             else yf.init(packed + pofs[yi], chunks_for(n1, B));
+            const uint32_t cmax = alpha - 1u;
+            int32_t next_move = K + 1 + 64;   // first column whose window starts one word lower
             int32_t j = 1;
             for (; j <= ncols; j++) {
-                const int64_t jk = (int64_t)j - K - 1;
-                const int64_t knew = jk > 0 ? (jk >> 6) : 0;
-                if (knew > k0) {
+                if (j == next_move) {
+                    next_move += 64;
                     // drop the top word into T, shift the window down one word
                     T += __popcll(Pv[0]) - __popcll(Mv[0]);
 #pragma unroll
                     for (int v = 0; v + 1 < W1; v++) { Pv[v] = Pv[v + 1]; Mv[v] = Mv[v + 1]; }
                     Pv[W1 - 1] = ~0ull;
                     Mv[W1 - 1] = 0ull;
-                    k0 = knew;
-                    const int old = base;
+                    k0++;
                     base = (base + 1 == R) ? 0 : base + 1;
-                    (void)old;
-                    int slot = base + W1 - 1;
-                    if (slot >= R) slot -= R;
-                    bd_build<B, R>(ring, T_, slot, xc, m, k0 + W1 - 1, rev, alpha);
-                    // early exit: minimum over the window exceeds K. Row 64*k0 (value T)
-                    // is still the top of the band at column j-1, so it takes part.
-                    int32_t run = 0, mn = 0;
 #pragma unroll
                     for (int v = 0; v < W1; v++) {
-#pragma unroll
-                        for (int q = 0; q < 16; q++) {
-                            const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
-                                                 ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
-                            const int32_t cand = run + s_nmin[idx];
-                            mn = cand < mn ? cand : mn;
-                            run += s_nsum[idx];
-                        }
+                        const int sl = base + v;
+                        soff[v] = (uint32_t)(sl >= R ? sl - R : sl) * T_;
                     }
-                    if (T + mn > K) {
-                        rejected = true;
-                        break;
+                    bd_build<B, R>(ring, T_, (int)(soff[W1 - 1] / T_), xc, m, k0 + W1 - 1, rev, alpha);
+                    if ((k0 & 1) == 0) {
+                        // early exit: minimum over the window exceeds K. Row 64*k0 (value T)
+                        // is still the top of the band at column j-1, so it takes part.
+                        int32_t run = 0, mn = 0;
+#pragma unroll
+                        for (int v = 0; v < W1; v++) {
+#pragma unroll
+                            for (int q = 0; q < 16; q++) {
+                                const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
+                                                     ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
+                                const int32_t cand = run + s_nmin[idx];
+                                mn = cand < mn ? cand : mn;
+                                run += s_nsum[idx];
+                            }
+                        }
+                        if (T + mn > K) {
+                            rejected = true;
+                            break;
+                        }
                     }
                 }
                 uint32_t c;
                 if (rev) { c = yb.code(); yb.advance(); }
                 else { c = yf.code(); yf.advance(); }
-                const bool cv = c < alpha;
-                const uint64_t *row = ring + (size_t)(cv ? c : 0u) * R * T_;
+                c = c < cmax ? c : cmax;   // codes of a validated string are < alpha
+                const uint64_t *row = ring + (size_t)c * R * T_;
                 uint64_t Eq[W1];
-                {
-                    int sl = base;
 #pragma unroll
-                    for (int v = 0; v < W1; v++) {
-                        Eq[v] = cv ? row[(size_t)sl * T_] : 0ull;
-                        sl = (sl + 1 == R) ? 0 : sl + 1;
-                    }
-                }
+                for (int v = 0; v < W1; v++) Eq[v] = row[soff[v]];
                 uint64_t A[W1], S[W1];
 #pragma unroll
                 for (int v = 0; v < W1; v++) A[v] = Eq[v] & Pv[v];
@@ -1064,7 +1065,8 @@ template <int W1, int B>
 static cudaError_t launch_bd(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                              uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
                              VerifyOut vo, cudaStream_t s) {
-    const int threads = warps * 32;
+    (void)warps;
+    const int threads = VBD_THREADS;
     const int R = W1 + 1;
     const size_t per_thread = (size_t)(alpha * R > 2 * W1 + 2 ? alpha * R : 2 * W1 + 2) * sizeof(uint64_t);
     const size_t smem = per_thread * threads;
