@@ -34,9 +34,24 @@ sys.path.insert(0, ROOT)
 
 KS = (50, 150, 250)
 METRIC = "verified pairs/s (candidate pairs verified per second of whole-join wall time)"
-# GB300: 152 SMs x 4 schedulers x 32 lanes issue one 32-bit instruction per lane per clock
-SMS, LANES_PER_SM, MAX_SM_MHZ = 152, 128, 2070.0
+# GB300: 152 SMs; the integer ALU pipe (add, logic, shift) retires 16 lanes per clock
+# per SM sub-partition, 64 per SM, at up to 2070 MHz
+SMS, ALU_LANES_PER_SM, MAX_SM_MHZ = 152, 64, 2070.0
 INT_OPS_PER_WORD_COLUMN = 26   # 32-bit ops of one 64-bit word of the bit-parallel step
+# DRAM bytes per verify launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the K=50/150/250 launches of one ncu capture of this workload), valid only
+# while the verify source is the one that was captured
+VERIFY_TRAFFIC = {"source_sha256_prefix": "65da4c7da4e3b0fd", "bytes_per_launch": 8193621}
+
+
+def verify_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if sha.startswith(VERIFY_TRAFFIC["source_sha256_prefix"]):
+        return VERIFY_TRAFFIC["bytes_per_launch"]
+    return None
 
 
 def parse():
@@ -276,7 +291,7 @@ def main():
     cells = sum(s["band_cells"] for _, _, s in stats)
     n_verify = sum(1 for _, _, s in stats if s["n_candidates"] > 0)
     ach_ops = word_cols * INT_OPS_PER_WORD_COLUMN / (verify_ms / 1e3) if verify_ms else 0.0
-    peak_ops = SMS * LANES_PER_SM * MAX_SM_MHZ * 1e6
+    peak_ops = SMS * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
     per_k = {}
     for K in Ks:
         rows = [s for k, _, s in stats if k == K]
@@ -334,13 +349,13 @@ def main():
             "join_wall_s_per_step": total_ms_max / args.steps / 1e3,
             "band_cells_per_s": allreduce_sum(cells, world) / (total_ms_max / 1e3),
             "per_K": per_k,
-            "roofline": {"kernel": "verify_kernel", "bound": "alu", "achieved": ach_ops / 1e12,
+            "roofline": {"kernel": "verify_bd_kernel", "bound": "alu", "achieved": ach_ops / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",
-                         "frac": ach_ops / peak_ops, "traffic": None,
+                         "frac": ach_ops / peak_ops, "traffic": verify_traffic(),
                          "launches": n_verify, "avg_launch_ms": verify_ms / max(n_verify, 1),
                          "ops_per_word_column": INT_OPS_PER_WORD_COLUMN,
                          "word_columns": word_cols,
-                         "peak_basis": "issue ceiling 152 SMs x 128 lanes x 2070 MHz (derived)"},
+                         "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"},
             "clocks": clocks,
             "gpu_launches": int(sum(s["kernel_launches"] for _, _, s in stats)),
             "e2e": e2e,
