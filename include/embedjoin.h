@@ -155,6 +155,33 @@ int ej_set_timing(ej_ctx *ctx, int enable);
 int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
 
 /*
+ * Schedule of ej_join's back half (a performance choice: the output never
+ * depends on it; the paper has no counterpart).
+ *   mode: 0 (default) persistent verifier where the band fits two lanes per pair
+ *     (up to 12 words per lane): a fixed grid whose warps pull candidate pairs
+ *     from a device work queue and refill a pair slot as soon as its pair is
+ *     decided; otherwise the grid-strided verifier. 1: the same as 0.
+ *     2: always the grid-strided verifier (one pass over the pairs; a warp's
+ *     slots start together and the warp ends with its slowest pair).
+ *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
+ *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
+ *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
+ *   order: 0 (default) or 1: candidates enter the queue by decreasing number of
+ *     tables in which the two strings collided (similar pairs, which run
+ *     longest, start first); 2: hash-table order.
+ */
+typedef struct {
+    int32_t mode;
+    int32_t slots_per_warp;
+    int32_t warps_per_subpartition;
+    int32_t order;
+} ej_schedule;
+
+/* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside
+ * the ranges above. */
+int ej_set_schedule(ej_ctx *ctx, const ej_schedule *schedule);
+
+/*
  * Validate the strings against the parameters and report the derived sizes
  * (N, out_len = 3N or params->out_len, L, the embedding layout). Checks
  * offsets (start at 0, non-decreasing), lengths (< 2^31), symbols (all in the

@@ -26,7 +26,7 @@ enum BufId {
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
-    B_HASH, B_APP, B_JCOUNT, B_NEXT,
+    B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS,
     B_NUM
 };
 
@@ -61,6 +61,7 @@ struct ej_ctx {
     uint64_t raw_cap_hint = 0;
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
+    ej_schedule sched{0, 0, 0, 0};   // ej_join's verifier schedule (ej_set_schedule)
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -563,7 +564,7 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     CK(cudaMemsetAsync(derr, 0, 4, s));
     CK(cudaMemsetAsync(dcnt + 4, 0, 2 * sizeof(uint64_t), s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
-    VerifyOut vo{fl, nullptr, nullptr, 0, nullptr, derr, (unsigned long long *)(dcnt + 4)};
+    VerifyOut vo{fl, nullptr, nullptr, 0, nullptr, derr, (unsigned long long *)(dcnt + 4), nullptr, nullptr};
     CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, pl.st.n, p->alphabet_size, pairs, np, p->K,
                      pl.max_len, vo, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
@@ -618,17 +619,42 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
         CK(cudaMemsetAsync(derr, 0, 4, s));
         CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
         CK(launch_emit_append(srk, srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
-        CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
+        if (ctx->sched.order != 2) {
+            // candidates handed to the verifier most-collided first: similar pairs,
+            // which run longest, start first
+            uint32_t *hcount = nullptr;
+            unsigned long long *bins = nullptr;
+            CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
+            CKS(ensure_t(ctx, B_BINS, (size_t)count_bins(), &bins));
+            CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
+            CK(cudaMemsetAsync(bins, 0, count_bins() * sizeof(unsigned long long), s));
+            CK(launch_dedup_ordered(raw, cap, table, hcount, hsize, bins, cand, cnt, s));
+        } else {
+            CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
+        }
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
-        VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4};
-        CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
-                         pl.max_len, vo, s));
+        unsigned int *tickets = nullptr;
+        CKS(ensure_t(ctx, B_TICKETS, (size_t)SM_TICKETS, &tickets));
+        CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
+        VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
+        const int pq_threads = (vc.G == 2 && ctx->sched.mode != 2) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
+        if (pq_threads > 0)
+            // defaults: 16 slots per warp, one working warp per SM sub-partition (the
+            // slots refill from the queue); measured best on the long-DNA shapes
+            CK(launch_verify_pq(vc.V, pq_threads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
+                                ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1,
+                                pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K, vo,
+                                s));
+        else
+            CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
+                             pl.max_len, vo, s));
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
         CK(cudaMemcpyAsync(ctx->h_cnt, cnt, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(ctx->h_cnt + 6, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         memcpy(hc, ctx->h_cnt, sizeof hc);
         if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+        if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: verifier work bound exceeded");
         if (hc[0] <= cap) break;
         if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
         cap = hc[0] + hc[0] / 4 + 1024;
@@ -764,6 +790,20 @@ int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
     ctx->vG = G;
     ctx->vV = V;
     ctx->vWarps = warps;
+    return EJ_OK;
+}
+
+int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
+    if (!ctx) return EJ_ERR_INVALID_ARG;
+    if (!sc) {
+        ctx->sched = ej_schedule{0, 0, 0, 0};
+        return EJ_OK;
+    }
+    if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
+        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 2)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d not supported",
+                    sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order);
+    ctx->sched = *sc;
     return EJ_OK;
 }
 

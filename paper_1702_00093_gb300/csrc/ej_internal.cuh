@@ -97,6 +97,7 @@ enum : uint32_t {
     DERR_SYMBOL = 2u,      // byte outside the alphabet
     DERR_PAIR = 4u,        // pair index out of range
     DERR_TIMEOUT = 8u,     // bounded wait gave up
+    DERR_GUARD = 16u,      // a persistent loop exceeded its work bound and stopped
 };
 
 // ---------------------------------------------------------------------------
@@ -211,6 +212,12 @@ cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids
                                cudaStream_t s);
 cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uint64_t hsize, uint64_t *cand,
                          unsigned long long *counters, cudaStream_t s);
+// Dedup that also orders the candidates by collision count (most first):
+// hcount (hsize uint32) and bins (count_bins() uint64) start at zero.
+int count_bins();
+cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                 unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
+                                 cudaStream_t s);
 int small_sort_max();
 cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s);
 
@@ -231,7 +238,11 @@ struct VerifyOut {
     const unsigned long long *np_dev;
     uint32_t *err;
     unsigned long long *work;
+    unsigned long long *queue;   // work-queue head of the persistent verifier (zeroed before the launch)
+    unsigned int *sm_tickets;    // per-SM working-warp tickets (SM_TICKETS entries, zeroed before the launch)
 };
+
+constexpr int SM_TICKETS = 1024;
 
 struct VerifyConfig {
     int G;          // lanes per pair
@@ -248,5 +259,14 @@ cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *p
                           const int32_t *lens, int64_t n, uint32_t alpha,
                           const uint64_t *pairs, int64_t np, int32_t K, int64_t max_len,
                           VerifyOut vo, cudaStream_t s);
+
+// Persistent verifier (two lanes per pair, W1 = 2..12 words per lane, pairs
+// pulled from vo.queue). spw_force > 0 fixes the pair slots per warp (1..16);
+// wps > 0 caps the working warps at wps per SM sub-partition (slots refill).
+size_t pq_smem_bytes(int W1, uint32_t alpha, int threads);
+int pq_threads_for(int W1, uint32_t alpha);   // 0 if no block size fits
+cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,
+                             const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
+                             int32_t K, VerifyOut vo, cudaStream_t s);
 
 }  // namespace ej

@@ -135,7 +135,7 @@ extern "C" int ej_verify_noalloc(const ej_strings *S, const ej_params *p, const 
     VerifyConfig vc = verify_pick(p->K, alpha, max_len);
     if (vc.G == 0) return EJ_ERR_UNSUPPORTED;
     uint64_t *count = (uint64_t *)(err + 4);
-    VerifyOut vo{flags, nullptr, nullptr, 0, nullptr, err, nullptr};
+    VerifyOut vo{flags, nullptr, nullptr, 0, nullptr, err, nullptr, nullptr, nullptr};
     NA_CK(launch_verify(vc, packed, pofs, B, lens, n, alpha, pairs, n_pairs, p->K, max_len, vo, s));
     NA_CK(exclusive_scan_u8(flags, foffs, n_pairs, count, scan_b, s));
     uint64_t hc[2] = {0, 0};

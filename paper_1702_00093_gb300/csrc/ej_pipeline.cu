@@ -162,6 +162,94 @@ cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uin
     return cudaGetLastError();
 }
 
+// Same insertion, without appending: hcount[slot] counts the copies of each
+// pair, i.e. the number of (embedding, function) tables in which the two
+// strings collided. counters: [0] raw count (read).
+__global__ void dedup_count_kernel(const uint64_t *__restrict__ raw, uint64_t cap, uint64_t *__restrict__ table,
+                                   uint32_t *__restrict__ hcount, uint64_t hsize,
+                                   const unsigned long long *__restrict__ counters) {
+    const unsigned long long nraw_all = counters[0];
+    const int64_t nraw = (int64_t)(nraw_all < cap ? nraw_all : cap);
+    const uint64_t EMPTY = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nraw; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = raw[i];
+        uint64_t h = pair_hash(key) & (hsize - 1);
+        for (uint64_t probe = 0; probe < hsize; probe++) {
+            const unsigned long long old = atomicCAS((unsigned long long *)&table[h], EMPTY, key);
+            if (old == EMPTY || old == key) {
+                atomicAdd(&hcount[h], 1u);
+                break;
+            }
+            h = (h + 1) & (hsize - 1);
+        }
+    }
+}
+
+constexpr int COUNT_BINS = 256;
+
+// bins[min(count, 255)] += 1 over the occupied slots; counters[2] = pairs.
+__global__ void count_hist_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ hcount,
+                                  uint64_t hsize, unsigned long long *__restrict__ bins,
+                                  unsigned long long *__restrict__ counters) {
+    __shared__ unsigned int sb[COUNT_BINS];
+    for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x) sb[t] = 0;
+    __syncthreads();
+    unsigned int mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        if (table[i] != ~0ull) {
+            const uint32_t c = hcount[i];
+            atomicAdd(&sb[c < COUNT_BINS ? c : COUNT_BINS - 1], 1u);
+            mine++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&counters[2], (unsigned long long)mine);
+    __syncthreads();
+    for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x)
+        if (sb[t]) atomicAdd(&bins[t], (unsigned long long)sb[t]);
+}
+
+// bins -> start offsets, highest count first (in place).
+__global__ void count_scan_kernel(unsigned long long *__restrict__ bins) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int c = COUNT_BINS - 1; c >= 0; c--) {
+            const unsigned long long v = bins[c];
+            bins[c] = acc;
+            acc += v;
+        }
+    }
+}
+
+__global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ hcount,
+                                     uint64_t hsize, unsigned long long *__restrict__ cursor,
+                                     uint64_t *__restrict__ cand) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) {
+            const uint32_t c = hcount[i];
+            const unsigned long long pos = atomicAdd(&cursor[c < COUNT_BINS ? c : COUNT_BINS - 1], 1ull);
+            cand[pos] = key;
+        }
+    }
+}
+
+int count_bins() { return COUNT_BINS; }
+
+cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                 unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
+                                 cudaStream_t s) {
+    int64_t g = ((int64_t)cap + 255) / 256;
+    dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
+    int64_t gh = ((int64_t)hsize + 255) / 256;
+    const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
+    count_hist_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, bins, counters);
+    count_scan_kernel<<<1, 32, 0, s>>>(bins);
+    count_scatter_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, bins, cand);
+    note_launches(4);
+    return cudaGetLastError();
+}
+
 // Sorts up to SMALL_SORT_MAX uint64 keys in one block (bitonic network in
 // shared memory); the count comes from the device.
 constexpr int SMALL_SORT_MAX = 8192;

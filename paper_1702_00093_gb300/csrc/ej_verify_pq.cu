@@ -1,0 +1,423 @@
+// Persistent verifier: the same exact test ED(x, y) <= K as the banded
+// bit-parallel verifiers (Section 3.3, the last loop of Algorithm 3), with the
+// pairs pulled from a device work queue so that a lane pair whose pair is done
+// takes the next one instead of idling until the slowest pair of its warp ends.
+//
+// Per pair, two lanes: the forward half computes D(., n1) for n1 = n/2 over a
+// block-aligned window of W1 64-row words, the backward half runs the same
+// recurrence on the reversed strings for the remaining n - n1 columns, and
+// ED(x, y) = min_i D(i, n1) + ED(x[i:], y[n1:]) joins them (the argument and the
+// boundary conditions are the ones of the block-aligned two-lane verifier).
+//
+// Scheduling. A warp advances its 16 pair slots in chunks of 64 columns and a
+// slot starts a new pair only at a chunk boundary, so that column j of every
+// pair falls on chunk position (j - 1) mod 64: the window moves, which happen at
+// columns j = K + 1 + 64t, all fall on the same chunk position K mod 64 and run
+// once per chunk for the whole warp. A finished slot waits at most one chunk.
+// The number of working warps is capped (by default one per SM sub-partition),
+// so that a batch larger than the slots keeps every slot busy until the queue
+// runs dry.
+//
+// Early exit. At every window move each half computes the minimum value m_h of
+// its window (including the row above it). A path of cost <= K crosses both
+// halves' current columns inside their bands, where the values are exact, so
+// m_fwd + m_bwd > K proves ED > K; both lanes of the pair stop.
+#include "ej_bitpar.cuh"
+
+namespace ej {
+
+namespace {
+
+constexpr int PQ_MAX_THREADS = 128;
+constexpr int64_t kMaxIters = 1ll << 24;   // loop passes per warp before the kernel gives up
+
+// 64/B symbols of a packed string starting at symbol o (any int64; symbols
+// outside [0, len) read as code 0), symbol t in bits [B*t, B*t + B).
+template <int B>
+__device__ __forceinline__ uint64_t sym_u64(const uint64_t *__restrict__ y64, int64_t nwords, int64_t o) {
+    const int64_t bit = o * B;
+    const int64_t w0 = bit >= 0 ? (bit >> 6) : -((-bit + 63) >> 6);
+    const uint32_t sh = (uint32_t)(bit - 64 * w0);
+    const uint64_t a = (w0 >= 0 && w0 < nwords) ? y64[w0] : 0ull;
+    const uint64_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? y64[w0 + 1] : 0ull;
+    return sh ? ((a >> sh) | (b << (64u - sh))) : a;
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Reverses the order of the 64/B symbols of a word.
+template <int B>
+__device__ __forceinline__ uint64_t sym_reverse(uint64_t u) {
+    if (B == 8) {
+        const uint32_t lo = (uint32_t)u, hi = (uint32_t)(u >> 32);
+        return ((uint64_t)__byte_perm(lo, 0u, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0u, 0x0123);
+    }
+    const uint64_t r = __brevll(u);   // B == 2: reverse bits, then swap the two bits of each symbol
+    return ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
+}
+
+template <int W1, int B>
+__global__ void __launch_bounds__(PQ_MAX_THREADS)
+verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+                 const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
+                 const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t nsm, int32_t spw_force,
+                 int32_t wps, VerifyOut vo) {
+    uint32_t *__restrict__ err = vo.err;
+    if (vo.np_dev) {
+        const int64_t dn = (int64_t)*vo.np_dev;
+        np = dn < np ? dn : np;
+    }
+    constexpr int R = W1 + 1;
+    constexpr int SPW = 64 / B;              // symbols per 64-bit word
+    constexpr uint64_t CMASK = (1ull << B) - 1ull;
+    extern __shared__ uint64_t smem[];
+    __shared__ int8_t s_nsum[256];
+    __shared__ int8_t s_nmin[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        const uint32_t P = t & 15u, M = t >> 4;
+        int run = 0, mn = 1 << 20;
+        for (int k = 0; k < 4; k++) {
+            run += (int)((P >> k) & 1u) - (int)((M >> k) & 1u);
+            mn = run < mn ? run : mn;
+        }
+        s_nsum[t] = (int8_t)run;
+        s_nmin[t] = (int8_t)mn;
+    }
+    __syncthreads();
+    const int T_ = blockDim.x;                // slot stride of the per-thread ring
+    uint64_t *ring = smem + threadIdx.x;      // (c*R + slot)*T_, reused as a dump area
+    const int lane = threadIdx.x & 31;
+    const bool rev = lane & 1;
+    const int slot = lane >> 1;
+    const int32_t w_min = (2 * K + 1 + 63) / 64;
+    const int32_t smove = K & 63;             // chunk position of every window move
+    const uint32_t cmax = alpha - 1u;
+
+    // Slots per warp and working warps. The working warps are chosen per SM
+    // (the first ones to take a ticket on their SM), so that they are spread
+    // evenly over the SMs whatever order the blocks were placed in; at most
+    // 4*wps per SM (wps per sub-partition), fewer when the batch is small.
+    const int64_t spw = spw_force > 0 ? (spw_force > 16 ? 16 : spw_force) : 16;
+    const int64_t warps_needed = (np + spw - 1) / spw;
+    int64_t per_sm = (warps_needed + nsm - 1) / (nsm > 0 ? nsm : 1);
+    if (wps > 0 && per_sm > 4ll * wps) per_sm = 4ll * wps;
+    unsigned ticket = 0;
+    if (lane == 0) ticket = atomicAdd(&vo.sm_tickets[sm_id() & (SM_TICKETS - 1)], 1u);
+    ticket = __shfl_sync(FULL, ticket, 0);
+    bool exhausted = (slot >= spw) || ((int64_t)ticket >= per_sm);
+    if (__all_sync(FULL, exhausted)) return;
+
+    unsigned long long loc_cells = 0, loc_cols = 0;
+    bool have = false, rejected = false;
+    int64_t p = 0, k0 = 0;
+    const uint4 *xc = packed;
+    const uint64_t *y64 = reinterpret_cast<const uint64_t *>(packed);
+    int64_t ywords = 0;
+    int32_t m = 0, n = 0, ncols = 0, Tacc = 0, jbase = 1, next_move = 0, rej_col = 0;
+    int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
+    int64_t iters = 0;       // loop passes of this warp (bounded, see kMaxIters)
+    int base = 0;
+    uint32_t soff[W1];
+    uint64_t Pv[W1], Mv[W1];
+#pragma unroll
+    for (int v = 0; v < W1; v++) { soff[v] = 0; Pv[v] = 0; Mv[v] = 0; }
+
+    while (true) {
+        if (++iters > kMaxIters) {
+            if (lane == 0) atomicOr(err, (uint32_t)DERR_GUARD);
+            break;
+        }
+        // refill free slots (both lanes of a slot agree on `have` and `exhausted`)
+        while (true) {
+            const bool need = !have && !exhausted;
+            const unsigned nb = __ballot_sync(FULL, need && !rev);
+            if (nb == 0u) break;
+            const int leader = __ffs(nb) - 1;
+            unsigned long long qb = 0;
+            if (lane == leader) qb = atomicAdd(vo.queue, (unsigned long long)__popc(nb));
+            qb = __shfl_sync(FULL, qb, leader);
+            if (need) {
+                const unsigned fl = (unsigned)(lane & ~1);
+                const int64_t idx = (int64_t)qb + __popc(nb & ((1u << fl) - 1u));
+                if (idx >= np) {
+                    exhausted = true;
+                } else {
+                    p = idx;
+                    const uint64_t pr = pairs[p];
+                    const int64_t a = (int64_t)(pr >> 32), b = (int64_t)(pr & 0xFFFFFFFFull);
+                    if (a >= n_str || b >= n_str) {
+                        if (!rev) atomicOr(err, (uint32_t)DERR_PAIR);
+                    } else {
+                        const int32_t la = lens[a], lb = lens[b];
+                        const bool a_long = la >= lb;
+                        const int64_t xi = a_long ? a : b, yi = a_long ? b : a;
+                        m = a_long ? la : lb;
+                        n = a_long ? lb : la;
+                        if (!rev) loc_cells += band_cells(m, n, K);
+                        if (m - n > K || n == 0) {
+                            if (!rev) emit_result(vo, p, pairs, n == 0 && m <= K);
+                        } else {
+                            const int32_t n1 = n / 2;
+                            ncols = rev ? n - n1 : n1;
+                            xc = packed + pofs[xi];
+                            y64 = reinterpret_cast<const uint64_t *>(packed + pofs[yi]);
+                            ywords = 2 * chunks_for(n, B);
+                            for (int wi = 0; wi < W1; wi++) bd_build<B, R>(ring, T_, wi, xc, m, wi, rev, alpha);
+#pragma unroll
+                            for (int v = 0; v < W1; v++) {
+                                Pv[v] = ~0ull;
+                                Mv[v] = 0ull;
+                                soff[v] = (uint32_t)(v * T_);
+                            }
+                            base = 0;
+                            k0 = 0;
+                            Tacc = 0;
+                            jbase = 1;
+                            next_move = K + 1 + 64;
+                            rejected = false;
+                            budget = (ncols >> 6) + 3;
+                            have = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL, have)) break;
+
+        // one chunk: columns jbase .. jbase+63 of every active slot
+        int32_t lim = (have && !rejected) ? ncols - jbase : -1;   // steps s <= lim are columns of the pair
+        // symbols of y (forward) or of reversed y, 64/B per word; the word after
+        // the current one is requested one word ahead
+        auto sym_word = [&](int64_t sidx) -> uint64_t {
+            return sym_u64<B>(y64, ywords, rev ? (int64_t)n - SPW - sidx : sidx);
+        };
+        uint64_t sreg = 0, snext = sym_word((int64_t)jbase - 1);
+        auto run_cols = [&](int s_begin, int s_end) {
+            for (int s = s_begin; s < s_end; s++) {
+                if ((s & (SPW - 1)) == 0) {
+                    sreg = rev ? sym_reverse<B>(snext) : snext;
+                    snext = sym_word((int64_t)jbase - 1 + s + SPW);
+                }
+                uint32_t c = (uint32_t)(sreg & CMASK);
+                sreg >>= B;
+                c = c < cmax ? c : cmax;
+                if (s <= lim) {
+                    const uint64_t *row = ring + (size_t)c * R * T_;
+                    uint64_t Eq[W1], A[W1], S[W1];
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+                        Eq[v] = row[soff[v]];
+                        A[v] = Eq[v] & Pv[v];
+                    }
+                    add_chain<W1>(S, A, Pv);
+                    uint64_t Ph[W1], Mh[W1];
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+                        const uint64_t Xh = (S[v] ^ Pv[v]) | Eq[v];
+                        Ph[v] = Mv[v] | ~(Xh | Pv[v]);
+                        Mh[v] = Pv[v] & Xh;
+                    }
+#pragma unroll
+                    for (int v = W1 - 1; v >= 0; v--) {
+                        const uint64_t inP = (v > 0) ? (Ph[v > 0 ? v - 1 : 0] >> 63) : 1ull;
+                        const uint64_t inM = (v > 0) ? (Mh[v > 0 ? v - 1 : 0] >> 63) : 0ull;
+                        Ph[v] = (Ph[v] << 1) | inP;
+                        Mh[v] = (Mh[v] << 1) | inM;
+                    }
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+                        const uint64_t X = Eq[v] | Mv[v];
+                        Pv[v] = Mh[v] | ~(X | Ph[v]);
+                        Mv[v] = Ph[v] & X;
+                    }
+                }
+            }
+        };
+        run_cols(0, smove);
+        {
+            // window move before column j = jbase + smove, then the joint bound
+            const int32_t j = jbase + smove;
+            const bool moving = have && !rejected && j == next_move && j <= ncols;
+            int32_t lb = 0;
+            if (moving) {
+                next_move += 64;
+                Tacc += __popcll(Pv[0]) - __popcll(Mv[0]);
+#pragma unroll
+                for (int v = 0; v + 1 < W1; v++) { Pv[v] = Pv[v + 1]; Mv[v] = Mv[v + 1]; }
+                Pv[W1 - 1] = ~0ull;
+                Mv[W1 - 1] = 0ull;
+                k0++;
+                base = (base + 1 == R) ? 0 : base + 1;
+#pragma unroll
+                for (int v = 0; v < W1; v++) {
+                    const int sl = base + v;
+                    soff[v] = (uint32_t)((sl >= R ? sl - R : sl) * T_);
+                }
+                bd_build<B, R>(ring, T_, (int)(soff[W1 - 1] / (uint32_t)T_), xc, m, k0 + W1 - 1, rev, alpha);
+                // minimum over the window at column j-1; row 64*k0 (value T) takes part
+                int32_t run = 0, mn = 0;
+#pragma unroll
+                for (int v = 0; v < W1; v++) {
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
+                                             ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
+                        const int32_t cand = run + s_nmin[idx];
+                        mn = cand < mn ? cand : mn;
+                        run += s_nsum[idx];
+                    }
+                }
+                lb = Tacc + (j - 1) + mn;
+            }
+            const int32_t lb_other = __shfl_xor_sync(FULL, lb, 1);
+            if (moving && lb + lb_other > K) {
+                rejected = true;
+                rej_col = j;
+                lim = -1;
+            }
+        }
+        run_cols(smove, 64);
+        jbase += 64;
+        if (have && --budget < 0 && !rejected && jbase <= ncols) {
+            // cannot happen for a consistent state: stop this pair and report it
+            atomicOr(err, (uint32_t)DERR_GUARD);
+            rejected = true;
+            rej_col = jbase;
+        }
+
+        // finished pairs: both halves done (all columns run, or rejected)
+        const bool lane_done = have && (rejected || jbase > ncols);
+        // every lane takes part in the shuffle (a short-circuit here would leave
+        // the warp's other lanes waiting at a different collective)
+        const int partner_done = __shfl_xor_sync(FULL, lane_done ? 1 : 0, 1);
+        const bool pair_done = lane_done && partner_done != 0;
+        if (__any_sync(FULL, pair_done)) {
+            const int32_t T = Tacc + (rejected ? rej_col - 1 : ncols);
+            if (pair_done) {
+                loc_cols += (unsigned long long)(rejected ? rej_col - 1 : ncols) * (unsigned long long)w_min;
+#pragma unroll
+                for (int v = 0; v < W1; v++) {
+                    ring[(size_t)(2 * v) * T_] = Pv[v];
+                    ring[(size_t)(2 * v + 1) * T_] = Mv[v];
+                }
+                ring[(size_t)(2 * W1) * T_] = (uint64_t)(uint32_t)T | ((uint64_t)k0 << 32);
+                ring[(size_t)(2 * W1 + 1) * T_] = rejected ? 1ull : 0ull;
+            }
+            __syncwarp();
+            if (pair_done && !rev) {
+                bool pass = false;
+                const uint64_t *rb = smem + threadIdx.x + 1;   // backward half's dump
+                const bool rej_b = rb[(size_t)(2 * W1 + 1) * T_] != 0ull;
+                if (!rejected && !rej_b) {
+                    const uint64_t tb = rb[(size_t)(2 * W1) * T_];
+                    const int32_t Tb = (int32_t)(uint32_t)(tb & 0xFFFFFFFFull);
+                    const int64_t k0b = (int64_t)(tb >> 32);
+                    const int64_t k0f = k0;
+                    const uint64_t *rf = ring;
+                    // forward rows [64 k0f, min(m, 64(k0f+W1))]; backward row i' is row m - i'
+                    const int64_t f_hi = min((int64_t)m, 64 * (k0f + W1));
+                    const int64_t b_hi = min((int64_t)m, 64 * (k0b + W1));
+                    const int64_t i_lo = max(64 * k0f, (int64_t)m - b_hi);
+                    const int64_t i_hi = min(f_hi, (int64_t)m - 64 * k0b);
+                    if (i_lo <= i_hi) {
+                        auto prefix = [&](const uint64_t *dump, int64_t k0x, int32_t Tx, int64_t rowx) -> int32_t {
+                            int32_t acc = Tx;
+                            const int64_t nrows = rowx - 64 * k0x;
+                            for (int v = 0; v < W1; v++) {
+                                const int64_t lo = 64ll * v;
+                                if (lo >= nrows) break;
+                                const uint64_t msk = (nrows - lo >= 64) ? ~0ull : ((1ull << (nrows - lo)) - 1ull);
+                                acc += __popcll(dump[(size_t)(2 * v) * T_] & msk) -
+                                       __popcll(dump[(size_t)(2 * v + 1) * T_] & msk);
+                            }
+                            return acc;
+                        };
+                        int32_t F = prefix(rf, k0f, T, i_lo);
+                        int32_t Bv = prefix(rb, k0b, Tb, (int64_t)m - i_lo);
+                        int32_t best = F + Bv;
+                        for (int64_t i = i_lo; i < i_hi; i++) {
+                            const int64_t rf_ = i - 64 * k0f;                 // bit of row i+1 in the forward window
+                            const int64_t rb_ = (int64_t)m - i - 64 * k0b - 1; // bit of row m-i in the backward window
+                            const uint64_t fp = rf[(size_t)(2 * (rf_ >> 6)) * T_], fm = rf[(size_t)(2 * (rf_ >> 6) + 1) * T_];
+                            const uint64_t bp = rb[(size_t)(2 * (rb_ >> 6)) * T_], bm = rb[(size_t)(2 * (rb_ >> 6) + 1) * T_];
+                            F += (int32_t)((fp >> (rf_ & 63)) & 1ull) - (int32_t)((fm >> (rf_ & 63)) & 1ull);
+                            Bv -= (int32_t)((bp >> (rb_ & 63)) & 1ull) - (int32_t)((bm >> (rb_ & 63)) & 1ull);
+                            best = min(best, F + Bv);
+                        }
+                        pass = best <= K;
+                    }
+                }
+                emit_result(vo, p, pairs, pass);
+            }
+            __syncwarp();
+            if (pair_done) have = false;
+        }
+    }
+
+    if (vo.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loc_cells += __shfl_xor_sync(FULL, loc_cells, o);
+            loc_cols += __shfl_xor_sync(FULL, loc_cols, o);
+        }
+        if (lane == 0) {
+            if (loc_cells) atomicAdd(&vo.work[0], loc_cells);
+            if (loc_cols) atomicAdd(&vo.work[1], loc_cols);
+        }
+    }
+}
+
+template <int W1, int B>
+cudaError_t launch_pq_t(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
+                        const uint64_t *pairs, int64_t np, int32_t K, int threads, int spw_force, int wps, VerifyOut vo,
+                        cudaStream_t s) {
+    const size_t smem = pq_smem_bytes(W1, alpha, threads);
+    cudaError_t e = cudaFuncSetAttribute(verify_pq_kernel<W1, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_pq_kernel<W1, B>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t blocks = (int64_t)sms * per_sm;
+    verify_pq_kernel<W1, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
+                                                                     sms, spw_force, wps, vo);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t pq_smem_bytes(int W1, uint32_t alpha, int threads) {
+    const size_t R = (size_t)W1 + 1;
+    const size_t per = alpha * R > (size_t)(2 * W1 + 2) ? alpha * R : (size_t)(2 * W1 + 2);
+    return per * sizeof(uint64_t) * (size_t)threads;
+}
+
+int pq_threads_for(int W1, uint32_t alpha) {
+    for (int t = PQ_MAX_THREADS; t >= 32; t >>= 1)
+        if (pq_smem_bytes(W1, alpha, t) <= 160 * 1024) return t;
+    return pq_smem_bytes(W1, alpha, 32) <= 220 * 1024 ? 32 : 0;
+}
+
+cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,
+                             const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
+                             int32_t K, VerifyOut vo, cudaStream_t s) {
+    if (np == 0) return cudaGetLastError();
+    if (!vo.queue || !vo.sm_tickets || threads < 32 || threads > PQ_MAX_THREADS || (threads & 31)) return cudaErrorInvalidValue;
+#define EJ_PQ(WW)                                                                                          \
+    if (W1 == WW) {                                                                                        \
+        if (B == 2) return launch_pq_t<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, s); \
+        return launch_pq_t<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, s);   \
+    }
+    EJ_PQ(2) EJ_PQ(3) EJ_PQ(4) EJ_PQ(5) EJ_PQ(6) EJ_PQ(7) EJ_PQ(8) EJ_PQ(9) EJ_PQ(10) EJ_PQ(11) EJ_PQ(12)
+#undef EJ_PQ
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ej

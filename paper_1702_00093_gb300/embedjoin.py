@@ -28,13 +28,19 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
-            "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc"]
+            "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
+            "ej_set_schedule"]
 
 
 class EJError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
         self.status = status
+
+
+class _Schedule(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("slots_per_warp", C.c_int32), ("warps_per_subpartition", C.c_int32),
+                ("order", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -111,6 +117,8 @@ def lib():
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
+        L.ej_set_schedule.argtypes = [vp, C.POINTER(_Schedule)]
+        L.ej_set_schedule.restype = C.c_int
         _lib = L
     return _lib
 
@@ -209,6 +217,14 @@ class Context:
         """Verifier tiling (G lanes per pair, V words per lane); zeros = automatic."""
         self._check(lib().ej_set_verify_config(self._h, lanes_per_pair, words_per_lane, warps),
                     "ej_set_verify_config")
+
+    def set_schedule(self, mode: int = 0, slots_per_warp: int = 0, warps_per_subpartition: int = 0,
+                     order: int = 0):
+        """ej_join's back-half schedule (ej_schedule): mode 0 persistent work queue,
+        2 grid-strided; slots per warp; working warps per SM sub-partition; order 0/1
+        by collision count, 2 hash order. All zeros = defaults."""
+        sc = _Schedule(mode, slots_per_warp, warps_per_subpartition, order)
+        self._check(lib().ej_set_schedule(self._h, C.byref(sc)), "ej_set_schedule")
 
     def set_timing(self, on: bool = True):
         self._check(lib().ej_set_timing(self._h, 1 if on else 0), "ej_set_timing")

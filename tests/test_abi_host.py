@@ -76,9 +76,11 @@ int main(void) {{
   printf("ej_strings %zu\\n", sizeof(ej_strings));
   printf("ej_plan_info %zu\\n", sizeof(ej_plan_info));
   printf("ej_join_stats %zu\\n", sizeof(ej_join_stats));
+  printf("ej_schedule %zu\\n", sizeof(ej_schedule));
   F(ej_params, seed) F(ej_params, alphabet) F(ej_params, alphabet_size) F(ej_params, K)
   F(ej_plan_info, embedding_bytes) F(ej_plan_info, key_count)
   F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total)
+  F(ej_schedule, warps_per_subpartition) F(ej_schedule, order)
   return 0;
 }}''')
     exe = tmp_path / "probe"
@@ -89,7 +91,9 @@ int main(void) {{
     assert int(got["ej_strings"]) == C.sizeof(ej._Strings)
     assert int(got["ej_plan_info"]) == C.sizeof(ej.PlanInfo)
     assert int(got["ej_join_stats"]) == C.sizeof(ej.JoinStats)
-    pairs = {"ej_params": ej._Params, "ej_plan_info": ej.PlanInfo, "ej_join_stats": ej.JoinStats}
+    assert int(got["ej_schedule"]) == C.sizeof(ej._Schedule)
+    pairs = {"ej_params": ej._Params, "ej_plan_info": ej.PlanInfo, "ej_join_stats": ej.JoinStats,
+             "ej_schedule": ej._Schedule}
     for key, val in got.items():
         if "." not in key:
             continue

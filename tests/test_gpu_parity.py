@@ -338,3 +338,50 @@ def test_verify_every_tiling_is_exact(ej, ctx, K, alphabet):
     finally:
         ctx.set_verify_config(0, 0, 0)
     assert tried >= 3
+
+
+def _near_pair_set(rng, K, alphabet, n_base=20, max_len=700):
+    """Bases of random length with one mutated copy each (0 .. 2K+2 edits): many
+    candidates on both sides of the threshold."""
+    sigma = len(alphabet)
+    base = [rng.integers(0, sigma, size=int(rng.integers(1, max_len))).astype(np.uint8) for _ in range(n_base)]
+    strs = []
+    for b in base:
+        strs += [b, synth.mutate(rng, b, int(rng.integers(0, 2 * K + 3)), sigma)]
+    lut = np.frombuffer(alphabet, np.uint8)
+    return synth.pack([lut[x].tobytes() for x in strs], alphabet)
+
+
+@pytest.mark.parametrize("K,alphabet", [(6, b"ACGT"), (60, b"ACGT"), (150, b"ACGT"), (40, synth.PROTEIN),
+                                        (90, synth.TEXT)])
+def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
+    """ej_join's back half under every schedule (persistent work queue with 1..16
+    slots per warp and capped warps, grid-strided; collision-count or hash order)
+    and every two-lane window width gives the oracle's pair set."""
+    rng = np.random.default_rng(1000 + K)
+    ss = _near_pair_set(rng, K, alphabet)
+    z = 3 if len(alphabet) == 4 else 2
+    params = ej.Params(K=K, r=4, m=8, z=z, seed=5, L=200, alphabet=alphabet)
+    ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=K, r=4, m=8, z=z, seed=5, L=200)
+    assert ref.n_candidates > 20 and 0 < len(ref.pairs) < ref.n_candidates
+    s = ej.Strings.from_set(ss, DEV)
+    W = (2 * K + 1 + 63) // 64
+    runs = 0
+    try:
+        for sched in [(0, 0, 0, 0), (2, 0, 0, 0), (0, 1, 0, 0), (0, 2, 0, 2), (0, 5, 1, 0), (0, 16, 1, 1),
+                      (0, 16, 2, 2), (0, 3, 1, 0), (2, 0, 0, 2)]:
+            ctx.set_schedule(*sched)
+            pairs, stats = ctx.join(s, params, device=DEV)
+            assert stats.n_candidates == ref.n_candidates
+            assert np.array_equal(_np_u64(pairs), ref.pairs), sched
+            runs += 1
+        ctx.set_schedule(0, 0)
+        for V in range(W + 1, 13):
+            ctx.set_verify_config(2, V, 0)
+            pairs, _ = ctx.join(s, params, device=DEV)
+            assert np.array_equal(_np_u64(pairs), ref.pairs), V
+            runs += 1
+    finally:
+        ctx.set_schedule(0, 0)
+        ctx.set_verify_config(0, 0, 0)
+    assert runs >= 7
