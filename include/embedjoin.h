@@ -169,12 +169,19 @@ int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, in
  *   order: 0 (default) or 1: candidates enter the queue by decreasing number of
  *     tables in which the two strings collided (similar pairs, which run
  *     longest, start first); 2: hash-table order.
+ *   buckets: 0 (default) or 1: equal signatures are grouped by hashing (per
+ *     table an open-addressing set whose slots head lists of records); a
+ *     record pairs with the later records of its list, so a bucket of b strings
+ *     costs b*(b-1)/2 length checks. 2: the tables are sorted by (signature,
+ *     length) and each record pairs with the window after it (the
+ *     ej_lsh_candidates path; cheaper for huge buckets of uneven lengths).
  */
 typedef struct {
     int32_t mode;
     int32_t slots_per_warp;
     int32_t warps_per_subpartition;
     int32_t order;
+    int32_t buckets;
 } ej_schedule;
 
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside

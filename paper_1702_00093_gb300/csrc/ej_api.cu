@@ -26,7 +26,7 @@ enum BufId {
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
-    B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS,
+    B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS, B_BKEYS, B_BHEADS, B_BNEXT,
     B_NUM
 };
 
@@ -61,7 +61,7 @@ struct ej_ctx {
     uint64_t raw_cap_hint = 0;
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
-    ej_schedule sched{0, 0, 0, 0};   // ej_join's verifier schedule (ej_set_schedule)
+    ej_schedule sched{0, 0, 0, 0, 0};   // ej_join's back-half schedule (ej_set_schedule)
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -599,7 +599,24 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     const uint64_t *srk = nullptr;
     const uint32_t *srid = nullptr;
-    CKS(sorted_records(ctx, pl, p, keys, &srk, &srid, s));
+    uint32_t *bnext = nullptr;
+    uint32_t *derr0 = (uint32_t *)ctx->bufs[B_DERR].p;
+    const bool hashed = ctx->sched.buckets != 2 && n * T < (int64_t)0xFFFFFFFFll;
+    if (hashed) {
+        // buckets by hashing: no sort of the r*m tables
+        const uint64_t H = bucket_slots_per_table(n);
+        uint64_t *bkeys = nullptr;
+        uint32_t *bheads = nullptr;
+        CKS(ensure_t(ctx, B_BKEYS, (size_t)(H * T), &bkeys));
+        CKS(ensure_t(ctx, B_BHEADS, (size_t)(H * T), &bheads));
+        CKS(ensure_t(ctx, B_BNEXT, (size_t)(n * T), &bnext));
+        CK(cudaMemsetAsync(bkeys, 0xFF, H * T * sizeof(uint64_t), s));
+        CK(cudaMemsetAsync(bheads, 0xFF, H * T * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(derr0, 0, 4, s));
+        CK(launch_bucket_insert(keys, n, T, H, bkeys, bheads, bnext, derr0, s));
+    } else {
+        CKS(sorted_records(ctx, pl, p, keys, &srk, &srid, s));
+    }
     VerifyConfig vc;
     CKS(pick_verify(ctx, p, pl, &vc));
     unsigned long long *cnt = nullptr;
@@ -616,9 +633,12 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
         CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
         CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
         CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
-        CK(cudaMemsetAsync(derr, 0, 4, s));
+        if (!hashed) CK(cudaMemsetAsync(derr, 0, 4, s));
         CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
-        CK(launch_emit_append(srk, srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
+        if (hashed)
+            CK(launch_bucket_emit(pl.lens, n, T, p->K, bnext, raw, cap, cnt, s));
+        else
+            CK(launch_emit_append(srk, srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
         if (ctx->sched.order != 2) {
             // candidates handed to the verifier most-collided first: similar pairs,
             // which run longest, start first
@@ -654,7 +674,7 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
         CK(cudaStreamSynchronize(s));
         memcpy(hc, ctx->h_cnt, sizeof hc);
         if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
-        if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: verifier work bound exceeded");
+        if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
         if (hc[0] <= cap) break;
         if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
         cap = hc[0] + hc[0] / 4 + 1024;
@@ -796,13 +816,15 @@ int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
 int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
     if (!ctx) return EJ_ERR_INVALID_ARG;
     if (!sc) {
-        ctx->sched = ej_schedule{0, 0, 0, 0};
+        ctx->sched = ej_schedule{0, 0, 0, 0, 0};
         return EJ_OK;
     }
     if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
-        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 2)
-        return fail(ctx, EJ_ERR_INVALID_ARG, "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d not supported",
-                    sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order);
+        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 2 ||
+        sc->buckets < 0 || sc->buckets > 2)
+        return fail(ctx, EJ_ERR_INVALID_ARG,
+                    "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",
+                    sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order, sc->buckets);
     ctx->sched = *sc;
     return EJ_OK;
 }

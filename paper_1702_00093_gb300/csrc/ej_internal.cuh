@@ -210,6 +210,13 @@ cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const u
 cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens, int64_t n,
                                int64_t T, int32_t K, uint64_t *raw, uint64_t cap, unsigned long long *counters,
                                cudaStream_t s);
+// Buckets by hashing (ej_join): per-table signature sets of H slots
+// (bucket_slots_per_table(n)); slot_keys filled with ~0, heads with 0xFF bytes.
+uint64_t bucket_slots_per_table(int64_t n);
+cudaError_t launch_bucket_insert(const uint64_t *keys, int64_t n, int64_t T, uint64_t H, uint64_t *slot_keys,
+                                 uint32_t *heads, uint32_t *next, uint32_t *err, cudaStream_t s);
+cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_t K, const uint32_t *next,
+                               uint64_t *raw, uint64_t cap, unsigned long long *counters, cudaStream_t s);
 cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uint64_t hsize, uint64_t *cand,
                          unsigned long long *counters, cudaStream_t s);
 // Dedup that also orders the candidates by collision count (most first):

@@ -106,6 +106,145 @@ cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Buckets by hashing (Alg. 3's per-table grouping of equal signatures, without
+// sorting): table t owns the slots [t*H, (t+1)*H) of an open-addressing set of
+// signatures; each slot heads a list of the records (t*n + i) that carry its
+// signature, linked through next[] in insertion order. A record pairs with the
+// records after it in its list, so every unordered pair of a bucket is seen
+// exactly once, and the length filter ||s_i| - |s_j|| <= K applies per pair.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t key_hash(uint64_t k) {
+    k ^= k >> 31;
+    k *= 0x7fb5d329728ea185ull;
+    k ^= k >> 27;
+    k *= 0x81dadef4bc2dd44dull;
+    k ^= k >> 33;
+    return k;
+}
+
+constexpr uint32_t LIST_END = 0xFFFFFFFFu;
+
+// slot_keys pre-filled with ~0 (never a signature: keys are < 2^64 - 1) and
+// heads with LIST_END.
+__global__ void bucket_insert_kernel(const uint64_t *__restrict__ keys, int64_t n, int64_t T, uint64_t H,
+                                     uint64_t *__restrict__ slot_keys, uint32_t *__restrict__ heads,
+                                     uint32_t *__restrict__ next, uint32_t *__restrict__ err) {
+    const int64_t total = n * T;
+    for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < total; rec += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = rec / n;
+        const uint64_t key = keys[rec];
+        uint64_t *sk = slot_keys + t * H;
+        uint64_t h = key_hash(key) & (H - 1);
+        bool placed = false;
+        for (uint64_t probe = 0; probe < H; probe++) {
+            const unsigned long long old = atomicCAS((unsigned long long *)&sk[h], ~0ull, key);
+            if (old == ~0ull || old == key) {
+                next[rec] = atomicExch(&heads[t * H + h], (uint32_t)rec);
+                placed = true;
+                break;
+            }
+            h = (h + 1) & (H - 1);
+        }
+        if (!placed) atomicOr(err, (uint32_t)DERR_GUARD);   // cannot happen with H >= n
+    }
+}
+
+// Pairs of every record with the later records of its list that pass the
+// length filter. counters: [0] raw pairs (may exceed cap), [1] largest bucket.
+__global__ void bucket_emit_kernel(const int32_t *__restrict__ lens, int64_t n, int64_t T, int32_t K,
+                                   const uint32_t *__restrict__ next, uint64_t *__restrict__ raw, uint64_t cap,
+                                   unsigned long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = n * T;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iters = (total + step - 1) / step;   // the same on every lane: collectives converge
+    unsigned long long mb = 0;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t rec = start + it * step;
+        int64_t i = 0, base_t = 0;
+        uint32_t q0 = LIST_END;
+        unsigned long long cnt = 0, len_list = 0;
+        int32_t li = 0;
+        if (rec < total) {
+            base_t = (rec / n) * n;
+            i = rec - base_t;
+            li = lens[i];
+            q0 = next[rec];
+            for (uint32_t q = q0; q != LIST_END; q = next[q]) {
+                const int32_t lj = lens[(int64_t)q - base_t];
+                const int32_t d = li > lj ? li - lj : lj - li;
+                cnt += d <= K ? 1u : 0u;
+                len_list++;
+            }
+            mb = max(mb, len_list + 1);
+        }
+        unsigned long long incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+        unsigned long long base = 0;
+        if (wtotal) {
+            if (lane == 31) base = atomicAdd(&counters[0], wtotal);
+            base = __shfl_sync(FULL, base, 31);
+        }
+        if (cnt > 0) {
+            uint64_t o = base + incl - cnt;
+            for (uint32_t q = q0; q != LIST_END; q = next[q]) {
+                const int64_t j = (int64_t)q - base_t;
+                const int32_t lj = lens[j];
+                const int32_t d = li > lj ? li - lj : lj - li;
+                if (d <= K) {
+                    if (o < cap) {
+                        const uint64_t lo = (uint64_t)(i < j ? i : j), hi = (uint64_t)(i < j ? j : i);
+                        raw[o] = (lo << 32) | hi;
+                    }
+                    o++;
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(FULL, mb, o);
+        mb = v > mb ? v : mb;
+    }
+    if (lane == 0 && mb) atomicMax(&counters[1], mb);
+}
+
+uint64_t bucket_slots_per_table(int64_t n) {
+    uint64_t H = 1;
+    while (H < (uint64_t)n + (uint64_t)n / 2 + 1) H <<= 1;
+    return H;
+}
+
+cudaError_t launch_bucket_insert(const uint64_t *keys, int64_t n, int64_t T, uint64_t H, uint64_t *slot_keys,
+                                 uint32_t *heads, uint32_t *next, uint32_t *err, cudaStream_t s) {
+    const int64_t total = n * T;
+    if (total > 0) {
+        const int64_t g = (total + 255) / 256;
+        bucket_insert_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(keys, n, T, H, slot_keys, heads, next,
+                                                                               err);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_t K, const uint32_t *next,
+                               uint64_t *raw, uint64_t cap, unsigned long long *counters, cudaStream_t s) {
+    const int64_t total = n * T;
+    if (total > 0) {
+        const int64_t g = (total + 255) / 256;
+        bucket_emit_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(lens, n, T, K, next, raw, cap, counters);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ uint64_t pair_hash(uint64_t k) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;

@@ -356,8 +356,9 @@ def _near_pair_set(rng, K, alphabet, n_base=20, max_len=700):
                                         (90, synth.TEXT)])
 def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
     """ej_join's back half under every schedule (persistent work queue with 1..16
-    slots per warp and capped warps, grid-strided; collision-count or hash order)
-    and every two-lane window width gives the oracle's pair set."""
+    slots per warp and capped warps, grid-strided; collision-count or hash order;
+    hashed or sorted buckets) and every two-lane window width gives the oracle's
+    pair set."""
     rng = np.random.default_rng(1000 + K)
     ss = _near_pair_set(rng, K, alphabet)
     z = 3 if len(alphabet) == 4 else 2
@@ -368,8 +369,8 @@ def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
     W = (2 * K + 1 + 63) // 64
     runs = 0
     try:
-        for sched in [(0, 0, 0, 0), (2, 0, 0, 0), (0, 1, 0, 0), (0, 2, 0, 2), (0, 5, 1, 0), (0, 16, 1, 1),
-                      (0, 16, 2, 2), (0, 3, 1, 0), (2, 0, 0, 2)]:
+        for sched in [(0, 0, 0, 0, 0), (2, 0, 0, 0, 0), (0, 1, 0, 0, 2), (0, 2, 0, 2, 0), (0, 5, 1, 0, 2),
+                      (0, 16, 1, 1, 1), (0, 16, 2, 2, 0), (0, 3, 1, 0, 0), (2, 0, 0, 2, 2)]:
             ctx.set_schedule(*sched)
             pairs, stats = ctx.join(s, params, device=DEV)
             assert stats.n_candidates == ref.n_candidates
