@@ -155,6 +155,40 @@ int ej_set_timing(ej_ctx *ctx, int enable);
 int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
 
 /*
+ * Batched joins as one CUDA graph (a performance form of ej_join; the paper has
+ * no counterpart). ej_batch_create plans the strings once (validate, pack),
+ * runs every parameter set once eagerly to size all buffers (the raw-pair
+ * capacity gets a margin of 1/8), optionally autotunes each join's back half on
+ * its own data (EJ_BATCH_AUTOTUNE: the verifier schedule of ej_set_schedule),
+ * and captures the whole device path of all joins into one graph: validate and
+ * pack once, then per parameter set, on its own stream so that the joins
+ * overlap, the walk and signatures, buckets, pairs, dedup and verification.
+ * ej_batch_run replays the graph on `stream` without any host synchronisation;
+ * ej_batch_result(i) waits for it and returns join i's pairs (sorted, the same
+ * as ej_join with params[i]) and its counters (no stage timings).
+ *
+ * The strings must be in device memory; the graph reads them at the addresses
+ * given here, so their contents may be rewritten between runs (by the caller,
+ * on the same stream) as long as n stays, offsets[n] does not grow and the
+ * longest string does not grow (nor change, when out_len and L are 0).
+ * ej_batch_result reports a violation (EJ_ERR_INVALID_ARG) or raw pairs beyond
+ * the capacity (EJ_ERR_CAPACITY); re-create the batch then. All parameter sets
+ * share one alphabet; injected test tables are not supported. The stream must
+ * not be the legacy default stream (it is captured). The batch keeps its own
+ * scratch per parameter set and must be destroyed before its context.
+ */
+typedef struct ej_batch ej_batch;
+#define EJ_BATCH_AUTOTUNE 1
+int ej_batch_create(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, int32_t n_params,
+                    int32_t flags, ej_batch **batch, void *stream);
+int ej_batch_run(ej_batch *batch, void *stream);
+int ej_batch_result(ej_batch *batch, int32_t index, uint64_t *out, int64_t capacity, int64_t *n_out,
+                    ej_join_stats *stats, void *stream);
+/* Kernel launches one ej_batch_run makes (kernel nodes of the graph). */
+int64_t ej_batch_kernel_count(const ej_batch *batch);
+void ej_batch_destroy(ej_batch *batch);
+
+/*
  * Schedule of ej_join's back half (a performance choice: the output never
  * depends on it; the paper has no counterpart).
  *   mode: 0 (default) persistent verifier where the band fits two lanes per pair

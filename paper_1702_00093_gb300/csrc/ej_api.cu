@@ -201,6 +201,8 @@ struct Plan {
     int64_t nb32 = 0;
 };
 
+int derive_lsh(ej_ctx *ctx, const ej_params *p, Plan *pl);
+
 // Stage strings, validate, compute lengths and derived sizes (synchronises s).
 int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_lsh, Plan *pl, cudaStream_t s) {
     if (!S) return fail(ctx, EJ_ERR_INVALID_ARG, "strings is NULL");
@@ -230,7 +232,7 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     CK(cudaMemsetAsync(derr, 0, 4 * sizeof(uint32_t), s));
     CKS(ensure_t(ctx, B_LENS, (size_t)(n > 0 ? n : 1), &pl->lens));
     unsigned long long *dmax = (unsigned long long *)(derr + 2);
-    CK(launch_validate(pl->st.bytes, pl->st.offsets, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->lens,
+    CK(launch_validate(pl->st.bytes, pl->st.offsets, n, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->lens,
                        derr, dmax, s));
     // pack into B-bit codes: chunk counts -> offsets -> pack (flags bad symbols)
     pl->B = packed_bits_for(p->alphabet_size);
@@ -255,7 +257,14 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     if (e & DERR_OFFSETS) return fail(ctx, EJ_ERR_INVALID_ARG, "offsets must start at 0 and be non-decreasing, lengths < 2^31");
     if (e & DERR_SYMBOL) return fail(ctx, EJ_ERR_INVALID_ARG, "a string byte is not in the alphabet");
     pl->max_len = (int64_t)((unsigned long long)ctx->h_cnt[1]);
-    if (need_lsh) {
+    if (need_lsh) CKS(derive_lsh(ctx, p, pl));
+    return EJ_OK;
+}
+
+// The parameter-dependent sizes of a plan: out_len (3N unless given), L, planes.
+int derive_lsh(ej_ctx *ctx, const ej_params *p, Plan *pl) {
+    const int64_t n = pl->st.n;
+    {
         uint64_t ol = p->out_len ? p->out_len : (uint64_t)(3 * pl->max_len);
         if (ol == 0) ol = 1;
         if (ol > 0x7fffffffull) return fail(ctx, EJ_ERR_INVALID_ARG, "out_len too large");
@@ -272,6 +281,23 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
         for (uint32_t v : ctx->posinj)
             if (v >= pl->L) return fail(ctx, EJ_ERR_INVALID_ARG, "injected position %u >= L", v);
     }
+    return EJ_OK;
+}
+
+// The device work of make_plan for an existing plan (validate -> chunk counts
+// -> scan -> pack), with the plan's sizes as bounds; no host synchronisation.
+int plan_device(ej_ctx *ctx, const Plan &pl, cudaStream_t s) {
+    const int64_t n = pl.st.n;
+    uint32_t *derr = (uint32_t *)ctx->bufs[B_DERR].p;
+    CK(cudaMemsetAsync(derr, 0, 4 * sizeof(uint32_t), s));
+    unsigned long long *dmax = (unsigned long long *)(derr + 2);
+    CK(launch_validate(pl.st.bytes, pl.st.offsets, n, pl.st.total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.lens,
+                       derr, dmax, s));
+    uint32_t *ccnt = (uint32_t *)ctx->bufs[B_CHUNK_CNT].p;
+    CK(launch_chunk_counts(pl.lens, n, pl.B, ccnt, s));
+    CK(exclusive_scan_u32(ccnt, (uint64_t *)pl.pofs, n + 1, nullptr, ctx->bufs[B_SCAN_TMP3].p, s));
+    CK(launch_pack(pl.st.bytes, pl.st.offsets, pl.lens, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.B, pl.pofs,
+                   (uint4 *)pl.packed, derr, s));
     return EJ_OK;
 }
 
@@ -588,98 +614,121 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
     return EJ_OK;
 }
 
-// ej_join's back half without host round trips between stages: bucket windows
-// append pairs, a device hash set keeps the first copy of each pair, the
-// verifier reads the candidate count from the device and appends passing pairs,
-// and only the output is sorted. The host reads the counters once, after the
-// verifier; if the raw pairs outgrew the capacity it enlarges it and reruns
-// from the append step (the sorted records are kept).
-int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t *out,
-              int64_t capacity, int64_t *n_out, ej_join_stats *stats, cudaStream_t s) {
-    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+// ej_join's back half without host round trips between stages: bucket the
+// signatures, emit the pairs of every bucket, a device hash set keeps the first
+// copy of each pair, the verifier reads the candidate count from the device and
+// appends passing pairs, and only the output is sorted. The host reads the
+// counters once, after the verifier; if the raw pairs outgrew the capacity it
+// enlarges it and reruns from the emit step (the buckets are kept).
+// back_buckets + back_attempt issue device work only (no host synchronisation,
+// no allocation once the buffers have their size), so they can be captured.
+struct BackState {
+    bool hashed = false;
     const uint64_t *srk = nullptr;
     const uint32_t *srid = nullptr;
     uint32_t *bnext = nullptr;
-    uint32_t *derr0 = (uint32_t *)ctx->bufs[B_DERR].p;
-    const bool hashed = ctx->sched.buckets != 2 && n * T < (int64_t)0xFFFFFFFFll;
-    if (hashed) {
+    VerifyConfig vc{0, 0, 0};
+};
+
+int back_buckets(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, BackState *bs,
+                 cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
+    uint32_t *derr = nullptr;
+    CKS(ensure_t(ctx, B_DERR, 8, &derr));
+    CK(cudaMemsetAsync(derr, 0, 4, s));
+    bs->hashed = ctx->sched.buckets != 2 && n * T < (int64_t)0xFFFFFFFFll;
+    if (bs->hashed) {
         // buckets by hashing: no sort of the r*m tables
         const uint64_t H = bucket_slots_per_table(n);
         uint64_t *bkeys = nullptr;
         uint32_t *bheads = nullptr;
         CKS(ensure_t(ctx, B_BKEYS, (size_t)(H * T), &bkeys));
         CKS(ensure_t(ctx, B_BHEADS, (size_t)(H * T), &bheads));
-        CKS(ensure_t(ctx, B_BNEXT, (size_t)(n * T), &bnext));
+        CKS(ensure_t(ctx, B_BNEXT, (size_t)(n * T), &bs->bnext));
         CK(cudaMemsetAsync(bkeys, 0xFF, H * T * sizeof(uint64_t), s));
         CK(cudaMemsetAsync(bheads, 0xFF, H * T * sizeof(uint32_t), s));
-        CK(cudaMemsetAsync(derr0, 0, 4, s));
-        CK(launch_bucket_insert(keys, n, T, H, bkeys, bheads, bnext, derr0, s));
+        CK(launch_bucket_insert(keys, n, T, H, bkeys, bheads, bs->bnext, derr, s));
     } else {
-        CKS(sorted_records(ctx, pl, p, keys, &srk, &srid, s));
+        CKS(sorted_records(ctx, pl, p, keys, &bs->srk, &bs->srid, s));
     }
-    VerifyConfig vc;
-    CKS(pick_verify(ctx, p, pl, &vc));
+    CKS(pick_verify(ctx, p, pl, &bs->vc));
+    return EJ_OK;
+}
+
+uint64_t raw_cap_start(ej_ctx *ctx, int64_t n) {
+    return ctx->raw_cap_hint ? ctx->raw_cap_hint : (uint64_t)(n * 4 > 65536 ? n * 4 : 65536);
+}
+
+int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackState &bs, uint64_t cap,
+                 cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     unsigned long long *cnt = nullptr;
     CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
     uint32_t *derr = (uint32_t *)ctx->bufs[B_DERR].p;
-    uint64_t cap = ctx->raw_cap_hint ? ctx->raw_cap_hint : (uint64_t)(n * 4 > 65536 ? n * 4 : 65536);
+    uint64_t hsize = 1;
+    while (hsize < 2 * cap) hsize <<= 1;
     uint64_t *raw = nullptr, *cand = nullptr, *table = nullptr, *app = nullptr;
-    unsigned long long hc[8];
-    for (int attempt = 0;; attempt++) {
-        uint64_t hsize = 1;
-        while (hsize < 2 * cap) hsize <<= 1;
-        CKS(ensure_t(ctx, B_RAW, (size_t)cap, &raw));
-        CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
-        CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
-        CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
-        CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
-        if (!hashed) CK(cudaMemsetAsync(derr, 0, 4, s));
-        CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
-        if (hashed)
-            CK(launch_bucket_emit(pl.lens, n, T, p->K, bnext, raw, cap, cnt, s));
-        else
-            CK(launch_emit_append(srk, srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
-        if (ctx->sched.order != 2) {
-            // candidates handed to the verifier most-collided first: similar pairs,
-            // which run longest, start first
-            uint32_t *hcount = nullptr;
-            unsigned long long *bins = nullptr;
-            CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
-            CKS(ensure_t(ctx, B_BINS, (size_t)count_bins(), &bins));
-            CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
-            CK(cudaMemsetAsync(bins, 0, count_bins() * sizeof(unsigned long long), s));
-            CK(launch_dedup_ordered(raw, cap, table, hcount, hsize, bins, cand, cnt, s));
-        } else {
-            CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
-        }
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
-        unsigned int *tickets = nullptr;
-        CKS(ensure_t(ctx, B_TICKETS, (size_t)SM_TICKETS, &tickets));
-        CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
-        VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
-        const int pq_threads = (vc.G == 2 && ctx->sched.mode != 2) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
-        if (pq_threads > 0)
-            // defaults: 16 slots per warp, one working warp per SM sub-partition (the
-            // slots refill from the queue); measured best on the long-DNA shapes
-            CK(launch_verify_pq(vc.V, pq_threads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
-                                ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1,
-                                pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K, vo,
-                                s));
-        else
-            CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
-                             pl.max_len, vo, s));
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
-        CK(cudaMemcpyAsync(ctx->h_cnt, cnt, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(ctx->h_cnt + 6, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        memcpy(hc, ctx->h_cnt, sizeof hc);
-        if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
-        if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
-        if (hc[0] <= cap) break;
-        if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
-        cap = hc[0] + hc[0] / 4 + 1024;
+    CKS(ensure_t(ctx, B_RAW, (size_t)cap, &raw));
+    CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
+    CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
+    CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
+    CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
+    if (bs.hashed)
+        CK(launch_bucket_emit(pl.lens, n, T, p->K, bs.bnext, raw, cap, cnt, s));
+    else
+        CK(launch_emit_append(bs.srk, bs.srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
+    if (ctx->sched.order != 2) {
+        // candidates handed to the verifier most-collided first: similar pairs,
+        // which run longest, start first
+        uint32_t *hcount = nullptr;
+        unsigned long long *bins = nullptr;
+        CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
+        CKS(ensure_t(ctx, B_BINS, (size_t)count_bins(), &bins));
+        CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(bins, 0, count_bins() * sizeof(unsigned long long), s));
+        CK(launch_dedup_ordered(raw, cap, table, hcount, hsize, bins, cand, cnt, s));
+    } else {
+        CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
     }
-    ctx->raw_cap_hint = cap;
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
+    unsigned int *tickets = nullptr;
+    CKS(ensure_t(ctx, B_TICKETS, (size_t)SM_TICKETS, &tickets));
+    CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
+    VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
+    const VerifyConfig &vc = bs.vc;
+    const int pq_threads = (vc.G == 2 && ctx->sched.mode != 2) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
+    if (pq_threads > 0)
+        // defaults: 16 slots per warp, one working warp per SM sub-partition (the
+        // slots refill from the queue); measured best on the long-DNA shapes
+        CK(launch_verify_pq(vc.V, pq_threads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
+                            ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1,
+                            pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K, vo,
+                            s));
+    else
+        CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
+                         pl.max_len, vo, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
+    return EJ_OK;
+}
+
+// Counters of the last attempt: [0] raw, [1] max bucket, [2] candidates,
+// [3] output, [4] band cells, [5] word columns, [6] device error bits.
+int back_read(ej_ctx *ctx, unsigned long long hc[8], cudaStream_t s) {
+    CK(cudaMemcpyAsync(ctx->h_cnt, ctx->bufs[B_JCOUNT].p, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt + 6, ctx->bufs[B_DERR].p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(hc, ctx->h_cnt, 8 * sizeof(unsigned long long));
+    hc[6] &= 0xffffffffull;
+    if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+    if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
+    return EJ_OK;
+}
+
+// Sort the appended output pairs and copy them to `out`.
+int back_finish(ej_ctx *ctx, const Plan &pl, const ej_params *p, const unsigned long long hc[8], uint64_t *out,
+                int64_t capacity, int64_t *n_out, ej_join_stats *stats, cudaStream_t s) {
+    const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     const int64_t cntout = (int64_t)hc[3];
     if (stats) {
         stats->n_raw_pairs = (int64_t)hc[0];
@@ -693,7 +742,8 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
     if (cntout > capacity)
         return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cntout, (long long)capacity);
     if (cntout == 0) return EJ_OK;
-    // sort the output pairs
+    uint64_t *app = (uint64_t *)ctx->bufs[B_APP].p, *raw = (uint64_t *)ctx->bufs[B_RAW].p;
+    unsigned long long *cnt = (unsigned long long *)ctx->bufs[B_JCOUNT].p;
     const uint64_t *sorted = app;
     if (cntout <= small_sort_max()) {
         CK(launch_small_sort(app, cnt + 3, (uint64_t)cntout, s));
@@ -718,6 +768,23 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
     return EJ_OK;
 }
 
+int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t *out,
+              int64_t capacity, int64_t *n_out, ej_join_stats *stats, cudaStream_t s) {
+    BackState bs;
+    CKS(back_buckets(ctx, pl, p, keys, &bs, s));
+    uint64_t cap = raw_cap_start(ctx, pl.st.n);
+    unsigned long long hc[8];
+    for (int attempt = 0;; attempt++) {
+        CKS(back_attempt(ctx, pl, p, bs, cap, s));
+        CKS(back_read(ctx, hc, s));
+        if (hc[0] <= cap) break;
+        if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
+        cap = hc[0] + hc[0] / 4 + 1024;
+    }
+    ctx->raw_cap_hint = cap;
+    return back_finish(ctx, pl, p, hc, out, capacity, n_out, stats, s);
+}
+
 // Output array: device pointer or a staging buffer to copy to host after.
 int out_target(ej_ctx *ctx, BufId id, void *user, size_t bytes, void **dev, bool *is_host) {
     if (is_device_ptr(user)) {
@@ -730,6 +797,102 @@ int out_target(ej_ctx *ctx, BufId id, void *user, size_t bytes, void **dev, bool
 }
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+#define CKB(b, expr)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) return fail((b)->ctx, EJ_ERR_CUDA, "%s", cudaGetErrorString(e_)); \
+    } while (0)
+
+// One join of a batch: its own context (scratch, counters), parameters and plan.
+struct BatchJoin {
+    ej_ctx *sub = nullptr;
+    ej_params p{};
+    std::vector<uint8_t> alphabet;
+    Plan pl;
+    BackState bs;
+    uint64_t cap = 0;
+    uint64_t *keys = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct ej_batch {
+    ej_ctx *ctx = nullptr;
+    Plan pl;
+    std::vector<BatchJoin> joins;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernel_nodes = 0;
+    bool ran = false;
+};
+
+namespace {
+
+void batch_free(ej_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto &j : b->joins) {
+        if (j.done) cudaEventDestroy(j.done);
+        if (j.side) cudaStreamDestroy(j.side);
+        if (j.sub) ej_destroy(j.sub);
+    }
+    delete b;
+}
+
+// Device work of one join (keys -> buckets -> pairs -> dedup -> verify) on its
+// side stream; no host synchronisation.
+int batch_join_device(BatchJoin &j, cudaStream_t s) {
+    CKS(keys_dev(j.sub, &j.p, j.pl, j.keys, s));
+    CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
+    CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s));
+    return EJ_OK;
+}
+
+// Schedules the autotuner tries for the back half of one join (verifier slots
+// per warp, working warps per SM sub-partition, queue order); the fastest on
+// the join's own data wins.
+const ej_schedule kTuneSet[] = {
+    {0, 16, 1, 0, 0}, {0, 16, 2, 0, 0}, {0, 8, 1, 0, 0}, {0, 16, 1, 2, 0}, {0, 12, 1, 0, 0}, {2, 0, 0, 0, 0},
+};
+
+int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
+    ej_ctx *ctx = j.sub;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    ej_schedule best_sc = j.sub->sched;
+    for (const ej_schedule &sc : kTuneSet) {
+        j.sub->sched = sc;
+        float t = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            CK(cudaEventRecord(e0, s));
+            CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
+            CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) t += ms;   // the first repetition warms the schedule up
+        }
+        if (t < best) {
+            best = t;
+            best_sc = sc;
+        }
+    }
+    j.sub->sched = best_sc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best_ms = best / 2.f;
+    return EJ_OK;
+}
+
 
 }  // namespace
 
@@ -1034,5 +1197,156 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     }
     return EJ_OK;
 }
+
+
+int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, int32_t n_params, int32_t flags,
+                    ej_batch **out, void *stream) {
+    if (!ctx || !out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/out");
+    *out = nullptr;
+    if (!S || !params || n_params < 1 || n_params > 64)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "a batch needs strings and 1..64 parameter sets");
+    if ((flags & ~EJ_BATCH_AUTOTUNE) != 0) return fail(ctx, EJ_ERR_INVALID_ARG, "unknown batch flags %d", flags);
+    if (S->n < 2 || !is_device_ptr(S->bytes) || !is_device_ptr(S->offsets))
+        return fail(ctx, EJ_ERR_INVALID_ARG, "a batch needs n >= 2 strings in device memory");
+    if (ctx->pi.size() || ctx->posinj.size())
+        return fail(ctx, EJ_ERR_INVALID_ARG, "injected test tables are not supported in a batch");
+    for (int32_t i = 1; i < n_params; i++)
+        if (params[i].alphabet_size != params[0].alphabet_size ||
+            memcmp(params[i].alphabet, params[0].alphabet, params[0].alphabet_size) != 0)
+            return fail(ctx, EJ_ERR_INVALID_ARG, "all parameter sets of a batch share one alphabet");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    ej_batch *b = new (std::nothrow) ej_batch();
+    if (!b) return EJ_ERR_OOM;
+    b->ctx = ctx;
+    const bool timing_was = ctx->timing;
+    ctx->timing = false;
+    auto bail = [&](int st) { ctx->timing = timing_was; batch_free(b); return st; };
+    int st = make_plan(ctx, S, &params[0], true, &b->pl, s);
+    if (st != EJ_OK) return bail(st);
+    b->joins.resize((size_t)n_params);
+    for (int32_t i = 0; i < n_params; i++) {
+        BatchJoin &j = b->joins[(size_t)i];
+        j.p = params[i];
+        j.alphabet.assign(params[i].alphabet, params[i].alphabet + params[i].alphabet_size);
+        j.p.alphabet = j.alphabet.data();
+        if ((st = check_params(ctx, &j.p, true)) != EJ_OK) return bail(st);
+        j.pl = b->pl;
+        if ((st = derive_lsh(ctx, &j.p, &j.pl)) != EJ_OK) return bail(st);
+        if ((st = ej_create(&j.sub, ctx->device)) != EJ_OK) return bail(st);
+        j.sub->sched = ctx->sched;
+        j.sub->vG = ctx->vG;
+        j.sub->vV = ctx->vV;
+        j.sub->vWarps = ctx->vWarps;
+        if (cudaStreamCreateWithFlags(&j.side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(ctx, EJ_ERR_CUDA, "stream/event creation failed"));
+        if ((st = upload_alphabet(j.sub, &j.p, s)) != EJ_OK) return bail(st);
+        if ((st = ensure_t(j.sub, B_KEYS, (size_t)j.p.r * j.p.m * b->pl.st.n, &j.keys)) != EJ_OK) return bail(st);
+        // eager pass: sizes every buffer (the raw-pair capacity gets a margin)
+        if ((st = keys_dev(j.sub, &j.p, j.pl, j.keys, s)) != EJ_OK) return bail(st);
+        if ((st = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s)) != EJ_OK) return bail(st);
+        uint64_t cap = raw_cap_start(j.sub, b->pl.st.n);
+        unsigned long long hc[8];
+        for (int attempt = 0;; attempt++) {
+            if ((st = back_attempt(j.sub, j.pl, &j.p, j.bs, cap, s)) != EJ_OK) return bail(st);
+            if ((st = back_read(j.sub, hc, s)) != EJ_OK) return bail(st);
+            if (hc[0] <= cap) break;
+            if (attempt > 2) return bail(fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts"));
+            cap = hc[0] + hc[0] / 4 + 1024;
+        }
+        j.cap = cap + cap / 8 + 1024;
+        if ((st = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s)) != EJ_OK) return bail(st);
+        if (flags & EJ_BATCH_AUTOTUNE) {
+            float ms = 0.f;
+            if ((st = batch_autotune(j, s, &ms)) != EJ_OK) return bail(st);
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager pass failed"));
+    }
+    // capture: plan (validate, pack) on the caller's stream, then every join on
+    // its own stream, joined back at the end
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_CUDA, "stream capture could not start (the stream must not be the legacy default stream)"));
+    int cst = plan_device(ctx, b->pl, s);
+    if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    for (auto &j : b->joins) {
+        if (cst != EJ_OK) break;
+        if (cudaStreamWaitEvent(j.side, b->fork, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
+        cst = batch_join_device(j, j.side);
+        if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
+        if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (cst != EJ_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return bail(cst != EJ_OK ? cst : fail(ctx, EJ_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_CUDA, "graph instantiation failed"));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) b->kernel_nodes++;
+    }
+    ctx->timing = timing_was;
+    *out = b;
+    return EJ_OK;
+}
+
+int ej_batch_run(ej_batch *b, void *stream) {
+    if (!b || !b->exec) return EJ_ERR_INVALID_ARG;
+    cudaSetDevice(b->ctx->device);
+    CKB(b, cudaGraphLaunch(b->exec, as_stream(stream)));
+    b->ran = true;
+    return EJ_OK;
+}
+
+int ej_batch_result(ej_batch *b, int32_t i, uint64_t *out, int64_t capacity, int64_t *n_out, ej_join_stats *stats,
+                    void *stream) {
+    if (!b || !n_out) return EJ_ERR_INVALID_ARG;
+    ej_ctx *ctx = b->ctx;
+    *n_out = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (i < 0 || (size_t)i >= b->joins.size()) return fail(ctx, EJ_ERR_INVALID_ARG, "join index %d out of range", i);
+    if (!b->ran) return fail(ctx, EJ_ERR_INVALID_ARG, "ej_batch_run has not been called");
+    if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    // the plan's validation of this run's strings
+    CK(cudaMemcpyAsync(ctx->h_cnt, ctx->bufs[B_DERR].p, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t e = (uint32_t)(ctx->h_cnt[0] & 0xffffffffu);
+    if (e & DERR_OFFSETS)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "offsets invalid or grown beyond the batch's plan (%lld bytes)", (long long)b->pl.st.total);
+    if (e & DERR_SYMBOL) return fail(ctx, EJ_ERR_INVALID_ARG, "a string byte is not in the alphabet");
+    const int64_t max_len = (int64_t)((unsigned long long)ctx->h_cnt[1]);
+    BatchJoin &j = b->joins[(size_t)i];
+    if (max_len > b->pl.max_len || (!j.p.out_len && !j.p.L && max_len != b->pl.max_len))
+        return fail(ctx, EJ_ERR_INVALID_ARG, "the longest string changed (%lld, planned %lld): re-create the batch",
+                    (long long)max_len, (long long)b->pl.max_len);
+    unsigned long long hc[8];
+    CKS(back_read(j.sub, hc, s));
+    if (hc[0] > j.cap)
+        return fail(ctx, EJ_ERR_CAPACITY, "raw pairs (%llu) exceed the batch's capacity (%llu): re-create the batch",
+                    hc[0], (unsigned long long)j.cap);
+    int64_t cnt = 0;
+    const int st = back_finish(j.sub, j.pl, &j.p, hc, out, capacity, &cnt, stats, s);
+    *n_out = cnt;
+    if (st != EJ_OK) return fail(ctx, st, "%s", ej_last_error(j.sub));
+    CK(cudaStreamSynchronize(s));
+    return EJ_OK;
+}
+
+int64_t ej_batch_kernel_count(const ej_batch *b) { return b ? b->kernel_nodes : 0; }
+
+void ej_batch_destroy(ej_batch *b) { batch_free(b); }
 
 }  // extern "C"

@@ -8,16 +8,19 @@ namespace ej {
 // Validation: offsets, lengths, symbols
 // ---------------------------------------------------------------------------
 
-__global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int64_t n,
+// total_cap bounds offsets[n]: beyond it every length is reported as 0 (and
+// DERR_OFFSETS set), so that buffers sized for total_cap bytes are never overrun.
+__global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int64_t n, int64_t total_cap,
                                         int32_t *__restrict__ lens, uint32_t *__restrict__ err,
                                         unsigned long long *__restrict__ max_len) {
     unsigned long long local_max = 0;
     uint32_t local_err = 0;
+    const bool over = offsets[n] > total_cap;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t a = offsets[i], b = offsets[i + 1];
         int64_t len = b - a;
-        if ((i == 0 && a != 0) || len < 0 || len >= (1ll << 31)) {
+        if (over || (i == 0 && a != 0) || len < 0 || len >= (1ll << 31)) {
             local_err |= DERR_OFFSETS;
             len = 0;
         }
@@ -35,13 +38,13 @@ __global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int
     }
 }
 
-cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n,
+cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n, int64_t total_cap,
                             const uint8_t *code_map, int32_t *lens, uint32_t *err,
                             unsigned long long *max_len, cudaStream_t s) {
     if (n > 0) {
         int grid = (int)((n + 255) / 256);
         if (grid > 4096) grid = 4096;
-        validate_offsets_kernel<<<grid, 256, 0, s>>>(offsets, n, lens, err, max_len);
+        validate_offsets_kernel<<<grid, 256, 0, s>>>(offsets, n, total_cap, lens, err, max_len);
         note_launches(1);
     }
     return cudaGetLastError();

@@ -106,7 +106,7 @@ enum : uint32_t {
 
 // Validation + lengths: lens[i] = offsets[i+1]-offsets[i]; err |= DERR_*;
 // stats[0] = max length (int64 via unsigned max), stats[1] = total bytes.
-cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n,
+cudaError_t launch_validate(const uint8_t *bytes, const int64_t *offsets, int64_t n, int64_t total_cap,
                             const uint8_t *code_map, int32_t *lens, uint32_t *err,
                             unsigned long long *max_len, cudaStream_t s);
 

@@ -122,7 +122,7 @@ extern "C" int ej_verify_noalloc(const ej_strings *S, const ej_params *p, const 
     NA_CK(cudaMemsetAsync(err, 0, 64, s));
     NA_CK(cudaMemcpyAsync(d_map, map, 256, cudaMemcpyHostToDevice, s));
     unsigned long long *dmax = (unsigned long long *)(err + 2);
-    NA_CK(launch_validate(S->bytes, S->offsets, n, d_map, lens, err, dmax, s));
+    NA_CK(launch_validate(S->bytes, S->offsets, n, total, d_map, lens, err, dmax, s));
     NA_CK(launch_chunk_counts(lens, n, B, ccnt, s));
     NA_CK(exclusive_scan_u32(ccnt, pofs, n + 1, nullptr, scan_a, s));
     NA_CK(launch_pack(S->bytes, S->offsets, lens, n, d_map, B, pofs, packed, err, s));

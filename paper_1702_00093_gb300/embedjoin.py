@@ -29,7 +29,8 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
-            "ej_set_schedule"]
+            "ej_set_schedule", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_batch_destroy"]
 
 
 class EJError(RuntimeError):
@@ -119,6 +120,17 @@ def lib():
         L.ej_set_verify_config.restype = C.c_int
         L.ej_set_schedule.argtypes = [vp, C.POINTER(_Schedule)]
         L.ej_set_schedule.restype = C.c_int
+        L.ej_batch_create.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), C.c_int32, C.c_int32,
+                                      C.POINTER(vp), vp]
+        L.ej_batch_create.restype = C.c_int
+        L.ej_batch_run.argtypes = [vp, vp]
+        L.ej_batch_run.restype = C.c_int
+        L.ej_batch_result.argtypes = [vp, C.c_int32, vp, i64, C.POINTER(i64), C.POINTER(JoinStats), vp]
+        L.ej_batch_result.restype = C.c_int
+        L.ej_batch_kernel_count.argtypes = [vp]
+        L.ej_batch_kernel_count.restype = i64
+        L.ej_batch_destroy.argtypes = [vp]
+        L.ej_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -275,6 +287,11 @@ class Context:
                                     _ptr(out), C.byref(n), _stream(stream)), "ej_verify")
         return n.value
 
+    def batch(self, s: Strings, params: list, autotune: bool = False, stream=None) -> "Batch":
+        """ej_batch_create: all joins of `params` over device strings `s` as one CUDA
+        graph (see Batch). `stream` must not be the legacy default stream."""
+        return Batch(self, s, params, autotune, stream)
+
     def join_into(self, s: Strings, p: Params, out, stream=None) -> tuple[int, JoinStats]:
         """ej_join into a caller buffer. Raises EJError with .needed on overflow."""
         cs, (cp, _keep) = s._c(), p._c()
@@ -351,3 +368,67 @@ def decode_embedding(emb_words: np.ndarray, walk_end: np.ndarray, r: int, n: int
     steps = np.arange(out_len)[None, None, :]
     codes = np.where(steps >= np.asarray(walk_end)[:, :, None], alphabet_size, codes).astype(np.uint8)
     return codes
+
+
+EJ_BATCH_AUTOTUNE = 1
+
+
+class Batch:
+    """ej_batch: the device path of several joins over the same device strings,
+    captured once as a CUDA graph. run() replays it (no host sync); result(i)
+    waits and returns join i's sorted pairs, as ej_join would."""
+
+    def __init__(self, ctx: Context, s: Strings, params: list, autotune: bool = False, stream=None):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        self._keep = [s, params]
+        cs = s._c()
+        cps = [p._c() for p in params]
+        arr = (_Params * len(params))(*[cp for cp, _ in cps])
+        self._keep.append(cps)
+        st = lib().ej_batch_create(ctx._h, C.byref(cs), arr, len(params), EJ_BATCH_AUTOTUNE if autotune else 0,
+                                   C.byref(self._h), _stream(stream))
+        ctx._check(st, "ej_batch_create")
+        self.n = len(params)
+        self.kernel_count = int(lib().ej_batch_kernel_count(self._h))
+
+    def run(self, stream=None):
+        self._ctx._check(lib().ej_batch_run(self._h, _stream(stream)), "ej_batch_run")
+
+    def result_into(self, i: int, out, stream=None) -> tuple[int, JoinStats]:
+        n = C.c_int64(0)
+        stats = JoinStats()
+        cap = 0 if out is None else int(out.shape[0])
+        st = lib().ej_batch_result(self._h, i, _ptr(out), cap, C.byref(n), C.byref(stats), _stream(stream))
+        if st == EJ_ERR_CAPACITY and n.value > cap:
+            e = EJError(st, "ej_batch_result: capacity")
+            e.needed = n.value
+            raise e
+        self._ctx._check(st, "ej_batch_result")
+        return n.value, stats
+
+    def result(self, i: int, device=None, capacity: int = 1 << 16, stream=None):
+        while True:
+            if device is None:
+                out = np.zeros(max(capacity, 1), dtype=np.uint64)
+            else:
+                import torch
+                out = torch.empty(max(capacity, 1), dtype=torch.int64, device=device)
+            try:
+                n, stats = self.result_into(i, out, stream)
+                return out[:n], stats
+            except EJError as e:
+                if getattr(e, "needed", None) is None:
+                    raise
+                capacity = e.needed
+
+    def close(self):
+        if self._h:
+            lib().ej_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,137 @@
+"""Batched joins as one CUDA graph (ej_batch_*): every join of the batch returns
+exactly what ej_join returns for the same parameters (and the oracle's pair
+set), across replays, after the strings are rewritten in place, and with the
+autotuner on; misuse is reported, not run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00093_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ej():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_00093_gb300 import build
+    build.build()
+    oracle.build()
+    from paper_1702_00093_gb300 import embedjoin
+    return embedjoin
+
+
+@pytest.fixture(scope="module")
+def ctx(ej):
+    c = ej.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.Stream()
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _params(ej, ss, Ks, kw):
+    return [ej.Params(K=K, alphabet=ss.alphabet, **kw(K)) for K in Ks]
+
+
+def test_batch_equals_join_and_oracle_long_dna(ej, ctx, stream):
+    ss = synth.long_dna(n_clusters=4, seed=77)
+    s = ej.Strings.from_set(ss, DEV)
+
+    def kw(K):
+        p = synth.long_dna_params(K)
+        return dict(r=p["r"], m=p["m"], z=p["z"], seed=p["seed"], L=p["L"])
+
+    params = _params(ej, ss, [50, 150, 250], kw)
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, stream=stream)
+        assert b.kernel_count > 3 * 10
+        for rep in range(2):
+            b.run(stream)
+            for i, p in enumerate(params):
+                got, st = b.result(i, device=DEV, stream=stream)
+                want, st_j = ctx.join(s, p, device=DEV, stream=stream)
+                assert np.array_equal(_u64(got), _u64(want))
+                assert st.n_candidates == st_j.n_candidates
+                if rep == 0:
+                    ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=p.K, r=p.r, m=p.m, z=p.z, seed=p.seed,
+                                      L=p.L)
+                    assert np.array_equal(_u64(got), ref.pairs)
+        b.close()
+
+
+def test_batch_rerun_after_rewriting_strings(ej, ctx, stream):
+    ss = synth.small_dna(0.5)
+    s = ej.Strings.from_set(ss, DEV)
+    params = _params(ej, ss, [4, 6, 9], lambda K: dict(r=3, m=10, z=12, seed=1))
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, stream=stream)
+        for rnd in range(3):
+            if rnd > 0:
+                # rewrite the contents in place (same lengths): rotate the alphabet
+                lut = torch.zeros(256, dtype=torch.uint8, device=DEV)
+                for c in range(4):
+                    lut[ss.alphabet[c]] = ss.alphabet[(c + rnd) % 4]
+                s.data.copy_(lut[s.data.long()])
+            b.run(stream)
+            for i, p in enumerate(params):
+                got, _ = b.result(i, device=DEV, stream=stream)
+                want, _ = ctx.join(s, p, device=DEV, stream=stream)
+                assert np.array_equal(_u64(got), _u64(want)), (rnd, i)
+        b.close()
+
+
+def test_batch_autotune_keeps_results(ej, ctx, stream):
+    ss = synth.protein_like(6, 200, median=150, lo=40, hi=500)
+    s = ej.Strings.from_set(ss, DEV)
+    L = int(2 * ss.lengths().mean())
+    params = _params(ej, ss, [10, 25], lambda K: dict(r=4, m=6, z=5, seed=3, L=L))
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, autotune=True, stream=stream)
+        b.run(stream)
+        for i, p in enumerate(params):
+            got, _ = b.result(i, device=DEV, stream=stream)
+            ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=p.K, r=p.r, m=p.m, z=p.z, seed=p.seed, L=p.L)
+            assert np.array_equal(_u64(got), ref.pairs)
+        b.close()
+
+
+def test_batch_misuse_is_reported(ej, ctx, stream):
+    ss = synth.small_dna(0.2)
+    params = _params(ej, ss, [5], lambda K: dict(r=2, m=4, z=8, seed=1))
+    # host strings
+    with pytest.raises(ej.EJError):
+        ctx.batch(ej.Strings(ss.data, ss.offsets), params, stream=stream)
+    # different alphabets in one batch
+    s = ej.Strings.from_set(ss, DEV)
+    other = ej.Params(K=5, r=2, m=4, z=8, seed=1, alphabet=b"ACGTN")
+    with pytest.raises(ej.EJError):
+        ctx.batch(s, params + [other], stream=stream)
+    # offsets[n] grows beyond the plan: the bytes buffer really holds the extra
+    # bytes, the validation kernel zeroes every length and flags it
+    data = torch.cat([torch.from_numpy(ss.data).to(DEV), torch.full((4096,), ord("A"), dtype=torch.uint8,
+                                                                     device=DEV)])
+    offs = torch.from_numpy(ss.offsets.astype(np.int64)).to(DEV)
+    s2 = ej.Strings(data, offs)
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s2, params, stream=stream)
+        b.run(stream)
+        b.result(0, device=DEV, stream=stream)
+        offs[-1] += 1000
+        b.run(stream)
+        with pytest.raises(ej.EJError) as e:
+            b.result(0, device=DEV, stream=stream)
+        assert e.value.status == ej.EJ_ERR_INVALID_ARG
+        b.close()
