@@ -165,7 +165,8 @@ int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, in
  * overlap, the walk and signatures, buckets, pairs, dedup and verification.
  * ej_batch_run replays the graph on `stream` without any host synchronisation;
  * ej_batch_result(i) waits for it and returns join i's pairs (sorted, the same
- * as ej_join with params[i]) and its counters (no stage timings).
+ * as ej_join with params[i]) and its counters (no stage timings;
+ * kernel_launches counts the kernels of the result call itself).
  *
  * The strings must be in device memory; the graph reads them at the addresses
  * given here, so their contents may be rewritten between runs (by the caller,

@@ -1320,6 +1320,7 @@ int ej_batch_result(ej_batch *b, int32_t i, uint64_t *out, int64_t capacity, int
     if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
+    const int64_t launches0 = launches_so_far();
     // the plan's validation of this run's strings
     CK(cudaMemcpyAsync(ctx->h_cnt, ctx->bufs[B_DERR].p, 16, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1342,6 +1343,7 @@ int ej_batch_result(ej_batch *b, int32_t i, uint64_t *out, int64_t capacity, int
     *n_out = cnt;
     if (st != EJ_OK) return fail(ctx, st, "%s", ej_last_error(j.sub));
     CK(cudaStreamSynchronize(s));
+    if (stats) stats->kernel_launches = launches_so_far() - launches0;   // the output sort
     return EJ_OK;
 }
 

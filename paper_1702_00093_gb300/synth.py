@@ -248,5 +248,23 @@ def protein_workload(n: int = 200000) -> StringSet:
     return protein_like(1003, n)
 
 
+def protein_params(K: int) -> dict:
+    """Protein-like workload: K = 10% / 15% of the median length 400 (40, 60);
+    r=7, m=7 (one table per embedding), z=8, L = twice the average length."""
+    return dict(K=K, r=7, m=7, z=8, L=890, seed=1)
+
+
+PROTEIN_KS = (40, 60)
+
+
 def text_workload(n: int = 350000) -> StringSet:
     return text_like(1004, n)
+
+
+def text_params(K: int) -> dict:
+    """Text-like workload: r=7, m=7, z = 10 / 9 / 9 for K = 100 / 200 / 300,
+    L = twice the average length."""
+    return dict(K=K, r=7, m=7, z={100: 10, 200: 9, 300: 9}.get(K, 9), L=3800, seed=1)
+
+
+TEXT_KS = (100, 200, 300)
