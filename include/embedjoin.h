@@ -155,6 +155,81 @@ int ej_set_timing(ej_ctx *ctx, int enable);
 int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
 
 /*
+ * Similarity search against a resident index (EmbedJoin's structure kept on the
+ * device; the paper has no serving counterpart). ej_index_create packs the
+ * strings, builds the walk tables and sampled positions of `params` (r, m, z, L,
+ * seed, alphabet; K is not used; L must be > 0 so that queries of any length are
+ * walked over the same sampling range) and groups every string's r*m signatures
+ * into per-table buckets. Synchronises `stream`. The index keeps its own device
+ * memory (packed strings, tables, buckets: about 1.4 GB for 10^6 strings with
+ * r = m = 7) until ej_index_destroy.
+ *
+ * ej_index_search finds, for every query q (host strings) with threshold K[q],
+ * the index strings s that share a signature with q in some table, pass
+ * ||q| - |s|| <= K[q] and have ED(q, s) <= K[q] (the join's candidate rule and
+ * test, from the query's side). Output: (q << 32 | s) ascending, q = query
+ * position, s = index position. Synchronous (one search batch; stream unused).
+ * Errors: EJ_ERR_INVALID_ARG (a query byte outside the alphabet, bad offsets,
+ * K < 0, device query buffers), EJ_ERR_CAPACITY (*n_out = needed).
+ */
+typedef struct ej_index ej_index;
+int ej_index_create(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, ej_index **index,
+                    void *stream);
+int64_t ej_index_size(const ej_index *index);
+int ej_index_search(ej_ctx *ctx, ej_index *index, const ej_strings *queries, const int32_t *K, uint64_t *out,
+                    int64_t capacity, int64_t *n_out, void *stream);
+void ej_index_destroy(ej_index *index);
+
+/*
+ * Serving loop over an index with continuous batching. A worker thread keeps up
+ * to `inflight` search batches on the GPU, each on its own stream with its own
+ * scratch; whenever one finishes it delivers its results and the requests that
+ * arrived meanwhile form the next batch (up to max_batch queries and
+ * max_batch_bytes query bytes), so batches overlap on the device. A batch whose
+ * scratch would have to grow is admitted only if the growth fits the free device
+ * memory minus hbm_reserve (and the server's total stays within hbm_budget, 0 =
+ * no budget); otherwise its requests wait. Results are the same as
+ * ej_index_search for the same query and K, whatever else is in flight.
+ *   ej_server_submit copies the query and returns a request id >= 0, or
+ *     -EJ_ERR_INVALID_ARG (byte outside the alphabet, K < 0).
+ *   ej_server_poll returns up to `max` finished requests (waiting up to wait_us
+ *     for the first); `matches` (ascending index positions) stays valid until
+ *     ej_server_release(id). latency_ms = submit to results; queue_ms = submit to
+ *     the launch of its batch.
+ *   ej_server_get_stats: latency percentiles over the requests finished since the
+ *     start or the last ej_server_reset_stats, batches, mean batch size,
+ *     queries/s over that span, capacity retries, deferred admissions.
+ */
+typedef struct ej_server ej_server;
+typedef struct {
+    int32_t max_batch;          /* queries per batch (0 = 256) */
+    int32_t inflight;           /* batches on the GPU at once (0 = 4) */
+    int64_t max_batch_bytes;    /* query bytes per batch (0 = 8 MiB) */
+    uint64_t hbm_reserve;       /* device memory left free (0 = 1 GiB) */
+    uint64_t hbm_budget;        /* cap on the server's scratch (0 = none) */
+} ej_server_config;
+typedef struct {
+    int64_t id;
+    int32_t status;
+    int32_t n_matches;
+    const uint32_t *matches;
+    double latency_ms;
+    double queue_ms;
+} ej_search_result;
+typedef struct {
+    int64_t completed, batches, retries, deferred;
+    double mean_batch, p50_ms, p99_ms, mean_ms, queries_per_s;
+    uint64_t device_bytes;
+} ej_server_stats;
+int ej_server_create(ej_index *index, const ej_server_config *config, ej_server **server);
+int64_t ej_server_submit(ej_server *server, const uint8_t *query, int32_t len, int32_t K);
+int ej_server_poll(ej_server *server, ej_search_result *out, int32_t max, int32_t *n, int32_t wait_us);
+int ej_server_release(ej_server *server, int64_t id);
+int ej_server_get_stats(ej_server *server, ej_server_stats *stats);
+int ej_server_reset_stats(ej_server *server);
+void ej_server_destroy(ej_server *server);
+
+/*
  * Batched joins as one CUDA graph (a performance form of ej_join; the paper has
  * no counterpart). ej_batch_create plans the strings once (validate, pack),
  * runs every parameter set once eagerly to size all buffers (the raw-pair

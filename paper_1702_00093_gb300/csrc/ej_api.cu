@@ -896,6 +896,32 @@ int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
 
 }  // namespace
 
+namespace ej {
+
+int ctx_pack(ej_ctx *ctx, const ej_strings *S, const ej_params *p, PackedSet *out, void *stream) {
+    cudaSetDevice(ctx->device);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, as_stream(stream)));
+    out->packed = pl.packed;
+    out->pofs = pl.pofs;
+    out->lens = pl.lens;
+    out->n = pl.st.n;
+    out->max_len = pl.max_len;
+    out->total = pl.st.total;
+    out->B = pl.B;
+    out->code_map = (const uint8_t *)ctx->bufs[B_CODEMAP].p;
+    out->alphabet_dev = (const uint8_t *)ctx->bufs[B_ALPHABET].p;
+    return EJ_OK;
+}
+
+int ctx_device(const ej_ctx *ctx) { return ctx->device; }
+
+int ctx_fail(ej_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
+
+int ctx_check_params(ej_ctx *ctx, const ej_params *p) { return check_params(ctx, p, true); }
+
+}  // namespace ej
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -225,6 +225,30 @@ int count_bins();
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
                                  cudaStream_t s);
+// Strings validated and packed into a context's buffers (valid until the next
+// call that plans strings on that context), for the index and the server.
+struct PackedSet {
+    const uint4 *packed;
+    const uint64_t *pofs;
+    const int32_t *lens;
+    int64_t n, max_len, total;
+    int B;
+    const uint8_t *code_map;       // raw byte -> code (255 = not in the alphabet), 256 entries
+    const uint8_t *alphabet_dev;   // the alphabet's bytes
+};
+int ctx_pack(ej_ctx *ctx, const ej_strings *S, const ej_params *p, PackedSet *out, void *stream);
+int ctx_device(const ej_ctx *ctx);
+int ctx_fail(ej_ctx *ctx, int code, const char *msg);
+int ctx_check_params(ej_ctx *ctx, const ej_params *p);
+
+// Search against a resident index (hashed buckets of the index's tables).
+cudaError_t launch_index_probe(const uint64_t *qkeys, int64_t Q, int64_t T, const int32_t *qlens, const int32_t *qK,
+                               const uint64_t *slot_keys, const uint32_t *heads, uint64_t H, const uint32_t *next,
+                               const int32_t *lens, int64_t n, uint64_t *raw, uint64_t cap,
+                               unsigned long long *counters, cudaStream_t s);
+cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                 const uint8_t *cls, int nc, unsigned long long *bins, uint64_t *cand,
+                                 unsigned long long *counters, cudaStream_t s);
 int small_sort_max();
 cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s);
 
@@ -247,6 +271,16 @@ struct VerifyOut {
     unsigned long long *work;
     unsigned long long *queue;   // work-queue head of the persistent verifier (zeroed before the launch)
     unsigned int *sm_tickets;    // per-SM working-warp tickets (SM_TICKETS entries, zeroed before the launch)
+    // Search (query x index) pairs (a << 32 | b): when packed_b is set, b indexes
+    // this second string set instead of the first (the persistent and grouped
+    // verifiers); thr[a], when set, is the pair's threshold (the query's K, at
+    // most the band's K), else K.
+    const uint4 *packed_b;
+    const uint64_t *pofs_b;
+    const int32_t *lens_b;
+    int64_t n_b;
+    const int32_t *thr;
+    const unsigned long long *pairs_off_dev;   // when set, the pairs start this many entries in (device value)
 };
 
 constexpr int SM_TICKETS = 1024;

@@ -389,6 +389,155 @@ cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *ta
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Search against a resident index (query x index pairs)
+// ---------------------------------------------------------------------------
+
+// For every (table t, query q): the index records that carry q's signature in
+// table t (one hash lookup in the table's signature set, then its record list)
+// and pass |len_q - len_i| <= K_q; pairs (q << 32 | i). counters: [0] raw pairs
+// (may exceed cap), [1] longest record list met.
+__global__ void index_probe_kernel(const uint64_t *__restrict__ qkeys, int64_t Q, int64_t T,
+                                   const int32_t *__restrict__ qlens, const int32_t *__restrict__ qK,
+                                   const uint64_t *__restrict__ slot_keys, const uint32_t *__restrict__ heads,
+                                   uint64_t H, const uint32_t *__restrict__ next, const int32_t *__restrict__ lens,
+                                   int64_t n, uint64_t *__restrict__ raw, uint64_t cap,
+                                   unsigned long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = Q * T;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iters = (total + step - 1) / step;   // the same on every lane: collectives converge
+    unsigned long long mb = 0;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t idx = start + it * step;
+        uint32_t q0 = LIST_END;
+        int64_t q = 0, base_t = 0;
+        int32_t lq = 0, kq = 0;
+        unsigned long long cnt = 0, len_list = 0;
+        if (idx < total) {
+            const int64_t t = idx / Q;
+            q = idx - t * Q;
+            base_t = t * n;
+            lq = qlens[q];
+            kq = qK[q];
+            const uint64_t key = qkeys[idx];
+            const uint64_t *sk = slot_keys + t * H;
+            uint64_t h = key_hash(key) & (H - 1);
+            for (uint64_t probe = 0; probe < H; probe++) {
+                const uint64_t v = sk[h];
+                if (v == key) {
+                    q0 = heads[t * H + h];
+                    break;
+                }
+                if (v == ~0ull) break;
+                h = (h + 1) & (H - 1);
+            }
+            for (uint32_t r = q0; r != LIST_END; r = next[r]) {
+                const int32_t li = lens[(int64_t)r - base_t];
+                const int32_t d = lq > li ? lq - li : li - lq;
+                cnt += d <= kq ? 1u : 0u;
+                len_list++;
+            }
+            mb = max(mb, len_list);
+        }
+        unsigned long long incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+        unsigned long long base = 0;
+        if (wtotal) {
+            if (lane == 31) base = atomicAdd(&counters[0], wtotal);
+            base = __shfl_sync(FULL, base, 31);
+        }
+        if (cnt > 0) {
+            uint64_t o = base + incl - cnt;
+            for (uint32_t r = q0; r != LIST_END; r = next[r]) {
+                const int64_t i = (int64_t)r - base_t;
+                const int32_t li = lens[i];
+                const int32_t d = lq > li ? lq - li : li - lq;
+                if (d <= kq) {
+                    if (o < cap) raw[o] = ((uint64_t)q << 32) | (uint64_t)i;
+                    o++;
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(FULL, mb, o);
+        mb = v > mb ? v : mb;
+    }
+    if (lane == 0 && mb) atomicMax(&counters[1], mb);
+}
+
+cudaError_t launch_index_probe(const uint64_t *qkeys, int64_t Q, int64_t T, const int32_t *qlens, const int32_t *qK,
+                               const uint64_t *slot_keys, const uint32_t *heads, uint64_t H, const uint32_t *next,
+                               const int32_t *lens, int64_t n, uint64_t *raw, uint64_t cap,
+                               unsigned long long *counters, cudaStream_t s) {
+    const int64_t total = Q * T;
+    if (total > 0) {
+        const int64_t g = (total + 255) / 256;
+        index_probe_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(qkeys, Q, T, qlens, qK, slot_keys, heads,
+                                                                              H, next, lens, n, raw, cap, counters);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// Dedup of query x index pairs, grouped by the verifier class of the query:
+// bins[c] = pairs of class c, bins[nc + c] = their start in cand (classes in
+// order), counters[2] = all pairs. bins (3*nc) and hcount start at zero.
+__global__ void class_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const uint8_t *__restrict__ cls,
+                                  unsigned long long *__restrict__ bins, unsigned long long *__restrict__ counters) {
+    unsigned int mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) {
+            atomicAdd(&bins[cls[key >> 32]], 1ull);
+            mine++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&counters[2], (unsigned long long)mine);
+}
+
+__global__ void class_scan_kernel(unsigned long long *__restrict__ bins, int nc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int c = 0; c < nc; c++) {
+            bins[nc + c] = acc;       // start
+            bins[2 * nc + c] = acc;   // cursor
+            acc += bins[c];
+        }
+    }
+}
+
+__global__ void class_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize,
+                                     const uint8_t *__restrict__ cls, unsigned long long *__restrict__ cursor,
+                                     uint64_t *__restrict__ cand) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) cand[atomicAdd(&cursor[cls[key >> 32]], 1ull)] = key;
+    }
+}
+
+cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                 const uint8_t *cls, int nc, unsigned long long *bins, uint64_t *cand,
+                                 unsigned long long *counters, cudaStream_t s) {
+    int64_t g = ((int64_t)cap + 255) / 256;
+    dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
+    int64_t gh = ((int64_t)hsize + 255) / 256;
+    const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
+    class_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, cls, bins, counters);
+    class_scan_kernel<<<1, 32, 0, s>>>(bins, nc);
+    class_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, cls, bins + 2 * nc, cand);
+    note_launches(4);
+    return cudaGetLastError();
+}
+
 // Sorts up to SMALL_SORT_MAX uint64 keys in one block (bitonic network in
 // shared memory); the count comes from the device.
 constexpr int SMALL_SORT_MAX = 8192;

@@ -50,6 +50,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
         const int64_t dn = (int64_t)*vo.np_dev;
         np = dn < np ? dn : np;
     }
+    if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
     constexpr int GPW = 32 / G;
     const int32_t w_min = (2 * K + 1 + 63) / 64;
     extern __shared__ uint64_t smem[];
@@ -78,31 +79,35 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
     for (int64_t wb = (int64_t)blockIdx.x * warps_per_block + warp; wb * GPW < np; wb += warps_total) {
         const int64_t p = wb * GPW + g;
         bool valid = p < np;
-        int32_t la = 0, lb = 0;
+        int32_t la = 0, lb = 0, kp = K;
         int64_t a = 0, b = 0;
+        const bool two = vo.packed_b != nullptr;   // b indexes the second set
         if (valid) {
             const uint64_t pr = pairs[p];
             a = (int64_t)(pr >> 32);
             b = (int64_t)(pr & 0xFFFFFFFFull);
-            if (a >= n_str || b >= n_str) {
+            if (a >= n_str || b >= (two ? vo.n_b : n_str)) {
                 if (gl == 0) atomicOr(err, (uint32_t)DERR_PAIR);
                 valid = false;
             } else {
                 la = lens[a];
-                lb = lens[b];
+                lb = two ? vo.lens_b[b] : lens[b];
+                kp = vo.thr ? vo.thr[a] : K;
             }
         }
         const bool a_long = la >= lb;
-        const int64_t xi = valid ? (a_long ? a : b) : 0, yi = valid ? (a_long ? b : a) : 0;
+        const uint4 *pa = packed + (valid ? pofs[a] : 0);
+        const uint4 *pb = valid ? (two ? vo.packed_b + vo.pofs_b[b] : packed + pofs[b]) : packed;
+        const uint4 *xc_base = a_long ? pa : pb, *yc_base = a_long ? pb : pa;
         const int32_t mlen = a_long ? la : lb;
         const int32_t nlen = a_long ? lb : la;
         bool decided = !valid;
         bool pass = false;
-        if (valid && mlen - nlen > K) {
+        if (valid && mlen - nlen > kp) {
             decided = true;
         } else if (valid && nlen == 0) {
             decided = true;
-            pass = mlen <= K;
+            pass = mlen <= kp;
         }
         int32_t ncols = decided ? 0 : nlen;
         const int32_t mrows = decided ? 0 : mlen;
@@ -111,7 +116,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
         // Peq[c]: bit K+i set iff code(x[i]) == c
         const int32_t mmax = __reduce_max_sync(FULL, mrows);
         if (mmax > 0) {
-            const uint4 *xc = packed + pofs[xi];
+            const uint4 *xc = xc_base;
             const int64_t xch = chunks_for(mrows, B);
             if (B == 2) {
                 // whole 64-bit words from the 2-bit codes, no atomics
@@ -150,7 +155,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
             __syncwarp();
         }
         SymReader<B> yr;
-        yr.init(packed + pofs[yi], chunks_for(ncols, B));
+        yr.init(yc_base, chunks_for(ncols, B));
 
         // column 0: rows -K..0 have difference -1, rows >= 1 have +1; T = K+1
         uint64_t Pv[V], Mv[V];
@@ -296,7 +301,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
                     gmin = t < gmin ? t : gmin;
                 }
                 const int32_t T0 = (G > 1) ? __shfl_sync(FULL, T, 0, G) : T;
-                if (act && T0 + gmin > K) {
+                if (act && T0 + gmin > kp) {
                     decided = true;
                     pass = false;
                     ncols = 0;
@@ -323,12 +328,12 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) cnt += __shfl_xor_sync(FULL, cnt, o, G);
             const int32_t T0 = (G > 1) ? __shfl_sync(FULL, T, 0, G) : T;
-            if (!decided) pass = (T0 + cnt) <= K;
+            if (!decided) pass = (T0 + cnt) <= kp;
         }
         if (valid && gl == 0) {
             emit_result(vo, p, pairs, pass);
             if (work) {
-                atomicAdd(&work[0], band_cells(mlen, nlen, K));
+                atomicAdd(&work[0], band_cells(mlen, nlen, kp));
                 atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
             }
         }

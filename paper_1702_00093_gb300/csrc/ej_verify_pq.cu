@@ -71,6 +71,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         const int64_t dn = (int64_t)*vo.np_dev;
         np = dn < np ? dn : np;
     }
+    if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
     constexpr int R = W1 + 1;
     constexpr int SPW = 64 / B;              // symbols per 64-bit word
     constexpr uint64_t CMASK = (1ull << B) - 1ull;
@@ -118,6 +119,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const uint64_t *y64 = reinterpret_cast<const uint64_t *>(packed);
     int64_t ywords = 0;
     int32_t m = 0, n = 0, ncols = 0, Tacc = 0, jbase = 1, next_move = 0, rej_col = 0;
+    int32_t kp = K;          // the pair's threshold (<= K, the band)
     int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
     int64_t iters = 0;       // loop passes of this warp (bounded, see kMaxIters)
     int base = 0;
@@ -149,22 +151,25 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                     p = idx;
                     const uint64_t pr = pairs[p];
                     const int64_t a = (int64_t)(pr >> 32), b = (int64_t)(pr & 0xFFFFFFFFull);
-                    if (a >= n_str || b >= n_str) {
+                    const bool two = vo.packed_b != nullptr;   // b indexes the second set
+                    if (a >= n_str || b >= (two ? vo.n_b : n_str)) {
                         if (!rev) atomicOr(err, (uint32_t)DERR_PAIR);
                     } else {
-                        const int32_t la = lens[a], lb = lens[b];
+                        const int32_t la = lens[a], lb = two ? vo.lens_b[b] : lens[b];
+                        const uint4 *pa = packed + pofs[a];
+                        const uint4 *pb = two ? vo.packed_b + vo.pofs_b[b] : packed + pofs[b];
                         const bool a_long = la >= lb;
-                        const int64_t xi = a_long ? a : b, yi = a_long ? b : a;
                         m = a_long ? la : lb;
                         n = a_long ? lb : la;
-                        if (!rev) loc_cells += band_cells(m, n, K);
-                        if (m - n > K || n == 0) {
-                            if (!rev) emit_result(vo, p, pairs, n == 0 && m <= K);
+                        kp = vo.thr ? vo.thr[a] : K;
+                        if (!rev) loc_cells += band_cells(m, n, kp);
+                        if (m - n > kp || n == 0) {
+                            if (!rev) emit_result(vo, p, pairs, n == 0 && m <= kp);
                         } else {
                             const int32_t n1 = n / 2;
                             ncols = rev ? n - n1 : n1;
-                            xc = packed + pofs[xi];
-                            y64 = reinterpret_cast<const uint64_t *>(packed + pofs[yi]);
+                            xc = a_long ? pa : pb;
+                            y64 = reinterpret_cast<const uint64_t *>(a_long ? pb : pa);
                             ywords = 2 * chunks_for(n, B);
                             for (int wi = 0; wi < W1; wi++) bd_build<B, R>(ring, T_, wi, xc, m, wi, rev, alpha);
 #pragma unroll
@@ -274,7 +279,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 lb = Tacc + (j - 1) + mn;
             }
             const int32_t lb_other = __shfl_xor_sync(FULL, lb, 1);
-            if (moving && lb + lb_other > K) {
+            if (moving && lb + lb_other > kp) {
                 rejected = true;
                 rej_col = j;
                 lim = -1;
@@ -348,7 +353,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                             Bv -= (int32_t)((bp >> (rb_ & 63)) & 1ull) - (int32_t)((bm >> (rb_ & 63)) & 1ull);
                             best = min(best, F + Bv);
                         }
-                        pass = best <= K;
+                        pass = best <= kp;
                     }
                 }
                 emit_result(vo, p, pairs, pass);

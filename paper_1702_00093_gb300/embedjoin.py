@@ -30,13 +30,34 @@ EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
             "ej_set_schedule", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
-            "ej_batch_destroy"]
+            "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
+            "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
+            "ej_server_reset_stats", "ej_server_destroy"]
 
 
 class EJError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
         self.status = status
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("inflight", C.c_int32), ("max_batch_bytes", C.c_int64),
+                ("hbm_reserve", C.c_uint64), ("hbm_budget", C.c_uint64)]
+
+
+class SearchResult(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("n_matches", C.c_int32),
+                ("matches", C.POINTER(C.c_uint32)), ("latency_ms", C.c_double), ("queue_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("retries", C.c_int64), ("deferred", C.c_int64),
+                ("mean_batch", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("queries_per_s", C.c_double), ("device_bytes", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class _Schedule(C.Structure):
@@ -131,6 +152,28 @@ def lib():
         L.ej_batch_kernel_count.restype = i64
         L.ej_batch_destroy.argtypes = [vp]
         L.ej_batch_destroy.restype = None
+        L.ej_index_create.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), C.POINTER(vp), vp]
+        L.ej_index_create.restype = C.c_int
+        L.ej_index_size.argtypes = [vp]
+        L.ej_index_size.restype = i64
+        L.ej_index_search.argtypes = [vp, vp, C.POINTER(_Strings), vp, vp, i64, C.POINTER(i64), vp]
+        L.ej_index_search.restype = C.c_int
+        L.ej_index_destroy.argtypes = [vp]
+        L.ej_index_destroy.restype = None
+        L.ej_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
+        L.ej_server_create.restype = C.c_int
+        L.ej_server_submit.argtypes = [vp, vp, C.c_int32, C.c_int32]
+        L.ej_server_submit.restype = i64
+        L.ej_server_poll.argtypes = [vp, C.POINTER(SearchResult), C.c_int32, C.POINTER(C.c_int32), C.c_int32]
+        L.ej_server_poll.restype = C.c_int
+        L.ej_server_release.argtypes = [vp, i64]
+        L.ej_server_release.restype = C.c_int
+        L.ej_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.ej_server_get_stats.restype = C.c_int
+        L.ej_server_reset_stats.argtypes = [vp]
+        L.ej_server_reset_stats.restype = C.c_int
+        L.ej_server_destroy.argtypes = [vp]
+        L.ej_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -425,6 +468,113 @@ class Batch:
     def close(self):
         if self._h:
             lib().ej_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_strings(queries):
+    """Host Strings from a list of bytes objects (or a host Strings as is)."""
+    if isinstance(queries, Strings):
+        return queries
+    lens = np.array([len(q) for q in queries], dtype=np.int64)
+    offs = np.zeros(len(queries) + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    data = np.frombuffer(b"".join(queries), dtype=np.uint8).copy() if offs[-1] else np.zeros(1, np.uint8)
+    return Strings(data, offs)
+
+
+class Index:
+    """ej_index: EmbedJoin's tables and buckets of a string set, resident on the GPU."""
+
+    def __init__(self, ctx: Context, s: Strings, p: Params, stream=None):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        cs, (cp, _keep) = s._c(), p._c()
+        ctx._check(lib().ej_index_create(ctx._h, C.byref(cs), C.byref(cp), C.byref(self._h), _stream(stream)),
+                   "ej_index_create")
+        self.n = int(lib().ej_index_size(self._h))
+
+    def search(self, queries, K, capacity: int = 1 << 16) -> np.ndarray:
+        """All (q << 32 | i) with ED(query q, index string i) <= K[q] among the
+        EmbedJoin candidates of q, ascending (uint64 numpy array)."""
+        hs = _host_strings(queries)
+        Ks = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (hs.n,)))
+        cs = hs._c()
+        while True:
+            out = np.zeros(max(capacity, 1), dtype=np.uint64)
+            n = C.c_int64(0)
+            st = lib().ej_index_search(self._ctx._h, self._h, C.byref(cs), _ptr(Ks), _ptr(out), out.shape[0],
+                                       C.byref(n), None)
+            if st == EJ_ERR_CAPACITY:
+                capacity = n.value
+                continue
+            self._ctx._check(st, "ej_index_search")
+            return out[:n.value].copy()
+
+    def close(self):
+        if self._h:
+            lib().ej_index_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """ej_server: continuous-batching search service over an Index."""
+
+    def __init__(self, index: Index, max_batch: int = 0, inflight: int = 0, max_batch_bytes: int = 0,
+                 hbm_reserve: int = 0, hbm_budget: int = 0):
+        self._index = index
+        self._h = C.c_void_p()
+        cfg = ServerConfig(max_batch, inflight, max_batch_bytes, hbm_reserve, hbm_budget)
+        st = lib().ej_server_create(index._h, C.byref(cfg), C.byref(self._h))
+        if st != EJ_OK:
+            raise EJError(st, "ej_server_create failed")
+        self._buf = (SearchResult * 1024)()
+
+    def submit(self, query: bytes, K: int) -> int:
+        buf = np.frombuffer(query, dtype=np.uint8) if len(query) else np.zeros(1, np.uint8)
+        rid = int(lib().ej_server_submit(self._h, _ptr(buf), len(query), int(K)))
+        if rid < 0:
+            raise EJError(-rid, "ej_server_submit: invalid query")
+        return rid
+
+    def poll(self, max_results: int = 1024, wait_us: int = 1000) -> list:
+        """Finished requests: (id, status, matches uint32 array, latency_ms, queue_ms)."""
+        n = C.c_int32(0)
+        m = min(max_results, len(self._buf))
+        st = lib().ej_server_poll(self._h, self._buf, m, C.byref(n), int(wait_us))
+        if st != EJ_OK:
+            raise EJError(st, "ej_server_poll")
+        out = []
+        for k in range(n.value):
+            r = self._buf[k]
+            mt = np.ctypeslib.as_array(r.matches, shape=(r.n_matches,)).copy() if r.n_matches else \
+                np.zeros(0, dtype=np.uint32)
+            out.append((int(r.id), int(r.status), mt, float(r.latency_ms), float(r.queue_ms)))
+            lib().ej_server_release(self._h, r.id)
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        lib().ej_server_get_stats(self._h, C.byref(st))
+        return st.as_dict()
+
+    def reset_stats(self):
+        lib().ej_server_reset_stats(self._h)
+
+    def close(self):
+        if self._h:
+            lib().ej_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -268,3 +268,62 @@ def text_params(K: int) -> dict:
 
 
 TEXT_KS = (100, 200, 300)
+
+
+# ---------------------------------------------------------------------------
+# Serving: a resident index and a stream of search queries
+# ---------------------------------------------------------------------------
+
+def serving_index(n: int = 1_000_000, seed: int = 1005, len_lo: int = 900, len_hi: int = 1100,
+                  dup_frac: float = 0.10, rate_lo: float = 0.01, rate_hi: float = 0.05) -> StringSet:
+    """Uniform {A,C,G,T} strings of length U[len_lo, len_hi]; a fraction are planted
+    near-duplicates (Poisson(rate * len) edits, rate U[rate_lo, rate_hi]) of others.
+    Order is shuffled; cluster = the original's position for the planted ones."""
+    rng = np.random.default_rng(seed)
+    n_dup = int(round(n * dup_frac))
+    n_orig = n - n_dup
+    lens_o = rng.integers(len_lo, len_hi + 1, size=n_orig).astype(np.int64)
+    offs_o = np.zeros(n_orig + 1, dtype=np.int64)
+    np.cumsum(lens_o, out=offs_o[1:])
+    codes_o = rng.integers(0, 4, size=int(offs_o[-1]), dtype=np.uint8)
+    src = rng.integers(0, max(n_orig, 1), size=n_dup)
+    dups = [mutate(rng, codes_o[offs_o[s]:offs_o[s + 1]], int(rng.poisson(rng.uniform(rate_lo, rate_hi) *
+                                                                             (offs_o[s + 1] - offs_o[s]))), 4)
+            for s in src]
+    lens = np.concatenate([lens_o, np.fromiter((d.shape[0] for d in dups), dtype=np.int64, count=n_dup)])
+    perm = rng.permutation(n)
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens[perm], out=offsets[1:])
+    data = np.empty(int(offsets[-1]), dtype=np.uint8)
+    lut = np.frombuffer(DNA, dtype=np.uint8)
+    for k in range(n):
+        i = int(perm[k])
+        data[offsets[k]:offsets[k + 1]] = codes_o[offs_o[i]:offs_o[i + 1]] if i < n_orig else dups[i - n_orig]
+    data = lut[data]
+    cl = np.concatenate([np.arange(n_orig, dtype=np.int64), src.astype(np.int64)])[perm]
+    return StringSet(data, offsets, DNA, cl)
+
+
+def serving_queries(index: StringSet, nq: int, seed: int = 1006, mutated_frac: float = 0.5,
+                    len_lo: int = 200, len_hi: int = 5000, k_lo: float = 0.01, k_hi: float = 0.10):
+    """Search queries: a fraction are index strings with Poisson(rate * len) edits
+    (rate U[1%,10%]), the rest fresh uniform strings of length U[len_lo, len_hi];
+    each query's K is U[k_lo, k_hi] of its own length. Returns (list of bytes, K int32)."""
+    rng = np.random.default_rng(seed)
+    lut = np.frombuffer(index.alphabet, np.uint8)
+    rev = np.zeros(256, np.uint8)
+    rev[lut] = np.arange(len(lut), dtype=np.uint8)
+    qs, ks = [], []
+    for _ in range(nq):
+        if rng.random() < mutated_frac:
+            i = int(rng.integers(0, index.n))
+            base = rev[index.data[index.offsets[i]:index.offsets[i + 1]]]
+            q = mutate(rng, base, int(rng.poisson(rng.uniform(0.01, 0.10) * base.shape[0])), 4)
+        else:
+            q = rng.integers(0, 4, size=int(rng.integers(len_lo, len_hi + 1)), dtype=np.uint8)
+        qs.append(lut[q].tobytes())
+        ks.append(int(round(rng.uniform(k_lo, k_hi) * len(q))))
+    return qs, np.array(ks, dtype=np.int32)
+
+
+SERVING_PARAMS = dict(r=7, m=7, z=8, L=1000, seed=1)
