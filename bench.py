@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-stage path")
     ap.add_argument("--autotune", action="store_true", help="autotune each join of the batch")
+    ap.add_argument("--paths", type=str, default="batch,join,plain",
+                    help="paths to time (batch = the graph-captured headline; without it the ej_join path heads "
+                         "the line, e.g. for profilers that do not follow stream capture)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-clusters", type=int, default=100)
     return ap.parse_args()
@@ -381,61 +384,65 @@ def main():
         return total
 
     with torch.cuda.stream(stream), ClockSampler(local) as clk:
-        # ---- headline: all joins of the step as one CUDA graph -------------------
-        batch = ctx.batch(strings, params, autotune=args.autotune, stream=stream)
-        outs = [torch.empty(1 << 16, dtype=torch.int64, device=dev) for _ in params]
-        bstats = {}
+        paths = set(args.paths.split(","))
+        use_batch = "batch" in paths
+        batch_ms, cand_step, launches_step, result_pairs, e2e = None, 0, 0, None, None
+        if use_batch:
+            # ---- headline: all joins of the step as one CUDA graph -------------------
+            batch = ctx.batch(strings, params, autotune=args.autotune, stream=stream)
+            outs = [torch.empty(1 << 16, dtype=torch.int64, device=dev) for _ in params]
+            bstats = {}
 
-        def batch_step():
-            batch.run(stream)
-            for i in range(len(params)):
-                while True:
-                    try:
-                        bstats[i] = batch.result_into(i, outs[i], stream)
-                        break
-                    except ej.EJError as e:
-                        if getattr(e, "needed", None) is None:
-                            raise
-                        outs[i] = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-
-        for _ in range(warm):
-            batch_step()
-        batch_ms = timed(batch_step, args.steps, clk)
-        cand_step = sum(st.n_candidates for _, st in bstats.values())
-        launches_step = batch.kernel_count + sum(st.kernel_launches for _, st in bstats.values())
-        result_pairs = [outs[i][:bstats[i][0]].clone() for i in range(len(params))]
-
-        # ---- end to end through the public API with host buffers -------------------
-        e2e = None
-        if args.e2e_steps > 0:
-            h_data = torch.from_numpy(ss.data).pin_memory()
-            h_off = torch.from_numpy(ss.offsets).pin_memory()
-            h_outs = [torch.empty(max(int(o.shape[0]), 1), dtype=torch.int64).pin_memory().numpy() for o in outs]
-            h_t, h_cand, d2h = 0.0, 0, 0
-            for it in range(args.e2e_steps + 1):
-                torch.cuda.synchronize()
-                barrier(world)
-                t0 = time.perf_counter()
-                strings.data.copy_(h_data, non_blocking=True)
-                strings.offsets.copy_(h_off, non_blocking=True)
+            def batch_step():
                 batch.run(stream)
-                step_c, step_out = 0, 0
                 for i in range(len(params)):
-                    n, st = batch.result_into(i, h_outs[i], stream)
-                    step_c += st.n_candidates
-                    step_out += n
-                dt = time.perf_counter() - t0
-                if it > 0:   # the first pass warms the host staging
-                    h_t += dt
-                    h_cand += step_c
-                    d2h += step_out * 8
-            h_t = allreduce(h_t, world, "max")
-            h_cand = allreduce(h_cand, world, "sum")
-            e2e = {"value": h_cand / h_t, "unit": "pairs/s",
-                   "h2d_bytes_per_step": int(ss.data.nbytes + ss.offsets.nbytes),
-                   "d2h_bytes_per_step": int(d2h / args.e2e_steps), "steps": args.e2e_steps,
-                   "ms_per_step": 1e3 * h_t / args.e2e_steps, "api": "ej_batch_run + ej_batch_result, host buffers"}
-        batch.close()   # its scratch is not needed by the other paths
+                    while True:
+                        try:
+                            bstats[i] = batch.result_into(i, outs[i], stream)
+                            break
+                        except ej.EJError as e:
+                            if getattr(e, "needed", None) is None:
+                                raise
+                            outs[i] = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+
+            for _ in range(warm):
+                batch_step()
+            batch_ms = timed(batch_step, args.steps, clk)
+            cand_step = sum(st.n_candidates for _, st in bstats.values())
+            launches_step = batch.kernel_count + sum(st.kernel_launches for _, st in bstats.values())
+            result_pairs = [outs[i][:bstats[i][0]].clone() for i in range(len(params))]
+
+            # ---- end to end through the public API with host buffers -------------------
+            e2e = None
+            if args.e2e_steps > 0:
+                h_data = torch.from_numpy(ss.data).pin_memory()
+                h_off = torch.from_numpy(ss.offsets).pin_memory()
+                h_outs = [torch.empty(max(int(o.shape[0]), 1), dtype=torch.int64).pin_memory().numpy() for o in outs]
+                h_t, h_cand, d2h = 0.0, 0, 0
+                for it in range(args.e2e_steps + 1):
+                    torch.cuda.synchronize()
+                    barrier(world)
+                    t0 = time.perf_counter()
+                    strings.data.copy_(h_data, non_blocking=True)
+                    strings.offsets.copy_(h_off, non_blocking=True)
+                    batch.run(stream)
+                    step_c, step_out = 0, 0
+                    for i in range(len(params)):
+                        n, st = batch.result_into(i, h_outs[i], stream)
+                        step_c += st.n_candidates
+                        step_out += n
+                    dt = time.perf_counter() - t0
+                    if it > 0:   # the first pass warms the host staging
+                        h_t += dt
+                        h_cand += step_c
+                        d2h += step_out * 8
+                h_t = allreduce(h_t, world, "max")
+                h_cand = allreduce(h_cand, world, "sum")
+                e2e = {"value": h_cand / h_t, "unit": "pairs/s",
+                       "h2d_bytes_per_step": int(ss.data.nbytes + ss.offsets.nbytes),
+                       "d2h_bytes_per_step": int(d2h / args.e2e_steps), "steps": args.e2e_steps,
+                       "ms_per_step": 1e3 * h_t / args.e2e_steps, "api": "ej_batch_run + ej_batch_result, host buffers"}
+            batch.close()   # its scratch is not needed by the other paths
 
         # ---- the same step through ej_join (stage timings, verify roofline) --------
         ctx.set_timing(True)
@@ -458,46 +465,56 @@ def main():
         for _ in range(warm):
             join_step()
         jstats.clear()
-        join_ms = timed(join_step, args.steps, None)
+        join_ms = timed(join_step, args.steps, None if use_batch else clk)
         same_join = True
+        join_pairs = []
         for i, p in enumerate(params):
             n, _ = ctx.join_into(strings, p, jout, stream)
-            same_join &= torch.equal(jout[:n], result_pairs[i])
+            join_pairs.append(jout[:n].clone())
+        if use_batch:
+            same_join = all(torch.equal(a, b) for a, b in zip(join_pairs, result_pairs))
+        else:
+            # the ej_join path heads the line
+            result_pairs = join_pairs
+            batch_ms = join_ms
+            cand_step = sum(s_["n_candidates"] for _, _, s_ in jstats) // args.steps
+            launches_step = sum(s_["kernel_launches"] for _, _, s_ in jstats) // args.steps
 
-        # ---- the plain per-stage path (on a fresh context) --------------------------
-        ctx.close()
-        ctx = ej.Context(local)
-        plain = [dataclasses.replace(p, out_len=p.L) for p in params]   # the walk is causal: prefix L
-        infos = [ctx.plan(strings, p, stream) for p in plain]
-        emb = torch.empty(max(i.embedding_bytes for i in infos) // 4 + 1, dtype=torch.int32, device=dev)
-        we = torch.empty(max(i.walk_end_count for i in infos) + 1, dtype=torch.int32, device=dev)
-        keys = torch.empty(max(i.key_count for i in infos) + 1, dtype=torch.int64, device=dev)
-        cand_buf = torch.empty(1 << 16, dtype=torch.int64, device=dev)
-        pout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
-        plain_res = {}
+        plain_ms, same_plain, cand_plain = None, None, 0
+        if "plain" in paths:
+            # ---- the plain per-stage path (on a fresh context) --------------------------
+            ctx.close()
+            ctx = ej.Context(local)
+            plain = [dataclasses.replace(p, out_len=p.L) for p in params]   # the walk is causal: prefix L
+            infos = [ctx.plan(strings, p, stream) for p in plain]
+            emb = torch.empty(max(i.embedding_bytes for i in infos) // 4 + 1, dtype=torch.int32, device=dev)
+            we = torch.empty(max(i.walk_end_count for i in infos) + 1, dtype=torch.int32, device=dev)
+            keys = torch.empty(max(i.key_count for i in infos) + 1, dtype=torch.int64, device=dev)
+            cand_buf = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+            pout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+            plain_res = {}
 
-        def plain_step():
-            nonlocal cand_buf, pout
-            for i, p in enumerate(plain):
-                ctx.embed(strings, p, emb, we, stream)
-                ctx.sign(strings, p, emb, we, keys, stream)
-                while True:
-                    try:
-                        nc, _ = ctx.lsh_candidates(strings, p, keys, cand_buf, stream)
-                        break
-                    except ej.EJError as e:
-                        if e.status != ej.EJ_ERR_CAPACITY:
-                            raise
-                        cand_buf = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-                        pout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-                k = ctx.verify(strings, p, cand_buf[:nc], pout, stream)
-                plain_res[i] = (nc, pout[:k].clone())
+            def plain_step():
+                nonlocal cand_buf, pout
+                for i, p in enumerate(plain):
+                    ctx.embed(strings, p, emb, we, stream)
+                    ctx.sign(strings, p, emb, we, keys, stream)
+                    while True:
+                        try:
+                            nc, _ = ctx.lsh_candidates(strings, p, keys, cand_buf, stream)
+                            break
+                        except ej.EJError as e:
+                            if e.status != ej.EJ_ERR_CAPACITY:
+                                raise
+                            cand_buf = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+                            pout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+                    k = ctx.verify(strings, p, cand_buf[:nc], pout, stream)
+                    plain_res[i] = (nc, pout[:k].clone())
 
-        plain_step()
-        plain_ms = timed(plain_step, args.plain_steps, None)
-        same_plain = all(torch.equal(plain_res[i][1], result_pairs[i]) for i in range(len(params)))
-        cand_plain = sum(plain_res[i][0] for i in range(len(params)))
-
+            plain_step()
+            plain_ms = timed(plain_step, args.plain_steps, None)
+            same_plain = all(torch.equal(plain_res[i][1], result_pairs[i]) for i in range(len(params)))
+            cand_plain = sum(plain_res[i][0] for i in range(len(params)))
     clocks = clk.summary()
 
     batch_ms_max = allreduce(batch_ms, world, "max")
@@ -531,18 +548,19 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{wl['desc'](ss, args)}; K={','.join(map(str, Ks))}; "
                                    f"r={params[0].r}, m={params[0].m}, z={'/'.join(str(p.z) for p in params)}, "
-                                   f"L={params[0].L}; one step = one join per K, the joins of a step captured "
-                                   f"as one CUDA graph (ej_batch)",
+                                   f"L={params[0].L}; one step = one join per K" +
+                                   (", the joins of a step captured as one CUDA graph (ej_batch)" if use_batch
+                                    else ", one ej_join call per K"),
                        "n": ss.n, "Ks": list(Ks), "l2": "flushed before each timed step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU", "autotune": args.autotune},
             "join_wall_s_per_step": batch_ms_max / args.steps / 1e3,
             "band_cells_per_s": allreduce(cells_step * args.steps, world, "sum") / (batch_ms_max / 1e3),
             "join_path": {"value": cand_step * args.steps / (join_ms / 1e3), "ms_per_step": join_ms / args.steps,
                           "api": "ej_join per K", "identical_output": bool(same_join)},
-            "plain_path": {"value": cand_plain * args.plain_steps / (plain_ms / 1e3),
-                           "ms_per_step": plain_ms / args.plain_steps, "steps": args.plain_steps,
-                           "api": "ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify per K",
-                           "identical_output": bool(same_plain)},
+            "plain_path": None if plain_ms is None else {
+                "value": cand_plain * args.plain_steps / (plain_ms / 1e3), "ms_per_step": plain_ms / args.plain_steps,
+                "steps": args.plain_steps, "api": "ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify per K",
+                "identical_output": bool(same_plain)},
             "per_K": per_k,
             "roofline": {"kernel": "verify_pq_kernel", "bound": "alu", "achieved": ach_ops / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",

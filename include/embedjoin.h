@@ -267,18 +267,26 @@ void ej_batch_destroy(ej_batch *batch);
 /*
  * Schedule of ej_join's back half (a performance choice: the output never
  * depends on it; the paper has no counterpart).
- *   mode: 0 (default) persistent verifier where the band fits two lanes per pair
- *     (up to 12 words per lane): a fixed grid whose warps pull candidate pairs
- *     from a device work queue and refill a pair slot as soon as its pair is
- *     decided; otherwise the grid-strided verifier. 1: the same as 0.
- *     2: always the grid-strided verifier (one pass over the pairs; a warp's
- *     slots start together and the warp ends with its slowest pair).
+ *   mode: 1: persistent verifier where the band fits two lanes per pair (up to
+ *     12 words per lane): a fixed grid whose warps pull candidate pairs from a
+ *     device work queue and refill a pair slot as soon as its pair is decided;
+ *     otherwise the grid-strided verifier. 2: always the grid-strided verifier
+ *     (one pass over the pairs; a warp's slots start together and the warp ends
+ *     with its slowest pair). 0 (default): 1 when the strings' mean length is at
+ *     least 2048 (long pairs, where refilling pays), else 2. In a batch,
+ *     persistent verifiers whose blocks need more than a quarter of an SM's
+ *     shared memory run one after another; everything else overlaps.
  *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
  *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
  *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
- *   order: 0 (default) or 1: candidates enter the queue by decreasing number of
- *     tables in which the two strings collided (similar pairs, which run
- *     longest, start first); 2: hash-table order.
+ *   order: the order in which candidates enter the verifier. 4: by length
+ *     class, longest first (the shorter string's length in 256 classes), so
+ *     that the pairs a warp takes have similar lengths and the longest start
+ *     first; 3: by the pair's first string (a counting sort: the pairs a warp
+ *     takes share their first string, so they read the same memory and, through
+ *     the length filter, have similar lengths); 1: by decreasing number of tables
+ *     in which the two strings collided; 2: hash-table order. 0 (default): 4
+ *     with the persistent verifier, 3 with the grid-strided one.
  *   buckets: 0 (default) or 1: equal signatures are grouped by hashing (per
  *     table an open-addressing set whose slots head lists of records); a
  *     record pairs with the later records of its list, so a bucket of b strings

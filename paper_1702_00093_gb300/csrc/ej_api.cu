@@ -26,7 +26,8 @@ enum BufId {
     B_COUNTS, B_OFFS, B_RAW, B_RAW_ALT, B_FLAGS, B_FLAG_OFFS, B_CAND,
     B_RS_COUNTS, B_RS_OFFS, B_SCAN_TMP, B_SCAN_TMP2, B_COUNTERS,
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
-    B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS, B_BKEYS, B_BHEADS, B_BNEXT,
+    B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS, B_BKEYS, B_BHEADS, B_BNEXT, B_FBINS, B_FSTARTS,
+    B_FSCAN,
     B_NUM
 };
 
@@ -659,8 +660,21 @@ uint64_t raw_cap_start(ej_ctx *ctx, int64_t n) {
     return ctx->raw_cap_hint ? ctx->raw_cap_hint : (uint64_t)(n * 4 > 65536 ? n * 4 : 65536);
 }
 
+// Threads per block of the persistent verifier this join uses, 0 for the
+// grid-strided one. Mode 0 picks the persistent verifier for long strings only
+// (mean length >= 2048): on short, mostly rejected pairs its per-pair refill
+// costs more than it saves (measured 2x slower on the protein-like shape).
+int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const VerifyConfig &vc) {
+    const bool long_pairs = pl.st.n > 0 && pl.st.total / pl.st.n >= 2048;
+    const bool want_pq = ctx->sched.mode == 1 || (ctx->sched.mode == 0 && long_pairs);
+    return (vc.G == 2 && want_pq) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
+}
+
+// verify_after / verify_done (optional): the verifier launch waits for the
+// first event and records the second (a batch chains its joins' verifiers, so
+// that persistent verifiers never run concurrently).
 int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackState &bs, uint64_t cap,
-                 cudaStream_t s) {
+                 cudaStream_t s, cudaEvent_t verify_after = nullptr, cudaEvent_t verify_done = nullptr) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     unsigned long long *cnt = nullptr;
     CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
@@ -678,16 +692,35 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
         CK(launch_bucket_emit(pl.lens, n, T, p->K, bs.bnext, raw, cap, cnt, s));
     else
         CK(launch_emit_append(bs.srk, bs.srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
-    if (ctx->sched.order != 2) {
-        // candidates handed to the verifier most-collided first: similar pairs,
-        // which run longest, start first
+    // queue order: 0 follows the verifier (persistent: length classes; grid-
+    // strided: by first string), measured best for each on the long-DNA and the
+    // protein-like / text-like shapes
+    const int pq_threads = pq_choice(ctx, pl, p, bs.vc);
+    const int order = ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
+    if (order == 3) {
+        // candidates ordered by their first string (a warp's pairs share it)
+        uint32_t *hcount = nullptr, *fbins = nullptr;
+        uint64_t *fstarts = nullptr;
+        void *fscan = nullptr;
+        CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
+        CKS(ensure_t(ctx, B_FBINS, (size_t)n + 1, &fbins));
+        CKS(ensure_t(ctx, B_FSTARTS, (size_t)n + 2, &fstarts));
+        CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(n + 1), &fscan));
+        CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(fbins, 0, (size_t)(n + 1) * sizeof(uint32_t), s));
+        CK(launch_dedup_by_first(raw, cap, table, hcount, hsize, n, fbins, fstarts, fscan, cand, cnt, s));
+    } else if (order != 2) {
+        // candidates handed to the verifier longest first (order 4: length classes,
+        // so that the pairs a warp takes have similar lengths) or most-collided
+        // first (order 1: similar pairs, which run longest)
         uint32_t *hcount = nullptr;
         unsigned long long *bins = nullptr;
         CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
         CKS(ensure_t(ctx, B_BINS, (size_t)count_bins(), &bins));
         CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
         CK(cudaMemsetAsync(bins, 0, count_bins() * sizeof(unsigned long long), s));
-        CK(launch_dedup_ordered(raw, cap, table, hcount, hsize, bins, cand, cnt, s));
+        CK(launch_dedup_ordered(raw, cap, table, hcount, hsize, bins, cand, cnt, order == 4 ? pl.lens : nullptr,
+                                pl.max_len, s));
     } else {
         CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
     }
@@ -697,7 +730,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
     VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
     const VerifyConfig &vc = bs.vc;
-    const int pq_threads = (vc.G == 2 && ctx->sched.mode != 2) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
+    if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
     if (pq_threads > 0)
         // defaults: 16 slots per warp, one working warp per SM sub-partition (the
         // slots refill from the queue); measured best on the long-DNA shapes
@@ -708,6 +741,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     else
         CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
                          pl.max_len, vo, s));
+    if (verify_done) CK(cudaEventRecord(verify_done, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
     return EJ_OK;
 }
@@ -815,6 +849,7 @@ struct BatchJoin {
     uint64_t *keys = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t verified = nullptr;   // this join's verifier finished (chains the verifiers)
 };
 
 }  // namespace
@@ -839,6 +874,7 @@ void batch_free(ej_batch *b) {
     if (b->fork) cudaEventDestroy(b->fork);
     for (auto &j : b->joins) {
         if (j.done) cudaEventDestroy(j.done);
+        if (j.verified) cudaEventDestroy(j.verified);
         if (j.side) cudaStreamDestroy(j.side);
         if (j.sub) ej_destroy(j.sub);
     }
@@ -847,10 +883,10 @@ void batch_free(ej_batch *b) {
 
 // Device work of one join (keys -> buckets -> pairs -> dedup -> verify) on its
 // side stream; no host synchronisation.
-int batch_join_device(BatchJoin &j, cudaStream_t s) {
+int batch_join_device(BatchJoin &j, cudaStream_t s, cudaEvent_t verify_after, cudaEvent_t verify_done) {
     CKS(keys_dev(j.sub, &j.p, j.pl, j.keys, s));
     CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
-    CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s));
+    CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s, verify_after, verify_done));
     return EJ_OK;
 }
 
@@ -858,7 +894,7 @@ int batch_join_device(BatchJoin &j, cudaStream_t s) {
 // per warp, working warps per SM sub-partition, queue order); the fastest on
 // the join's own data wins.
 const ej_schedule kTuneSet[] = {
-    {0, 16, 1, 0, 0}, {0, 16, 2, 0, 0}, {0, 8, 1, 0, 0}, {0, 16, 1, 2, 0}, {0, 12, 1, 0, 0}, {2, 0, 0, 0, 0},
+    {1, 16, 1, 4, 0}, {1, 16, 2, 4, 0}, {1, 16, 1, 3, 0}, {1, 16, 1, 1, 0}, {2, 0, 0, 3, 0}, {2, 0, 0, 4, 0},
 };
 
 int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
@@ -1009,7 +1045,7 @@ int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
         return EJ_OK;
     }
     if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
-        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 2 ||
+        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 4 ||
         sc->buckets < 0 || sc->buckets > 2)
         return fail(ctx, EJ_ERR_INVALID_ARG,
                     "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",
@@ -1265,7 +1301,8 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         j.sub->vV = ctx->vV;
         j.sub->vWarps = ctx->vWarps;
         if (cudaStreamCreateWithFlags(&j.side, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&j.verified, cudaEventDisableTiming) != cudaSuccess)
             return bail(fail(ctx, EJ_ERR_CUDA, "stream/event creation failed"));
         if ((st = upload_alphabet(j.sub, &j.p, s)) != EJ_OK) return bail(st);
         if ((st = ensure_t(j.sub, B_KEYS, (size_t)j.p.r * j.p.m * b->pl.st.n, &j.keys)) != EJ_OK) return bail(st);
@@ -1297,10 +1334,17 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return bail(fail(ctx, EJ_ERR_CUDA, "stream capture could not start (the stream must not be the legacy default stream)"));
     int cst = plan_device(ctx, b->pl, s);
     if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    // persistent verifiers whose blocks take more than a quarter of an SM's shared
+    // memory run one after another (two of them sharing the SMs measured up to 10x
+    // slower); lighter ones, and every other stage, overlap
+    cudaEvent_t prev_verify = nullptr;
     for (auto &j : b->joins) {
         if (cst != EJ_OK) break;
         if (cudaStreamWaitEvent(j.side, b->fork, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
-        cst = batch_join_device(j, j.side);
+        const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
+        const bool heavy = pt > 0 && pq_smem_bytes(j.bs.vc.V, j.p.alphabet_size, pt) > 56 * 1024;
+        cst = batch_join_device(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
+        if (heavy) prev_verify = j.verified;
         if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
         if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
     }

@@ -219,12 +219,14 @@ cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_
                                uint64_t *raw, uint64_t cap, unsigned long long *counters, cudaStream_t s);
 cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uint64_t hsize, uint64_t *cand,
                          unsigned long long *counters, cudaStream_t s);
-// Dedup that also orders the candidates by collision count (most first):
-// hcount (hsize uint32) and bins (count_bins() uint64) start at zero.
+// Dedup that also orders the candidates, highest bin first: by collision count
+// (lens null) or by length class (the shorter string's length scaled by
+// max_len to 256 classes). hcount (hsize uint32) and bins (count_bins() uint64)
+// start at zero.
 int count_bins();
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
-                                 cudaStream_t s);
+                                 const int32_t *lens, int64_t max_len, cudaStream_t s);
 // Strings validated and packed into a context's buffers (valid until the next
 // call that plans strings on that context), for the index and the server.
 struct PackedSet {
@@ -249,6 +251,11 @@ cudaError_t launch_index_probe(const uint64_t *qkeys, int64_t Q, int64_t T, cons
 cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  const uint8_t *cls, int nc, unsigned long long *bins, uint64_t *cand,
                                  unsigned long long *counters, cudaStream_t s);
+// Dedup ordered by the pair's first string (counting sort over n bins): bins
+// (n + 1 uint32) and hcount start at zero; starts holds n + 2 uint64.
+cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                  int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
+                                  unsigned long long *counters, cudaStream_t s);
 int small_sort_max();
 cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s);
 

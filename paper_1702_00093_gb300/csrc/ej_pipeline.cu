@@ -326,18 +326,30 @@ __global__ void dedup_count_kernel(const uint64_t *__restrict__ raw, uint64_t ca
 
 constexpr int COUNT_BINS = 256;
 
-// bins[min(count, 255)] += 1 over the occupied slots; counters[2] = pairs.
+// Queue bin of a candidate: its collision count, or (lens set) its length
+// class, the shorter string's length scaled to 0..255 (both: higher bins first).
+__device__ __forceinline__ uint32_t order_bin(uint64_t key, uint32_t count, const int32_t *__restrict__ lens,
+                                              uint32_t len_scale) {
+    if (!lens) return count < COUNT_BINS ? count : COUNT_BINS - 1;
+    const int32_t a = lens[key >> 32], b = lens[key & 0xFFFFFFFFull];
+    const uint32_t sh = (uint32_t)(a < b ? a : b);
+    const uint64_t c = ((uint64_t)sh * COUNT_BINS) / ((uint64_t)len_scale + 1);
+    return c < COUNT_BINS ? (uint32_t)c : COUNT_BINS - 1;
+}
+
+// bins[bin] += 1 over the occupied slots; counters[2] = pairs.
 __global__ void count_hist_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ hcount,
-                                  uint64_t hsize, unsigned long long *__restrict__ bins,
+                                  uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
+                                  unsigned long long *__restrict__ bins,
                                   unsigned long long *__restrict__ counters) {
     __shared__ unsigned int sb[COUNT_BINS];
     for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x) sb[t] = 0;
     __syncthreads();
     unsigned int mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
-        if (table[i] != ~0ull) {
-            const uint32_t c = hcount[i];
-            atomicAdd(&sb[c < COUNT_BINS ? c : COUNT_BINS - 1], 1u);
+        const uint64_t key = table[i];
+        if (key != ~0ull) {
+            atomicAdd(&sb[order_bin(key, hcount[i], lens, len_scale)], 1u);
             mine++;
         }
     }
@@ -361,30 +373,68 @@ __global__ void count_scan_kernel(unsigned long long *__restrict__ bins) {
 }
 
 __global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ hcount,
-                                     uint64_t hsize, unsigned long long *__restrict__ cursor,
-                                     uint64_t *__restrict__ cand) {
+                                     uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
+                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ cand) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) cand[atomicAdd(&cursor[order_bin(key, hcount[i], lens, len_scale)], 1ull)] = key;
+    }
+}
+
+// Order by the pair's first string (a counting sort on i of (i << 32 | j)):
+// consecutive candidates share their first string, so a warp's pairs read the
+// same string and, through the length filter, have similar lengths.
+__global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, uint32_t *__restrict__ bins,
+                                  unsigned long long *__restrict__ counters) {
+    unsigned int mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
-            const uint32_t c = hcount[i];
-            const unsigned long long pos = atomicAdd(&cursor[c < COUNT_BINS ? c : COUNT_BINS - 1], 1ull);
-            cand[pos] = key;
+            atomicAdd(&bins[key >> 32], 1u);
+            mine++;
         }
     }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&counters[2], (unsigned long long)mine);
+}
+
+__global__ void first_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize,
+                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ cand) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) cand[atomicAdd(&cursor[key >> 32], 1ull)] = key;
+    }
+}
+
+cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
+                                  int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
+                                  unsigned long long *counters, cudaStream_t s) {
+    int64_t g = ((int64_t)cap + 255) / 256;
+    dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
+    int64_t gh = ((int64_t)hsize + 255) / 256;
+    const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
+    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, bins, counters);
+    note_launches(2);
+    cudaError_t e = exclusive_scan_u32(bins, starts, n + 1, nullptr, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, (unsigned long long *)starts, cand);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 int count_bins() { return COUNT_BINS; }
 
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
-                                 cudaStream_t s) {
+                                 const int32_t *lens, int64_t max_len, cudaStream_t s) {
     int64_t g = ((int64_t)cap + 255) / 256;
     dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
     int64_t gh = ((int64_t)hsize + 255) / 256;
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
-    count_hist_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, bins, counters);
+    const uint32_t scale = (uint32_t)(max_len > 0x7fffffff ? 0x7fffffff : max_len);
+    count_hist_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, lens, scale, bins, counters);
     count_scan_kernel<<<1, 32, 0, s>>>(bins);
-    count_scatter_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, bins, cand);
+    count_scatter_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, lens, scale, bins, cand);
     note_launches(4);
     return cudaGetLastError();
 }

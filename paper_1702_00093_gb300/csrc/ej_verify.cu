@@ -635,7 +635,7 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         s_nmin[t] = (int8_t)mn;
     }
     __syncthreads();
-    constexpr int T_ = VBD_THREADS;      // slot stride (every launch uses VBD_THREADS threads)
+    const int T_ = blockDim.x;           // slot stride of the per-thread ring
     uint64_t *ring = smem + threadIdx.x;  // per thread: (c*R + slot)*T_, reused as a dump area
     const int lane = threadIdx.x & 31;
     const bool rev = lane & 1;
@@ -833,10 +833,13 @@ template <int W1, int B>
 static cudaError_t launch_bd(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                              uint32_t alpha, const uint64_t *pairs, int64_t np, int32_t K, int warps,
                              VerifyOut vo, cudaStream_t s) {
-    (void)warps;
-    const int threads = VBD_THREADS;
+    // blocks of `warps` warps (fewer when the per-thread ring of a large alphabet
+    // would not fit shared memory)
+    int threads = (warps > 0 ? warps : 4) * 32;
+    if (threads > VBD_THREADS) threads = VBD_THREADS;
     const int R = W1 + 1;
     const size_t per_thread = (size_t)(alpha * R > 2 * W1 + 2 ? alpha * R : 2 * W1 + 2) * sizeof(uint64_t);
+    while (threads > 32 && per_thread * threads > 200 * 1024) threads >>= 1;
     const size_t smem = per_thread * threads;
     cudaError_t e = cudaFuncSetAttribute(verify_bd_kernel<W1, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -369,14 +369,15 @@ def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
     W = (2 * K + 1 + 63) // 64
     runs = 0
     try:
-        for sched in [(0, 0, 0, 0, 0), (2, 0, 0, 0, 0), (0, 1, 0, 0, 2), (0, 2, 0, 2, 0), (0, 5, 1, 0, 2),
-                      (0, 16, 1, 1, 1), (0, 16, 2, 2, 0), (0, 3, 1, 0, 0), (2, 0, 0, 2, 2)]:
+        for sched in [(0, 0, 0, 0, 0), (2, 0, 0, 0, 0), (1, 0, 0, 0, 0), (1, 1, 0, 0, 2), (1, 2, 0, 2, 0),
+                      (1, 5, 1, 0, 2), (1, 16, 1, 1, 1), (1, 16, 2, 2, 0), (1, 3, 1, 0, 0), (2, 0, 0, 2, 2),
+                      (2, 0, 0, 3, 0), (1, 16, 1, 3, 0), (0, 0, 0, 3, 2), (1, 16, 1, 4, 0), (2, 0, 0, 4, 2)]:
             ctx.set_schedule(*sched)
             pairs, stats = ctx.join(s, params, device=DEV)
             assert stats.n_candidates == ref.n_candidates
             assert np.array_equal(_np_u64(pairs), ref.pairs), sched
             runs += 1
-        ctx.set_schedule(0, 0)
+        ctx.set_schedule(1, 0)   # the persistent verifier at every window width
         for V in range(W + 1, 13):
             ctx.set_verify_config(2, V, 0)
             pairs, _ = ctx.join(s, params, device=DEV)
