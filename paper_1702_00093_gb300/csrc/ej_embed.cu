@@ -477,20 +477,29 @@ constexpr size_t ES_TABLE_MAX = 48 * 1024;   // next-step table kept in shared m
 
 // Per-embedding stride of the next-step table, even so that every table starts
 // on a 4-byte boundary.
+// Rows of L + 2 entries: arrival steps a = L and L + 1 (the walk has passed the
+// sampling range) map to L + 1, so the walk needs no range check.
+__host__ __device__ __forceinline__ uint32_t next_row(uint32_t L) { return L + 2; }
+
 __host__ __device__ __forceinline__ uint64_t next_stride(uint32_t alpha, uint32_t L) {
-    return ((uint64_t)alpha * L + 1) & ~1ull;
+    return ((uint64_t)alpha * next_row(L) + 1) & ~1ull;
 }
 
-// next[l][c][a] = next1_c(a) + 1 for a < L (16-bit), from the step bitmaps.
+// next[l][c][a] = next1_c(a) + 1 for a < L, L + 1 for a in {L, L+1} (16-bit),
+// from the step bitmaps.
 __global__ void next_table_kernel(const uint32_t *__restrict__ tsym, uint32_t r, uint32_t alpha, uint32_t L,
                                   uint16_t *__restrict__ next) {
-    const uint32_t LW = sym_words(L);
-    const uint64_t total = (uint64_t)r * alpha * L;
+    const uint32_t LW = sym_words(L), NR = next_row(L);
+    const uint64_t total = (uint64_t)r * alpha * NR;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = (uint32_t)(idx % L);
-        const uint64_t lc = idx / L;   // l * alpha + c
+        const uint32_t a = (uint32_t)(idx % NR);
+        const uint64_t lc = idx / NR;   // l * alpha + c
         const uint64_t l = lc / alpha, c = lc % alpha;
+        if (a >= L) {
+            next[l * next_stride(alpha, L) + c * NR + a] = (uint16_t)(L + 1);
+            continue;
+        }
         const uint32_t *row = tsym + lc * LW;
         uint32_t wi = a >> 5;
         uint32_t w = row[wi] >> (a & 31u);
@@ -500,13 +509,13 @@ __global__ void next_table_kernel(const uint32_t *__restrict__ tsym, uint32_t r,
             w = row[wi];
             base = wi << 5;
         }
-        next[l * next_stride(alpha, L) + c * L + a] = (uint16_t)(base + (uint32_t)__ffs((int)w));
+        next[l * next_stride(alpha, L) + c * NR + a] = (uint16_t)(base + (uint32_t)__ffs((int)w));
     }
 }
 
 cudaError_t launch_next_table(const uint32_t *tsym, uint32_t r, uint32_t alpha, uint32_t L, uint16_t *next,
                               cudaStream_t s) {
-    const uint64_t total = (uint64_t)r * alpha * L;
+    const uint64_t total = (uint64_t)r * alpha * next_row(L);
     uint64_t g = (total + 255) / 256;
     next_table_kernel<<<(unsigned)(g > 4096 ? 4096 : (g ? g : 1)), 256, 0, s>>>(tsym, r, alpha, L, next);
     note_launches(1);
@@ -516,7 +525,7 @@ cudaError_t launch_next_table(const uint32_t *tsym, uint32_t r, uint32_t alpha, 
 size_t next_table_elems(uint32_t r, uint32_t alpha, uint32_t L) { return (size_t)r * next_stride(alpha, L); }
 
 bool embed_sign_uses_table(uint32_t alpha, uint32_t L) {
-    return (size_t)alpha * L * 2 <= ES_TABLE_MAX && L < 65535u;
+    return (size_t)alpha * next_row(L) * 2 <= ES_TABLE_MAX && L < 65534u;
 }
 
 static size_t es_code_words(uint32_t alpha, uint32_t M) {
@@ -527,7 +536,7 @@ static size_t es_code_words(uint32_t alpha, uint32_t M) {
 size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
     const size_t M = (size_t)m * z;
     if (M > 16384 || z > 65535 || m > 65535) return 0;
-    const size_t table = embed_sign_uses_table(alpha, L) ? (size_t)alpha * L * 2 : (size_t)alpha * sym_words(L) * 4;
+    const size_t table = embed_sign_uses_table(alpha, L) ? (size_t)alpha * next_row(L) * 2 : (size_t)alpha * sym_words(L) * 4;
     const size_t bytes = (size_t)z * 8 + (M + 1) * 4 + M * 4 + ((table + 7) & ~(size_t)7) +
                          es_code_words(alpha, (uint32_t)M) * 4 * ES_THREADS;
     return bytes <= 200 * 1024 ? bytes : 0;
@@ -593,7 +602,8 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     uint32_t *s_pos = (uint32_t *)(s_pow + z);                 // [M+1], sentinel at M
     uint32_t *s_rank = s_pos + M + 1;                          // [M]: step-order index of sample f*z+q
     uint32_t *s_tab = s_rank + M;                              // bitmaps [alpha][LW] or next table
-    const size_t tab_bytes = TABLE ? (size_t)alpha * L * 2 : (size_t)alpha * LW * 4;
+    const uint32_t NR = next_row(L);
+    const size_t tab_bytes = TABLE ? (size_t)alpha * NR * 2 : (size_t)alpha * LW * 4;
     uint16_t *s_next = (uint16_t *)s_tab;
     uint32_t *s_code = (uint32_t *)((char *)s_tab + ((tab_bytes + 7) & ~(size_t)7));  // [words][ES_THREADS]
     for (uint32_t i = threadIdx.x; i <= M; i += blockDim.x) {
@@ -606,7 +616,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     if (TABLE) {
         const uint32_t *src = (const uint32_t *)(next + (size_t)l * next_stride(alpha, L));
         uint32_t *dst = (uint32_t *)s_next;
-        const uint32_t nw = (alpha * L + 1) / 2;
+        const uint32_t nw = (alpha * NR + 1) / 2;
         for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
     } else {
         for (uint32_t i = threadIdx.x; i < alpha * LW; i += blockDim.x) s_tab[i] = tsym[(size_t)l * alpha * LW + i];
@@ -622,13 +632,71 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
 
     const int64_t s = (int64_t)blockIdx.x * ES_THREADS + threadIdx.x;
     const int32_t len = s < n ? lens[s] : 0;
+    uint32_t *my = s_code + threadIdx.x;
+    if (TABLE) {
+        // 16 characters per block: their codes come from one 32-bit word (B = 2)
+        // or one 16-byte chunk (B = 8) read a block ahead; the loop conditions
+        // are tested once per block and characters past the end record nothing.
+        // Recorded codes enter a shift register from the top (sample j of a word
+        // ends at bits CB*j once the word is full).
+        constexpr int WPB = B / 2;   // 32-bit words per 16-character block
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(packed + (s < n ? pofs[s] : 0));
+        const int32_t nblk = (len + 15) / 16;
+        uint32_t cur[WPB], nxt[WPB];
+#pragma unroll
+        for (int w = 0; w < WPB; w++) {
+            cur[w] = nblk > 0 ? src[w] : 0u;
+            nxt[w] = 0u;
+        }
+        uint32_t a = 0, k = 0, ps = s_pos[0], acc = 0;
+        for (int32_t b = 0; b < nblk && k < M; b++) {
+            if (b + 1 < nblk) {
+#pragma unroll
+                for (int w = 0; w < WPB; w++) nxt[w] = src[(size_t)(b + 1) * WPB + w];
+            }
+            const int32_t rem = len - 16 * b;
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const uint32_t c = (cur[(t * B) >> 5] >> ((t * B) & 31)) & ((1u << B) - 1u);
+                const uint32_t a_next = s_next[c * NR + a];
+                const bool live = t < rem;
+                const bool hit = live && ps < a_next;   // a sample inside this character's steps
+                acc = hit ? ((acc >> CB) | (c << (32 - CB))) : acc;
+                k += hit ? 1u : 0u;
+                if (hit && k % PER == 0) my[(size_t)(k / PER - 1) * ES_THREADS] = acc;
+                ps = s_pos[k];
+                while (live && ps < a_next) {   // rare: another sample in the same character
+                    acc = (acc >> CB) | (c << (32 - CB));
+                    k++;
+                    if (k % PER == 0) my[(size_t)(k / PER - 1) * ES_THREADS] = acc;
+                    ps = s_pos[k];
+                }
+                a = a_next;
+            }
+#pragma unroll
+            for (int w = 0; w < WPB; w++) cur[w] = nxt[w];
+        }
+        if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc >> (CB * (PER - k % PER));
+        if (s < n) {
+            for (uint32_t f = 0; f < m; f++) {
+                uint64_t key = 0;
+                for (uint32_t q = 0; q < z; q++) {
+                    const uint32_t rk = s_rank[f * z + q];
+                    const uint32_t c = (rk < k)
+                                           ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                           : alpha;
+                    key += (uint64_t)c * s_pow[q];
+                }
+                keys[((size_t)l * m + f) * n + s] = key;
+            }
+        }
+        return;
+    }
     WordReader<B> rd;
     rd.init(packed + (s < n ? pofs[s] : 0), s < n ? chunks_for(len, B) : 0);
-    uint32_t *my = s_code + threadIdx.x;
     // next step after the current character: first step >= a with pi = 1, plus one
     auto step_after = [&](uint32_t c, uint32_t a) -> uint32_t {
         if (a >= L) return L + 1;   // past every sample
-        if (TABLE) return s_next[c * L + a];
         const uint32_t *row = s_tab + c * LW + (a >> 5);
         const uint32_t sh = a & 31u;
         const uint32_t lo = __funnelshift_r(row[0], row[1], sh);
