@@ -273,9 +273,9 @@ void ej_batch_destroy(ej_batch *batch);
  *     otherwise the grid-strided verifier. 2: always the grid-strided verifier
  *     (one pass over the pairs; a warp's slots start together and the warp ends
  *     with its slowest pair). 0 (default): 1 when the strings' mean length is at
- *     least 2048 (long pairs, where refilling pays), else 2. In a batch,
- *     persistent verifiers whose blocks need more than a quarter of an SM's
- *     shared memory run one after another; everything else overlaps.
+ *     least 2048 (long pairs, where refilling pays), else 2.
+ *   chain (batches): persistent verifiers of a batch's joins that are chained run
+ *     one after another (the other stages still overlap); see the field.
  *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
  *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
  *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
@@ -300,6 +300,10 @@ typedef struct {
     int32_t warps_per_subpartition;
     int32_t order;
     int32_t buckets;
+    int32_t chain;   /* batches: 0 (default) or 2: the persistent verifiers of a batch's joins
+                        run one after another; 1: they may overlap (faster median, but two
+                        persistent grids sharing the SMs were measured up to 10x slower at
+                        times) */
 } ej_schedule;
 
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside

@@ -62,7 +62,7 @@ struct ej_ctx {
     uint64_t raw_cap_hint = 0;
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
-    ej_schedule sched{0, 0, 0, 0, 0};   // ej_join's back-half schedule (ej_set_schedule)
+    ej_schedule sched{0, 0, 0, 0, 0, 0};   // ej_join's back-half schedule (ej_set_schedule)
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -1041,12 +1041,12 @@ int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
 int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
     if (!ctx) return EJ_ERR_INVALID_ARG;
     if (!sc) {
-        ctx->sched = ej_schedule{0, 0, 0, 0, 0};
+        ctx->sched = ej_schedule{0, 0, 0, 0, 0, 0};
         return EJ_OK;
     }
     if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
         sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 4 ||
-        sc->buckets < 0 || sc->buckets > 2)
+        sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 2)
         return fail(ctx, EJ_ERR_INVALID_ARG,
                     "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",
                     sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order, sc->buckets);
@@ -1334,15 +1334,16 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return bail(fail(ctx, EJ_ERR_CUDA, "stream capture could not start (the stream must not be the legacy default stream)"));
     int cst = plan_device(ctx, b->pl, s);
     if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
-    // persistent verifiers whose blocks take more than a quarter of an SM's shared
-    // memory run one after another (two of them sharing the SMs measured up to 10x
-    // slower); lighter ones, and every other stage, overlap
+    // persistent verifiers run one after another unless chain == 1: two persistent
+    // grids sharing the SMs (each capping its working warps per SM) measured from
+    // slightly faster to 10x slower from one replay to the next; every other stage
+    // overlaps
     cudaEvent_t prev_verify = nullptr;
     for (auto &j : b->joins) {
         if (cst != EJ_OK) break;
         if (cudaStreamWaitEvent(j.side, b->fork, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
         const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
-        const bool heavy = pt > 0 && pq_smem_bytes(j.bs.vc.V, j.p.alphabet_size, pt) > 56 * 1024;
+        const bool heavy = pt > 0 && j.sub->sched.chain != 1;
         cst = batch_join_device(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
         if (heavy) prev_verify = j.verified;
         if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;

@@ -28,7 +28,6 @@ namespace ej {
 
 namespace {
 
-constexpr int PQ_MAX_THREADS = 128;
 constexpr int64_t kMaxIters = 1ll << 24;   // loop passes per warp before the kernel gives up
 
 // 64/B symbols of a packed string starting at symbol o (any int64; symbols
@@ -60,8 +59,8 @@ __device__ __forceinline__ uint64_t sym_reverse(uint64_t u) {
     return ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
 }
 
-template <int W1, int B>
-__global__ void __launch_bounds__(PQ_MAX_THREADS)
+template <int W1, int B, int TPB>
+__global__ void __launch_bounds__(TPB)
 verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
                  const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t nsm, int32_t spw_force,
@@ -73,6 +72,9 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     }
     if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
     constexpr int R = W1 + 1;
+    constexpr int R2 = 2 * R;                // ring slots per symbol: every word is kept twice,
+                                             // at slot k mod R and k mod R + R, so that the
+                                             // window's W1 words sit at consecutive slots
     constexpr int SPW = 64 / B;              // symbols per 64-bit word
     constexpr uint64_t CMASK = (1ull << B) - 1ull;
     extern __shared__ uint64_t smem[];
@@ -89,8 +91,8 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         s_nmin[t] = (int8_t)mn;
     }
     __syncthreads();
-    const int T_ = blockDim.x;                // slot stride of the per-thread ring
-    uint64_t *ring = smem + threadIdx.x;      // (c*R + slot)*T_, reused as a dump area
+    constexpr int T_ = TPB;                   // slot stride of the per-thread ring
+    uint64_t *ring = smem + threadIdx.x;      // (c*R2 + slot)*T_, reused as a dump area
     const int lane = threadIdx.x & 31;
     const bool rev = lane & 1;
     const int slot = lane >> 1;
@@ -123,10 +125,15 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
     int64_t iters = 0;       // loop passes of this warp (bounded, see kMaxIters)
     int base = 0;
-    uint32_t soff[W1];
     uint64_t Pv[W1], Mv[W1];
 #pragma unroll
-    for (int v = 0; v < W1; v++) { soff[v] = 0; Pv[v] = 0; Mv[v] = 0; }
+    for (int v = 0; v < W1; v++) { Pv[v] = 0; Mv[v] = 0; }
+    // Peq word k (of x or of reversed x) into ring slot `slot` and its twin
+    auto build_word = [&](int slot, int64_t k) {
+        bd_build<B, R2>(ring, T_, slot, xc, m, k, rev, alpha);
+        for (uint32_t c = 0; c < alpha; c++)
+            ring[(size_t)(c * R2 + slot + R) * T_] = ring[(size_t)(c * R2 + slot) * T_];
+    };
 
     while (true) {
         if (++iters > kMaxIters) {
@@ -171,12 +178,11 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                             xc = a_long ? pa : pb;
                             y64 = reinterpret_cast<const uint64_t *>(a_long ? pb : pa);
                             ywords = 2 * chunks_for(n, B);
-                            for (int wi = 0; wi < W1; wi++) bd_build<B, R>(ring, T_, wi, xc, m, wi, rev, alpha);
+                            for (int wi = 0; wi < W1; wi++) build_word(wi, wi);
 #pragma unroll
                             for (int v = 0; v < W1; v++) {
                                 Pv[v] = ~0ull;
                                 Mv[v] = 0ull;
-                                soff[v] = (uint32_t)(v * T_);
                             }
                             base = 0;
                             k0 = 0;
@@ -202,6 +208,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         };
         uint64_t sreg = 0, snext = sym_word((int64_t)jbase - 1);
         auto run_cols = [&](int s_begin, int s_end) {
+#pragma unroll 2
             for (int s = s_begin; s < s_end; s++) {
                 if ((s & (SPW - 1)) == 0) {
                     sreg = rev ? sym_reverse<B>(snext) : snext;
@@ -211,11 +218,11 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 sreg >>= B;
                 c = c < cmax ? c : cmax;
                 if (s <= lim) {
-                    const uint64_t *row = ring + (size_t)c * R * T_;
+                    const uint64_t *row = ring + ((size_t)c * R2 + base) * T_;   // the window's words
                     uint64_t Eq[W1], A[W1], S[W1];
 #pragma unroll
                     for (int v = 0; v < W1; v++) {
-                        Eq[v] = row[soff[v]];
+                        Eq[v] = row[v * T_];
                         A[v] = Eq[v] & Pv[v];
                     }
                     add_chain<W1>(S, A, Pv);
@@ -257,12 +264,10 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 Mv[W1 - 1] = 0ull;
                 k0++;
                 base = (base + 1 == R) ? 0 : base + 1;
-#pragma unroll
-                for (int v = 0; v < W1; v++) {
-                    const int sl = base + v;
-                    soff[v] = (uint32_t)((sl >= R ? sl - R : sl) * T_);
+                {
+                    const int sl = base + W1 - 1;
+                    build_word(sl >= R ? sl - R : sl, k0 + W1 - 1);
                 }
-                bd_build<B, R>(ring, T_, (int)(soff[W1 - 1] / (uint32_t)T_), xc, m, k0 + W1 - 1, rev, alpha);
                 // minimum over the window at column j-1; row 64*k0 (value T) takes part
                 int32_t run = 0, mn = 0;
 #pragma unroll
@@ -376,37 +381,48 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     }
 }
 
-template <int W1, int B>
-cudaError_t launch_pq_t(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
-                        const uint64_t *pairs, int64_t np, int32_t K, int threads, int spw_force, int wps, VerifyOut vo,
-                        cudaStream_t s) {
+template <int W1, int B, int TPB>
+cudaError_t launch_pq_tt(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
+                         const uint64_t *pairs, int64_t np, int32_t K, int spw_force, int wps, VerifyOut vo,
+                         cudaStream_t s) {
+    constexpr int threads = TPB;
     const size_t smem = pq_smem_bytes(W1, alpha, threads);
-    cudaError_t e = cudaFuncSetAttribute(verify_pq_kernel<W1, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(verify_pq_kernel<W1, B, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_pq_kernel<W1, B>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_pq_kernel<W1, B, TPB>, threads, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t blocks = (int64_t)sms * per_sm;
-    verify_pq_kernel<W1, B><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
+    verify_pq_kernel<W1, B, TPB><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
                                                                      sms, spw_force, wps, vo);
     note_launches(1);
     return cudaGetLastError();
 }
 
+template <int W1, int B>
+cudaError_t launch_pq_t(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
+                        const uint64_t *pairs, int64_t np, int32_t K, int threads, int spw_force, int wps, VerifyOut vo,
+                        cudaStream_t s) {
+    if (threads == 128)
+        return launch_pq_tt<W1, B, 128>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
+    if (threads == 32)
+        return launch_pq_tt<W1, B, 32>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 size_t pq_smem_bytes(int W1, uint32_t alpha, int threads) {
-    const size_t R = (size_t)W1 + 1;
-    const size_t per = alpha * R > (size_t)(2 * W1 + 2) ? alpha * R : (size_t)(2 * W1 + 2);
+    const size_t R2 = 2 * ((size_t)W1 + 1);
+    const size_t per = alpha * R2 > (size_t)(2 * W1 + 2) ? alpha * R2 : (size_t)(2 * W1 + 2);
     return per * sizeof(uint64_t) * (size_t)threads;
 }
 
 int pq_threads_for(int W1, uint32_t alpha) {
-    for (int t = PQ_MAX_THREADS; t >= 32; t >>= 1)
-        if (pq_smem_bytes(W1, alpha, t) <= 160 * 1024) return t;
+    if (pq_smem_bytes(W1, alpha, 128) <= 160 * 1024) return 128;
     return pq_smem_bytes(W1, alpha, 32) <= 220 * 1024 ? 32 : 0;
 }
 
@@ -414,7 +430,7 @@ cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const 
                              const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
                              int32_t K, VerifyOut vo, cudaStream_t s) {
     if (np == 0) return cudaGetLastError();
-    if (!vo.queue || !vo.sm_tickets || threads < 32 || threads > PQ_MAX_THREADS || (threads & 31)) return cudaErrorInvalidValue;
+    if (!vo.queue || !vo.sm_tickets || (threads != 128 && threads != 32)) return cudaErrorInvalidValue;
 #define EJ_PQ(WW)                                                                                          \
     if (W1 == WW) {                                                                                        \
         if (B == 2) return launch_pq_t<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, s); \

@@ -62,7 +62,7 @@ class ServerStats(C.Structure):
 
 class _Schedule(C.Structure):
     _fields_ = [("mode", C.c_int32), ("slots_per_warp", C.c_int32), ("warps_per_subpartition", C.c_int32),
-                ("order", C.c_int32), ("buckets", C.c_int32)]
+                ("order", C.c_int32), ("buckets", C.c_int32), ("chain", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -274,11 +274,9 @@ class Context:
                     "ej_set_verify_config")
 
     def set_schedule(self, mode: int = 0, slots_per_warp: int = 0, warps_per_subpartition: int = 0,
-                     order: int = 0, buckets: int = 0):
-        """ej_join's back-half schedule (ej_schedule): mode 0 persistent work queue,
-        2 grid-strided; slots per warp; working warps per SM sub-partition; order 0/1
-        by collision count, 2 hash order; buckets 0/1 hashed, 2 sorted. Zeros = defaults."""
-        sc = _Schedule(mode, slots_per_warp, warps_per_subpartition, order, buckets)
+                     order: int = 0, buckets: int = 0, chain: int = 0):
+        """ej_join's back-half schedule (ej_schedule); zeros = defaults. See the header."""
+        sc = _Schedule(mode, slots_per_warp, warps_per_subpartition, order, buckets, chain)
         self._check(lib().ej_set_schedule(self._h, C.byref(sc)), "ej_set_schedule")
 
     def set_timing(self, on: bool = True):

@@ -80,7 +80,7 @@ int main(void) {{
   F(ej_params, seed) F(ej_params, alphabet) F(ej_params, alphabet_size) F(ej_params, K)
   F(ej_plan_info, embedding_bytes) F(ej_plan_info, key_count)
   F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total)
-  F(ej_schedule, warps_per_subpartition) F(ej_schedule, order) F(ej_schedule, buckets)
+  F(ej_schedule, warps_per_subpartition) F(ej_schedule, order) F(ej_schedule, buckets) F(ej_schedule, chain)
   return 0;
 }}''')
     exe = tmp_path / "probe"
