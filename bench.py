@@ -51,7 +51,7 @@ VERIFY_SOURCE = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify_
 # DRAM bytes per verify launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over the K=50/150/250 launches of one ncu capture of the long-DNA workload), valid
 # only while the verify source is the one that was captured
-VERIFY_TRAFFIC = {"source_sha256_prefix": "a8a17106c98fc680", "bytes_per_launch": 8661760}
+VERIFY_TRAFFIC = {"source_sha256_prefix": "0435fac629cf7d59", "bytes_per_launch": 8663210}
 
 
 def workloads():
