@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--workload", choices=["long_dna", "protein", "text", "serving"], default="long_dna")
     ap.add_argument("--index-size", type=int, default=1_000_000, help="serving: strings in the index")
     ap.add_argument("--queries", type=int, default=4000, help="serving: queries in the stream")
-    ap.add_argument("--rates", type=str, default="500,2000,8000,32000", help="serving: offered queries/s")
+    ap.add_argument("--rates", type=str, default="500,2000,8000,32000,128000", help="serving: offered queries/s")
     ap.add_argument("--clusters", type=int, default=2000, help="clusters of 10 strings (long DNA)")
     ap.add_argument("--n", type=int, default=0, help="protein / text: number of strings (0 = the workload's)")
     ap.add_argument("--Ks", type=str, default="", help="comma-separated K values (default: the workload's)")

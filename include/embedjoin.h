@@ -185,11 +185,15 @@ void ej_index_destroy(ej_index *index);
  * to `inflight` search batches on the GPU, each on its own stream with its own
  * scratch; whenever one finishes it delivers its results and the requests that
  * arrived meanwhile form the next batch (up to max_batch queries and
- * max_batch_bytes query bytes), so batches overlap on the device. A batch whose
- * scratch would have to grow is admitted only if the growth fits the free device
- * memory minus hbm_reserve (and the server's total stays within hbm_budget, 0 =
- * no budget); otherwise its requests wait. Results are the same as
- * ej_index_search for the same query and K, whatever else is in flight.
+ * max_batch_bytes query bytes), so batches overlap on the device. Every slot's
+ * scratch is sized for a full batch at creation (if that fits hbm_budget) and
+ * at least doubles when a batch needs more. A batch whose scratch would have to
+ * grow is admitted only if the growth fits the free device memory minus
+ * hbm_reserve and the server's total stays within hbm_budget (0 = no budget):
+ * otherwise it waits while other batches are in flight; with none in flight it
+ * is cut to fewer queries, and a single query that still does not fit finishes
+ * with status EJ_ERR_OOM. Results are the same as ej_index_search for the same
+ * query and K, whatever else is in flight.
  *   ej_server_submit copies the query and returns a request id >= 0, or
  *     -EJ_ERR_INVALID_ARG (byte outside the alphabet, K < 0).
  *   ej_server_poll returns up to `max` finished requests (waiting up to wait_us

@@ -952,6 +952,16 @@ int ctx_pack(ej_ctx *ctx, const ej_strings *S, const ej_params *p, PackedSet *ou
 
 int ctx_device(const ej_ctx *ctx) { return ctx->device; }
 
+int ctx_sorted_records(ej_ctx *ctx, const PackedSet &set, const ej_params *p, const uint64_t *keys,
+                       const uint64_t **rk, const uint32_t **rid, cudaStream_t s) {
+    cudaSetDevice(ctx->device);
+    Plan pl;
+    pl.st.n = set.n;
+    pl.lens = const_cast<int32_t *>(set.lens);
+    pl.max_len = set.max_len;
+    return sorted_records(ctx, pl, p, keys, rk, rid, s);
+}
+
 int ctx_fail(ej_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
 
 int ctx_check_params(ej_ctx *ctx, const ej_params *p) { return check_params(ctx, p, true); }

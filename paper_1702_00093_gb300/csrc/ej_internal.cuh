@@ -243,11 +243,20 @@ int ctx_device(const ej_ctx *ctx);
 int ctx_fail(ej_ctx *ctx, int code, const char *msg);
 int ctx_check_params(ej_ctx *ctx, const ej_params *p);
 
-// Search against a resident index (hashed buckets of the index's tables).
+// Records of every table sorted by signature, ties by (length, id), for the
+// packed set `set`: rk[T][n] signatures, rid[T][n] ids, in the context's scratch.
+int ctx_sorted_records(ej_ctx *ctx, const PackedSet &set, const ej_params *p, const uint64_t *keys,
+                       const uint64_t **rk, const uint32_t **rid, cudaStream_t s);
+
+// Search against a resident index: per table, records sorted by signature then
+// length (rec = len << 32 | id) and a hashed set mapping each signature to its
+// run [x, y) of records.
+cudaError_t launch_index_runs(const uint64_t *rk, const uint32_t *rid, const int32_t *lens, int64_t n, int64_t T,
+                              uint64_t H, uint64_t *slot_keys, uint2 *runs, uint64_t *rec, uint32_t *err,
+                              cudaStream_t s);
 cudaError_t launch_index_probe(const uint64_t *qkeys, int64_t Q, int64_t T, const int32_t *qlens, const int32_t *qK,
-                               const uint64_t *slot_keys, const uint32_t *heads, uint64_t H, const uint32_t *next,
-                               const int32_t *lens, int64_t n, uint64_t *raw, uint64_t cap,
-                               unsigned long long *counters, cudaStream_t s);
+                               const uint64_t *slot_keys, const uint2 *runs, uint64_t H, const uint64_t *rec,
+                               int64_t n, uint64_t *raw, uint64_t cap, unsigned long long *counters, cudaStream_t s);
 cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  const uint8_t *cls, int nc, unsigned long long *bins, uint64_t *cand,
                                  unsigned long long *counters, cudaStream_t s);

@@ -443,16 +443,105 @@ cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *ta
 // Search against a resident index (query x index pairs)
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// Index buckets (the per-table grouping of equal signatures of Alg. 3, kept
+// resident for search): the records of table t are sorted by signature, ties by
+// (length, id), and stored as rec[t*n + p] = (len << 32) | id. A bucket is the
+// run [start, end) of one signature; table t's open-addressing set (slots
+// [t*H, (t+1)*H)) maps the signature to its run. The length filter
+// ||s_q| - |s_i|| <= K is then a sub-run found by binary search, so a probe costs
+// O(log bucket) plus what it emits, however large the bucket.
+// ---------------------------------------------------------------------------
+
+// Records and run starts: rk/rid are the sorted signatures and ids ([T][n]).
+// slot_keys pre-filled with ~0 (never a signature).
+__global__ void index_runs_kernel(const uint64_t *__restrict__ rk, const uint32_t *__restrict__ rid,
+                                  const int32_t *__restrict__ lens, int64_t n, int64_t T, uint64_t H,
+                                  uint64_t *__restrict__ slot_keys, uint2 *__restrict__ runs,
+                                  uint64_t *__restrict__ rec, uint32_t *__restrict__ err) {
+    const int64_t total = n * T;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = g / n, p = g - t * n;
+        const uint32_t id = rid[g];
+        rec[g] = ((uint64_t)(uint32_t)lens[id] << 32) | id;
+        const uint64_t key = rk[g];
+        if (p > 0 && rk[g - 1] == key) continue;
+        uint64_t *sk = slot_keys + t * H;
+        uint64_t h = key_hash(key) & (H - 1);
+        bool placed = false;
+        for (uint64_t probe = 0; probe < H; probe++) {
+            const unsigned long long old = atomicCAS((unsigned long long *)&sk[h], ~0ull, key);
+            if (old == ~0ull) {   // each signature starts exactly one run: never found already present
+                runs[t * H + h].x = (uint32_t)p;
+                placed = true;
+                break;
+            }
+            h = (h + 1) & (H - 1);
+        }
+        if (!placed) atomicOr(err, (uint32_t)DERR_GUARD);   // cannot happen with H > n
+    }
+}
+
+// Run ends: the last record of each run finds its signature's slot.
+__global__ void index_run_ends_kernel(const uint64_t *__restrict__ rk, int64_t n, int64_t T, uint64_t H,
+                                      const uint64_t *__restrict__ slot_keys, uint2 *__restrict__ runs,
+                                      uint32_t *__restrict__ err) {
+    const int64_t total = n * T;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = g / n, p = g - t * n;
+        const uint64_t key = rk[g];
+        if (p + 1 < n && rk[g + 1] == key) continue;
+        const uint64_t *sk = slot_keys + t * H;
+        uint64_t h = key_hash(key) & (H - 1);
+        bool found = false;
+        for (uint64_t probe = 0; probe < H; probe++) {
+            const uint64_t v = sk[h];
+            if (v == key) {
+                runs[t * H + h].y = (uint32_t)(p + 1);
+                found = true;
+                break;
+            }
+            if (v == ~0ull) break;
+            h = (h + 1) & (H - 1);
+        }
+        if (!found) atomicOr(err, (uint32_t)DERR_GUARD);
+    }
+}
+
+cudaError_t launch_index_runs(const uint64_t *rk, const uint32_t *rid, const int32_t *lens, int64_t n, int64_t T,
+                              uint64_t H, uint64_t *slot_keys, uint2 *runs, uint64_t *rec, uint32_t *err,
+                              cudaStream_t s) {
+    const int64_t total = n * T;
+    if (total == 0) return cudaSuccess;
+    const int64_t g = (total + 255) / 256;
+    const unsigned grid = (unsigned)(g > 65536 ? 65536 : g);
+    index_runs_kernel<<<grid, 256, 0, s>>>(rk, rid, lens, n, T, H, slot_keys, runs, rec, err);
+    index_run_ends_kernel<<<grid, 256, 0, s>>>(rk, n, T, H, slot_keys, runs, err);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+// First p in [lo, hi) with rec[p] >= v (rec ascending on the run).
+__device__ __forceinline__ uint32_t run_lower_bound(const uint64_t *__restrict__ rec, uint32_t lo, uint32_t hi,
+                                                    uint64_t v) {
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(rec + mid) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // For every (table t, query q): the index records that carry q's signature in
-// table t (one hash lookup in the table's signature set, then its record list)
-// and pass |len_q - len_i| <= K_q; pairs (q << 32 | i). counters: [0] raw pairs
-// (may exceed cap), [1] longest record list met.
+// table t and pass |len_q - len_i| <= K_q, as pairs (q << 32 | i). Each lane
+// finds its sub-run; the warp then writes the sub-runs one after another,
+// 32 consecutive pairs at a time. counters: [0] raw pairs (may exceed cap),
+// [1] largest bucket met.
 __global__ void index_probe_kernel(const uint64_t *__restrict__ qkeys, int64_t Q, int64_t T,
                                    const int32_t *__restrict__ qlens, const int32_t *__restrict__ qK,
-                                   const uint64_t *__restrict__ slot_keys, const uint32_t *__restrict__ heads,
-                                   uint64_t H, const uint32_t *__restrict__ next, const int32_t *__restrict__ lens,
-                                   int64_t n, uint64_t *__restrict__ raw, uint64_t cap,
-                                   unsigned long long *__restrict__ counters) {
+                                   const uint64_t *__restrict__ slot_keys, const uint2 *__restrict__ runs,
+                                   uint64_t H, const uint64_t *__restrict__ rec, int64_t n,
+                                   uint64_t *__restrict__ raw, uint64_t cap, unsigned long long *__restrict__ counters) {
     const int lane = threadIdx.x & 31;
     const int64_t total = Q * T;
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
@@ -461,35 +550,32 @@ __global__ void index_probe_kernel(const uint64_t *__restrict__ qkeys, int64_t Q
     unsigned long long mb = 0;
     for (int64_t it = 0; it < iters; it++) {
         const int64_t idx = start + it * step;
-        uint32_t q0 = LIST_END;
-        int64_t q = 0, base_t = 0;
-        int32_t lq = 0, kq = 0;
-        unsigned long long cnt = 0, len_list = 0;
+        int64_t q = 0;
+        const uint64_t *trec = rec;
+        uint32_t lo = 0, cnt = 0;
         if (idx < total) {
             const int64_t t = idx / Q;
             q = idx - t * Q;
-            base_t = t * n;
-            lq = qlens[q];
-            kq = qK[q];
+            trec = rec + t * n;
+            const int64_t lq = qlens[q], kq = qK[q];
             const uint64_t key = qkeys[idx];
             const uint64_t *sk = slot_keys + t * H;
             uint64_t h = key_hash(key) & (H - 1);
             for (uint64_t probe = 0; probe < H; probe++) {
                 const uint64_t v = sk[h];
                 if (v == key) {
-                    q0 = heads[t * H + h];
+                    const uint2 run = runs[t * H + h];
+                    mb = max(mb, (unsigned long long)(run.y - run.x));
+                    const int64_t lmin = lq - kq, lmax = lq + kq;   // lengths are < 2^31
+                    const uint64_t vlo = lmin > 0 ? (uint64_t)lmin << 32 : 0ull;
+                    const uint64_t vhi = (uint64_t)(lmax + 1) << 32;
+                    lo = run_lower_bound(trec, run.x, run.y, vlo);
+                    cnt = run_lower_bound(trec, lo, run.y, vhi) - lo;
                     break;
                 }
                 if (v == ~0ull) break;
                 h = (h + 1) & (H - 1);
             }
-            for (uint32_t r = q0; r != LIST_END; r = next[r]) {
-                const int32_t li = lens[(int64_t)r - base_t];
-                const int32_t d = lq > li ? lq - li : li - lq;
-                cnt += d <= kq ? 1u : 0u;
-                len_list++;
-            }
-            mb = max(mb, len_list);
         }
         unsigned long long incl = cnt;
 #pragma unroll
@@ -498,22 +584,21 @@ __global__ void index_probe_kernel(const uint64_t *__restrict__ qkeys, int64_t Q
             if (lane >= o) incl += v;
         }
         const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+        if (wtotal == 0) continue;
         unsigned long long base = 0;
-        if (wtotal) {
-            if (lane == 31) base = atomicAdd(&counters[0], wtotal);
-            base = __shfl_sync(FULL, base, 31);
-        }
-        if (cnt > 0) {
-            uint64_t o = base + incl - cnt;
-            for (uint32_t r = q0; r != LIST_END; r = next[r]) {
-                const int64_t i = (int64_t)r - base_t;
-                const int32_t li = lens[i];
-                const int32_t d = lq > li ? lq - li : li - lq;
-                if (d <= kq) {
-                    if (o < cap) raw[o] = ((uint64_t)q << 32) | (uint64_t)i;
-                    o++;
-                }
-            }
+        if (lane == 31) base = atomicAdd(&counters[0], wtotal);
+        base = __shfl_sync(FULL, base, 31);
+        const unsigned long long mine = base + incl - cnt;
+        unsigned todo = __ballot_sync(FULL, cnt > 0);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t c = __shfl_sync(FULL, cnt, l), first = __shfl_sync(FULL, lo, l);
+            const unsigned long long ob = __shfl_sync(FULL, mine, l);
+            const uint64_t hi_word = (uint64_t)__shfl_sync(FULL, (unsigned long long)q, l) << 32;
+            const uint64_t *src = (const uint64_t *)__shfl_sync(FULL, (unsigned long long)trec, l) + first;
+            for (uint32_t k = lane; k < c; k += 32)
+                if (ob + k < cap) raw[ob + k] = hi_word | (uint32_t)__ldg(src + k);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -524,14 +609,13 @@ __global__ void index_probe_kernel(const uint64_t *__restrict__ qkeys, int64_t Q
 }
 
 cudaError_t launch_index_probe(const uint64_t *qkeys, int64_t Q, int64_t T, const int32_t *qlens, const int32_t *qK,
-                               const uint64_t *slot_keys, const uint32_t *heads, uint64_t H, const uint32_t *next,
-                               const int32_t *lens, int64_t n, uint64_t *raw, uint64_t cap,
-                               unsigned long long *counters, cudaStream_t s) {
+                               const uint64_t *slot_keys, const uint2 *runs, uint64_t H, const uint64_t *rec,
+                               int64_t n, uint64_t *raw, uint64_t cap, unsigned long long *counters, cudaStream_t s) {
     const int64_t total = Q * T;
     if (total > 0) {
         const int64_t g = (total + 255) / 256;
-        index_probe_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(qkeys, Q, T, qlens, qK, slot_keys, heads,
-                                                                              H, next, lens, n, raw, cap, counters);
+        index_probe_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(qkeys, Q, T, qlens, qK, slot_keys, runs,
+                                                                              H, rec, n, raw, cap, counters);
         note_launches(1);
     }
     return cudaGetLastError();

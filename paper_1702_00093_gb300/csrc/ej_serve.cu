@@ -43,10 +43,12 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-// Grows (never shrinks) a device buffer; contents are not kept.
+// Grows (never shrinks) a device buffer, at least doubling it, so that growth
+// (whose cudaFree synchronises the device) stays rare; contents are not kept.
 cudaError_t dev_grow(DevBuf &b, size_t bytes, size_t *grown = nullptr) {
     if (bytes == 0) bytes = 16;
     if (b.p && bytes <= b.bytes) return cudaSuccess;
+    if (b.p && bytes < 2 * b.bytes) bytes = 2 * b.bytes;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -92,14 +94,14 @@ struct ej_index {
     int64_t T = 0;
     uint64_t H = 0;
     bool use_table = false;
-    DevBuf pos, tsym, spos, stag, next, skeys, heads, recnext, err;
+    DevBuf pos, tsym, spos, stag, next, skeys, runs, rec, err;
 };
 
 namespace {
 
 void index_free(ej_index *x) {
     if (!x) return;
-    for (DevBuf *b : {&x->pos, &x->tsym, &x->spos, &x->stag, &x->next, &x->skeys, &x->heads, &x->recnext, &x->err})
+    for (DevBuf *b : {&x->pos, &x->tsym, &x->spos, &x->stag, &x->next, &x->skeys, &x->runs, &x->rec, &x->err})
         dev_free(*b);
     if (x->own) ej_destroy(x->own);
     delete x;
@@ -173,6 +175,42 @@ size_t slot_growth(const Slot &sl, const ej_index &x, int64_t Q, int64_t total, 
     return g;
 }
 
+// Sizes the slot's buffers (pinned staging and device scratch) for a batch of Q
+// queries with `total` bytes and nc window classes at the slot's capacity.
+cudaError_t slot_reserve(Slot &sl, const ej_index &x, int64_t Q, int64_t total, int nc) {
+    const size_t in_bytes = (((size_t)total + 7) & ~(size_t)7) + (size_t)(Q + 1) * 8 + (size_t)Q * 5 + 64;
+    if (in_bytes > sl.h_in_bytes) {
+        const size_t want = std::max(in_bytes, 2 * sl.h_in_bytes);
+        if (sl.h_in) cudaFreeHost(sl.h_in);
+        sl.h_in = nullptr;
+        sl.h_in_bytes = 0;
+        SV(cudaMallocHost(&sl.h_in, want));
+        sl.h_in_bytes = want;
+    }
+    const uint64_t cap = sl.cap, hs = hsize_for(cap);
+    const int64_t chunk_bound = (total * x.set.B + 127) / 128 + Q + 1;
+    size_t grown = 0;
+    SV(dev_grow(sl.in, in_bytes, &grown));
+    SV(dev_grow(sl.qlens, (size_t)Q * 4, &grown));
+    SV(dev_grow(sl.ccnt, (size_t)(Q + 1) * 4, &grown));
+    SV(dev_grow(sl.qpofs, (size_t)(Q + 2) * 8, &grown));
+    SV(dev_grow(sl.scan, scan_temp_bytes(Q + 1), &grown));
+    SV(dev_grow(sl.qpacked, (size_t)chunk_bound * 16, &grown));
+    SV(dev_grow(sl.qkeys, (size_t)x.T * Q * 8, &grown));
+    SV(dev_grow(sl.raw, cap * 8, &grown));
+    SV(dev_grow(sl.table, hs * 8, &grown));
+    SV(dev_grow(sl.hcount, hs * 4, &grown));
+    SV(dev_grow(sl.bins, (size_t)3 * nc * 8, &grown));
+    SV(dev_grow(sl.cand, cap * 8, &grown));
+    SV(dev_grow(sl.app, cap * 8, &grown));
+    SV(dev_grow(sl.cnt, 8 * 8, &grown));
+    SV(dev_grow(sl.derr, 16, &grown));
+    SV(dev_grow(sl.queue, (size_t)nc * 8, &grown));
+    SV(dev_grow(sl.tickets, (size_t)nc * SM_TICKETS * 4, &grown));
+    sl.device_bytes += grown;
+    return cudaSuccess;
+}
+
 // Issues the whole search of `qs` on the slot's stream (no host synchronisation)
 // and records sl.done. Query bytes are copied into pinned staging first.
 cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &qs) {
@@ -203,13 +241,7 @@ cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &q
     const size_t off_k = off_o + (size_t)(Q + 1) * 8;
     const size_t off_c = off_k + (size_t)Q * 4;
     const size_t in_bytes = off_c + (size_t)Q + 64;
-    if (in_bytes > sl.h_in_bytes) {
-        if (sl.h_in) cudaFreeHost(sl.h_in);
-        sl.h_in = nullptr;
-        sl.h_in_bytes = 0;
-        SV(cudaMallocHost(&sl.h_in, in_bytes));
-        sl.h_in_bytes = in_bytes;
-    }
+    SV(slot_reserve(sl, x, Q, total, nc));
     uint8_t *hb = (uint8_t *)sl.h_in;
     int64_t *ho = (int64_t *)(hb + off_o);
     int32_t *hk = (int32_t *)(hb + off_k);
@@ -223,28 +255,7 @@ cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &q
         hc[i] = cls[i];
     }
     ho[Q] = o;
-    // device buffers
     const uint64_t cap = sl.cap, hs = hsize_for(cap);
-    const int64_t chunk_bound = (total * x.set.B + 127) / 128 + Q + 1;
-    size_t grown = 0;
-    SV(dev_grow(sl.in, in_bytes, &grown));
-    SV(dev_grow(sl.qlens, (size_t)Q * 4, &grown));
-    SV(dev_grow(sl.ccnt, (size_t)(Q + 1) * 4, &grown));
-    SV(dev_grow(sl.qpofs, (size_t)(Q + 2) * 8, &grown));
-    SV(dev_grow(sl.scan, scan_temp_bytes(Q + 1), &grown));
-    SV(dev_grow(sl.qpacked, (size_t)chunk_bound * 16, &grown));
-    SV(dev_grow(sl.qkeys, (size_t)x.T * Q * 8, &grown));
-    SV(dev_grow(sl.raw, cap * 8, &grown));
-    SV(dev_grow(sl.table, hs * 8, &grown));
-    SV(dev_grow(sl.hcount, hs * 4, &grown));
-    SV(dev_grow(sl.bins, (size_t)3 * nc * 8, &grown));
-    SV(dev_grow(sl.cand, cap * 8, &grown));
-    SV(dev_grow(sl.app, cap * 8, &grown));
-    SV(dev_grow(sl.cnt, 8 * 8, &grown));
-    SV(dev_grow(sl.derr, 16, &grown));
-    SV(dev_grow(sl.queue, (size_t)nc * 8, &grown));
-    SV(dev_grow(sl.tickets, (size_t)nc * SM_TICKETS * 4, &grown));
-    sl.device_bytes += grown;
     const cudaStream_t s = sl.s;
     uint8_t *d_in = P<uint8_t>(sl.in);
     const uint8_t *qbytes = d_in;
@@ -275,8 +286,7 @@ cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &q
                          P<uint64_t>(sl.qkeys), s));
     // buckets -> pairs -> dedup by class
     SV(launch_index_probe(P<uint64_t>(sl.qkeys), Q, x.T, P<int32_t>(sl.qlens), qK, P<uint64_t>(x.skeys),
-                          P<uint32_t>(x.heads), x.H, P<uint32_t>(x.recnext), x.set.lens, x.set.n, P<uint64_t>(sl.raw),
-                          cap, cnt, s));
+                          P<uint2>(x.runs), x.H, P<uint64_t>(x.rec), x.set.n, P<uint64_t>(sl.raw), cap, cnt, s));
     SV(launch_dedup_classes(P<uint64_t>(sl.raw), cap, P<uint64_t>(sl.table), P<uint32_t>(sl.hcount), hs, qcls, nc,
                             bins, P<uint64_t>(sl.cand), cnt, s));
     // verify, one launch per window class
@@ -407,8 +417,8 @@ int ej_index_create(ej_ctx *ctx, const ej_strings *S, const ej_params *p, ej_ind
               dev_grow(keys, (size_t)T * x->set.n * 8) == cudaSuccess;
     x->H = bucket_slots_per_table(x->set.n);
     ok = ok && dev_grow(x->skeys, (size_t)x->H * T * 8) == cudaSuccess &&
-         dev_grow(x->heads, (size_t)x->H * T * 4) == cudaSuccess &&
-         dev_grow(x->recnext, (size_t)x->set.n * T * 4) == cudaSuccess && dev_grow(x->err, 16) == cudaSuccess;
+         dev_grow(x->runs, (size_t)x->H * T * 8) == cudaSuccess &&
+         dev_grow(x->rec, (size_t)x->set.n * T * 8) == cudaSuccess && dev_grow(x->err, 16) == cudaSuccess;
     if (!ok) {
         dev_free(keys);
         return bail(EJ_ERR_OOM, "index allocation failed");
@@ -423,14 +433,22 @@ int ej_index_create(ej_ctx *ctx, const ej_strings *S, const ej_params *p, ej_ind
                               P<uint32_t>(x->tsym), x->use_table ? P<uint16_t>(x->next) : nullptr,
                               P<uint32_t>(x->spos), P<uint32_t>(x->stag), P<uint64_t>(keys), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->skeys.p, 0xFF, x->skeys.bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(x->heads.p, 0xFF, x->heads.bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->runs.p, 0, x->runs.bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->err.p, 0, 16, s);
+    // records sorted by signature, then length, in a scratch context released below
+    ej_ctx *scratch = nullptr;
+    const uint64_t *rk = nullptr;
+    const uint32_t *rid = nullptr;
+    if (e == cudaSuccess && ej_create(&scratch, x->device) != EJ_OK) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess && ctx_sorted_records(scratch, x->set, &x->p, P<uint64_t>(keys), &rk, &rid, s) != EJ_OK)
+        e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
-        e = launch_bucket_insert(P<uint64_t>(keys), x->set.n, T, x->H, P<uint64_t>(x->skeys), P<uint32_t>(x->heads),
-                                 P<uint32_t>(x->recnext), P<uint32_t>(x->err), s);
+        e = launch_index_runs(rk, rid, x->set.lens, x->set.n, T, x->H, P<uint64_t>(x->skeys), P<uint2>(x->runs),
+                              P<uint64_t>(x->rec), P<uint32_t>(x->err), s);
     uint32_t herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, x->err.p, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (scratch) ej_destroy(scratch);
     dev_free(keys);
     if (e != cudaSuccess) return bail(EJ_ERR_CUDA, cudaGetErrorString(e));
     if (herr) return bail(EJ_ERR_CUDA, "index bucket insertion failed");
@@ -602,21 +620,49 @@ void server_loop(ej_server *srv) {
                     srv->pending.pop_front();
                 }
             }
-            // admission by free HBM: the slot may grow only into free memory
-            int64_t total = 0;
-            for (const Query &q : qs) total += q.len;
-            const size_t growth = slot_growth(ss.sl, x, (int64_t)qs.size(), total, ss.sl.cap);
-            size_t free_b = 0, total_b = 0;
-            cudaMemGetInfo(&free_b, &total_b);
-            const bool fits = growth == 0 || (growth + srv->cfg.hbm_reserve <= free_b &&
-                                              (srv->cfg.hbm_budget == 0 ||
-                                               srv->device_bytes + growth <= srv->cfg.hbm_budget));
-            if (!fits) {
+            // admission by free HBM: the slot may grow only into free memory and
+            // within the budget. While other batches are in flight the batch waits;
+            // with nothing in flight it is cut down, and a single query that still
+            // does not fit fails with EJ_ERR_OOM rather than waiting forever.
+            bool others_busy = false;
+            for (const SlotState &o : srv->slots) others_busy = others_busy || o.busy;
+            bool fits = false;
+            for (;;) {
+                int64_t total = 0;
+                for (const Query &q : qs) total += q.len;
+                const size_t growth = slot_growth(ss.sl, x, (int64_t)qs.size(), total, ss.sl.cap);
+                size_t free_b = 0, total_b = 0;
+                if (growth) cudaMemGetInfo(&free_b, &total_b);
+                fits = growth == 0 || (growth + srv->cfg.hbm_reserve <= free_b &&
+                                       (srv->cfg.hbm_budget == 0 ||
+                                        srv->device_bytes + growth <= srv->cfg.hbm_budget));
+                if (fits || others_busy || qs.size() <= 1) break;
+                std::lock_guard<std::mutex> lk(srv->mu);
+                srv->pending.push_front(ss.batch.back());
+                ss.batch.pop_back();
+                qs.pop_back();
+            }
+            if (!fits && others_busy) {
                 std::lock_guard<std::mutex> lk(srv->mu);
                 for (auto it = ss.batch.rbegin(); it != ss.batch.rend(); ++it) srv->pending.push_front(*it);
                 ss.batch.clear();
                 srv->deferred++;
                 break;
+            }
+            if (!fits) {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                for (int64_t id : ss.batch) {
+                    Request &r = srv->reqs[id];
+                    r.status = EJ_ERR_OOM;
+                    r.done = true;
+                    r.t_done = Clock::now();
+                    srv->completed.push_back(id);
+                }
+                srv->last_error = "query does not fit the server's HBM budget";
+                ss.batch.clear();
+                srv->cv_done.notify_all();
+                did = true;
+                continue;
             }
             const size_t before = ss.sl.device_bytes;
             const Clock::time_point now = Clock::now();
@@ -684,12 +730,23 @@ int ej_server_create(ej_index *x, const ej_server_config *cfg, ej_server **out) 
     srv->cfg = c;
     cudaSetDevice(x->device);
     srv->slots.resize((size_t)c.inflight);
-    for (SlotState &ss : srv->slots)
-        if (slot_init(ss.sl) != cudaSuccess) {
+    // every slot sized up front for a full batch (max_batch queries, max_batch_bytes
+    // bytes, up to 32 window classes), so that growth during serving is rare
+    // (within the HBM budget, if one is set; beyond it slots grow on demand)
+    for (SlotState &ss : srv->slots) {
+        cudaError_t e = slot_init(ss.sl);
+        // room for 2048 candidate pairs per query of a full batch before a retry
+        ss.sl.cap = std::max<uint64_t>(ss.sl.cap, (uint64_t)c.max_batch * 2048);
+        const size_t full = slot_growth(ss.sl, *x, c.max_batch, c.max_batch_bytes, ss.sl.cap);
+        if (e == cudaSuccess && (c.hbm_budget == 0 || srv->device_bytes + full <= c.hbm_budget))
+            e = slot_reserve(ss.sl, *x, c.max_batch, c.max_batch_bytes, 32);
+        if (e != cudaSuccess) {
             for (SlotState &t : srv->slots) slot_free(t.sl);
             delete srv;
             return EJ_ERR_CUDA;
         }
+        srv->device_bytes += ss.sl.device_bytes;
+    }
     srv->worker = std::thread(server_loop, srv);
     *out = srv;
     return EJ_OK;

@@ -166,3 +166,48 @@ def test_serving_misuse(ej, ctx, setup):
     with pytest.raises(ej.EJError):          # an index needs L > 0
         ej.Index(ctx, ej.Strings.from_set(idx_ss, DEV), ej.Params(K=0, r=2, m=2, z=4, seed=1, L=0,
                                                                   alphabet=idx_ss.alphabet))
+
+
+def test_hbm_budget_admission(ej, setup):
+    idx_ss, qs, ks, index = setup
+    nq = 24
+    offline = index.search(qs[:nq], ks[:nq])
+    per_q = {q: sorted(int(v) & 0xFFFFFFFF for v in offline if int(v) >> 32 == q) for q in range(nq)}
+    cfg = dict(max_batch=4, inflight=2, max_batch_bytes=16384)
+    # the scratch a server of this shape sizes up front
+    srv = ej.Server(index, **cfg)
+    presized = srv.stats()["device_bytes"]
+    srv.close()
+    assert presized > 0
+    long_q = bytes(np.random.default_rng(5).choice(np.frombuffer(idx_ss.alphabet, np.uint8), 200000))
+    # a budget of exactly that: ordinary batches run, a query that would make a
+    # slot grow beyond it finishes with EJ_ERR_OOM, and the server carries on
+    srv = ej.Server(index, hbm_budget=presized, **cfg)
+    try:
+        ids = {srv.submit(qs[q], int(ks[q])): q for q in range(nq // 2)}
+        big = srv.submit(long_q, 5)
+        ids.update({srv.submit(qs[q], int(ks[q])): q for q in range(nq // 2, nq)})
+        got = {}
+        deadline = time.time() + 60
+        while len(got) < nq + 1 and time.time() < deadline:
+            for rid, status, matches, _, _ in srv.poll(256, 2000):
+                got[rid] = (status, list(matches))
+        assert len(got) == nq + 1
+        assert got[big][0] == ej.EJ_ERR_OOM
+        for rid, q in ids.items():
+            assert got[rid] == (0, per_q[q])
+        st = srv.stats()
+        assert st["device_bytes"] <= presized
+    finally:
+        srv.close()
+    # a budget too small for any scratch: every request fails the same way
+    srv = ej.Server(index, hbm_budget=1, **cfg)
+    try:
+        rid = srv.submit(qs[0], int(ks[0]))
+        res = []
+        deadline = time.time() + 30
+        while not res and time.time() < deadline:
+            res = srv.poll(8, 2000)
+        assert res and res[0][0] == rid and res[0][1] == ej.EJ_ERR_OOM
+    finally:
+        srv.close()
