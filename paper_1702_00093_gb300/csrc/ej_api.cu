@@ -850,6 +850,10 @@ struct BatchJoin {
     cudaStream_t side = nullptr;
     cudaEvent_t done = nullptr;
     cudaEvent_t verified = nullptr;   // this join's verifier finished (chains the verifiers)
+    cudaEvent_t keyed = nullptr;      // this join's keys are written
+    int src = -1;                     // join whose walks give this join's keys (-1: its own)
+    uint64_t modulus = 0;             // keys = src keys mod modulus (0: same z)
+    bool alias = false;               // same r, m, z as src: read src's keys directly
 };
 
 }  // namespace
@@ -875,19 +879,64 @@ void batch_free(ej_batch *b) {
     for (auto &j : b->joins) {
         if (j.done) cudaEventDestroy(j.done);
         if (j.verified) cudaEventDestroy(j.verified);
+        if (j.keyed) cudaEventDestroy(j.keyed);
         if (j.side) cudaStreamDestroy(j.side);
         if (j.sub) ej_destroy(j.sub);
     }
     delete b;
 }
 
-// Device work of one join (keys -> buckets -> pairs -> dedup -> verify) on its
-// side stream; no host synchronisation.
-int batch_join_device(BatchJoin &j, cudaStream_t s, cudaEvent_t verify_after, cudaEvent_t verify_done) {
-    CKS(keys_dev(j.sub, &j.p, j.pl, j.keys, s));
+// Keys of one join on stream s: its own walk and signatures, or derived from
+// its source join's keys (which must already be written on s's timeline).
+int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s) {
+    if (j.src < 0) return keys_dev(j.sub, &j.p, j.pl, j.keys, s);
+    if (j.alias) return EJ_OK;
+    ej_ctx *ctx = j.sub;
+    const BatchJoin &src = joins[(size_t)j.src];
+    CK(launch_derive_keys(src.keys, src.p.m, j.pl.st.n, j.p.r, j.p.m, j.modulus, j.keys, s));
+    return EJ_OK;
+}
+
+// Back half of one join (buckets -> pairs -> dedup -> verify) on its side
+// stream; no host synchronisation.
+int batch_join_back(BatchJoin &j, cudaStream_t s, cudaEvent_t verify_after, cudaEvent_t verify_done) {
     CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
     CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s, verify_after, verify_done));
     return EJ_OK;
+}
+
+// Join a's walks cover join b's signatures: same seed and sampling range, and
+// at least as many embeddings, functions and samples per function.
+bool batch_covers(const BatchJoin &a, const BatchJoin &b) {
+    return a.p.seed == b.p.seed && a.pl.L == b.pl.L && a.p.r >= b.p.r && a.p.m >= b.p.m && a.p.z >= b.p.z;
+}
+
+// Sources: a join walks its strings itself unless another join covers it (and
+// is not covered back, or is equal and earlier); it then takes the first such
+// self-walking join's keys. Covering is transitive, so one always exists.
+void batch_sources(std::vector<BatchJoin> &joins) {
+    const size_t n = joins.size();
+    std::vector<bool> root(n, true);
+    for (size_t i = 0; i < n; i++)
+        for (size_t k = 0; k < n && root[i]; k++)
+            if (k != i && batch_covers(joins[k], joins[i]) && (!batch_covers(joins[i], joins[k]) || k < i))
+                root[i] = false;
+    for (size_t i = 0; i < n; i++) {
+        BatchJoin &j = joins[i];
+        if (root[i]) continue;
+        for (size_t k = 0; k < n; k++)
+            if (root[k] && batch_covers(joins[k], j)) {
+                j.src = (int)k;
+                break;
+            }
+        const BatchJoin &src = joins[(size_t)j.src];
+        j.alias = src.p.r == j.p.r && src.p.m == j.p.m && src.p.z == j.p.z;
+        j.modulus = 0;
+        if (j.p.z < src.p.z) {
+            j.modulus = 1;
+            for (uint32_t q = 0; q < j.p.z; q++) j.modulus *= (uint64_t)j.p.alphabet_size + 1;
+        }
+    }
 }
 
 // Schedules the autotuner tries for the back half of one join (verifier slots
@@ -1312,12 +1361,26 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         j.sub->vWarps = ctx->vWarps;
         if (cudaStreamCreateWithFlags(&j.side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&j.verified, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&j.verified, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&j.keyed, cudaEventDisableTiming) != cudaSuccess)
             return bail(fail(ctx, EJ_ERR_CUDA, "stream/event creation failed"));
         if ((st = upload_alphabet(j.sub, &j.p, s)) != EJ_OK) return bail(st);
-        if ((st = ensure_t(j.sub, B_KEYS, (size_t)j.p.r * j.p.m * b->pl.st.n, &j.keys)) != EJ_OK) return bail(st);
-        // eager pass: sizes every buffer (the raw-pair capacity gets a margin)
-        if ((st = keys_dev(j.sub, &j.p, j.pl, j.keys, s)) != EJ_OK) return bail(st);
+    }
+    // joins whose signatures another join's walks already cover take their keys
+    // from it instead of walking the strings again
+    batch_sources(b->joins);
+    for (auto &j : b->joins)
+        if (!j.alias && (st = ensure_t(j.sub, B_KEYS, (size_t)j.p.r * j.p.m * b->pl.st.n, &j.keys)) != EJ_OK)
+            return bail(st);
+    for (auto &j : b->joins)
+        if (j.alias) j.keys = b->joins[(size_t)j.src].keys;
+    // eager pass: keys (sources first), then every join's back half, which sizes
+    // every buffer (the raw-pair capacity gets a margin)
+    for (auto &j : b->joins)
+        if (j.src < 0 && (st = batch_join_keys(b->joins, j, s)) != EJ_OK) return bail(st);
+    for (auto &j : b->joins)
+        if (j.src >= 0 && (st = batch_join_keys(b->joins, j, s)) != EJ_OK) return bail(st);
+    for (auto &j : b->joins) {
         if ((st = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s)) != EJ_OK) return bail(st);
         uint64_t cap = raw_cap_start(j.sub, b->pl.st.n);
         unsigned long long hc[8];
@@ -1344,6 +1407,15 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return bail(fail(ctx, EJ_ERR_CUDA, "stream capture could not start (the stream must not be the legacy default stream)"));
     int cst = plan_device(ctx, b->pl, s);
     if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    // keys: the self-walking joins first, then the derived ones after their source
+    for (int pass = 0; pass < 2 && cst == EJ_OK; pass++)
+        for (auto &j : b->joins) {
+            if (cst != EJ_OK || (pass == 0) != (j.src < 0)) continue;
+            cudaEvent_t after = j.src < 0 ? b->fork : b->joins[(size_t)j.src].keyed;
+            if (cudaStreamWaitEvent(j.side, after, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
+            cst = batch_join_keys(b->joins, j, j.side);
+            if (cst == EJ_OK && cudaEventRecord(j.keyed, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
+        }
     // persistent verifiers run one after another unless chain == 1: two persistent
     // grids sharing the SMs (each capping its working warps per SM) measured from
     // slightly faster to 10x slower from one replay to the next; every other stage
@@ -1351,10 +1423,9 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
     cudaEvent_t prev_verify = nullptr;
     for (auto &j : b->joins) {
         if (cst != EJ_OK) break;
-        if (cudaStreamWaitEvent(j.side, b->fork, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
         const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
         const bool heavy = pt > 0 && j.sub->sched.chain != 1;
-        cst = batch_join_device(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
+        cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
         if (heavy) prev_verify = j.verified;
         if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
         if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;

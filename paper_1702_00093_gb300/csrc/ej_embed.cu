@@ -787,4 +787,30 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
     return cudaGetLastError();
 }
 
+// Signatures of a parameter set (r, m, z) from those of a wider one (r_src >= r,
+// m_src >= m, z_src >= z, same seed and L). The bits pi_l(sigma) and positions
+// P[l][f][q] of Sec. 3 depend on (l, f, q) alone, so embedding l and function f
+// sample the same steps in both sets, and the key sum_q c_q (alpha+1)^q of the
+// first z samples is the wider key mod (alpha+1)^z.
+__global__ void derive_keys_kernel(const uint64_t *__restrict__ src, uint32_t m_src, int64_t n, uint32_t r,
+                                   uint32_t m, uint64_t modulus, uint64_t *__restrict__ dst) {
+    const int64_t total = (int64_t)r * m * n;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = g / n, s = g - t * n;
+        const int64_t l = t / m, f = t - l * m;
+        const uint64_t v = src[(l * m_src + f) * n + s];
+        dst[g] = modulus ? v % modulus : v;
+    }
+}
+
+cudaError_t launch_derive_keys(const uint64_t *src, uint32_t m_src, int64_t n, uint32_t r, uint32_t m,
+                               uint64_t modulus, uint64_t *dst, cudaStream_t s) {
+    const int64_t total = (int64_t)r * m * n;
+    if (total == 0) return cudaGetLastError();
+    const int64_t g = (total + 255) / 256;
+    derive_keys_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, s>>>(src, m_src, n, r, m, modulus, dst);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace ej

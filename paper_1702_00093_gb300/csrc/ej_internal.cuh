@@ -155,6 +155,11 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
                               const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
                               const uint32_t *stag, uint64_t *keys, cudaStream_t s);
+// Keys [r][m][n] of (r, m, z) from keys [r_src][m_src][n] of a set with the same
+// seed and L and r_src >= r, m_src >= m, z_src >= z: dst = src mod modulus
+// ((alpha+1)^z; 0 = plain copy when z = z_src).
+cudaError_t launch_derive_keys(const uint64_t *src, uint32_t m_src, int64_t n, uint32_t r, uint32_t m,
+                               uint64_t modulus, uint64_t *dst, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Scan and sort primitives (ej_sort.cu)

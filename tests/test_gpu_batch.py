@@ -72,6 +72,34 @@ def test_batch_equals_join_and_oracle_long_dna(ej, ctx, stream):
         b.close()
 
 
+def test_batch_shares_walks_across_parameter_sets(ej, ctx, stream):
+    """Joins whose (r, m, z) another join of the batch covers (same seed and L)
+    take their keys from that join's walks: a narrower set by the modulus of the
+    wider key, an equal set directly. Each must still return exactly ej_join's
+    pairs, and a join with another seed walks on its own."""
+    ss = synth.small_dna(0.5)
+    s = ej.Strings.from_set(ss, DEV)
+    a = ss.alphabet
+    params = [ej.Params(K=6, alphabet=a, r=2, m=6, z=9, seed=1),
+              ej.Params(K=5, alphabet=a, r=3, m=10, z=12, seed=1),
+              ej.Params(K=7, alphabet=a, r=3, m=10, z=12, seed=1),
+              ej.Params(K=6, alphabet=a, r=3, m=4, z=12, seed=1),
+              ej.Params(K=6, alphabet=a, r=3, m=10, z=11, seed=2)]
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, stream=stream)
+        b.run(stream)
+        outs = []
+        for i, p in enumerate(params):
+            got, st = b.result(i, device=DEV, stream=stream)
+            want, st_j = ctx.join(s, p, device=DEV, stream=stream)
+            assert np.array_equal(_u64(got), _u64(want)), i
+            assert st.n_candidates == st_j.n_candidates
+            outs.append(_u64(got))
+        b.close()
+    ref = oracle.join(ss.data, ss.offsets, a, K=6, r=2, m=6, z=9, seed=1)
+    assert np.array_equal(outs[0], ref.pairs)
+
+
 def test_batch_rerun_after_rewriting_strings(ej, ctx, stream):
     ss = synth.small_dna(0.5)
     s = ej.Strings.from_set(ss, DEV)
