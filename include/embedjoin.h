@@ -278,8 +278,9 @@ void ej_batch_destroy(ej_batch *batch);
  *     (one pass over the pairs; a warp's slots start together and the warp ends
  *     with its slowest pair). 0 (default): 1 when the strings' mean length is at
  *     least 2048 (long pairs, where refilling pays), else 2.
- *   chain (batches): persistent verifiers of a batch's joins that are chained run
- *     one after another (the other stages still overlap); see the field.
+ *   chain (batches): how the persistent verifiers of a batch's joins share the
+ *     GPU (merged, chained or overlapping; the other stages always overlap);
+ *     see the field.
  *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
  *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
  *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
@@ -304,10 +305,15 @@ typedef struct {
     int32_t warps_per_subpartition;
     int32_t order;
     int32_t buckets;
-    int32_t chain;   /* batches: 0 (default) or 2: the persistent verifiers of a batch's joins
-                        run one after another; 1: they may overlap (faster median, but two
-                        persistent grids sharing the SMs were measured up to 10x slower at
-                        times) */
+    int32_t chain;   /* batches, joins that use the persistent verifier: 3: one merged launch
+                        verifies them all, at the widest of their bands, each pair with its
+                        own join's K, largest K first (the queue runs from one join's pairs
+                        into the next, so no join waits for another's last pairs); 2: one
+                        launch per join, one after another; 1: one launch per join, free to
+                        overlap (two persistent grids sharing the SMs were measured up to
+                        10x slower at times); 0 (default): 3 when the wider band adds at
+                        most half the word-columns of the joins' own bands (candidate counts
+                        of the sizing pass), else 2 */
 } ej_schedule;
 
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "ej_internal.cuh"
@@ -672,9 +673,11 @@ int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const Verif
 
 // verify_after / verify_done (optional): the verifier launch waits for the
 // first event and records the second (a batch chains its joins' verifiers, so
-// that persistent verifiers never run concurrently).
+// that persistent verifiers never run concurrently). defer (optional): no
+// verifier launch; *defer describes this join's share of a merged launch.
 int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackState &bs, uint64_t cap,
-                 cudaStream_t s, cudaEvent_t verify_after = nullptr, cudaEvent_t verify_done = nullptr) {
+                 cudaStream_t s, cudaEvent_t verify_after = nullptr, cudaEvent_t verify_done = nullptr,
+                 VerifySeg *defer = nullptr) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     unsigned long long *cnt = nullptr;
     CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
@@ -725,6 +728,10 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
         CK(launch_dedup(raw, cap, table, hsize, cand, cnt, s));
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], s));
+    if (defer) {
+        *defer = VerifySeg{cand, cnt + 2, cap, p->K, app, cnt + 3, cap, cnt + 4, derr};
+        return EJ_OK;
+    }
     unsigned int *tickets = nullptr;
     CKS(ensure_t(ctx, B_TICKETS, (size_t)SM_TICKETS, &tickets));
     CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
@@ -854,6 +861,8 @@ struct BatchJoin {
     int src = -1;                     // join whose walks give this join's keys (-1: its own)
     uint64_t modulus = 0;             // keys = src keys mod modulus (0: same z)
     bool alias = false;               // same r, m, z as src: read src's keys directly
+    uint64_t ncand = 0;               // candidates in the eager pass
+    int seg = -1;                     // share of the merged verifier launch (-1: none)
 };
 
 }  // namespace
@@ -867,6 +876,12 @@ struct ej_batch {
     cudaGraphExec_t exec = nullptr;
     int64_t kernel_nodes = 0;
     bool ran = false;
+    // merged persistent verifier: one launch over the joins' candidates in turn
+    std::vector<int> merged;           // join indices in launch order (largest K first)
+    int mW1 = 0, mK = 0, mthreads = 0;
+    VerifySeg *segs_dev = nullptr;
+    unsigned long long *mqueue = nullptr;
+    unsigned int *mtickets = nullptr;
 };
 
 namespace {
@@ -876,6 +891,9 @@ void batch_free(ej_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->segs_dev) cudaFree(b->segs_dev);
+    if (b->mqueue) cudaFree(b->mqueue);
+    if (b->mtickets) cudaFree(b->mtickets);
     for (auto &j : b->joins) {
         if (j.done) cudaEventDestroy(j.done);
         if (j.verified) cudaEventDestroy(j.verified);
@@ -945,6 +963,70 @@ void batch_sources(std::vector<BatchJoin> &joins) {
 const ej_schedule kTuneSet[] = {
     {1, 16, 1, 4, 0}, {1, 16, 2, 4, 0}, {1, 16, 1, 3, 0}, {1, 16, 1, 1, 0}, {2, 0, 0, 3, 0}, {2, 0, 0, 4, 0},
 };
+
+// Merged verification (ej_schedule.chain 0 or 3): the joins that use the
+// persistent verifier are verified by one launch at the widest of their bands,
+// each pair with its own join's K, largest K first. The work queue then runs
+// from one join's candidates into the next, so no launch waits for another
+// launch's last pairs. Mode 0 merges when the wider band adds at most half of
+// the word-columns the joins' own bands would run (estimated from the eager
+// pass's candidate counts); otherwise, as mode 2, the launches are chained.
+int batch_plan_merge(ej_batch *b) {
+    ej_ctx *ctx = b->ctx;
+    const int mode = ctx->sched.chain;
+    if (mode == 1 || mode == 2) return EJ_OK;
+    std::vector<int> pq;
+    for (size_t i = 0; i < b->joins.size(); i++) {
+        BatchJoin &j = b->joins[i];
+        if (pq_choice(j.sub, j.pl, &j.p, j.bs.vc) > 0) pq.push_back((int)i);
+    }
+    if (pq.size() < 2) return EJ_OK;
+    std::stable_sort(pq.begin(), pq.end(), [&](int x, int y) { return b->joins[(size_t)x].p.K > b->joins[(size_t)y].p.K; });
+    if (pq.size() > (size_t)MAX_VERIFY_SEGS) pq.resize(MAX_VERIFY_SEGS);
+    int W1 = 0, K = 0;
+    double own = 0.0, wide = 0.0;
+    for (int i : pq) {
+        const BatchJoin &j = b->joins[(size_t)i];
+        W1 = std::max(W1, j.bs.vc.V);
+        K = std::max(K, (int)j.p.K);
+    }
+    for (int i : pq) {
+        const BatchJoin &j = b->joins[(size_t)i];
+        own += (double)j.ncand * j.bs.vc.V;
+        wide += (double)j.ncand * W1;
+    }
+    if (mode == 0 && wide > 1.5 * own) return EJ_OK;
+    const int threads = pq_threads_for(W1, b->joins[0].p.alphabet_size);
+    if (threads == 0 || W1 < (2 * K + 1 + 63) / 64 + 1) return EJ_OK;
+    CK(cudaMalloc(&b->segs_dev, pq.size() * sizeof(VerifySeg)));
+    CK(cudaMalloc(&b->mqueue, sizeof(unsigned long long)));
+    CK(cudaMalloc(&b->mtickets, SM_TICKETS * sizeof(unsigned int)));
+    b->merged = pq;
+    b->mW1 = W1;
+    b->mK = K;
+    b->mthreads = threads;
+    for (size_t k = 0; k < pq.size(); k++) b->joins[(size_t)pq[k]].seg = (int)k;
+    return EJ_OK;
+}
+
+// The merged launch on stream s (after every merged join's candidates).
+int batch_merged_verify(ej_batch *b, cudaStream_t s) {
+    ej_ctx *ctx = b->ctx;
+    CK(cudaMemsetAsync(b->mqueue, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(b->mtickets, 0, SM_TICKETS * sizeof(unsigned int), s));
+    uint64_t total_cap = 0;
+    for (int i : b->merged) total_cap += b->joins[(size_t)i].cap;
+    VerifyOut vo{};
+    vo.queue = b->mqueue;
+    vo.sm_tickets = b->mtickets;
+    vo.segs = b->segs_dev;
+    vo.nseg = (int32_t)b->merged.size();
+    const Plan &pl = b->pl;
+    CK(launch_verify_pq(b->mW1, b->mthreads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
+                        ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1, pl.packed, pl.pofs,
+                        pl.B, pl.lens, pl.st.n, b->joins[0].p.alphabet_size, nullptr, (int64_t)total_cap, b->mK, vo, s));
+    return EJ_OK;
+}
 
 int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
     ej_ctx *ctx = j.sub;
@@ -1105,7 +1187,7 @@ int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
     }
     if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
         sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 4 ||
-        sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 2)
+        sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 3)
         return fail(ctx, EJ_ERR_INVALID_ARG,
                     "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",
                     sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order, sc->buckets);
@@ -1391,6 +1473,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
             if (attempt > 2) return bail(fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts"));
             cap = hc[0] + hc[0] / 4 + 1024;
         }
+        j.ncand = hc[2];
         j.cap = cap + cap / 8 + 1024;
         if ((st = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s)) != EJ_OK) return bail(st);
         if (flags & EJ_BATCH_AUTOTUNE) {
@@ -1399,6 +1482,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager pass failed"));
     }
+    if ((st = batch_plan_merge(b)) != EJ_OK) return bail(st);
     // capture: plan (validate, pack) on the caller's stream, then every join on
     // its own stream, joined back at the end
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
@@ -1421,14 +1505,26 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
     // slightly faster to 10x slower from one replay to the next; every other stage
     // overlaps
     cudaEvent_t prev_verify = nullptr;
+    std::vector<VerifySeg> segs_h(b->merged.size());
     for (auto &j : b->joins) {
         if (cst != EJ_OK) break;
-        const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
-        const bool heavy = pt > 0 && j.sub->sched.chain != 1;
-        cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
-        if (heavy) prev_verify = j.verified;
+        if (j.seg >= 0) {
+            // verified by the merged launch below
+            cst = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, j.side);
+            if (cst == EJ_OK)
+                cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &segs_h[(size_t)j.seg]);
+        } else {
+            const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
+            const bool heavy = pt > 0 && ctx->sched.chain != 1;
+            cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
+            if (heavy) prev_verify = j.verified;
+        }
         if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
         if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+    }
+    if (cst == EJ_OK && !b->merged.empty()) {
+        if (prev_verify && cudaStreamWaitEvent(s, prev_verify, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+        if (cst == EJ_OK) cst = batch_merged_verify(b, s);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &g);
@@ -1438,6 +1534,9 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return bail(cst != EJ_OK ? cst : fail(ctx, EJ_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
     }
     b->graph = g;
+    if (!b->merged.empty() && cudaMemcpy(b->segs_dev, segs_h.data(), segs_h.size() * sizeof(VerifySeg),
+                                         cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_CUDA, "merged verifier table upload failed"));
     if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "graph instantiation failed"));
     size_t nn = 0;

@@ -282,6 +282,21 @@ cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, 
 // app[0 .. app_cap) with *app_count counting them (order unspecified).
 // np_dev (optional) holds the number of pairs on the device; the host-side
 // np is then only an upper bound used to size the grid.
+// One join's share of a merged persistent-verifier launch: its candidates
+// (count on the device, at most cap), its threshold and its outputs.
+struct VerifySeg {
+    const uint64_t *pairs;
+    const unsigned long long *np_dev;
+    uint64_t cap;
+    int32_t K;
+    uint64_t *app;
+    unsigned long long *app_count;
+    uint64_t app_cap;
+    unsigned long long *work;   // [0] band cells, [1] word columns (at this join's band)
+    uint32_t *err;
+};
+constexpr int MAX_VERIFY_SEGS = 8;
+
 struct VerifyOut {
     uint8_t *flags;
     uint64_t *app;
@@ -302,6 +317,12 @@ struct VerifyOut {
     int64_t n_b;
     const int32_t *thr;
     const unsigned long long *pairs_off_dev;   // when set, the pairs start this many entries in (device value)
+    // Merged launch (persistent verifier, self-joins): when segs is set, the
+    // queue runs over the nseg joins' candidates one join after another, each
+    // pair decided with its join's K (at most the band's) and written to its
+    // join's outputs; pairs, np, app*, work and err above are not used.
+    const VerifySeg *segs;
+    int32_t nseg;
 };
 
 constexpr int SM_TICKETS = 1024;

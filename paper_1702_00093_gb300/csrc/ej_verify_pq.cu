@@ -66,11 +66,43 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                  const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t nsm, int32_t spw_force,
                  int32_t wps, VerifyOut vo) {
     uint32_t *__restrict__ err = vo.err;
-    if (vo.np_dev) {
-        const int64_t dn = (int64_t)*vo.np_dev;
-        np = dn < np ? dn : np;
+    const VerifySeg *__restrict__ segs = vo.segs;   // merged launch: the joins' candidates in turn
+    const int nseg = segs ? vo.nseg : 0;
+    __shared__ long long s_cum[MAX_VERIFY_SEGS + 1];
+    if (segs) {
+        if (threadIdx.x == 0) {
+            long long acc = 0;
+            for (int g = 0; g < nseg; g++) {
+                s_cum[g] = acc;
+                const long long c = (long long)*segs[g].np_dev;
+                acc += c < (long long)segs[g].cap ? c : (long long)segs[g].cap;
+            }
+            s_cum[nseg] = acc;
+        }
+    } else {
+        if (vo.np_dev) {
+            const int64_t dn = (int64_t)*vo.np_dev;
+            np = dn < np ? dn : np;
+        }
+        if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
     }
-    if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
+    // error bits of one pair (its join's word in a merged launch), or of the warp
+    auto pair_err = [&](int g, uint32_t bits) { atomicOr(segs ? segs[g].err : err, bits); };
+    auto warp_err = [&](uint32_t bits) {
+        if (!segs) atomicOr(err, bits);
+        else
+            for (int g = 0; g < nseg; g++) atomicOr(segs[g].err, bits);
+    };
+    // a finished pair's result: to its join's outputs in a merged launch
+    auto emit = [&](int g, int64_t q, bool pass) {
+        if (!segs) {
+            emit_result(vo, q, pairs, pass);
+        } else if (pass) {
+            const VerifySeg &sg_ = segs[g];
+            const unsigned long long idx = atomicAdd(sg_.app_count, 1ull);
+            if (idx < sg_.app_cap) sg_.app[idx] = sg_.pairs[q];
+        }
+    };
     constexpr int R = W1 + 1;
     constexpr int R2 = 2 * R;                // ring slots per symbol: every word is kept twice,
                                              // at slot k mod R and k mod R + R, so that the
@@ -91,6 +123,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         s_nmin[t] = (int8_t)mn;
     }
     __syncthreads();
+    if (segs) np = s_cum[nseg];
     constexpr int T_ = TPB;                   // slot stride of the per-thread ring
     uint64_t *ring = smem + threadIdx.x;      // (c*R2 + slot)*T_, reused as a dump area
     const int lane = threadIdx.x & 31;
@@ -122,6 +155,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     int64_t ywords = 0;
     int32_t m = 0, n = 0, ncols = 0, Tacc = 0, jbase = 1, next_move = 0, rej_col = 0;
     int32_t kp = K;          // the pair's threshold (<= K, the band)
+    int sg = 0;              // the pair's join (merged launch)
     int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
     int64_t iters = 0;       // loop passes of this warp (bounded, see kMaxIters)
     int base = 0;
@@ -137,7 +171,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
 
     while (true) {
         if (++iters > kMaxIters) {
-            if (lane == 0) atomicOr(err, (uint32_t)DERR_GUARD);
+            if (lane == 0) warp_err((uint32_t)DERR_GUARD);
             break;
         }
         // refill free slots (both lanes of a slot agree on `have` and `exhausted`)
@@ -156,11 +190,18 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                     exhausted = true;
                 } else {
                     p = idx;
-                    const uint64_t pr = pairs[p];
+                    const uint64_t *pp = pairs;
+                    if (segs) {
+                        sg = 0;
+                        while (sg + 1 < nseg && idx >= s_cum[sg + 1]) sg++;
+                        p = idx - s_cum[sg];
+                        pp = segs[sg].pairs;
+                    }
+                    const uint64_t pr = pp[p];
                     const int64_t a = (int64_t)(pr >> 32), b = (int64_t)(pr & 0xFFFFFFFFull);
                     const bool two = vo.packed_b != nullptr;   // b indexes the second set
                     if (a >= n_str || b >= (two ? vo.n_b : n_str)) {
-                        if (!rev) atomicOr(err, (uint32_t)DERR_PAIR);
+                        if (!rev) pair_err(sg, (uint32_t)DERR_PAIR);
                     } else {
                         const int32_t la = lens[a], lb = two ? vo.lens_b[b] : lens[b];
                         const uint4 *pa = packed + pofs[a];
@@ -168,10 +209,13 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                         const bool a_long = la >= lb;
                         m = a_long ? la : lb;
                         n = a_long ? lb : la;
-                        kp = vo.thr ? vo.thr[a] : K;
-                        if (!rev) loc_cells += band_cells(m, n, kp);
+                        kp = segs ? segs[sg].K : (vo.thr ? vo.thr[a] : K);
+                        if (!rev) {
+                            if (segs) atomicAdd(&segs[sg].work[0], band_cells(m, n, kp));
+                            else loc_cells += band_cells(m, n, kp);
+                        }
                         if (m - n > kp || n == 0) {
-                            if (!rev) emit_result(vo, p, pairs, n == 0 && m <= kp);
+                            if (!rev) emit(sg, p, n == 0 && m <= kp);
                         } else {
                             const int32_t n1 = n / 2;
                             ncols = rev ? n - n1 : n1;
@@ -294,7 +338,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         jbase += 64;
         if (have && --budget < 0 && !rejected && jbase <= ncols) {
             // cannot happen for a consistent state: stop this pair and report it
-            atomicOr(err, (uint32_t)DERR_GUARD);
+            pair_err(sg, (uint32_t)DERR_GUARD);
             rejected = true;
             rej_col = jbase;
         }
@@ -308,7 +352,9 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         if (__any_sync(FULL, pair_done)) {
             const int32_t T = Tacc + (rejected ? rej_col - 1 : ncols);
             if (pair_done) {
-                loc_cols += (unsigned long long)(rejected ? rej_col - 1 : ncols) * (unsigned long long)w_min;
+                const unsigned long long cols = (unsigned long long)(rejected ? rej_col - 1 : ncols);
+                if (segs) atomicAdd(&segs[sg].work[1], cols * (unsigned long long)((2 * kp + 1 + 63) / 64));
+                else loc_cols += cols * (unsigned long long)w_min;
 #pragma unroll
                 for (int v = 0; v < W1; v++) {
                     ring[(size_t)(2 * v) * T_] = Pv[v];
@@ -361,7 +407,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                         pass = best <= kp;
                     }
                 }
-                emit_result(vo, p, pairs, pass);
+                emit(sg, p, pass);
             }
             __syncwarp();
             if (pair_done) have = false;

@@ -100,6 +100,33 @@ def test_batch_shares_walks_across_parameter_sets(ej, ctx, stream):
     assert np.array_equal(outs[0], ref.pairs)
 
 
+@pytest.mark.parametrize("chain", [0, 1, 2, 3])
+def test_batch_persistent_verifiers_merged_chained_or_overlapping(ej, stream, chain):
+    """Joins on the persistent verifier with different bands (W1 = 2, 3, 5):
+    verified by one merged launch at the widest band (chain 3), one launch per
+    join in turn (2) or overlapping (1); every join returns ej_join's pairs and
+    counts its band cells at its own K."""
+    c = ej.Context(0)
+    try:
+        c.set_schedule(mode=1, chain=chain)
+        ss = synth.small_dna(0.5)
+        s = ej.Strings.from_set(ss, DEV)
+        params = _params(ej, ss, [4, 40, 100, 20], lambda K: dict(r=3, m=10, z=12, seed=1))
+        with torch.cuda.stream(stream):
+            b = c.batch(s, params, stream=stream)
+            for rep in range(2):
+                b.run(stream)
+                for i, p in enumerate(params):
+                    got, st = b.result(i, device=DEV, stream=stream)
+                    want, st_j = c.join(s, p, device=DEV, stream=stream)
+                    assert np.array_equal(_u64(got), _u64(want)), (chain, i)
+                    assert st.n_candidates == st_j.n_candidates
+                    assert st.band_cells == st_j.band_cells
+            b.close()
+    finally:
+        c.close()
+
+
 def test_batch_rerun_after_rewriting_strings(ej, ctx, stream):
     ss = synth.small_dna(0.5)
     s = ej.Strings.from_set(ss, DEV)
