@@ -11,11 +11,14 @@ HBM. --workload protein / text select the protein-like (n=200000, K=40,60) and
 text-like (n=350000, K=100,200,300) sets instead.
 
 The headline runs the step through ej_batch: the joins of a step captured once
-as a CUDA graph (each join on its own stream) and replayed every step, outputs
-read back sorted. Beside it the same step is timed through one ej_join call per
-K (whose per-stage events give the stage breakdown and the verify roofline) and
-through the plain per-stage calls ej_embed -> ej_sign -> ej_lsh_candidates ->
-ej_verify; all three must return the same pair sets.
+as a CUDA graph (each join on its own stream, one merged verifier launch over
+all joins' candidates) and replayed every step, outputs read back sorted; the
+roofline is that merged launch's, timed with CUDA events inside the batch.
+Beside it the same step is timed through one ej_join call per K (whose
+per-stage events give the stage breakdown and a per-launch verify roofline)
+and through the plain per-stage calls ej_embed -> ej_sign -> ej_lsh_candidates
+-> ej_verify; all three must return the same pair sets. --batch-eager issues
+the batch's work without a graph (the same work, for per-kernel profilers).
 
 Metric: candidate pairs verified per second of whole-step wall time (the
 "verified pairs/s" of the headline metric; join wall time and band cells/s are
@@ -48,10 +51,11 @@ METRIC = "verified pairs/s (candidate pairs verified per second of whole-join wa
 SMS, ALU_LANES_PER_SM, MAX_SM_MHZ = 152, 64, 2070.0
 INT_OPS_PER_WORD_COLUMN = 26   # 32-bit ops of one 64-bit word of the bit-parallel step
 VERIFY_SOURCE = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify_pq.cu")
-# DRAM bytes per verify launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the K=50/150/250 launches of one ncu capture of the long-DNA workload), valid
-# only while the verify source is the one that was captured
-VERIFY_TRAFFIC = {"source_sha256_prefix": "0435fac629cf7d59", "bytes_per_launch": 8663210}
+# DRAM bytes per verify launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the long-DNA workload: "merged" = the batch's merged launch,
+# "join" = mean over the K=50/150/250 launches of ej_join; valid only while the
+# verify source is the one that was captured
+VERIFY_TRAFFIC = {"source_sha256_prefix": "543eb403d5eb9127", "bytes_per_launch": {"merged": 11593472, "join": None}}
 
 
 def workloads():
@@ -76,11 +80,11 @@ def workloads():
     }
 
 
-def verify_traffic():
+def verify_traffic(kind):
     with open(VERIFY_SOURCE, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     if VERIFY_TRAFFIC["source_sha256_prefix"] and sha.startswith(VERIFY_TRAFFIC["source_sha256_prefix"]):
-        return VERIFY_TRAFFIC["bytes_per_launch"]
+        return VERIFY_TRAFFIC["bytes_per_launch"][kind]
     return None
 
 
@@ -100,6 +104,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-stage path")
     ap.add_argument("--autotune", action="store_true", help="autotune each join of the batch")
+    ap.add_argument("--batch-eager", action="store_true",
+                    help="issue the batch's work without a CUDA graph (same work; for per-kernel profilers)")
     ap.add_argument("--paths", type=str, default="batch,join,plain",
                     help="paths to time (batch = the graph-captured headline; without it the ej_join path heads "
                          "the line, e.g. for profilers that do not follow stream capture)")
@@ -387,18 +393,20 @@ def main():
         paths = set(args.paths.split(","))
         use_batch = "batch" in paths
         batch_ms, cand_step, launches_step, result_pairs, e2e = None, 0, 0, None, None
+        merged_ms, merged_word_cols, eager_ms, same_eager = [], 0, None, None
         if use_batch:
             # ---- headline: all joins of the step as one CUDA graph -------------------
-            batch = ctx.batch(strings, params, autotune=args.autotune, stream=stream)
+            batch = ctx.batch(strings, params, autotune=args.autotune, stream=stream, eager=args.batch_eager)
             outs = [torch.empty(1 << 16, dtype=torch.int64, device=dev) for _ in params]
             bstats = {}
 
-            def batch_step():
-                batch.run(stream)
+            def batch_step(b=None):
+                b = b or batch
+                b.run(stream)
                 for i in range(len(params)):
                     while True:
                         try:
-                            bstats[i] = batch.result_into(i, outs[i], stream)
+                            bstats[i] = b.result_into(i, outs[i], stream)
                             break
                         except ej.EJError as e:
                             if getattr(e, "needed", None) is None:
@@ -443,6 +451,27 @@ def main():
                        "d2h_bytes_per_step": int(d2h / args.e2e_steps), "steps": args.e2e_steps,
                        "ms_per_step": 1e3 * h_t / args.e2e_steps, "api": "ej_batch_run + ej_batch_result, host buffers"}
             batch.close()   # its scratch is not needed by the other paths
+
+            # ---- the same batch issued without a graph: times the merged verifier ----
+            # launch with CUDA events on its stream (a graph replay cannot be timed
+            # per kernel), for the roofline of the step's dominant kernel
+            if not args.batch_eager:
+                eb = ctx.batch(strings, params, autotune=args.autotune, stream=stream, eager=True)
+
+                def eager_step():
+                    batch_step(eb)
+                    try:
+                        merged_ms.append(eb.verify_ms())
+                    except ej.EJError:
+                        pass
+
+                for _ in range(warm):
+                    eager_step()
+                merged_ms.clear()
+                eager_ms = timed(eager_step, args.steps, clk)
+                merged_word_cols = sum(st.verify_word_columns for _, st in bstats.values())
+                same_eager = all(torch.equal(outs[i][:bstats[i][0]], result_pairs[i]) for i in range(len(params)))
+                eb.close()
 
         # ---- the same step through ej_join (stage timings, verify roofline) --------
         ctx.set_timing(True)
@@ -540,6 +569,26 @@ def main():
             "band_cells": rows[0]["band_cells"],
         }
     cells_step = sum(v["band_cells"] for v in per_k.values())
+    join_roofline = {"kernel": "verify_pq_kernel (one launch per join)", "bound": "alu",
+                     "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",
+                     "frac": ach_ops / peak_ops, "traffic": verify_traffic("join"),
+                     "launches": n_verify, "avg_launch_ms": verify_ms / max(n_verify, 1),
+                     "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": word_cols,
+                     "measured_in": "the ej_join pass (CUDA events around each verify launch, its stream)",
+                     "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"}
+    roofline = join_roofline
+    if merged_ms:
+        m_ms = statistics.mean(merged_ms)
+        m_ops = merged_word_cols * INT_OPS_PER_WORD_COLUMN / (m_ms / 1e3)
+        roofline = {"kernel": "verify_pq_kernel (the batch's merged launch over all joins' candidates)",
+                    "bound": "alu", "achieved": m_ops / 1e12, "peak": peak_ops / 1e12,
+                    "unit": "Tops/s (32-bit integer ops)", "frac": m_ops / peak_ops,
+                    "traffic": verify_traffic("merged"), "launches": len(merged_ms), "avg_launch_ms": m_ms,
+                    "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": merged_word_cols,
+                    "word_columns_basis": "columns advanced x 64-bit words of each join's own band",
+                    "measured_in": "the batch issued without a graph (same kernels), timed steps: CUDA events "
+                                   "around the merged launch, on its stream",
+                    "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"}
 
     if rank == 0:
         line = {
@@ -561,14 +610,13 @@ def main():
                 "value": cand_plain * args.plain_steps / (plain_ms / 1e3), "ms_per_step": plain_ms / args.plain_steps,
                 "steps": args.plain_steps, "api": "ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify per K",
                 "identical_output": bool(same_plain)},
+            "eager_batch_path": None if eager_ms is None else {
+                "ms_per_step": eager_ms / args.steps, "value": cand_step * args.steps / (eager_ms / 1e3),
+                "api": "ej_batch with EJ_BATCH_EAGER (the same work issued every step without a graph)",
+                "identical_output": bool(same_eager)},
             "per_K": per_k,
-            "roofline": {"kernel": "verify_pq_kernel", "bound": "alu", "achieved": ach_ops / 1e12,
-                         "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",
-                         "frac": ach_ops / peak_ops, "traffic": verify_traffic(),
-                         "launches": n_verify, "avg_launch_ms": verify_ms / max(n_verify, 1),
-                         "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": word_cols,
-                         "measured_in": "the ej_join pass (CUDA events around each verify launch, its stream)",
-                         "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"},
+            "roofline": roofline,
+            "join_path_roofline": join_roofline,
             "clocks": clocks,
             "gpu_launches": int(launches_step * args.steps),
             "e2e": e2e,

@@ -259,6 +259,10 @@ void ej_server_destroy(ej_server *server);
  */
 typedef struct ej_batch ej_batch;
 #define EJ_BATCH_AUTOTUNE 1
+/* EJ_BATCH_EAGER: no graph; every ej_batch_run issues the same device work on
+ * its stream (for tools that cannot follow graph launches, e.g. per-kernel
+ * profilers). ej_batch_create then also runs the batch once. */
+#define EJ_BATCH_EAGER 2
 int ej_batch_create(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, int32_t n_params,
                     int32_t flags, ej_batch **batch, void *stream);
 int ej_batch_run(ej_batch *batch, void *stream);
@@ -266,6 +270,10 @@ int ej_batch_result(ej_batch *batch, int32_t index, uint64_t *out, int64_t capac
                     ej_join_stats *stats, void *stream);
 /* Kernel launches one ej_batch_run makes (kernel nodes of the graph). */
 int64_t ej_batch_kernel_count(const ej_batch *batch);
+/* Device time (ms, CUDA events on its stream) of the merged verifier launch in
+ * the last run of an EJ_BATCH_EAGER batch (see ej_schedule.chain); waits for it.
+ * EJ_ERR_INVALID_ARG if the batch is a graph, has no merged launch or has not run. */
+int ej_batch_verify_ms(ej_batch *batch, float *ms);
 void ej_batch_destroy(ej_batch *batch);
 
 /*

@@ -753,6 +753,18 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     return EJ_OK;
 }
 
+// This join's share of a merged verifier launch: the buffers back_attempt
+// with capacity cap uses (already sized; nothing is launched).
+int back_segment(ej_ctx *ctx, const ej_params *p, uint64_t cap, VerifySeg *seg) {
+    unsigned long long *cnt = nullptr;
+    uint64_t *cand = nullptr, *app = nullptr;
+    CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
+    CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
+    CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
+    *seg = VerifySeg{cand, cnt + 2, cap, p->K, app, cnt + 3, cap, cnt + 4, (uint32_t *)ctx->bufs[B_DERR].p};
+    return EJ_OK;
+}
+
 // Counters of the last attempt: [0] raw, [1] max bucket, [2] candidates,
 // [3] output, [4] band cells, [5] word columns, [6] device error bits.
 int back_read(ej_ctx *ctx, unsigned long long hc[8], cudaStream_t s) {
@@ -882,6 +894,8 @@ struct ej_batch {
     VerifySeg *segs_dev = nullptr;
     unsigned long long *mqueue = nullptr;
     unsigned int *mtickets = nullptr;
+    cudaEvent_t v0 = nullptr, v1 = nullptr;   // around the merged launch
+    bool eager = false;                       // no graph: every run issues the work
 };
 
 namespace {
@@ -891,6 +905,8 @@ void batch_free(ej_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->v0) cudaEventDestroy(b->v0);
+    if (b->v1) cudaEventDestroy(b->v1);
     if (b->segs_dev) cudaFree(b->segs_dev);
     if (b->mqueue) cudaFree(b->mqueue);
     if (b->mtickets) cudaFree(b->mtickets);
@@ -1026,6 +1042,54 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
                         ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1, pl.packed, pl.pofs,
                         pl.B, pl.lens, pl.st.n, b->joins[0].p.alphabet_size, nullptr, (int64_t)total_cap, b->mK, vo, s));
     return EJ_OK;
+}
+
+// The batch's device work on stream s (captured once into the graph, or issued
+// by every run of an eager batch): plan (validate, pack) on s, then every join
+// on its own stream, joined back into s at the end.
+int batch_issue(ej_batch *b, cudaStream_t s) {
+    ej_ctx *ctx = b->ctx;
+    int cst = plan_device(ctx, b->pl, s);
+    if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    // keys: the self-walking joins first, then the derived ones after their source
+    for (int pass = 0; pass < 2 && cst == EJ_OK; pass++)
+        for (auto &j : b->joins) {
+            if (cst != EJ_OK || (pass == 0) != (j.src < 0)) continue;
+            cudaEvent_t after = j.src < 0 ? b->fork : b->joins[(size_t)j.src].keyed;
+            if (cudaStreamWaitEvent(j.side, after, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
+            cst = batch_join_keys(b->joins, j, j.side);
+            if (cst == EJ_OK && cudaEventRecord(j.keyed, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
+        }
+    // persistent verifiers run one after another unless chain == 1: two persistent
+    // grids sharing the SMs (each capping its working warps per SM) measured from
+    // slightly faster to 10x slower from one replay to the next; every other stage
+    // overlaps
+    cudaEvent_t prev_verify = nullptr;
+    VerifySeg unused{};
+    for (auto &j : b->joins) {
+        if (cst != EJ_OK) break;
+        if (j.seg >= 0) {
+            // verified by the merged launch below
+            cst = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, j.side);
+            if (cst == EJ_OK)
+                cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &unused);
+        } else {
+            const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
+            const bool heavy = pt > 0 && ctx->sched.chain != 1;
+            cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
+            if (heavy) prev_verify = j.verified;
+        }
+        if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
+        if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+    }
+    if (cst == EJ_OK && !b->merged.empty()) {
+        if (prev_verify && cudaStreamWaitEvent(s, prev_verify, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+        // timed in eager batches (under capture a record is only an ordering edge)
+        if (cst == EJ_OK && b->eager && cudaEventRecord(b->v0, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+        if (cst == EJ_OK) cst = batch_merged_verify(b, s);
+        if (cst == EJ_OK && b->eager && cudaEventRecord(b->v1, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    }
+    return cst;
 }
 
 int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
@@ -1408,7 +1472,8 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
     *out = nullptr;
     if (!S || !params || n_params < 1 || n_params > 64)
         return fail(ctx, EJ_ERR_INVALID_ARG, "a batch needs strings and 1..64 parameter sets");
-    if ((flags & ~EJ_BATCH_AUTOTUNE) != 0) return fail(ctx, EJ_ERR_INVALID_ARG, "unknown batch flags %d", flags);
+    if ((flags & ~(EJ_BATCH_AUTOTUNE | EJ_BATCH_EAGER)) != 0)
+        return fail(ctx, EJ_ERR_INVALID_ARG, "unknown batch flags %d", flags);
     if (S->n < 2 || !is_device_ptr(S->bytes) || !is_device_ptr(S->offsets))
         return fail(ctx, EJ_ERR_INVALID_ARG, "a batch needs n >= 2 strings in device memory");
     if (ctx->pi.size() || ctx->posinj.size())
@@ -1483,49 +1548,35 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager pass failed"));
     }
     if ((st = batch_plan_merge(b)) != EJ_OK) return bail(st);
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->v0) != cudaSuccess || cudaEventCreate(&b->v1) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));
+    if (!b->merged.empty()) {
+        std::vector<VerifySeg> segs_h(b->merged.size());
+        for (auto &j : b->joins)
+            if (j.seg >= 0 && (st = back_segment(j.sub, &j.p, j.cap, &segs_h[(size_t)j.seg])) != EJ_OK) return bail(st);
+        if (cudaMemcpy(b->segs_dev, segs_h.data(), segs_h.size() * sizeof(VerifySeg), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(fail(ctx, EJ_ERR_CUDA, "merged verifier table upload failed"));
+    }
+    if (flags & EJ_BATCH_EAGER) {
+        // no graph: every run issues the same work; one run here checks it and
+        // counts its kernels
+        b->eager = true;
+        const int64_t l0 = launches_so_far();
+        if ((st = batch_issue(b, s)) != EJ_OK) return bail(st);
+        b->kernel_nodes = launches_so_far() - l0;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager batch run failed"));
+        b->ran = true;
+        ctx->timing = timing_was;
+        *out = b;
+        return EJ_OK;
+    }
     // capture: plan (validate, pack) on the caller's stream, then every join on
     // its own stream, joined back at the end
-    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
-        return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "stream capture could not start (the stream must not be the legacy default stream)"));
-    int cst = plan_device(ctx, b->pl, s);
-    if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
-    // keys: the self-walking joins first, then the derived ones after their source
-    for (int pass = 0; pass < 2 && cst == EJ_OK; pass++)
-        for (auto &j : b->joins) {
-            if (cst != EJ_OK || (pass == 0) != (j.src < 0)) continue;
-            cudaEvent_t after = j.src < 0 ? b->fork : b->joins[(size_t)j.src].keyed;
-            if (cudaStreamWaitEvent(j.side, after, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
-            cst = batch_join_keys(b->joins, j, j.side);
-            if (cst == EJ_OK && cudaEventRecord(j.keyed, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
-        }
-    // persistent verifiers run one after another unless chain == 1: two persistent
-    // grids sharing the SMs (each capping its working warps per SM) measured from
-    // slightly faster to 10x slower from one replay to the next; every other stage
-    // overlaps
-    cudaEvent_t prev_verify = nullptr;
-    std::vector<VerifySeg> segs_h(b->merged.size());
-    for (auto &j : b->joins) {
-        if (cst != EJ_OK) break;
-        if (j.seg >= 0) {
-            // verified by the merged launch below
-            cst = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, j.side);
-            if (cst == EJ_OK)
-                cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &segs_h[(size_t)j.seg]);
-        } else {
-            const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
-            const bool heavy = pt > 0 && ctx->sched.chain != 1;
-            cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
-            if (heavy) prev_verify = j.verified;
-        }
-        if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
-        if (cst == EJ_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
-    }
-    if (cst == EJ_OK && !b->merged.empty()) {
-        if (prev_verify && cudaStreamWaitEvent(s, prev_verify, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
-        if (cst == EJ_OK) cst = batch_merged_verify(b, s);
-    }
+    const int cst = batch_issue(b, s);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (cst != EJ_OK || ce != cudaSuccess || !g) {
@@ -1534,9 +1585,6 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return bail(cst != EJ_OK ? cst : fail(ctx, EJ_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
     }
     b->graph = g;
-    if (!b->merged.empty() && cudaMemcpy(b->segs_dev, segs_h.data(), segs_h.size() * sizeof(VerifySeg),
-                                         cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(ctx, EJ_ERR_CUDA, "merged verifier table upload failed"));
     if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "graph instantiation failed"));
     size_t nn = 0;
@@ -1553,10 +1601,26 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
 }
 
 int ej_batch_run(ej_batch *b, void *stream) {
-    if (!b || !b->exec) return EJ_ERR_INVALID_ARG;
+    if (!b || (!b->exec && !b->eager)) return EJ_ERR_INVALID_ARG;
     cudaSetDevice(b->ctx->device);
-    CKB(b, cudaGraphLaunch(b->exec, as_stream(stream)));
+    if (b->eager) {
+        const int st = batch_issue(b, as_stream(stream));
+        if (st != EJ_OK) return st;
+    } else {
+        CKB(b, cudaGraphLaunch(b->exec, as_stream(stream)));
+    }
     b->ran = true;
+    return EJ_OK;
+}
+
+int ej_batch_verify_ms(ej_batch *b, float *ms) {
+    if (!b || !ms) return EJ_ERR_INVALID_ARG;
+    *ms = 0.f;
+    if (b->merged.empty() || !b->ran || !b->eager)
+        return fail(b->ctx, EJ_ERR_INVALID_ARG, "no merged verifier launch of an eager batch has run");
+    cudaSetDevice(b->ctx->device);
+    CKB(b, cudaEventSynchronize(b->v1));
+    CKB(b, cudaEventElapsedTime(ms, b->v0, b->v1));
     return EJ_OK;
 }
 

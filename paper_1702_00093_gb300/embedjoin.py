@@ -30,6 +30,7 @@ EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
             "ej_set_schedule", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_batch_verify_ms",
             "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
             "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
             "ej_server_reset_stats", "ej_server_destroy"]
@@ -148,6 +149,8 @@ def lib():
         L.ej_batch_run.restype = C.c_int
         L.ej_batch_result.argtypes = [vp, C.c_int32, vp, i64, C.POINTER(i64), C.POINTER(JoinStats), vp]
         L.ej_batch_result.restype = C.c_int
+        L.ej_batch_verify_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        L.ej_batch_verify_ms.restype = C.c_int
         L.ej_batch_kernel_count.argtypes = [vp]
         L.ej_batch_kernel_count.restype = i64
         L.ej_batch_destroy.argtypes = [vp]
@@ -328,10 +331,11 @@ class Context:
                                     _ptr(out), C.byref(n), _stream(stream)), "ej_verify")
         return n.value
 
-    def batch(self, s: Strings, params: list, autotune: bool = False, stream=None) -> "Batch":
+    def batch(self, s: Strings, params: list, autotune: bool = False, stream=None, eager: bool = False) -> "Batch":
         """ej_batch_create: all joins of `params` over device strings `s` as one CUDA
-        graph (see Batch). `stream` must not be the legacy default stream."""
-        return Batch(self, s, params, autotune, stream)
+        graph (see Batch), or issued anew by every run when `eager`. `stream` must
+        not be the legacy default stream."""
+        return Batch(self, s, params, autotune, stream, eager)
 
     def join_into(self, s: Strings, p: Params, out, stream=None) -> tuple[int, JoinStats]:
         """ej_join into a caller buffer. Raises EJError with .needed on overflow."""
@@ -412,6 +416,7 @@ def decode_embedding(emb_words: np.ndarray, walk_end: np.ndarray, r: int, n: int
 
 
 EJ_BATCH_AUTOTUNE = 1
+EJ_BATCH_EAGER = 2
 
 
 class Batch:
@@ -419,7 +424,8 @@ class Batch:
     captured once as a CUDA graph. run() replays it (no host sync); result(i)
     waits and returns join i's sorted pairs, as ej_join would."""
 
-    def __init__(self, ctx: Context, s: Strings, params: list, autotune: bool = False, stream=None):
+    def __init__(self, ctx: Context, s: Strings, params: list, autotune: bool = False, stream=None,
+                 eager: bool = False):
         self._ctx = ctx
         self._h = C.c_void_p()
         self._keep = [s, params]
@@ -427,14 +433,20 @@ class Batch:
         cps = [p._c() for p in params]
         arr = (_Params * len(params))(*[cp for cp, _ in cps])
         self._keep.append(cps)
-        st = lib().ej_batch_create(ctx._h, C.byref(cs), arr, len(params), EJ_BATCH_AUTOTUNE if autotune else 0,
-                                   C.byref(self._h), _stream(stream))
+        flags = (EJ_BATCH_AUTOTUNE if autotune else 0) | (EJ_BATCH_EAGER if eager else 0)
+        st = lib().ej_batch_create(ctx._h, C.byref(cs), arr, len(params), flags, C.byref(self._h), _stream(stream))
         ctx._check(st, "ej_batch_create")
         self.n = len(params)
         self.kernel_count = int(lib().ej_batch_kernel_count(self._h))
 
     def run(self, stream=None):
         self._ctx._check(lib().ej_batch_run(self._h, _stream(stream)), "ej_batch_run")
+
+    def verify_ms(self) -> float:
+        """Device time of the merged verifier launch in the last run (ms)."""
+        ms = C.c_float(0.0)
+        self._ctx._check(lib().ej_batch_verify_ms(self._h, C.byref(ms)), "ej_batch_verify_ms")
+        return float(ms.value)
 
     def result_into(self, i: int, out, stream=None) -> tuple[int, JoinStats]:
         n = C.c_int64(0)

@@ -122,6 +122,22 @@ def test_batch_persistent_verifiers_merged_chained_or_overlapping(ej, stream, ch
                     assert np.array_equal(_u64(got), _u64(want)), (chain, i)
                     assert st.n_candidates == st_j.n_candidates
                     assert st.band_cells == st_j.band_cells
+            with pytest.raises(ej.EJError):   # timed only without a graph
+                b.verify_ms()
+            # the same work issued without a graph
+            e = c.batch(s, params, stream=stream, eager=True)
+            assert e.kernel_count == b.kernel_count
+            e.run(stream)
+            for i, p in enumerate(params):
+                got, _ = e.result(i, device=DEV, stream=stream)
+                want, _ = b.result(i, device=DEV, stream=stream)
+                assert np.array_equal(_u64(got), _u64(want)), (chain, i)
+            if chain == 3:
+                assert e.verify_ms() > 0
+            elif chain in (1, 2):
+                with pytest.raises(ej.EJError):
+                    e.verify_ms()
+            e.close()
             b.close()
     finally:
         c.close()
