@@ -249,7 +249,7 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     CKS(ensure_t(ctx, B_PACKED, (size_t)chunk_bound, &packed));
     CK(launch_chunk_counts(pl->lens, n, pl->B, ccnt, s));
     CK(exclusive_scan_u32(ccnt, pofs, n + 1, nullptr, stmp, s));
-    CK(launch_pack(pl->st.bytes, pl->st.offsets, pl->lens, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->B,
+    CK(launch_pack(pl->st.bytes, pl->st.offsets, pl->lens, n, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->B,
                    pofs, packed, derr, s));
     pl->packed = packed;
     pl->pofs = pofs;
@@ -298,8 +298,8 @@ int plan_device(ej_ctx *ctx, const Plan &pl, cudaStream_t s) {
     uint32_t *ccnt = (uint32_t *)ctx->bufs[B_CHUNK_CNT].p;
     CK(launch_chunk_counts(pl.lens, n, pl.B, ccnt, s));
     CK(exclusive_scan_u32(ccnt, (uint64_t *)pl.pofs, n + 1, nullptr, ctx->bufs[B_SCAN_TMP3].p, s));
-    CK(launch_pack(pl.st.bytes, pl.st.offsets, pl.lens, n, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.B, pl.pofs,
-                   (uint4 *)pl.packed, derr, s));
+    CK(launch_pack(pl.st.bytes, pl.st.offsets, pl.lens, n, pl.st.total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl.B,
+                   pl.pofs, (uint4 *)pl.packed, derr, s));
     return EJ_OK;
 }
 

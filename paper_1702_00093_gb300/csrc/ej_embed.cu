@@ -20,7 +20,7 @@ __global__ void validate_offsets_kernel(const int64_t *__restrict__ offsets, int
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t a = offsets[i], b = offsets[i + 1];
         int64_t len = b - a;
-        if (over || (i == 0 && a != 0) || len < 0 || len >= (1ll << 31)) {
+        if (over || (i == 0 && a != 0) || a < 0 || b > total_cap || len < 0 || len >= (1ll << 31)) {
             local_err |= DERR_OFFSETS;
             len = 0;
         }
@@ -84,71 +84,86 @@ __device__ __forceinline__ uint64_t spread_even(uint32_t v) {
 // the word of group g = gbase+u and the warp stores 32 words (256 bytes) at
 // once. 8-bit codes are stored byte for byte. Symbols past the end of a
 // string are written as 0 up to its chunk boundary.
+// One warp per string. With 2-bit codes a lane turns 16 consecutive bytes into
+// one 32-bit half of an output word (symbol s of the word at bits 2s, 2s+1); with
+// 8-bit codes 4 bytes into one 32-bit word. The bytes are read as aligned 32-bit
+// words (five cover any 16-byte window, two any 4-byte one) where those words lie
+// inside the byte array [bytes, bytes + total), else one by one; positions past
+// the string's end give code 0.
+__device__ __forceinline__ uint32_t pack_code(const uint8_t *s_map, uint32_t byte, bool &bad) {
+    const uint32_t c = s_map[byte];
+    if (c == 255u) {
+        bad = true;
+        return 0u;
+    }
+    return c;
+}
+
 __global__ void pack_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
-                            const int32_t *__restrict__ lens, int64_t n, const uint8_t *__restrict__ code_map,
-                            int B, const uint64_t *__restrict__ pofs, uint4 *__restrict__ packed,
-                            uint32_t *__restrict__ err) {
+                            const int32_t *__restrict__ lens, int64_t n, int64_t total,
+                            const uint8_t *__restrict__ code_map, int B, const uint64_t *__restrict__ pofs,
+                            uint4 *__restrict__ packed, uint32_t *__restrict__ err) {
     __shared__ uint8_t s_map[256];
     for (int t = threadIdx.x; t < 256; t += blockDim.x) s_map[t] = code_map[t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uintptr_t base = (uintptr_t)bytes;
+    const uintptr_t wlo = (base + 3) & ~(uintptr_t)3;            // whole words inside the array
+    const uintptr_t whi = (base + (uintptr_t)total) & ~(uintptr_t)3;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const int64_t len = lens[i];
         const uint8_t *x = bytes + offsets[i];
-        const int64_t nch = chunks_for(len, B);
-        if (B == 2) {
-            uint64_t *dst = (uint64_t *)(packed + pofs[i]);
-            const int64_t nwords = 2 * nch;            // 32 symbols per 64-bit word
-            for (int64_t gbase = 0; gbase < nwords; gbase += 32) {
-                uint32_t my0 = 0, my1 = 0;   // bit planes of group gbase+lane
-                const int gend = (int)((nwords - gbase) < 32 ? (nwords - gbase) : 32);
-                for (int u0 = 0; u0 < gend; u0 += 8) {
-                    uint32_t code[8];
+        uint32_t *dst = reinterpret_cast<uint32_t *>(packed + pofs[i]);
+        const int64_t nout = 4 * chunks_for(len, B);    // 32-bit output words
+        const int per = B == 2 ? 16 : 4;                // bytes per output word
+#pragma unroll 2
+        for (int64_t h = lane; h < nout; h += 32) {
+            const int64_t k0 = (int64_t)per * h;
+            const int cnt = len - k0 >= per ? per : (len > k0 ? (int)(len - k0) : 0);
+            uint32_t out = 0;
+            if (cnt > 0) {
+                const uintptr_t pa = (uintptr_t)(x + k0);
+                const uintptr_t w0 = pa & ~(uintptr_t)3;
+                const uint32_t sh = (uint32_t)(pa & 3u) * 8u;
+                if (w0 >= wlo && w0 + (uintptr_t)(per + 4) <= whi) {
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(w0);
+                    if (B == 2) {
+                        uint32_t W[5];
 #pragma unroll
-                    for (int v = 0; v < 8; v++) {   // eight independent loads in flight
-                        const int64_t k = (gbase + u0 + v) * 32 + lane;
-                        code[v] = (u0 + v < gend && k < len) ? (uint32_t)x[k] : 256u;
-                    }
+                        for (int q = 0; q < 5; q++) W[q] = __ldg(wp + q);
 #pragma unroll
-                    for (int v = 0; v < 8; v++) {
-                        uint32_t c = 0;
-                        if (code[v] < 256u) {
-                            c = s_map[code[v]];
-                            if (c == 255u) { bad = true; c = 0u; }
+                        for (int q = 0; q < 4; q++) {
+                            const uint32_t v = __funnelshift_r(W[q], W[q + 1], sh);
+#pragma unroll
+                            for (int j = 0; j < 4; j++)
+                                if (4 * q + j < cnt) out |= pack_code(s_map, (v >> (8 * j)) & 255u, bad) << (2 * (4 * q + j));
                         }
-                        const uint32_t p0 = __ballot_sync(FULL, c & 1u);
-                        const uint32_t p1 = __ballot_sync(FULL, (c >> 1) & 1u);
-                        my0 = (lane == u0 + v) ? p0 : my0;
-                        my1 = (lane == u0 + v) ? p1 : my1;
+                    } else {
+                        const uint32_t v = __funnelshift_r(__ldg(wp), __ldg(wp + 1), sh);
+#pragma unroll
+                        for (int j = 0; j < 4; j++)
+                            if (j < cnt) out |= pack_code(s_map, (v >> (8 * j)) & 255u, bad) << (8 * j);
                     }
+                } else {
+                    for (int j = 0; j < cnt; j++)
+                        out |= pack_code(s_map, x[k0 + j], bad) << ((B == 2 ? 2 : 8) * j);
                 }
-                if (lane < gend) dst[gbase + lane] = spread_even(my0) | (spread_even(my1) << 1);
             }
-        } else {
-            uint8_t *dst = (uint8_t *)(packed + pofs[i]);
-            const int64_t nbytes = 16 * nch;
-            for (int64_t k = lane; k < nbytes; k += 32) {
-                uint32_t code = 0;
-                if (k < len) {
-                    code = s_map[x[k]];
-                    if (code == 255u) { bad = true; code = 0u; }
-                }
-                dst[k] = (uint8_t)code;
-            }
+            dst[h] = out;
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, (uint32_t)DERR_SYMBOL);
 }
 
-cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
+cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n, int64_t total,
                         const uint8_t *code_map, int B, const uint64_t *pofs, uint4 *packed,
                         uint32_t *err, cudaStream_t s) {
     if (n > 0) {
         int64_t blocks = (n + 7) / 8;   // 8 warps per block
-        pack_kernel<<<(unsigned)(blocks > 8192 ? 8192 : blocks), 256, 0, s>>>(bytes, offsets, lens, n, code_map, B,
-                                                                                pofs, packed, err);
+        pack_kernel<<<(unsigned)(blocks > 8192 ? 8192 : blocks), 256, 0, s>>>(bytes, offsets, lens, n, total, code_map,
+                                                                                B, pofs, packed, err);
         note_launches(1);
     }
     return cudaGetLastError();

@@ -122,7 +122,8 @@ cudaError_t launch_positions(uint64_t seed, uint32_t r, uint32_t m, uint32_t z, 
 // Chunk counts per string (u32) from lengths.
 cudaError_t launch_chunk_counts(const int32_t *lens, int64_t n, int B, uint32_t *counts, cudaStream_t s);
 // Pack bytes -> codes; bytes outside the alphabet set DERR_SYMBOL (code 0 is stored).
-cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n,
+// total: bytes in the array (every validated string lies inside [0, total)).
+cudaError_t launch_pack(const uint8_t *bytes, const int64_t *offsets, const int32_t *lens, int64_t n, int64_t total,
                         const uint8_t *code_map, int B, const uint64_t *pofs, uint4 *packed,
                         uint32_t *err, cudaStream_t s);
 

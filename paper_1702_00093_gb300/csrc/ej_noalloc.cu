@@ -125,7 +125,7 @@ extern "C" int ej_verify_noalloc(const ej_strings *S, const ej_params *p, const 
     NA_CK(launch_validate(S->bytes, S->offsets, n, total, d_map, lens, err, dmax, s));
     NA_CK(launch_chunk_counts(lens, n, B, ccnt, s));
     NA_CK(exclusive_scan_u32(ccnt, pofs, n + 1, nullptr, scan_a, s));
-    NA_CK(launch_pack(S->bytes, S->offsets, lens, n, d_map, B, pofs, packed, err, s));
+    NA_CK(launch_pack(S->bytes, S->offsets, lens, n, total, d_map, B, pofs, packed, err, s));
     uint64_t h[2] = {0, 0};
     NA_CK(cudaMemcpyAsync(h, err, 16, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));

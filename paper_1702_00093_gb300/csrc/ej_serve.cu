@@ -278,7 +278,7 @@ cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &q
                        (unsigned long long *)(derr + 2), s));
     SV(launch_chunk_counts(P<int32_t>(sl.qlens), Q, x.set.B, P<uint32_t>(sl.ccnt), s));
     SV(exclusive_scan_u32(P<uint32_t>(sl.ccnt), P<uint64_t>(sl.qpofs), Q + 1, nullptr, sl.scan.p, s));
-    SV(launch_pack(qbytes, qoffs, P<int32_t>(sl.qlens), Q, x.set.code_map, x.set.B, P<uint64_t>(sl.qpofs),
+    SV(launch_pack(qbytes, qoffs, P<int32_t>(sl.qlens), Q, total, x.set.code_map, x.set.B, P<uint64_t>(sl.qpofs),
                    P<uint4>(sl.qpacked), derr, s));
     SV(launch_embed_sign(P<uint4>(sl.qpacked), P<uint64_t>(sl.qpofs), P<int32_t>(sl.qlens), Q, x.p.r, x.p.m, x.p.z,
                          x.p.L, x.p.alphabet_size, x.set.B, P<uint32_t>(x.tsym),

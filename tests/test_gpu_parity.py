@@ -200,6 +200,34 @@ def test_ragged_and_degenerate_strings(ej, ctx):
         check_all_stages(ej, ctx, ss, params)
 
 
+@pytest.mark.parametrize("alphabet", [b"ACGT", synth.TEXT])
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_pack_at_every_alignment(ej, ctx, alphabet, shift):
+    """Packing reads the byte array as aligned words where it can: strings of
+    every length 0..70 start at every byte offset, in an array whose own start is
+    shifted by 0..3 bytes; the embedding (which consumes every code) equals the
+    oracle's."""
+    rng = np.random.default_rng(11 + shift)
+    lut = np.frombuffer(alphabet, np.uint8)
+    strs = [lut[rng.integers(0, len(alphabet), size=int(L))].tobytes() for L in rng.permutation(71)]
+    ss = synth.pack(strs, alphabet)
+    big = torch.zeros(len(ss.data) + 8, dtype=torch.uint8, device=DEV)
+    big[shift:shift + len(ss.data)] = torch.from_numpy(ss.data).to(DEV)
+    s = ej.Strings(big[shift:shift + len(ss.data)], torch.from_numpy(ss.offsets).to(DEV))
+    params = ej.Params(K=3, r=2, m=2, z=3, seed=7, alphabet=alphabet)
+    info = ctx.plan(s, params)
+    emb = torch.zeros(max(info.embedding_bytes // 4, 1), dtype=torch.int32, device=DEV)
+    we = torch.zeros(max(params.r * ss.n, 1), dtype=torch.int32, device=DEV)
+    ctx.embed(s, params, emb, we)
+    torch.cuda.synchronize()
+    codes = ej.decode_embedding(emb.cpu().numpy().view(np.uint32)[: info.embedding_bytes // 4],
+                                we.cpu().numpy()[: params.r * ss.n].reshape(params.r, ss.n),
+                                params.r, ss.n, info.out_len, info.planes, len(alphabet))
+    ref_emb, ref_we = oracle.embed(ss.data, ss.offsets, alphabet, params.r, info.out_len, params.seed)
+    assert np.array_equal(codes, ref_emb)
+    assert np.array_equal(we.cpu().numpy()[: params.r * ss.n].reshape(params.r, ss.n), ref_we)
+
+
 def test_tiny_inputs(ej, ctx):
     params = ej.Params(K=2, r=2, m=2, z=2, seed=1, alphabet=b"ACGT")
     for strs in ([], [b"ACGT"], [b"", b""], [b"A", b"C"]):
@@ -278,6 +306,12 @@ def test_invalid_inputs_are_rejected(ej, ctx):
     assert e.value.status == ej.EJ_ERR_INVALID_ARG
     bad = ej.Strings(torch.zeros(8, dtype=torch.uint8, device=DEV) + 65,
                      torch.tensor([0, 5, 3], dtype=torch.int64, device=DEV))
+    with pytest.raises(ej.EJError) as e:
+        ctx.join(bad, ej.Params(K=1, r=1, m=1, z=1, alphabet=b"A"), device=DEV)
+    assert e.value.status == ej.EJ_ERR_INVALID_ARG
+    # a string starting before the array (the one before it is negative too)
+    bad = ej.Strings(torch.zeros(8, dtype=torch.uint8, device=DEV) + 65,
+                     torch.tensor([0, -3, 5], dtype=torch.int64, device=DEV))
     with pytest.raises(ej.EJError) as e:
         ctx.join(bad, ej.Params(K=1, r=1, m=1, z=1, alphabet=b"A"), device=DEV)
     assert e.value.status == ej.EJ_ERR_INVALID_ARG
