@@ -303,7 +303,12 @@ void ej_batch_destroy(ej_batch *batch);
  *   buckets: 0 (default) or 1: equal signatures are grouped by hashing (per
  *     table an open-addressing set whose slots head lists of records); a
  *     record pairs with the later records of its list, so a bucket of b strings
- *     costs b*(b-1)/2 length checks. 2: the tables are sorted by (signature,
+ *     costs b*(b-1)/2 length checks. In a batch, 0 also shares buckets: joins
+ *     with the same seed, L, r and m (up to 4) take their pairs from the
+ *     buckets of the one with the smallest z, whose signatures are the coarsest
+ *     (a signature of z samples is one of more samples modulo (|alphabet|+1)^z),
+ *     each partner checked against the join's own signature and K; 1 keeps
+ *     every join's own buckets. 2: the tables are sorted by (signature,
  *     length) and each record pairs with the window after it (the
  *     ej_lsh_candidates path; cheaper for huge buckets of uneven lengths).
  */

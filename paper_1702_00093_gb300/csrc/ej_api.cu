@@ -677,7 +677,7 @@ int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const Verif
 // verifier launch; *defer describes this join's share of a merged launch.
 int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackState &bs, uint64_t cap,
                  cudaStream_t s, cudaEvent_t verify_after = nullptr, cudaEvent_t verify_done = nullptr,
-                 VerifySeg *defer = nullptr) {
+                 VerifySeg *defer = nullptr, bool emitted = false) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     unsigned long long *cnt = nullptr;
     CKS(ensure_t(ctx, B_JCOUNT, 8, &cnt));
@@ -689,9 +689,13 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
     CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
     CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
-    CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+    // emitted: the raw pairs and counters [0], [1] are already written (shared
+    // buckets of a batch)
+    CK(cudaMemsetAsync(emitted ? cnt + 2 : cnt, 0, (emitted ? 6 : 8) * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
-    if (bs.hashed)
+    if (emitted)
+        ;
+    else if (bs.hashed)
         CK(launch_bucket_emit(pl.lens, n, T, p->K, bs.bnext, raw, cap, cnt, s));
     else
         CK(launch_emit_append(bs.srk, bs.srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
@@ -875,6 +879,9 @@ struct BatchJoin {
     bool alias = false;               // same r, m, z as src: read src's keys directly
     uint64_t ncand = 0;               // candidates in the eager pass
     int seg = -1;                     // share of the merged verifier launch (-1: none)
+    int bucket_owner = -1;            // join whose buckets give this join's pairs (-1: its own)
+    std::vector<int> bucket_members;  // owner: the joins (itself first) its buckets serve
+    cudaEvent_t emitted = nullptr;    // owner: every member's pairs are written
 };
 
 }  // namespace
@@ -914,6 +921,7 @@ void batch_free(ej_batch *b) {
         if (j.done) cudaEventDestroy(j.done);
         if (j.verified) cudaEventDestroy(j.verified);
         if (j.keyed) cudaEventDestroy(j.keyed);
+        if (j.emitted) cudaEventDestroy(j.emitted);
         if (j.side) cudaStreamDestroy(j.side);
         if (j.sub) ej_destroy(j.sub);
     }
@@ -928,14 +936,6 @@ int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s)
     ej_ctx *ctx = j.sub;
     const BatchJoin &src = joins[(size_t)j.src];
     CK(launch_derive_keys(src.keys, src.p.m, j.pl.st.n, j.p.r, j.p.m, j.modulus, j.keys, s));
-    return EJ_OK;
-}
-
-// Back half of one join (buckets -> pairs -> dedup -> verify) on its side
-// stream; no host synchronisation.
-int batch_join_back(BatchJoin &j, cudaStream_t s, cudaEvent_t verify_after, cudaEvent_t verify_done) {
-    CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
-    CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s, verify_after, verify_done));
     return EJ_OK;
 }
 
@@ -1044,6 +1044,72 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
     return EJ_OK;
 }
 
+// Shared buckets (ej_schedule.buckets 0): joins with hashed buckets and the
+// same seed, L, r and m take their raw pairs from the buckets of the one with
+// the fewest samples per function (its signatures are the coarsest), up to
+// MAX_SHARED_BUCKETS joins per owner; see bucket_emit_shared_kernel.
+int batch_plan_buckets(ej_batch *b) {
+    ej_ctx *ctx = b->ctx;
+    if (ctx->sched.buckets != 0) return EJ_OK;
+    const size_t n = b->joins.size();
+    std::vector<bool> used(n, false);
+    for (size_t i = 0; i < n; i++) {
+        if (used[i] || !b->joins[i].bs.hashed) continue;
+        const BatchJoin &a = b->joins[i];
+        std::vector<int> group;
+        for (size_t k = i; k < n; k++) {
+            const BatchJoin &c = b->joins[k];
+            if (!used[k] && c.bs.hashed && c.p.seed == a.p.seed && c.pl.L == a.pl.L && c.p.r == a.p.r &&
+                c.p.m == a.p.m)
+                group.push_back((int)k);
+        }
+        for (size_t g0 = 0; g0 + 1 < group.size(); g0 += MAX_SHARED_BUCKETS) {
+            std::vector<int> chunk(group.begin() + (long)g0,
+                                   group.begin() + (long)std::min(group.size(), g0 + MAX_SHARED_BUCKETS));
+            if (chunk.size() < 2) break;
+            int owner = chunk[0];
+            for (int k : chunk)
+                if (b->joins[(size_t)k].p.z < b->joins[(size_t)owner].p.z) owner = k;
+            BatchJoin &o = b->joins[(size_t)owner];
+            o.bucket_members.push_back(owner);
+            for (int k : chunk)
+                if (k != owner) {
+                    o.bucket_members.push_back(k);
+                    b->joins[(size_t)k].bucket_owner = owner;
+                }
+            CK(cudaEventCreateWithFlags(&o.emitted, cudaEventDisableTiming));
+        }
+        for (int k : group) used[(size_t)k] = true;
+    }
+    return EJ_OK;
+}
+
+// An owner's buckets and its members' raw pairs, on the owner's stream (after
+// the owner's keys); the members' keys must be recorded in their `keyed` events.
+int batch_shared_emit(ej_batch *b, BatchJoin &o) {
+    ej_ctx *ctx = o.sub;
+    CKS(back_buckets(o.sub, o.pl, &o.p, o.keys, &o.bs, o.side));
+    SharedEmit se{};
+    se.njoins = (int32_t)o.bucket_members.size();
+    for (size_t k = 0; k < o.bucket_members.size(); k++) {
+        BatchJoin &m = b->joins[(size_t)o.bucket_members[k]];
+        if (&m != &o) CK(cudaStreamWaitEvent(o.side, m.keyed, 0));
+        unsigned long long *cnt = nullptr;
+        uint64_t *raw = nullptr;
+        CKS(ensure_t(m.sub, B_JCOUNT, 8, &cnt));
+        CKS(ensure_t(m.sub, B_RAW, (size_t)m.cap, &raw));
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), o.side));
+        se.keys[k] = m.keys;
+        se.K[k] = m.p.K;
+        se.raw[k] = raw;
+        se.cap[k] = m.cap;
+        se.counters[k] = cnt;
+    }
+    CK(launch_bucket_emit_shared(o.pl.lens, o.pl.st.n, (int64_t)o.p.r * o.p.m, o.bs.bnext, se, o.side));
+    CK(cudaEventRecord(o.emitted, o.side));
+    return EJ_OK;
+}
+
 // The batch's device work on stream s (captured once into the graph, or issued
 // by every run of an eager batch): plan (validate, pack) on s, then every join
 // on its own stream, joined back into s at the end.
@@ -1064,19 +1130,29 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
     // grids sharing the SMs (each capping its working warps per SM) measured from
     // slightly faster to 10x slower from one replay to the next; every other stage
     // overlaps
+    // shared buckets: each owner inserts and emits its members' pairs
+    for (auto &j : b->joins)
+        if (cst == EJ_OK && !j.bucket_members.empty()) cst = batch_shared_emit(b, j);
     cudaEvent_t prev_verify = nullptr;
     VerifySeg unused{};
     for (auto &j : b->joins) {
         if (cst != EJ_OK) break;
+        const bool shared = j.bucket_owner >= 0 || !j.bucket_members.empty();
+        if (j.bucket_owner >= 0 &&
+            cudaStreamWaitEvent(j.side, b->joins[(size_t)j.bucket_owner].emitted, 0) != cudaSuccess) {
+            cst = EJ_ERR_CUDA;
+            break;
+        }
+        if (!shared) cst = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, j.side);
+        if (cst != EJ_OK) break;
         if (j.seg >= 0) {
             // verified by the merged launch below
-            cst = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, j.side);
-            if (cst == EJ_OK)
-                cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &unused);
+            cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &unused, shared);
         } else {
             const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
             const bool heavy = pt > 0 && ctx->sched.chain != 1;
-            cst = batch_join_back(j, j.side, heavy ? prev_verify : nullptr, heavy ? j.verified : nullptr);
+            cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, heavy ? prev_verify : nullptr,
+                               heavy ? j.verified : nullptr, nullptr, shared);
             if (heavy) prev_verify = j.verified;
         }
         if (cst == EJ_OK && cudaEventRecord(j.done, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
@@ -1548,6 +1624,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager pass failed"));
     }
     if ((st = batch_plan_merge(b)) != EJ_OK) return bail(st);
+    if ((st = batch_plan_buckets(b)) != EJ_OK) return bail(st);
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&b->v0) != cudaSuccess || cudaEventCreate(&b->v1) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));

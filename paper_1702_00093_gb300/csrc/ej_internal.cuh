@@ -219,6 +219,19 @@ cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids
 // Buckets by hashing (ej_join): per-table signature sets of H slots
 // (bucket_slots_per_table(n)); slot_keys filled with ~0, heads with 0xFF bytes.
 uint64_t bucket_slots_per_table(int64_t n);
+// Pairs of several joins from the record lists of the coarsest one's buckets
+// (joins with the same seed, L, r, m; see bucket_emit_shared_kernel).
+constexpr int MAX_SHARED_BUCKETS = 4;
+struct SharedEmit {
+    int32_t njoins;
+    const uint64_t *keys[MAX_SHARED_BUCKETS];        // each join's signatures [T][n]
+    int32_t K[MAX_SHARED_BUCKETS];
+    uint64_t *raw[MAX_SHARED_BUCKETS];
+    uint64_t cap[MAX_SHARED_BUCKETS];
+    unsigned long long *counters[MAX_SHARED_BUCKETS];   // [0] raw pairs, [1] largest bucket
+};
+cudaError_t launch_bucket_emit_shared(const int32_t *lens, int64_t n, int64_t T, const uint32_t *next,
+                                      const SharedEmit &se, cudaStream_t s);
 cudaError_t launch_bucket_insert(const uint64_t *keys, int64_t n, int64_t T, uint64_t H, uint64_t *slot_keys,
                                  uint32_t *heads, uint32_t *next, uint32_t *err, cudaStream_t s);
 cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_t K, const uint32_t *next,

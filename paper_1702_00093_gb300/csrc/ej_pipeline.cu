@@ -245,6 +245,114 @@ cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_
     return cudaGetLastError();
 }
 
+// Shared buckets of a batch: joins with the same embeddings and functions
+// (seed, L, r, m) whose z differ. A signature of z samples is the finer one of
+// z' > z samples modulo (|alphabet|+1)^z, so every bucket of the finer joins
+// lies inside a bucket of the coarsest one. The records are inserted into the
+// coarsest join's buckets only; every record walks the later records of its list
+// once and hands each partner to every join whose own signatures and length
+// filter it passes. Per join the emitted pairs are exactly those of its own
+// buckets (each unordered pair once per table), and counters[1] gets its largest
+// bucket. At most MAX_SHARED_BUCKETS joins.
+__global__ void bucket_emit_shared_kernel(const int32_t *__restrict__ lens, int64_t n, int64_t T,
+                                          const uint32_t *__restrict__ next, SharedEmit se) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = n * T;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iters = (total + step - 1) / step;   // the same on every lane: collectives converge
+    const int nj = se.njoins;
+    unsigned long long mb[MAX_SHARED_BUCKETS];
+#pragma unroll
+    for (int j = 0; j < MAX_SHARED_BUCKETS; j++) mb[j] = 0;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t rec = start + it * step;
+        int64_t i = 0, base_t = 0;
+        uint32_t q0 = LIST_END;
+        unsigned long long cnt[MAX_SHARED_BUCKETS], same[MAX_SHARED_BUCKETS];
+        uint64_t ki[MAX_SHARED_BUCKETS];
+#pragma unroll
+        for (int j = 0; j < MAX_SHARED_BUCKETS; j++) { cnt[j] = 0; same[j] = 0; ki[j] = 0; }
+        int32_t li = 0;
+        if (rec < total) {
+            base_t = (rec / n) * n;
+            i = rec - base_t;
+            li = lens[i];
+            q0 = next[rec];
+            if (q0 != LIST_END) {
+#pragma unroll
+                for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                    if (j < nj) ki[j] = se.keys[j][rec];
+                for (uint32_t q = q0; q != LIST_END; q = next[q]) {
+                    const int32_t lq = lens[(int64_t)q - base_t];
+                    const int32_t d = li > lq ? li - lq : lq - li;
+#pragma unroll
+                    for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                        if (j < nj && se.keys[j][q] == ki[j]) {
+                            same[j]++;
+                            cnt[j] += d <= se.K[j] ? 1u : 0u;
+                        }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MAX_SHARED_BUCKETS; j++) mb[j] = max(mb[j], same[j] + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_SHARED_BUCKETS; j++) {
+            if (j >= nj) break;
+            unsigned long long incl = cnt[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+            unsigned long long base = 0;
+            if (wtotal) {
+                if (lane == 31) base = atomicAdd(&se.counters[j][0], wtotal);
+                base = __shfl_sync(FULL, base, 31);
+            }
+            cnt[j] = base + incl - cnt[j];   // this lane's first output slot
+        }
+        if (q0 != LIST_END) {
+            for (uint32_t q = q0; q != LIST_END; q = next[q]) {
+                const int64_t jq = (int64_t)q - base_t;
+                const int32_t lq = lens[jq];
+                const int32_t d = li > lq ? li - lq : lq - li;
+                const uint64_t lo = (uint64_t)(i < jq ? i : jq), hi = (uint64_t)(i < jq ? jq : i);
+#pragma unroll
+                for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                    if (j < nj && d <= se.K[j] && se.keys[j][q] == ki[j]) {
+                        if (cnt[j] < se.cap[j]) se.raw[j][cnt[j]] = (lo << 32) | hi;
+                        cnt[j]++;
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MAX_SHARED_BUCKETS; j++) {
+        if (j >= nj) break;
+        unsigned long long m = mb[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(FULL, m, o);
+            m = v > m ? v : m;
+        }
+        if (lane == 0 && m) atomicMax(&se.counters[j][1], m);
+    }
+}
+
+cudaError_t launch_bucket_emit_shared(const int32_t *lens, int64_t n, int64_t T, const uint32_t *next,
+                                      const SharedEmit &se, cudaStream_t s) {
+    const int64_t total = n * T;
+    if (se.njoins < 1 || se.njoins > MAX_SHARED_BUCKETS) return cudaErrorInvalidValue;
+    if (total > 0) {
+        const int64_t g = (total + 255) / 256;
+        bucket_emit_shared_kernel<<<(unsigned)(g > 32768 ? 32768 : g), 256, 0, s>>>(lens, n, T, next, se);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ uint64_t pair_hash(uint64_t k) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;
