@@ -903,6 +903,10 @@ struct ej_batch {
     unsigned int *mtickets = nullptr;
     cudaEvent_t v0 = nullptr, v1 = nullptr;   // around the merged launch
     bool eager = false;                       // no graph: every run issues the work
+    // results staged by the run itself: per join 8 counters + the error word, and
+    // the plan's error word and longest string (pinned), complete at `done`
+    unsigned long long *h_stat = nullptr;
+    cudaEvent_t done = nullptr;
 };
 
 namespace {
@@ -914,6 +918,8 @@ void batch_free(ej_batch *b) {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->v0) cudaEventDestroy(b->v0);
     if (b->v1) cudaEventDestroy(b->v1);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->h_stat) cudaFreeHost(b->h_stat);
     if (b->segs_dev) cudaFree(b->segs_dev);
     if (b->mqueue) cudaFree(b->mqueue);
     if (b->mtickets) cudaFree(b->mtickets);
@@ -1165,6 +1171,22 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
         if (cst == EJ_OK) cst = batch_merged_verify(b, s);
         if (cst == EJ_OK && b->eager && cudaEventRecord(b->v1, s) != cudaSuccess) cst = EJ_ERR_CUDA;
     }
+    // results: every join's output sorted on the device (up to small_sort_max()
+    // pairs; ej_batch_result sorts larger ones) and all counters copied to pinned
+    // host memory, so that reading the results waits once
+    for (size_t k = 0; k < b->joins.size() && cst == EJ_OK; k++) {
+        BatchJoin &j = b->joins[k];
+        unsigned long long *cnt = (unsigned long long *)j.sub->bufs[B_JCOUNT].p;
+        if (launch_small_sort((uint64_t *)j.sub->bufs[B_APP].p, cnt + 3, (uint64_t)small_sort_max(), s) != cudaSuccess ||
+            cudaMemcpyAsync(b->h_stat + 16 * k, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(b->h_stat + 16 * k + 8, j.sub->bufs[B_DERR].p, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
+            cst = EJ_ERR_CUDA;
+    }
+    if (cst == EJ_OK && cudaMemcpyAsync(b->h_stat + 16 * b->joins.size(), ctx->bufs[B_DERR].p, 16,
+                                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        cst = EJ_ERR_CUDA;
     return cst;
 }
 
@@ -1626,8 +1648,12 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
     if ((st = batch_plan_merge(b)) != EJ_OK) return bail(st);
     if ((st = batch_plan_buckets(b)) != EJ_OK) return bail(st);
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&b->v0) != cudaSuccess || cudaEventCreate(&b->v1) != cudaSuccess)
+        cudaEventCreate(&b->v0) != cudaSuccess || cudaEventCreate(&b->v1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));
+    if (cudaMallocHost(&b->h_stat, (16 * b->joins.size() + 2) * sizeof(unsigned long long)) != cudaSuccess)
+        return bail(fail(ctx, EJ_ERR_OOM, "pinned result staging"));
+    memset(b->h_stat, 0, (16 * b->joins.size() + 2) * sizeof(unsigned long long));
     if (!b->merged.empty()) {
         std::vector<VerifySeg> segs_h(b->merged.size());
         for (auto &j : b->joins)
@@ -1643,7 +1669,8 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         const int64_t l0 = launches_so_far();
         if ((st = batch_issue(b, s)) != EJ_OK) return bail(st);
         b->kernel_nodes = launches_so_far() - l0;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager batch run failed"));
+        if (cudaEventRecord(b->done, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(fail(ctx, EJ_ERR_CUDA, "eager batch run failed"));
         b->ran = true;
         ctx->timing = timing_was;
         *out = b;
@@ -1686,6 +1713,7 @@ int ej_batch_run(ej_batch *b, void *stream) {
     } else {
         CKB(b, cudaGraphLaunch(b->exec, as_stream(stream)));
     }
+    CKB(b, cudaEventRecord(b->done, as_stream(stream)));
     b->ran = true;
     return EJ_OK;
 }
@@ -1713,29 +1741,53 @@ int ej_batch_result(ej_batch *b, int32_t i, uint64_t *out, int64_t capacity, int
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
     const int64_t launches0 = launches_so_far();
-    // the plan's validation of this run's strings
-    CK(cudaMemcpyAsync(ctx->h_cnt, ctx->bufs[B_DERR].p, 16, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const uint32_t e = (uint32_t)(ctx->h_cnt[0] & 0xffffffffu);
+    // the run staged every counter in pinned memory: one wait for the run
+    CKB(b, cudaEventSynchronize(b->done));
+    const unsigned long long *plan = b->h_stat + 16 * b->joins.size();
+    const uint32_t e = (uint32_t)(plan[0] & 0xffffffffu);
     if (e & DERR_OFFSETS)
         return fail(ctx, EJ_ERR_INVALID_ARG, "offsets invalid or grown beyond the batch's plan (%lld bytes)", (long long)b->pl.st.total);
     if (e & DERR_SYMBOL) return fail(ctx, EJ_ERR_INVALID_ARG, "a string byte is not in the alphabet");
-    const int64_t max_len = (int64_t)((unsigned long long)ctx->h_cnt[1]);
+    const int64_t max_len = (int64_t)plan[1];
     BatchJoin &j = b->joins[(size_t)i];
     if (max_len > b->pl.max_len || (!j.p.out_len && !j.p.L && max_len != b->pl.max_len))
         return fail(ctx, EJ_ERR_INVALID_ARG, "the longest string changed (%lld, planned %lld): re-create the batch",
                     (long long)max_len, (long long)b->pl.max_len);
     unsigned long long hc[8];
-    CKS(back_read(j.sub, hc, s));
+    memcpy(hc, b->h_stat + 16 * (size_t)i, 6 * sizeof(unsigned long long));
+    hc[6] = b->h_stat[16 * (size_t)i + 8] & 0xffffffffull;
+    hc[7] = 0;
+    if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+    if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
     if (hc[0] > j.cap)
         return fail(ctx, EJ_ERR_CAPACITY, "raw pairs (%llu) exceed the batch's capacity (%llu): re-create the batch",
                     hc[0], (unsigned long long)j.cap);
     int64_t cnt = 0;
-    const int st = back_finish(j.sub, j.pl, &j.p, hc, out, capacity, &cnt, stats, s);
+    int st = EJ_OK;
+    if ((int64_t)hc[3] <= small_sort_max()) {
+        // sorted by the run: copy only
+        cnt = (int64_t)hc[3];
+        if (stats) {
+            stats->n_raw_pairs = (int64_t)hc[0];
+            stats->max_bucket = (int64_t)hc[1];
+            stats->n_candidates = (int64_t)hc[2];
+            stats->n_out = cnt;
+            stats->band_cells = hc[4];
+            stats->verify_word_columns = hc[5];
+        }
+        if (cnt > capacity) {
+            *n_out = cnt;
+            return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt, (long long)capacity);
+        }
+        if (cnt) CKB(b, cudaMemcpyAsync(out, j.sub->bufs[B_APP].p, (size_t)cnt * sizeof(uint64_t), cudaMemcpyDefault, s));
+    } else {
+        st = back_finish(j.sub, j.pl, &j.p, hc, out, capacity, &cnt, stats, s);
+    }
     *n_out = cnt;
     if (st != EJ_OK) return fail(ctx, st, "%s", ej_last_error(j.sub));
-    CK(cudaStreamSynchronize(s));
-    if (stats) stats->kernel_launches = launches_so_far() - launches0;   // the output sort
+    // a host `out` is complete on return; a device one is ordered on `stream`
+    if (cnt && !is_device_ptr(out)) CKB(b, cudaStreamSynchronize(s));
+    if (stats) stats->kernel_launches = launches_so_far() - launches0;   // a sort of a large output
     return EJ_OK;
 }
 

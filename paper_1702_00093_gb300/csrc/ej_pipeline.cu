@@ -788,7 +788,8 @@ __global__ void __launch_bounds__(1024)
 small_sort_kernel(uint64_t *__restrict__ a, const unsigned long long *__restrict__ count_dev, uint64_t n_cap) {
     __shared__ uint64_t s[SMALL_SORT_MAX];
     const unsigned long long c = *count_dev;
-    const int n = (int)(c < n_cap ? c : n_cap);
+    if (c > n_cap) return;   // left for a larger sort
+    const int n = (int)c;
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < n ? a[i] : ~0ull;

@@ -196,6 +196,34 @@ def test_batch_rerun_after_rewriting_strings(ej, ctx, stream):
         b.close()
 
 
+def test_batch_large_output_to_device_and_host(ej, ctx, stream):
+    """A join with more output pairs than the run sorts on the device (8192):
+    ej_batch_result sorts those itself; results into device and host buffers
+    equal ej_join's."""
+    rng = np.random.default_rng(3)
+    base = rng.integers(0, 4, size=300).astype(np.uint8)
+    strs = []
+    for k in range(160):                      # 160 near-copies: 12720 pairs within K
+        x = base.copy()
+        x[rng.integers(0, 300)] = rng.integers(0, 4)
+        strs.append(np.frombuffer(b"ACGT", np.uint8)[x].tobytes())
+    ss = synth.pack(strs, b"ACGT")
+    s = ej.Strings.from_set(ss, DEV)
+    params = _params(ej, ss, [2, 1], lambda K: dict(r=2, m=4, z=6, seed=3))
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, stream=stream)
+        b.run(stream)
+        for i, p in enumerate(params):
+            want, _ = ctx.join(s, p, device=DEV, stream=stream)
+            got, st = b.result(i, device=DEV, stream=stream)
+            assert np.array_equal(_u64(got), _u64(want)), i
+            host, _ = b.result(i, device=None, stream=stream)
+            assert np.array_equal(host.view(np.uint64), _u64(want)), i
+            if i == 0:
+                assert st.n_out > 8192
+        b.close()
+
+
 def test_batch_autotune_keeps_results(ej, ctx, stream):
     ss = synth.protein_like(6, 200, median=150, lo=40, hi=500)
     s = ej.Strings.from_set(ss, DEV)
