@@ -243,9 +243,12 @@ void ej_server_destroy(ej_server *server);
  * pack once, then per parameter set, on its own stream so that the joins
  * overlap, the walk and signatures, buckets, pairs, dedup and verification.
  * ej_batch_run replays the graph on `stream` without any host synchronisation;
- * ej_batch_result(i) waits for it and returns join i's pairs (sorted, the same
- * as ej_join with params[i]) and its counters (no stage timings;
- * kernel_launches counts the kernels of the result call itself).
+ * the run itself sorts every join's output (up to 8192 pairs) and stages the
+ * counters in pinned host memory. ej_batch_result(i) waits for the run and
+ * returns join i's pairs (sorted, the same as ej_join with params[i]) and its
+ * counters (no stage timings; kernel_launches counts the kernels of the result
+ * call itself: a sort of a larger output). A device `out` is written in stream
+ * order on `stream`; a host `out` is complete on return.
  *
  * The strings must be in device memory; the graph reads them at the addresses
  * given here, so their contents may be rewritten between runs (by the caller,
