@@ -569,7 +569,8 @@ def main():
             "band_cells": rows[0]["band_cells"],
         }
     cells_step = sum(v["band_cells"] for v in per_k.values())
-    join_roofline = {"kernel": "verify_pq_kernel (one launch per join)", "bound": "alu",
+    join_roofline = {"kernel": "the verifier of ej_join, one launch per join (persistent verify_pq_kernel for "
+                               "mean string length >= 2048, else grid-strided verify_bd_kernel)", "bound": "alu",
                      "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",
                      "frac": ach_ops / peak_ops, "traffic": verify_traffic("join"),
                      "launches": n_verify, "avg_launch_ms": verify_ms / max(n_verify, 1),
