@@ -335,7 +335,8 @@ int make_tables(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint32_t **tabl
 
 // Keys [r*m][n] for the plan's strings into `keys` (device): the fused walk
 // when its tables fit in shared memory, else embed (prefix of length L) + sign.
-int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cudaStream_t s) {
+int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cudaStream_t s,
+             const PrefixKeys *prefix = nullptr) {
     const int64_t n = pl.st.n;
     if (n == 0) return EJ_OK;
     uint32_t *pos = nullptr;
@@ -370,7 +371,8 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         }
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
         CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
-                             tsym, next, spos, stag, keys, s));
+                             tsym, next, spos, stag, keys, s, prefix));
+        prefix = nullptr;   // written by the walk
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
     } else {
         // materialise only the prefix [0, L) of every embedding
@@ -388,6 +390,14 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         CK(launch_embed(pl.packed, pl.pofs, pl.lens, n, p->r, table, pl.B, pl2.out_len, pl.planes, emb, we, s));
         CK(launch_sign(emb, we, n, p->r, p->m, p->z, pl2.out_len, pl.planes, p->alphabet_size, pos, keys, s));
         if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    }
+    if (prefix) {
+        // the unfused path: the prefix keys as the keys modulo (alpha+1)^z
+        for (int e = 0; e < prefix->n; e++) {
+            uint64_t mod = 1;
+            for (uint32_t q = 0; q < prefix->z[e]; q++) mod *= (uint64_t)p->alphabet_size + 1;
+            CK(launch_derive_keys(keys, p->m, n, p->r, p->m, prefix->z[e] < p->z ? mod : 0, prefix->keys[e], s));
+        }
     }
     if (pi_dev || pos_inj) CK(cudaStreamSynchronize(s));
     return EJ_OK;
@@ -877,6 +887,7 @@ struct BatchJoin {
     int src = -1;                     // join whose walks give this join's keys (-1: its own)
     uint64_t modulus = 0;             // keys = src keys mod modulus (0: same z)
     bool alias = false;               // same r, m, z as src: read src's keys directly
+    bool in_walk = false;             // same r, m, smaller z: written by src's walk kernel
     uint64_t ncand = 0;               // candidates in the eager pass
     int seg = -1;                     // share of the merged verifier launch (-1: none)
     int bucket_owner = -1;            // join whose buckets give this join's pairs (-1: its own)
@@ -937,8 +948,17 @@ void batch_free(ej_batch *b) {
 // Keys of one join on stream s: its own walk and signatures, or derived from
 // its source join's keys (which must already be written on s's timeline).
 int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s) {
-    if (j.src < 0) return keys_dev(j.sub, &j.p, j.pl, j.keys, s);
-    if (j.alias) return EJ_OK;
+    if (j.src < 0) {
+        PrefixKeys pk{};
+        for (const BatchJoin &d : joins)
+            if (d.in_walk && &joins[(size_t)d.src] == &j) {
+                pk.z[pk.n] = d.p.z;
+                pk.keys[pk.n] = d.keys;
+                pk.n++;
+            }
+        return keys_dev(j.sub, &j.p, j.pl, j.keys, s, pk.n ? &pk : nullptr);
+    }
+    if (j.alias || j.in_walk) return EJ_OK;
     ej_ctx *ctx = j.sub;
     const BatchJoin &src = joins[(size_t)j.src];
     CK(launch_derive_keys(src.keys, src.p.m, j.pl.st.n, j.p.r, j.p.m, j.modulus, j.keys, s));
@@ -971,6 +991,10 @@ void batch_sources(std::vector<BatchJoin> &joins) {
             }
         const BatchJoin &src = joins[(size_t)j.src];
         j.alias = src.p.r == j.p.r && src.p.m == j.p.m && src.p.z == j.p.z;
+        int taken = 0;
+        for (const BatchJoin &d : joins)
+            if (d.in_walk && d.src == j.src) taken++;
+        j.in_walk = !j.alias && src.p.r == j.p.r && src.p.m == j.p.m && taken < MAX_PREFIX_KEYS;
         j.modulus = 0;
         if (j.p.z < src.p.z) {
             j.modulus = 1;
@@ -1174,14 +1198,19 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
     // results: every join's output sorted on the device (up to small_sort_max()
     // pairs; ej_batch_result sorts larger ones) and all counters copied to pinned
     // host memory, so that reading the results waits once
+    // (each join on its own stream, after its verifier)
+    if (cst == EJ_OK && !b->merged.empty() && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
     for (size_t k = 0; k < b->joins.size() && cst == EJ_OK; k++) {
         BatchJoin &j = b->joins[k];
+        const cudaStream_t js = j.side;
         unsigned long long *cnt = (unsigned long long *)j.sub->bufs[B_JCOUNT].p;
-        if (launch_small_sort((uint64_t *)j.sub->bufs[B_APP].p, cnt + 3, (uint64_t)small_sort_max(), s) != cudaSuccess ||
-            cudaMemcpyAsync(b->h_stat + 16 * k, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+        if ((j.seg >= 0 && cudaStreamWaitEvent(js, b->fork, 0) != cudaSuccess) ||
+            launch_small_sort((uint64_t *)j.sub->bufs[B_APP].p, cnt + 3, (uint64_t)small_sort_max(), js) != cudaSuccess ||
+            cudaMemcpyAsync(b->h_stat + 16 * k, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, js) !=
                 cudaSuccess ||
             cudaMemcpyAsync(b->h_stat + 16 * k + 8, j.sub->bufs[B_DERR].p, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                            s) != cudaSuccess)
+                            js) != cudaSuccess ||
+            cudaEventRecord(j.done, js) != cudaSuccess || cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess)
             cst = EJ_ERR_CUDA;
     }
     if (cst == EJ_OK && cudaMemcpyAsync(b->h_stat + 16 * b->joins.size(), ctx->bufs[B_DERR].p, 16,

@@ -609,7 +609,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                   const int32_t *__restrict__ lens, int64_t n, uint32_t m, uint32_t z, uint32_t L,
                   uint32_t alpha, const uint32_t *__restrict__ tsym, const uint16_t *__restrict__ next,
                   const uint32_t *__restrict__ spos, const uint32_t *__restrict__ stag,
-                  uint64_t *__restrict__ keys) {
+                  uint64_t *__restrict__ keys, PrefixKeys pk) {
     constexpr uint32_t PER = 32 / CB;   // codes per word
     extern __shared__ uint64_t es_smem[];
     const uint32_t l = blockIdx.y, M = m * z, LW = sym_words(L);
@@ -701,6 +701,8 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                                            ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
                                            : alpha;
                     key += (uint64_t)c * s_pow[q];
+                    for (int e = 0; e < pk.n; e++)
+                        if (q + 1 == pk.z[e]) pk.keys[e][((size_t)l * m + f) * n + s] = key;
                 }
                 keys[((size_t)l * m + f) * n + s] = key;
             }
@@ -766,6 +768,8 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                                        ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
                                        : alpha;
                 key += (uint64_t)c * s_pow[q];
+                for (int e = 0; e < pk.n; e++)
+                    if (q + 1 == pk.z[e]) pk.keys[e][((size_t)l * m + f) * n + s] = key;
             }
             keys[((size_t)l * m + f) * n + s] = key;
         }
@@ -776,27 +780,32 @@ template <int B, bool TABLE, int CB>
 static void es_launch(dim3 grid, size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs,
                       const int32_t *lens, int64_t n, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha,
                       const uint32_t *tsym, const uint16_t *next, const uint32_t *spos, const uint32_t *stag,
-                      uint64_t *keys) {
+                      uint64_t *keys, const PrefixKeys &pk) {
     cudaFuncSetAttribute(embed_sign_kernel<B, TABLE, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     embed_sign_kernel<B, TABLE, CB><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym,
-                                                                   next, spos, stag, keys);
+                                                                   next, spos, stag, keys, pk);
 }
 
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
                               const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
-                              const uint32_t *stag, uint64_t *keys, cudaStream_t s) {
+                              const uint32_t *stag, uint64_t *keys, cudaStream_t s, const PrefixKeys *prefix) {
     if (n == 0) return cudaGetLastError();
+    PrefixKeys pk{};
+    if (prefix) pk = *prefix;
+    if (pk.n < 0 || pk.n > MAX_PREFIX_KEYS) return cudaErrorInvalidValue;
+    for (int e = 0; e < pk.n; e++)
+        if (pk.z[e] < 1 || pk.z[e] > z || !pk.keys[e]) return cudaErrorInvalidValue;
     const size_t smem = embed_sign_smem(alpha, L, m, z);
     if (smem == 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((n + ES_THREADS - 1) / ES_THREADS), r);
     const bool table = embed_sign_uses_table(alpha, L) && next != nullptr;
     if (B == 2) {
-        if (table) es_launch<2, true, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
-        else es_launch<2, false, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
+        if (table) es_launch<2, true, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        else es_launch<2, false, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
     } else {
-        if (table) es_launch<8, true, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
-        else es_launch<8, false, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys);
+        if (table) es_launch<8, true, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        else es_launch<8, false, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
     }
     note_launches(1);
     return cudaGetLastError();

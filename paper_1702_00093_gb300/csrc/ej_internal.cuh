@@ -152,10 +152,19 @@ bool embed_sign_uses_table(uint32_t alpha, uint32_t L);
 size_t next_table_elems(uint32_t r, uint32_t alpha, uint32_t L);
 cudaError_t launch_next_table(const uint32_t *tsym, uint32_t r, uint32_t alpha, uint32_t L, uint16_t *next,
                               cudaStream_t s);
+// Optional extra outputs of the fused walk: the keys of the first z[e] <= z
+// samples of every function (the same walks and tables), keys[e] [r][m][n].
+constexpr int MAX_PREFIX_KEYS = 3;
+struct PrefixKeys {
+    int32_t n;
+    uint32_t z[MAX_PREFIX_KEYS];
+    uint64_t *keys[MAX_PREFIX_KEYS];
+};
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
                               const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
-                              const uint32_t *stag, uint64_t *keys, cudaStream_t s);
+                              const uint32_t *stag, uint64_t *keys, cudaStream_t s,
+                              const PrefixKeys *prefix = nullptr);
 // Keys [r][m][n] of (r, m, z) from keys [r_src][m_src][n] of a set with the same
 // seed and L and r_src >= r, m_src >= m, z_src >= z: dst = src mod modulus
 // ((alpha+1)^z; 0 = plain copy when z = z_src).
