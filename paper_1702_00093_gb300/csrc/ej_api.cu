@@ -636,6 +636,8 @@ int verify_dev(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *
 // no allocation once the buffers have their size), so they can be captured.
 struct BackState {
     bool hashed = false;
+    bool table_smem = false;           // hashed, each table's buckets built in shared memory
+    const uint64_t *keys = nullptr;    // the signatures (table_smem)
     const uint64_t *srk = nullptr;
     const uint32_t *srid = nullptr;
     uint32_t *bnext = nullptr;
@@ -649,7 +651,11 @@ int back_buckets(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t
     CKS(ensure_t(ctx, B_DERR, 8, &derr));
     CK(cudaMemsetAsync(derr, 0, 4, s));
     bs->hashed = ctx->sched.buckets != 2 && n * T < (int64_t)0xFFFFFFFFll;
-    if (bs->hashed) {
+    bs->table_smem = bs->hashed && bucket_table_smem(n) > 0;
+    bs->keys = keys;
+    if (bs->table_smem) {
+        // built by the emitting kernel, one block per table
+    } else if (bs->hashed) {
         // buckets by hashing: no sort of the r*m tables
         const uint64_t H = bucket_slots_per_table(n);
         uint64_t *bkeys = nullptr;
@@ -703,9 +709,17 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     // buckets of a batch)
     CK(cudaMemsetAsync(emitted ? cnt + 2 : cnt, 0, (emitted ? 6 : 8) * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
-    if (emitted)
-        ;
-    else if (bs.hashed)
+    if (emitted) {
+    } else if (bs.table_smem) {
+        SharedEmit se{};
+        se.njoins = 1;
+        se.keys[0] = bs.keys;
+        se.K[0] = p->K;
+        se.raw[0] = raw;
+        se.cap[0] = cap;
+        se.counters[0] = cnt;
+        CK(launch_bucket_table(pl.lens, n, T, se, s));
+    } else if (bs.hashed)
         CK(launch_bucket_emit(pl.lens, n, T, p->K, bs.bnext, raw, cap, cnt, s));
     else
         CK(launch_emit_append(bs.srk, bs.srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
@@ -1135,7 +1149,10 @@ int batch_shared_emit(ej_batch *b, BatchJoin &o) {
         se.cap[k] = m.cap;
         se.counters[k] = cnt;
     }
-    CK(launch_bucket_emit_shared(o.pl.lens, o.pl.st.n, (int64_t)o.p.r * o.p.m, o.bs.bnext, se, o.side));
+    if (o.bs.table_smem)
+        CK(launch_bucket_table(o.pl.lens, o.pl.st.n, (int64_t)o.p.r * o.p.m, se, o.side));
+    else
+        CK(launch_bucket_emit_shared(o.pl.lens, o.pl.st.n, (int64_t)o.p.r * o.p.m, o.bs.bnext, se, o.side));
     CK(cudaEventRecord(o.emitted, o.side));
     return EJ_OK;
 }

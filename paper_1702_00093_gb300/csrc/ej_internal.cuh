@@ -241,6 +241,11 @@ struct SharedEmit {
 };
 cudaError_t launch_bucket_emit_shared(const int32_t *lens, int64_t n, int64_t T, const uint32_t *next,
                                       const SharedEmit &se, cudaStream_t s);
+// The same pairs with each table's buckets built in shared memory by one block
+// (bucket_table_smem(n) > 0: n below 2^16 - 2 and the slots fit); se.keys[0]
+// are the bucket signatures. No global bucket state.
+size_t bucket_table_smem(int64_t n);
+cudaError_t launch_bucket_table(const int32_t *lens, int64_t n, int64_t T, const SharedEmit &se, cudaStream_t s);
 cudaError_t launch_bucket_insert(const uint64_t *keys, int64_t n, int64_t T, uint64_t H, uint64_t *slot_keys,
                                  uint32_t *heads, uint32_t *next, uint32_t *err, cudaStream_t s);
 cudaError_t launch_bucket_emit(const int32_t *lens, int64_t n, int64_t T, int32_t K, const uint32_t *next,

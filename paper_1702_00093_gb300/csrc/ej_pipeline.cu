@@ -353,6 +353,154 @@ cudaError_t launch_bucket_emit_shared(const int32_t *lens, int64_t n, int64_t T,
     return cudaGetLastError();
 }
 
+// Buckets of one table in shared memory (one block per table, n small enough
+// for 16-bit record indices and the slots in shared memory). Slot h holds the
+// first record of its signature (the owner, low 16 bits) and the head of the
+// list of the later ones (high 16 bits); s_next links the list. Built with
+// shared-memory atomics; then every listed record pairs with the owner and with
+// the records after it in the list, which is every unordered pair of the bucket
+// once. The pairs go to each join of `se` whose own signature and K they pass,
+// as in bucket_emit_shared_kernel (se.keys[0] are the bucket signatures).
+constexpr uint32_t TB_EMPTY = 0xFFFFFFFFu;
+constexpr uint16_t TB_NONE = 0xFFFFu;   // end of a list
+constexpr uint16_t TB_OWNER = 0xFFFEu;  // s_next of an owner
+
+size_t bucket_table_smem(int64_t n) {
+    if (n < 1 || n >= 0xFFFE) return 0;
+    const uint64_t H = bucket_slots_per_table(n);
+    const size_t bytes = (size_t)H * 4 + (((size_t)n * 2 + 15) & ~(size_t)15);
+    return bytes <= 200 * 1024 ? bytes : 0;
+}
+
+__global__ void __launch_bounds__(1024)
+bucket_table_kernel(const int32_t *__restrict__ lens, int64_t n, uint32_t H, SharedEmit se) {
+    extern __shared__ uint32_t tb_smem[];
+    uint32_t *slot = tb_smem;
+    uint16_t *nxt = reinterpret_cast<uint16_t *>(tb_smem + H);
+    const int64_t t = blockIdx.x;
+    const uint64_t *bk = se.keys[0] + t * n;
+    const int lane = threadIdx.x & 31;
+    const int nj = se.njoins;
+    for (uint32_t h = threadIdx.x; h < H; h += blockDim.x) slot[h] = TB_EMPTY;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t k = bk[i];
+        nxt[i] = TB_OWNER;   // (kept if no slot were found, which H > n rules out)
+        uint32_t h = (uint32_t)(key_hash(k) & (uint64_t)(H - 1));
+        for (uint32_t probe = 0; probe < H; probe++) {
+            const uint32_t old = atomicCAS(&slot[h], TB_EMPTY, (uint32_t)i | ((uint32_t)TB_NONE << 16));
+            if (old == TB_EMPTY) break;
+            if (bk[old & 0xFFFFu] == k) {
+                // a later record of this signature: push it onto the slot's list
+                uint32_t cur = old, seen;
+                while ((seen = atomicCAS(&slot[h], cur, (cur & 0xFFFFu) | ((uint32_t)i << 16))) != cur) cur = seen;
+                nxt[i] = (uint16_t)(cur >> 16);
+                break;
+            }
+            h = (h + 1) & (H - 1);
+        }
+    }
+    __syncthreads();
+    const int64_t iters = (n + blockDim.x - 1) / blockDim.x;   // the same on every lane
+    unsigned long long mb[MAX_SHARED_BUCKETS];
+#pragma unroll
+    for (int j = 0; j < MAX_SHARED_BUCKETS; j++) mb[j] = 0;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t i = it * blockDim.x + threadIdx.x;
+        uint32_t owner = TB_NONE;
+        uint16_t q0 = TB_NONE;
+        int32_t li = 0;
+        unsigned long long cnt[MAX_SHARED_BUCKETS], same[MAX_SHARED_BUCKETS];
+        uint64_t ki[MAX_SHARED_BUCKETS];
+#pragma unroll
+        for (int j = 0; j < MAX_SHARED_BUCKETS; j++) { cnt[j] = 0; same[j] = 0; ki[j] = 0; }
+        if (i < n) {
+            if (nxt[i] != TB_OWNER) {
+                // a listed record: its owner (re-probe) and the list after it
+                const uint64_t k = bk[i];
+                uint32_t h = (uint32_t)(key_hash(k) & (uint64_t)(H - 1));
+                for (uint32_t probe = 0; probe < H; probe++) {
+                    const uint32_t v = slot[h];
+                    if (v != TB_EMPTY && bk[v & 0xFFFFu] == k) {
+                        owner = v & 0xFFFFu;
+                        break;
+                    }
+                    h = (h + 1) & (H - 1);
+                }
+                q0 = owner < (uint32_t)n ? nxt[i] : TB_NONE;
+                li = lens[i];
+#pragma unroll
+                for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                    if (j < nj) ki[j] = se.keys[j][t * n + i];
+                // partners: the owner, then the list after i
+                for (uint32_t q = owner; q < (uint32_t)n; q = (q == owner) ? q0 : nxt[q]) {
+                    const int32_t lq = lens[q];
+                    const int32_t d = li > lq ? li - lq : lq - li;
+#pragma unroll
+                    for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                        if (j < nj && se.keys[j][t * n + q] == ki[j]) {
+                            same[j]++;
+                            cnt[j] += d <= se.K[j] ? 1u : 0u;
+                        }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MAX_SHARED_BUCKETS; j++) mb[j] = max(mb[j], same[j] + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_SHARED_BUCKETS; j++) {
+            if (j >= nj) break;
+            unsigned long long incl = cnt[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned long long wtotal = __shfl_sync(FULL, incl, 31);
+            unsigned long long base = 0;
+            if (wtotal) {
+                if (lane == 31) base = atomicAdd(&se.counters[j][0], wtotal);
+                base = __shfl_sync(FULL, base, 31);
+            }
+            cnt[j] = base + incl - cnt[j];
+        }
+        if (owner != TB_NONE) {
+            for (uint32_t q = owner; q < (uint32_t)n; q = (q == owner) ? q0 : nxt[q]) {
+                const int32_t lq = lens[q];
+                const int32_t d = li > lq ? li - lq : lq - li;
+                const uint64_t lo = (uint64_t)(i < (int64_t)q ? i : (int64_t)q), hi = (uint64_t)(i < (int64_t)q ? (int64_t)q : i);
+#pragma unroll
+                for (int j = 0; j < MAX_SHARED_BUCKETS; j++)
+                    if (j < nj && d <= se.K[j] && se.keys[j][t * n + q] == ki[j]) {
+                        if (cnt[j] < se.cap[j]) se.raw[j][cnt[j]] = (lo << 32) | hi;
+                        cnt[j]++;
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MAX_SHARED_BUCKETS; j++) {
+        if (j >= nj) break;
+        unsigned long long m = mb[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(FULL, m, o);
+            m = v > m ? v : m;
+        }
+        if (lane == 0 && m) atomicMax(&se.counters[j][1], m);
+    }
+}
+
+cudaError_t launch_bucket_table(const int32_t *lens, int64_t n, int64_t T, const SharedEmit &se, cudaStream_t s) {
+    const size_t smem = bucket_table_smem(n);
+    if (smem == 0 || se.njoins < 1 || se.njoins > MAX_SHARED_BUCKETS) return cudaErrorInvalidValue;
+    if (n * T == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(bucket_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    bucket_table_kernel<<<(unsigned)T, 1024, smem, s>>>(lens, n, (uint32_t)bucket_slots_per_table(n), se);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ uint64_t pair_hash(uint64_t k) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;
