@@ -616,16 +616,21 @@ __global__ void count_hist_kernel(const uint64_t *__restrict__ table, const uint
         if (sb[t]) atomicAdd(&bins[t], (unsigned long long)sb[t]);
 }
 
-// bins -> start offsets, highest count first (in place).
+// bins -> start offsets, highest bin first (in place); one block of COUNT_BINS
+// threads, thread t owning bin COUNT_BINS-1-t (a shared-memory scan).
 __global__ void count_scan_kernel(unsigned long long *__restrict__ bins) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        unsigned long long acc = 0;
-        for (int c = COUNT_BINS - 1; c >= 0; c--) {
-            const unsigned long long v = bins[c];
-            bins[c] = acc;
-            acc += v;
-        }
+    __shared__ unsigned long long sc[COUNT_BINS];
+    const int t = threadIdx.x;
+    const unsigned long long own = bins[COUNT_BINS - 1 - t];
+    sc[t] = own;
+    __syncthreads();
+    for (int o = 1; o < COUNT_BINS; o <<= 1) {
+        const unsigned long long v = t >= o ? sc[t - o] : 0ull;
+        __syncthreads();
+        sc[t] += v;
+        __syncthreads();
     }
+    bins[COUNT_BINS - 1 - t] = sc[t] - own;
 }
 
 __global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ hcount,
@@ -689,7 +694,7 @@ cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *ta
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
     const uint32_t scale = (uint32_t)(max_len > 0x7fffffff ? 0x7fffffff : max_len);
     count_hist_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, lens, scale, bins, counters);
-    count_scan_kernel<<<1, 32, 0, s>>>(bins);
+    count_scan_kernel<<<1, COUNT_BINS, 0, s>>>(bins);
     count_scatter_kernel<<<gs, 256, 0, s>>>(table, hcount, hsize, lens, scale, bins, cand);
     note_launches(4);
     return cudaGetLastError();
