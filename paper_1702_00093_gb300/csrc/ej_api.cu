@@ -335,10 +335,13 @@ int make_tables(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint32_t **tabl
 
 // Keys [r*m][n] for the plan's strings into `keys` (device): the fused walk
 // when its tables fit in shared memory, else embed (prefix of length L) + sign.
+// phase 1 issues only the tables (bits, positions: parameters only), phase 2
+// only the walk over the strings (tables already built), 0 both.
 int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cudaStream_t s,
-             const PrefixKeys *prefix = nullptr) {
+             const PrefixKeys *prefix = nullptr, int phase = 0) {
     const int64_t n = pl.st.n;
     if (n == 0) return EJ_OK;
+    const bool tables = phase != 2, walk = phase != 1;
     uint32_t *pos = nullptr;
     CKS(ensure_t(ctx, B_POS, (size_t)p->r * p->m * p->z, &pos));
     const uint8_t *pi_dev = nullptr;
@@ -355,25 +358,29 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         CK(cudaMemcpyAsync(d, ctx->posinj.data(), ctx->posinj.size() * 4, cudaMemcpyHostToDevice, s));
         pos_inj = d;
     }
-    CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_inj, pos, s));
+    if (tables) CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_inj, pos, s));
     if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z) > 0) {
         uint32_t *tsym = nullptr, *spos = nullptr, *stag = nullptr;
         CKS(ensure_t(ctx, B_TSYM, symbol_table_words(p->r, p->alphabet_size, pl.L), &tsym));
         CKS(ensure_t(ctx, B_SPOS, (size_t)p->r * p->m * p->z, &spos));
         CKS(ensure_t(ctx, B_STAG, (size_t)p->r * p->m * p->z, &stag));
-        CK(launch_symbol_table(p->seed, p->r, pl.L, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,
-                               pi_dev, ctx->pi_steps, tsym, s));
-        CK(launch_sort_samples(pos, p->r, p->m, p->z, spos, stag, s));
+        if (tables) {
+            CK(launch_symbol_table(p->seed, p->r, pl.L, (const uint8_t *)ctx->bufs[B_ALPHABET].p, p->alphabet_size,
+                                   pi_dev, ctx->pi_steps, tsym, s));
+            CK(launch_sort_samples(pos, p->r, p->m, p->z, spos, stag, s));
+        }
         uint16_t *next = nullptr;
         if (embed_sign_uses_table(p->alphabet_size, pl.L)) {
             CKS(ensure_t(ctx, B_NEXT, next_table_elems(p->r, p->alphabet_size, pl.L), &next));
-            CK(launch_next_table(tsym, p->r, p->alphabet_size, pl.L, next, s));
+            if (tables) CK(launch_next_table(tsym, p->r, p->alphabet_size, pl.L, next, s));
         }
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
-        CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
-                             tsym, next, spos, stag, keys, s, prefix));
+        if (walk) {
+            if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+            CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
+                                 tsym, next, spos, stag, keys, s, prefix));
+            if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+        }
         prefix = nullptr;   // written by the walk
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
     } else {
         // materialise only the prefix [0, L) of every embedding
         Plan pl2 = pl;
@@ -384,14 +391,17 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         CKS(ensure_t(ctx, B_TABLE, (size_t)p->r * pl2.out_len * words, &table));
         CKS(ensure_t(ctx, B_EMB, (size_t)(emb_bytes(pl2, p->r) / 4), &emb));
         CKS(ensure_t(ctx, B_WALK, (size_t)p->r * n, &we));
-        CK(launch_bit_table(p->seed, p->r, pl2.out_len, (const uint8_t *)ctx->bufs[B_ALPHABET].p,
-                            p->alphabet_size, words, pi_dev, ctx->pi_steps, table, s));
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
-        CK(launch_embed(pl.packed, pl.pofs, pl.lens, n, p->r, table, pl.B, pl2.out_len, pl.planes, emb, we, s));
-        CK(launch_sign(emb, we, n, p->r, p->m, p->z, pl2.out_len, pl.planes, p->alphabet_size, pos, keys, s));
-        if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+        if (tables)
+            CK(launch_bit_table(p->seed, p->r, pl2.out_len, (const uint8_t *)ctx->bufs[B_ALPHABET].p,
+                                p->alphabet_size, words, pi_dev, ctx->pi_steps, table, s));
+        if (walk) {
+            if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+            CK(launch_embed(pl.packed, pl.pofs, pl.lens, n, p->r, table, pl.B, pl2.out_len, pl.planes, emb, we, s));
+            CK(launch_sign(emb, we, n, p->r, p->m, p->z, pl2.out_len, pl.planes, p->alphabet_size, pos, keys, s));
+            if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+        }
     }
-    if (prefix) {
+    if (prefix && walk) {
         // the unfused path: the prefix keys as the keys modulo (alpha+1)^z
         for (int e = 0; e < prefix->n; e++) {
             uint64_t mod = 1;
@@ -916,6 +926,7 @@ struct ej_batch {
     Plan pl;
     std::vector<BatchJoin> joins;
     cudaEvent_t fork = nullptr;
+    cudaEvent_t start = nullptr;      // the run's start on its stream (the tables wait for it)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernel_nodes = 0;
@@ -941,6 +952,7 @@ void batch_free(ej_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->start) cudaEventDestroy(b->start);
     if (b->v0) cudaEventDestroy(b->v0);
     if (b->v1) cudaEventDestroy(b->v1);
     if (b->done) cudaEventDestroy(b->done);
@@ -961,7 +973,7 @@ void batch_free(ej_batch *b) {
 
 // Keys of one join on stream s: its own walk and signatures, or derived from
 // its source join's keys (which must already be written on s's timeline).
-int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s) {
+int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s, int phase = 0) {
     if (j.src < 0) {
         PrefixKeys pk{};
         for (const BatchJoin &d : joins)
@@ -970,9 +982,9 @@ int batch_join_keys(std::vector<BatchJoin> &joins, BatchJoin &j, cudaStream_t s)
                 pk.keys[pk.n] = d.keys;
                 pk.n++;
             }
-        return keys_dev(j.sub, &j.p, j.pl, j.keys, s, pk.n ? &pk : nullptr);
+        return keys_dev(j.sub, &j.p, j.pl, j.keys, s, pk.n ? &pk : nullptr, phase);
     }
-    if (j.alias || j.in_walk) return EJ_OK;
+    if (j.alias || j.in_walk || phase == 1) return EJ_OK;
     ej_ctx *ctx = j.sub;
     const BatchJoin &src = joins[(size_t)j.src];
     CK(launch_derive_keys(src.keys, src.p.m, j.pl.st.n, j.p.r, j.p.m, j.modulus, j.keys, s));
@@ -1162,7 +1174,16 @@ int batch_shared_emit(ej_batch *b, BatchJoin &o) {
 // on its own stream, joined back into s at the end.
 int batch_issue(ej_batch *b, cudaStream_t s) {
     ej_ctx *ctx = b->ctx;
-    int cst = plan_device(ctx, b->pl, s);
+    int cst = EJ_OK;
+    // the walking joins' tables (bits, positions) depend on the parameters only:
+    // they are built on the joins' streams while s validates and packs
+    if (cudaEventRecord(b->start, s) != cudaSuccess) cst = EJ_ERR_CUDA;
+    for (auto &j : b->joins) {
+        if (cst != EJ_OK || j.src >= 0) continue;
+        if (cudaStreamWaitEvent(j.side, b->start, 0) != cudaSuccess) cst = EJ_ERR_CUDA;
+        if (cst == EJ_OK) cst = batch_join_keys(b->joins, j, j.side, 1);
+    }
+    if (cst == EJ_OK) cst = plan_device(ctx, b->pl, s);
     if (cst == EJ_OK && cudaEventRecord(b->fork, s) != cudaSuccess) cst = EJ_ERR_CUDA;
     // keys: the self-walking joins first, then the derived ones after their source
     for (int pass = 0; pass < 2 && cst == EJ_OK; pass++)
@@ -1170,7 +1191,7 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
             if (cst != EJ_OK || (pass == 0) != (j.src < 0)) continue;
             cudaEvent_t after = j.src < 0 ? b->fork : b->joins[(size_t)j.src].keyed;
             if (cudaStreamWaitEvent(j.side, after, 0) != cudaSuccess) { cst = EJ_ERR_CUDA; break; }
-            cst = batch_join_keys(b->joins, j, j.side);
+            cst = batch_join_keys(b->joins, j, j.side, 2);
             if (cst == EJ_OK && cudaEventRecord(j.keyed, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
         }
     // persistent verifiers run one after another unless chain == 1: two persistent
@@ -1694,6 +1715,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
     if ((st = batch_plan_merge(b)) != EJ_OK) return bail(st);
     if ((st = batch_plan_buckets(b)) != EJ_OK) return bail(st);
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&b->v0) != cudaSuccess || cudaEventCreate(&b->v1) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(ctx, EJ_ERR_CUDA, "event creation failed"));
