@@ -421,3 +421,31 @@ def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
         ctx.set_schedule(0, 0)
         ctx.set_verify_config(0, 0, 0)
     assert runs >= 7
+
+
+@pytest.mark.parametrize("n", [21845, 21846])
+def test_buckets_in_shared_memory_and_global(ej, ctx, n):
+    """Tables of up to 21845 records are bucketed in shared memory, larger ones in
+    global memory: at the boundary both give the sorted path's pairs, and the
+    smaller set's pairs equal the oracle's (short strings over ACGT with z = 4,
+    so the buckets hold dozens of records)."""
+    rng = np.random.default_rng(n)
+    lut = np.frombuffer(b"ACGT", np.uint8)
+    strs = [lut[rng.integers(0, 4, size=int(rng.integers(8, 13)))].tobytes() for _ in range(n)]
+    ss = synth.pack(strs, b"ACGT")
+    s = ej.Strings.from_set(ss, DEV)
+    params = ej.Params(K=1, r=2, m=3, z=4, seed=9, alphabet=b"ACGT")
+    try:
+        ctx.set_schedule(buckets=0)
+        hashed, st_h = ctx.join(s, params, device=DEV, capacity=1 << 20)
+        ctx.set_schedule(buckets=2)
+        srt, st_s = ctx.join(s, params, device=DEV, capacity=1 << 20)
+    finally:
+        ctx.set_schedule()
+    assert st_h.n_candidates == st_s.n_candidates > 1000 and st_h.n_raw_pairs == st_s.n_raw_pairs
+    assert st_h.max_bucket > 20
+    assert np.array_equal(_np_u64(hashed), _np_u64(srt))
+    if n == 21845:
+        ref = oracle.join(ss.data, ss.offsets, b"ACGT", K=1, r=2, m=3, z=4, seed=9)
+        assert ref.n_candidates == st_h.n_candidates
+        assert np.array_equal(_np_u64(hashed), ref.pairs)
