@@ -1,5 +1,7 @@
 // Validation, random-bit tables, CGK embedding (Algorithm 1) and bit-sampling
 // signatures (Theorem 1 with AND amplification, Section 3.2).
+#include <utility>
+
 #include "ej_internal.cuh"
 
 namespace ej {
@@ -695,14 +697,17 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
         if (s < n) {
             for (uint32_t f = 0; f < m; f++) {
                 uint64_t key = 0;
-                for (uint32_t q = 0; q < z; q++) {
-                    const uint32_t rk = s_rank[f * z + q];
-                    const uint32_t c = (rk < k)
-                                           ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
-                                           : alpha;
-                    key += (uint64_t)c * s_pow[q];
-                    for (int e = 0; e < pk.n; e++)
-                        if (q + 1 == pk.z[e]) pk.keys[e][((size_t)l * m + f) * n + s] = key;
+                uint32_t q = 0;
+                for (int e = 0; e <= pk.n; e++) {   // the prefix keys (ascending z) on the way
+                    const uint32_t qe = e < pk.n ? pk.z[e] : z;
+                    for (; q < qe; q++) {
+                        const uint32_t rk = s_rank[f * z + q];
+                        const uint32_t c = (rk < k)
+                                               ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                               : alpha;
+                        key += (uint64_t)c * s_pow[q];
+                    }
+                    if (e < pk.n) pk.keys[e][((size_t)l * m + f) * n + s] = key;
                 }
                 keys[((size_t)l * m + f) * n + s] = key;
             }
@@ -762,14 +767,17 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     if (s < n) {
         for (uint32_t f = 0; f < m; f++) {
             uint64_t key = 0;
-            for (uint32_t q = 0; q < z; q++) {
-                const uint32_t rk = s_rank[f * z + q];
-                const uint32_t c = (rk < k_end)
-                                       ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
-                                       : alpha;
-                key += (uint64_t)c * s_pow[q];
-                for (int e = 0; e < pk.n; e++)
-                    if (q + 1 == pk.z[e]) pk.keys[e][((size_t)l * m + f) * n + s] = key;
+            uint32_t q = 0;
+            for (int e = 0; e <= pk.n; e++) {   // the prefix keys (ascending z) on the way
+                const uint32_t qe = e < pk.n ? pk.z[e] : z;
+                for (; q < qe; q++) {
+                    const uint32_t rk = s_rank[f * z + q];
+                    const uint32_t c = (rk < k_end)
+                                           ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                           : alpha;
+                    key += (uint64_t)c * s_pow[q];
+                }
+                if (e < pk.n) pk.keys[e][((size_t)l * m + f) * n + s] = key;
             }
             keys[((size_t)l * m + f) * n + s] = key;
         }
@@ -796,6 +804,11 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
     if (pk.n < 0 || pk.n > MAX_PREFIX_KEYS) return cudaErrorInvalidValue;
     for (int e = 0; e < pk.n; e++)
         if (pk.z[e] < 1 || pk.z[e] > z || !pk.keys[e]) return cudaErrorInvalidValue;
+    for (int e = 1; e < pk.n; e++)   // ascending z (the kernel stores them in that order)
+        for (int f = e; f > 0 && pk.z[f] < pk.z[f - 1]; f--) {
+            std::swap(pk.z[f], pk.z[f - 1]);
+            std::swap(pk.keys[f], pk.keys[f - 1]);
+        }
     const size_t smem = embed_sign_smem(alpha, L, m, z);
     if (smem == 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((n + ES_THREADS - 1) / ES_THREADS), r);
