@@ -242,6 +242,14 @@ void ej_server_destroy(ej_server *server);
  * and captures the whole device path of all joins into one graph: validate and
  * pack once, then per parameter set, on its own stream so that the joins
  * overlap, the walk and signatures, buckets, pairs, dedup and verification.
+ * Work that several parameter sets share is done once. A set whose (r, m, z)
+ * another set with the same seed and L covers takes its signatures from that
+ * set's walks (the key of fewer samples is the wider key modulo
+ * (|alphabet|+1)^z). Sets with the same seed, L, r and m take their raw pairs
+ * from the buckets of the one with the smallest z (ej_schedule.buckets). The
+ * sets on the persistent verifier are verified by one merged launch, each pair
+ * with its own set's K (ej_schedule.chain). Every set still gets exactly
+ * ej_join's candidates and output.
  * ej_batch_run replays the graph on `stream` without any host synchronisation;
  * the run itself sorts every join's output (up to 8192 pairs) and stages the
  * counters in pinned host memory. ej_batch_result(i) waits for the run and
