@@ -320,6 +320,32 @@ def test_keys_are_injective_mixed_radix():
                 assert k == 0
 
 
+def test_fewer_samples_give_the_wider_key_modulo_and_nested_buckets():
+    # Positions are drawn per (embedding, function, sample) from a counter (reading 2),
+    # so parameter sets that differ only in z (or use fewer embeddings / functions)
+    # sample the same steps for their common (l, f, q). The key of the first z samples
+    # is then the key of z' > z samples modulo (|alphabet|+1)^z, and equal keys at z'
+    # imply equal keys at z: a batch of joins relies on both facts to share walks and
+    # buckets.
+    ss = synth.dna_clusters(7, 10, 6, 20, 60, edits_mean=3.0)
+    out_len = 3 * int(ss.lengths().max())
+    emb, we = oracle.embed(ss.data, ss.offsets, ss.alphabet, 3, out_len, seed=11)
+    wide = oracle.sign(emb, we, oracle.positions(11, 3, 5, 9, out_len), 4)        # r=3, m=5, z=9
+    for r, m, z in [(3, 5, 6), (2, 5, 9), (3, 2, 4), (1, 1, 1)]:
+        pos = oracle.positions(11, r, m, z, out_len)
+        keys = oracle.sign(emb[:r], we[:r], pos, 4)
+        for l in range(r):
+            for f in range(m):
+                got = keys[l * m + f]
+                want = wide[l * 5 + f] % np.uint64(5 ** z)
+                assert np.array_equal(got, want), (r, m, z, l, f)
+                # nested buckets: equal wide keys imply equal narrow ones
+                w = wide[l * 5 + f]
+                same_w = w[:, None] == w[None, :]
+                same_n = got[:, None] == got[None, :]
+                assert not np.any(same_w & ~same_n)
+
+
 def test_alg3_candidates_equal_pairwise_definition():
     # Alg. 3's sliding window with eviction equals the set
     # {(i, j): i < j, ||s_i| - |s_j|| <= K, some table has equal keys}.
