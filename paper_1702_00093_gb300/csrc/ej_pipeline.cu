@@ -1,7 +1,9 @@
-// Back half of ej_join without host round trips: bucket windows append their
-// pairs, a device hash set removes duplicates (Alg. 3's deduplication), and the
-// verified output is sorted at the end. Counts stay on the device; the host
-// reads them once, after verification.
+// Back half of ej_join without host round trips: buckets (sorted windows, hashed
+// record lists in global memory, or per-table sets in shared memory) append their
+// pairs, a device hash set removes duplicates (Alg. 3's deduplication) and orders
+// the candidates for the verifier, and the verified output is sorted at the end.
+// Counts stay on the device; the host reads them once, after verification. The
+// resident-index search (its buckets and probe) is here as well.
 #include "ej_internal.cuh"
 
 namespace ej {

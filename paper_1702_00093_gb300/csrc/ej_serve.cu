@@ -3,7 +3,8 @@
 // The index is EmbedJoin's data structure kept on the device: the strings (packed
 // codes), the random walk tables and sampled positions of its parameters, and,
 // per (embedding, function) table, the signatures of every string grouped into
-// buckets (an open-addressing signature set whose slots head lists of records).
+// buckets (the table's records sorted by signature, then length, and an
+// open-addressing set mapping each signature to its run of records).
 // A query q with threshold K_q follows Alg. 3 from the query's side: its own
 // walk and signatures with the same tables (Alg. 1, Thm. 1), the index strings
 // sharing a signature in any table and passing ||q| - |s|| <= K_q, dedup, and
