@@ -88,6 +88,10 @@ def lib():
             L.or_verify.argtypes = [vp, vp, vp, i64, i32, vp]
             L.or_join_bruteforce.restype = i64
             L.or_join_bruteforce.argtypes = [vp, vp, i64, i32, vp, i64]
+            L.or_join_bruteforce_cutoff.restype = i64
+            L.or_join_bruteforce_cutoff.argtypes = [vp, vp, i64, i32, vp, i64]
+            L.or_ed_banded_cutoff.restype = i32
+            L.or_ed_banded_cutoff.argtypes = [vp, i64, vp, i64, i32]
             L.or_join.restype = C.c_int
             L.or_join.argtypes = [vp, vp, i64, C.POINTER(_Params), vp, i64, vp, i64,
                                   C.POINTER(_Stats)]
@@ -196,6 +200,12 @@ def ed_banded(x: bytes, y: bytes, K: int) -> int:
     return int(lib().or_ed_banded(_p(xa), len(x), _p(ya), len(y), K))
 
 
+def ed_banded_cutoff(x: bytes, y: bytes, K: int) -> int:
+    """min(ED(x, y), K+1) by the banded DP stopped at Ukkonen's cutoff."""
+    xa, ya = _u8(x), _u8(y)
+    return int(lib().or_ed_banded_cutoff(_p(xa), len(x), _p(ya), len(y), K))
+
+
 def ed_full(x: bytes, y: bytes) -> int:
     xa, ya = _u8(x), _u8(y)
     return int(lib().or_ed_full(_p(xa), len(x), _p(ya), len(y)))
@@ -210,9 +220,16 @@ def verify(data, offsets, pairs: np.ndarray, K: int) -> np.ndarray:
     return flags[:pairs.shape[0]]
 
 
-def join_bruteforce(data, offsets, K: int) -> np.ndarray:
+def join_bruteforce(data, offsets, K: int, cutoff: bool = False) -> np.ndarray:
+    """Every pair i<j with ED <= K (the definition, Section 1), sorted; cutoff
+    stops each pair's DP at Ukkonen's cutoff (same result, for larger samples)."""
     data, offsets = _strings(data, offsets)
     n = offsets.shape[0] - 1
+    if cutoff:
+        cap = max(n * (n - 1) // 2, 1)
+        out = np.zeros(cap, dtype=np.uint64)
+        cnt = lib().or_join_bruteforce_cutoff(_p(data), _p(offsets), n, K, _p(out), cap)
+        return out[:cnt]
     cnt = lib().or_join_bruteforce(_p(data), _p(offsets), n, K, None, 0)
     out = np.zeros(max(cnt, 1), dtype=np.uint64)
     lib().or_join_bruteforce(_p(data), _p(offsets), n, K, _p(out), cnt)

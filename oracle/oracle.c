@@ -362,6 +362,71 @@ int32_t or_ed_banded(const uint8_t *x, int64_t lx, const uint8_t *y, int64_t ly,
     return res;
 }
 
+/* The band DP of or_ed_banded with Ukkonen's cutoff: once every cell of a row's
+   band exceeds K, so does every later cell (a cell is never below the minimum of
+   the row above: each recurrence term adds 0 or 1 to a cell of that row, or 1 to
+   an earlier cell of its own row), so the answer is K + 1. Returns the same
+   min(ED, K + 1) as or_ed_banded; used for brute-force truth on larger samples. */
+int32_t or_ed_banded_cutoff(const uint8_t *x, int64_t lx, const uint8_t *y, int64_t ly, int32_t K) {
+    if (K < 0) return 0;
+    int64_t diff = ly - lx;
+    if (diff > K || -diff > K) return K + 1;
+    int64_t W = 2 * (int64_t)K + 1;
+    int32_t cap = K + 1;
+    int32_t *prev = (int32_t *)malloc((size_t)(W + 2) * sizeof(int32_t));
+    int32_t *cur = (int32_t *)malloc((size_t)(W + 2) * sizeof(int32_t));
+    if (!prev || !cur) { free(prev); free(cur); return -1; }
+    for (int64_t d = 0; d < W + 2; d++) prev[d] = cur[d] = cap;
+    for (int64_t d = 0; d < W; d++) {
+        int64_t j = d - K;
+        prev[d + 1] = (j >= 0 && j <= ly) ? (int32_t)(j < cap ? j : cap) : cap;
+    }
+    for (int64_t i = 1; i <= lx; i++) {
+        int32_t row_min = cap;
+        for (int64_t d = 0; d < W; d++) {
+            int64_t j = i + d - K;
+            int32_t v;
+            if (j < 0 || j > ly) {
+                v = cap;
+            } else if (j == 0) {
+                v = (int32_t)(i < cap ? i : cap);
+            } else {
+                int32_t diag = prev[d + 1] + (x[i - 1] != y[j - 1]);
+                int32_t up = prev[d + 2] + 1;
+                int32_t left = cur[d] + 1;
+                v = diag < up ? diag : up;
+                v = v < left ? v : left;
+                if (v > cap) v = cap;
+            }
+            cur[d + 1] = v;
+            if (v < row_min) row_min = v;
+        }
+        int32_t *tmp = prev; prev = cur; cur = tmp;
+        cur[0] = cur[W + 1] = cap;
+        if (row_min >= cap) { free(prev); free(cur); return cap; }
+    }
+    int32_t res = prev[(ly - lx) + K + 1];
+    free(prev); free(cur);
+    return res;
+}
+
+/* Brute-force join (Section 1) with the cutoff DP: every pair i<j with ED <= K,
+   written to out (capacity entries at most); returns the count. */
+int64_t or_join_bruteforce_cutoff(const uint8_t *data, const int64_t *offsets, int64_t n, int32_t K,
+                                  uint64_t *out, int64_t capacity) {
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            int32_t d = or_ed_banded_cutoff(data + offsets[i], offsets[i + 1] - offsets[i],
+                                            data + offsets[j], offsets[j + 1] - offsets[j], K);
+            if (d >= 0 && d <= K) {
+                if (cnt < capacity && out) out[cnt] = ((uint64_t)i << 32) | (uint64_t)j;
+                cnt++;
+            }
+        }
+    return cnt;
+}
+
 /* Wagner-Fischer full DP (the definition of edit distance, Section 1). */
 int64_t or_ed_full(const uint8_t *x, int64_t lx, const uint8_t *y, int64_t ly) {
     int64_t *prev = (int64_t *)malloc((size_t)(ly + 1) * sizeof(int64_t));

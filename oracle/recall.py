@@ -1,0 +1,49 @@
+"""Recall of EmbedJoin against the brute-force join (Section 1's definition), on
+seeded samples of each workload. The method's pair set comes from the oracle's
+join (Alg. 3 with Alg. 2; the GPU path is bit-identical to it). The true pair
+set is every pair with ED <= K, from the brute-force join with the cutoff DP.
+Test infrastructure: it calls only the oracle and the seeded input generators.
+
+    python -m oracle.recall            # one JSON line per (workload, K)
+"""
+import json
+import time
+
+import oracle
+from paper_1702_00093_gb300 import synth
+
+
+def samples():
+    """(name, string set, Ks, params(K)) for every join workload, at sizes the
+    brute force finishes in seconds."""
+    small = synth.SMALL_DNA_PARAMS
+    yield ("small DNA, n=1000 (the full workload)", synth.small_dna(), [small["K"]],
+           lambda K: dict(r=small["r"], m=small["m"], z=small["z"], seed=small["seed"], L=0))
+    yield ("long DNA, 20 clusters of 10 (n=200)", synth.long_dna(n_clusters=20, seed=1002), [50, 150, 250],
+           synth.long_dna_params)
+    yield "protein-like, n=1000", synth.protein_like(1003, 1000), list(synth.PROTEIN_KS), synth.protein_params
+    yield "text-like, n=300", synth.text_like(1004, 300), list(synth.TEXT_KS), synth.text_params
+
+
+def main():
+    oracle.build()
+    for name, ss, Ks, params in samples():
+        for K in Ks:
+            p = params(K)
+            t0 = time.perf_counter()
+            res = oracle.join(ss.data, ss.offsets, ss.alphabet, K=K, r=p["r"], m=p["m"], z=p["z"], seed=p["seed"],
+                              L=p.get("L", 0), keep_candidates=False)
+            t1 = time.perf_counter()
+            truth = oracle.join_bruteforce(ss.data, ss.offsets, K, cutoff=True)
+            t2 = time.perf_counter()
+            got, want = set(res.pairs.tolist()), set(truth.tolist())
+            found = len(got & want)
+            print(json.dumps({"workload": name, "K": K, "n": ss.n, "true_pairs": len(want), "found": found,
+                              "recall": found / len(want) if want else None,
+                              "precision": found / len(got) if got else None,
+                              "candidates": res.n_candidates, "join_s": round(t1 - t0, 2),
+                              "bruteforce_s": round(t2 - t1, 2)}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

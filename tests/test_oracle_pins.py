@@ -209,6 +209,31 @@ def _rle(seq):
     return runs
 
 
+def test_cutoff_dp_equals_banded_dp_and_bruteforce():
+    # Ukkonen's cutoff only stops the band DP early: min(ED, K+1) is unchanged,
+    # on random, similar and equal pairs, and the brute-force join is the same.
+    rng = np.random.default_rng(21)
+    lut = np.frombuffer(b"ACGT", np.uint8)
+    for _ in range(300):
+        a = lut[rng.integers(0, 4, size=int(rng.integers(0, 120)))].tobytes()
+        if rng.random() < 0.5:
+            b = bytearray(a)
+            for _ in range(int(rng.integers(0, 12))):
+                if b and rng.random() < 0.5:
+                    del b[int(rng.integers(0, len(b)))]
+                else:
+                    b.insert(int(rng.integers(0, len(b) + 1)), int(lut[rng.integers(0, 4)]))
+            b = bytes(b)
+        else:
+            b = lut[rng.integers(0, 4, size=int(rng.integers(0, 120)))].tobytes()
+        for K in (0, 1, 3, 8, 20, 60):
+            assert oracle.ed_banded_cutoff(a, b, K) == oracle.ed_banded(a, b, K), (a, b, K)
+    ss = synth.dna_clusters(5, 8, 6, 15, 40, edits_mean=3.0)
+    for K in (1, 3, 6):
+        assert np.array_equal(oracle.join_bruteforce(ss.data, ss.offsets, K, cutoff=True),
+                              oracle.join_bruteforce(ss.data, ss.offsets, K))
+
+
 def test_cgk_structure_invariants():
     # Alg. 1 emits x[i] for one or more steps before moving to x[i+1], then
     # pads with bottom: the output has length out_len, bottom only as a
