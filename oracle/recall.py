@@ -5,8 +5,10 @@ set is every pair with ED <= K, from the brute-force join with the cutoff DP.
 Test infrastructure: it calls only the oracle and the seeded input generators.
 
     python -m oracle.recall            # one JSON line per (workload, K)
+    python -m oracle.recall --sweep-z  # long DNA and text-like: recall and candidates per z
 """
 import json
+import sys
 import time
 
 import oracle
@@ -25,8 +27,27 @@ def samples():
     yield "text-like, n=300", synth.text_like(1004, 300), list(synth.TEXT_KS), synth.text_params
 
 
+def sweep_z():
+    """Recall and candidate count of the long-DNA and text-like samples for each
+    number of samples per function z (r, m, L and the seed as in the workload)."""
+    for name, ss, Ks, params in list(samples())[1::2]:
+        for K in Ks:
+            truth = set(oracle.join_bruteforce(ss.data, ss.offsets, K, cutoff=True).tolist())
+            p = params(K)
+            for z in range(max(2, p["z"] - 8), p["z"] + 1):
+                res = oracle.join(ss.data, ss.offsets, ss.alphabet, K=K, r=p["r"], m=p["m"], z=z, seed=p["seed"],
+                                  L=p.get("L", 0), keep_candidates=False)
+                found = len(set(res.pairs.tolist()) & truth)
+                print(json.dumps({"workload": name, "K": K, "z": z, "paper_rule_z": p["z"], "true_pairs": len(truth),
+                                  "found": found, "recall": found / len(truth) if truth else None,
+                                  "candidates": res.n_candidates}), flush=True)
+
+
 def main():
     oracle.build()
+    if "--sweep-z" in sys.argv:
+        sweep_z()
+        return
     for name, ss, Ks, params in samples():
         for K in Ks:
             p = params(K)
