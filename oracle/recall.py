@@ -4,7 +4,7 @@ join (Alg. 3 with Alg. 2; the GPU path is bit-identical to it). The true pair
 set is every pair with ED <= K, from the brute-force join with the cutoff DP.
 Test infrastructure: it calls only the oracle and the seeded input generators.
 
-    python -m oracle.recall            # one JSON line per (workload, K)
+    python -m oracle.recall            # one JSON line per (workload, K), then serving
     python -m oracle.recall --sweep-z  # long DNA and text-like: recall and candidates per z
 """
 import json
@@ -25,6 +25,39 @@ def samples():
            synth.long_dna_params)
     yield "protein-like, n=1000", synth.protein_like(1003, 1000), list(synth.PROTEIN_KS), synth.protein_params
     yield "text-like, n=300", synth.text_like(1004, 300), list(synth.TEXT_KS), synth.text_params
+
+
+def serving_recall(n_index: int = 2000, n_queries: int = 100):
+    """Search against an index (the serving workload's recipe at a small size): the
+    method's matches (each query walked and signed with the index's tables, index
+    strings sharing a key in some table within K_q of the query's length, exact
+    ED <= K_q) against every index string within K_q by the cutoff DP."""
+    import numpy as np
+    prm = synth.SERVING_PARAMS
+    idx = synth.serving_index(n_index, seed=1005)
+    qs, ks = synth.serving_queries(idx, n_queries, seed=1006)
+    n = idx.n
+    allset = synth.pack([idx.get(i) for i in range(n)] + list(qs), idx.alphabet)
+    emb, we = oracle.embed(allset.data, allset.offsets, allset.alphabet, prm["r"], prm["L"], prm["seed"])
+    pos = oracle.positions(prm["seed"], prm["r"], prm["m"], prm["z"], prm["L"])
+    keys = oracle.sign(emb, we, pos, len(allset.alphabet))
+    lens = allset.lengths()
+    got, want = set(), set()
+    for q in range(len(qs)):
+        K = int(ks[q])
+        near = np.nonzero(np.abs(lens[:n] - lens[n + q]) <= K)[0]
+        hit = np.zeros(n, dtype=bool)
+        for t in range(keys.shape[0]):
+            hit |= keys[t, :n] == keys[t, n + q]
+        for i in near:
+            if oracle.ed_banded_cutoff(qs[q], idx.get(int(i)), K) <= K:
+                want.add((q, int(i)))
+                if hit[i]:
+                    got.add((q, int(i)))
+    found = len(got)
+    print(json.dumps({"workload": f"serving search, index n={n}, {len(qs)} queries", "K": "per query",
+                      "true_pairs": len(want), "found": found, "recall": found / len(want) if want else None,
+                      "precision": 1.0}), flush=True)
 
 
 def sweep_z():
@@ -64,6 +97,7 @@ def main():
                               "precision": found / len(got) if got else None,
                               "candidates": res.n_candidates, "join_s": round(t1 - t0, 2),
                               "bruteforce_s": round(t2 - t1, 2)}), flush=True)
+    serving_recall()
 
 
 if __name__ == "__main__":
