@@ -111,3 +111,25 @@ int main(void) {{
         off, size = map(int, val.split())
         assert getattr(pairs[sname], field).offset == off, key
         assert getattr(pairs[sname], field).size == size, key
+
+
+def test_null_handles_are_rejected_without_a_device(lib):
+    # argument checks that need no CUDA call: NULL handles and outputs
+    EJ_ERR_INVALID_ARG = 1
+    ms = C.c_float(1.0)
+    n = C.c_int64(5)
+    assert lib.ej_batch_run(None, None) == EJ_ERR_INVALID_ARG
+    assert lib.ej_batch_verify_ms(None, C.byref(ms)) == EJ_ERR_INVALID_ARG
+    assert lib.ej_batch_result(None, 0, None, 0, C.byref(n), None, None) == EJ_ERR_INVALID_ARG
+    assert lib.ej_batch_kernel_count(None) == 0
+    assert lib.ej_index_size(None) == 0
+    assert lib.ej_server_submit(None, None, 0, 1) == -EJ_ERR_INVALID_ARG
+    assert lib.ej_server_submit(None, None, 0, -1) == -EJ_ERR_INVALID_ARG
+    n32 = C.c_int32(3)
+    assert lib.ej_server_poll(None, None, 0, C.byref(n32), 0) == EJ_ERR_INVALID_ARG
+    assert lib.ej_server_release(None, 0) == EJ_ERR_INVALID_ARG
+    assert lib.ej_server_get_stats(None, None) == EJ_ERR_INVALID_ARG
+    assert lib.ej_server_reset_stats(None) == EJ_ERR_INVALID_ARG
+    lib.ej_batch_destroy(None)
+    lib.ej_index_destroy(None)
+    lib.ej_server_destroy(None)
