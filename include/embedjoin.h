@@ -319,9 +319,13 @@ void ej_batch_destroy(ej_batch *batch);
  *     buckets of the one with the smallest z, whose signatures are the coarsest
  *     (a signature of z samples is one of more samples modulo (|alphabet|+1)^z),
  *     each partner checked against the join's own signature and K; 1 keeps
- *     every join's own buckets. 2: the tables are sorted by (signature,
- *     length) and each record pairs with the window after it (the
- *     ej_lsh_candidates path; cheaper for huge buckets of uneven lengths).
+ *     every join's own buckets. Tables of up to 21845 records are bucketed in
+ *     shared memory, one block per table, which pays for small buckets only.
+ *     2: the tables are sorted by (signature, length) and each record pairs
+ *     with the window after it (the ej_lsh_candidates path). It is much
+ *     cheaper when a few signatures collect thousands of strings, e.g. short
+ *     strings whose walks end early and whose samples are mostly the bottom
+ *     symbol.
  */
 typedef struct {
     int32_t mode;
