@@ -19,6 +19,8 @@ Parity status per function:
                                      values)
   join                             : pinned (running example output; worked
                                      example; precision against brute force)
+  keys (streamed walk + signatures) : pinned equal to sign(embed(...))
+  verify_cutoff                    : pinned equal to verify (banded DP)
 """
 from __future__ import annotations
 
@@ -86,6 +88,10 @@ def lib():
             L.or_ed_full.argtypes = [vp, i64, vp, i64]
             L.or_verify.restype = None
             L.or_verify.argtypes = [vp, vp, vp, i64, i32, vp]
+            L.or_verify_cutoff.restype = None
+            L.or_verify_cutoff.argtypes = [vp, vp, vp, i64, i32, vp]
+            L.or_keys_range.restype = C.c_int
+            L.or_keys_range.argtypes = [vp, vp, i64, i64, vp, u32, u32, u32, u32, u32, u64, vp, vp]
             L.or_join_bruteforce.restype = i64
             L.or_join_bruteforce.argtypes = [vp, vp, i64, i32, vp, i64]
             L.or_join_bruteforce_cutoff.restype = i64
@@ -177,6 +183,24 @@ def sign(emb: np.ndarray, walk_end: np.ndarray, pos: np.ndarray, alpha: int) -> 
     return keys
 
 
+def keys(data, offsets, alphabet: bytes, r: int, m: int, z: int, L: int, seed: int,
+         lo: int = 0, hi: int | None = None) -> np.ndarray:
+    """Signature keys uint64 [r*m][hi-lo] of strings lo..hi-1, walked and signed
+    one string at a time (the same keys as sign(embed(...)) over [0, L))."""
+    data, offsets = _strings(data, offsets)
+    n = offsets.shape[0] - 1
+    hi = n if hi is None else hi
+    ab = _u8(alphabet)
+    pos = positions(seed, r, m, z, L)
+    out = np.zeros((r * m, max(hi - lo, 0)), dtype=np.uint64)
+    if hi > lo:
+        rc = lib().or_keys_range(_p(data), _p(offsets), lo, hi, _p(ab), len(alphabet), r, m, z, L, seed,
+                                 _p(pos), _p(out))
+        if rc != 0:
+            raise ValueError(f"oracle keys failed: {rc}")
+    return out
+
+
 def candidates(data, offsets, keys: np.ndarray, K: int) -> np.ndarray:
     """Algorithm 3's candidate set (sorted unique uint64 pairs)."""
     data, offsets = _strings(data, offsets)
@@ -217,6 +241,15 @@ def verify(data, offsets, pairs: np.ndarray, K: int) -> np.ndarray:
     pairs = np.ascontiguousarray(pairs, dtype=np.uint64)
     flags = np.zeros(max(pairs.shape[0], 1), dtype=np.uint8)
     lib().or_verify(_p(data), _p(offsets), _p(pairs), pairs.shape[0], K, _p(flags))
+    return flags[:pairs.shape[0]]
+
+
+def verify_cutoff(data, offsets, pairs: np.ndarray, K: int) -> np.ndarray:
+    """verify() with the DP stopped at Ukkonen's cutoff (same flags)."""
+    data, offsets = _strings(data, offsets)
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint64)
+    flags = np.zeros(max(pairs.shape[0], 1), dtype=np.uint8)
+    lib().or_verify_cutoff(_p(data), _p(offsets), _p(pairs), pairs.shape[0], K, _p(flags))
     return flags[:pairs.shape[0]]
 
 

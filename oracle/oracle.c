@@ -166,6 +166,36 @@ void or_sign_all(const uint8_t *emb, const int64_t *walk_end, int64_t n, uint32_
                     pos + ((uint64_t)l * m + f) * z, z, alpha);
 }
 
+/* Signatures of strings [s0, s1) straight from the walks (Alg. 1, then the
+ * AND signature of Section 3.2 for every function), one string and one
+ * embedding at a time, so large sets need no [r][n][out_len] buffer. The walk
+ * runs for steps [0, L) only: every sampled position is below L, and a walk
+ * that has not finished by step L reads the same symbols there as a longer
+ * one. keys is [r*m][s1-s0]; pos is [r][m][z] (or_positions_all). Returns 0
+ * or an error code (a byte outside the alphabet). */
+int or_keys_range(const uint8_t *data, const int64_t *offsets, int64_t s0, int64_t s1,
+                  const uint8_t *alphabet, uint32_t alpha, uint32_t r, uint32_t m, uint32_t z,
+                  uint32_t L, uint64_t seed, const uint32_t *pos, uint64_t *keys) {
+    uint8_t code_of[256];
+    memset(code_of, 255, sizeof code_of);
+    for (uint32_t c = 0; c < alpha; c++) code_of[alphabet[c]] = (uint8_t)c;
+    for (int64_t p = offsets[s0]; p < offsets[s1]; p++)
+        if (code_of[data[p]] == 255) return OR_ERR_ARG;
+    uint8_t *t = (uint8_t *)malloc((size_t)(L ? L : 1));
+    if (!t) return OR_ERR_OOM;
+    const int64_t cnt = s1 - s0;
+    for (uint32_t l = 0; l < r; l++)
+        for (int64_t s = s0; s < s1; s++) {
+            int64_t we = or_cgk_embed(data + offsets[s], offsets[s + 1] - offsets[s], code_of, alpha,
+                                      seed, l, (int64_t)L, NULL, 0, t);
+            for (uint32_t f = 0; f < m; f++)
+                keys[((int64_t)l * m + f) * cnt + (s - s0)] =
+                    or_signature_key(t, we, pos + ((uint64_t)l * m + f) * z, z, alpha);
+        }
+    free(t);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* EmbedJoin candidate generation, Algorithm 3 (sliding window over buckets) */
 /* ------------------------------------------------------------------------ */
@@ -455,6 +485,18 @@ void or_verify(const uint8_t *data, const int64_t *offsets, const uint64_t *pair
         int64_t a = (int64_t)(pairs[k] >> 32), b = (int64_t)(pairs[k] & 0xffffffffu);
         int32_t d = or_ed_banded(data + offsets[a], offsets[a + 1] - offsets[a], data + offsets[b],
                                  offsets[b + 1] - offsets[b], K);
+        flags[k] = (d >= 0 && d <= K) ? 1 : 0;
+    }
+}
+
+/* The verification loop with the cutoff DP (same flags as or_verify, faster
+ * on pairs far above K): flags[k] = 1 iff ED(pair k) <= K. */
+void or_verify_cutoff(const uint8_t *data, const int64_t *offsets, const uint64_t *pairs, int64_t np,
+                      int32_t K, uint8_t *flags) {
+    for (int64_t k = 0; k < np; k++) {
+        int64_t a = (int64_t)(pairs[k] >> 32), b = (int64_t)(pairs[k] & 0xffffffffu);
+        int32_t d = or_ed_banded_cutoff(data + offsets[a], offsets[a + 1] - offsets[a],
+                                        data + offsets[b], offsets[b + 1] - offsets[b], K);
         flags[k] = (d >= 0 && d <= K) ? 1 : 0;
     }
 }

@@ -402,3 +402,33 @@ def test_join_precision_and_recall_small_dna():
     # every candidate that passed verification is a true pair and vice versa
     cand = set(_pairs(res.candidates))
     assert got == cand & truth
+
+
+def test_streamed_keys_equal_signatures_of_materialised_embeddings():
+    # The streamed form (walk one string over [0, L), sign it, drop the walk)
+    # must give the keys of Alg. 1's full embedding signed by Section 3.2's AND
+    # functions, whatever range of strings it is asked for; strings whose walks
+    # do not finish by L (long ones) and empty strings included.
+    rng = np.random.default_rng(31)
+    for alphabet, L in [(b"ACGT", 60), (synth.TEXT, 150)]:
+        lut = np.frombuffer(alphabet, np.uint8)
+        strs = [lut[rng.integers(0, len(alphabet), size=int(rng.integers(0, 140)))].tobytes()
+                for _ in range(90)]
+        ss = synth.pack(strs, alphabet)
+        out_len = max(3 * int(ss.lengths().max()), L)
+        emb, we = oracle.embed(ss.data, ss.offsets, alphabet, 3, out_len, seed=4)
+        want = oracle.sign(emb, we, oracle.positions(4, 3, 5, 6, L), len(alphabet))
+        got = np.concatenate([oracle.keys(ss.data, ss.offsets, alphabet, 3, 5, 6, L, 4, lo, hi)
+                              for lo, hi in [(0, 17), (17, 18), (18, 90)]], axis=1)
+        assert np.array_equal(got, want)
+
+
+def test_cutoff_verify_equals_banded_verify():
+    ss = synth.dna_clusters(9, 10, 8, 20, 160, edits_mean=6.0)
+    rng = np.random.default_rng(5)
+    pairs = np.array(sorted({(int(min(a, b)) << 32) | int(max(a, b))
+                             for a, b in rng.integers(0, ss.n, size=(400, 2)) if a != b}), dtype=np.uint64)
+    for K in (0, 2, 6, 15, 40):
+        v = oracle.verify(ss.data, ss.offsets, pairs, K)
+        assert np.array_equal(oracle.verify_cutoff(ss.data, ss.offsets, pairs, K), v)
+    assert v.sum() > 10
