@@ -155,6 +155,21 @@ int ej_set_timing(ej_ctx *ctx, int enable);
 int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, int warps_per_block);
 
 /*
+ * Failure detection (the paper has no counterpart): the persistent verifier
+ * (ej_schedule.mode 1, and the merged launch of a batch) bounds the passes of
+ * each warp's work loop, so that a kernel that could not finish its queue
+ * stops instead of running on. When the bound runs out the kernel records it
+ * and returns, and the call reports EJ_ERR_TIMEOUT; the context stays usable.
+ * passes: loop passes per warp (one pass advances the warp's pairs by 64
+ * columns); 0 restores the default of 2^24, far above what any valid input
+ * needs. A small value is a test hook that makes the bound run out on
+ * ordinary input. Calls made after this one use it; a graph-captured batch
+ * keeps the value it was created with. Errors: EJ_ERR_INVALID_ARG for
+ * passes < 0.
+ */
+int ej_set_loop_bound(ej_ctx *ctx, int64_t passes);
+
+/*
  * Similarity search against a resident index (EmbedJoin's structure kept on the
  * device; the paper has no serving counterpart). ej_index_create packs the
  * strings, builds the walk tables and sampled positions of `params` (r, m, z, L,
@@ -428,15 +443,19 @@ int ej_verify(ej_ctx *ctx, const ej_strings *strings, const ej_params *params,
  * is reserved up front by another allocator, and services that must not call
  * cudaMalloc/cudaFree on their request path (those calls can synchronise the
  * device). No context is needed; the call never allocates. Its scratch is one
- * file-scope device array of EJ_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU
- * which loads the library keeps until the process exits.
+ * file-scope device array of EJ_NOALLOC_SCRATCH_BYTES (64 MiB). A GPU holds it
+ * from when the array's module is loaded on it until the process exits: with
+ * lazy module loading (the CUDA default) that is the first call on that
+ * device, with eager loading (CUDA_MODULE_LOADING=EAGER) the library load.
  *  - strings->bytes, strings->offsets, pairs and out must be device memory;
  *    params supplies K and the alphabet only; out holds n_pairs entries.
  *  - Output and result are those of ej_verify (passing pairs in input order,
  *    count in *n_out); the call synchronises `stream` before returning.
  *  - Scratch needed: about 16 bytes per string, the packed codes (total bytes x
  *    2/8 for alphabets of at most 4 symbols, else x 1) and 9 bytes per pair;
- *    beyond EJ_NOALLOC_SCRATCH_BYTES the call returns EJ_ERR_TOO_LARGE.
+ *    beyond EJ_NOALLOC_SCRATCH_BYTES the call returns EJ_ERR_TOO_LARGE (checked
+ *    before any scratch is written, also for counts whose byte size would
+ *    overflow).
  *  - All calls share the array and it keeps the previous call's contents (the
  *    call clears what must start at zero). Calls whose GPU work overlaps, on
  *    different streams or host threads, race on it: serialise them.

@@ -64,6 +64,7 @@ struct ej_ctx {
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
     ej_schedule sched{0, 0, 0, 0, 0, 0};   // ej_join's back-half schedule (ej_set_schedule)
+    int64_t loop_bound = 0;   // persistent verifier: loop passes per warp (ej_set_loop_bound; 0 = default)
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -774,6 +775,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     CKS(ensure_t(ctx, B_TICKETS, (size_t)SM_TICKETS, &tickets));
     CK(cudaMemsetAsync(tickets, 0, SM_TICKETS * sizeof(unsigned int), s));
     VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
+    vo.max_passes = ctx->loop_bound;
     const VerifyConfig &vc = bs.vc;
     if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
     if (pq_threads > 0)
@@ -812,6 +814,8 @@ int back_read(ej_ctx *ctx, unsigned long long hc[8], cudaStream_t s) {
     memcpy(hc, ctx->h_cnt, 8 * sizeof(unsigned long long));
     hc[6] &= 0xffffffffull;
     if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+    if ((uint32_t)hc[6] & DERR_TIMEOUT)
+        return fail(ctx, EJ_ERR_TIMEOUT, "the persistent verifier gave up after its bound of loop passes per warp");
     if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
     return EJ_OK;
 }
@@ -1093,6 +1097,7 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
     vo.sm_tickets = b->mtickets;
     vo.segs = b->segs_dev;
     vo.nseg = (int32_t)b->merged.size();
+    vo.max_passes = ctx->loop_bound;
     const Plan &pl = b->pl;
     CK(launch_verify_pq(b->mW1, b->mthreads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
                         ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1, pl.packed, pl.pofs,
@@ -1392,6 +1397,12 @@ int ej_set_timing(ej_ctx *c, int enable) {
     return EJ_OK;
 }
 
+int ej_set_loop_bound(ej_ctx *c, int64_t passes) {
+    if (!c || passes < 0) return EJ_ERR_INVALID_ARG;
+    c->loop_bound = passes;
+    return EJ_OK;
+}
+
 int ej_set_verify_config(ej_ctx *ctx, int G, int V, int warps) {
     if (!ctx) return EJ_ERR_INVALID_ARG;
     if (G == 0 && V == 0) {
@@ -1671,6 +1682,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         j.sub->vG = ctx->vG;
         j.sub->vV = ctx->vV;
         j.sub->vWarps = ctx->vWarps;
+        j.sub->loop_bound = ctx->loop_bound;
         if (cudaStreamCreateWithFlags(&j.side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&j.verified, cudaEventDisableTiming) != cudaSuccess ||
@@ -1826,6 +1838,8 @@ int ej_batch_result(ej_batch *b, int32_t i, uint64_t *out, int64_t capacity, int
     hc[6] = b->h_stat[16 * (size_t)i + 8] & 0xffffffffull;
     hc[7] = 0;
     if ((uint32_t)hc[6] & DERR_PAIR) return fail(ctx, EJ_ERR_INVALID_ARG, "internal: pair index out of range");
+    if ((uint32_t)hc[6] & DERR_TIMEOUT)
+        return fail(ctx, EJ_ERR_TIMEOUT, "the persistent verifier gave up after its bound of loop passes per warp");
     if ((uint32_t)hc[6] & DERR_GUARD) return fail(ctx, EJ_ERR_CUDA, "internal: a work bound was exceeded");
     if (hc[0] > j.cap)
         return fail(ctx, EJ_ERR_CAPACITY, "raw pairs (%llu) exceed the batch's capacity (%llu): re-create the batch",

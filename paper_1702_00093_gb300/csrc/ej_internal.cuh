@@ -351,6 +351,9 @@ struct VerifyOut {
     // join's outputs; pairs, np, app*, work and err above are not used.
     const VerifySeg *segs;
     int32_t nseg;
+    // Persistent verifier: loop passes per warp before it gives up and sets
+    // DERR_TIMEOUT (0 = the default bound, 2^24).
+    int64_t max_passes;
 };
 
 constexpr int SM_TICKETS = 1024;

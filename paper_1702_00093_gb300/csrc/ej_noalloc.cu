@@ -10,7 +10,9 @@
 // cudaMalloc, cudaFree or any allocating library routine.
 //
 // Consequences the caller must know:
-//  - every GPU that loads this library holds the array until the process exits;
+//  - every GPU on which the array's module is loaded holds it until the process
+//    exits: with lazy module loading (the CUDA default) from the first call on
+//    that device, with eager loading from when the library is loaded;
 //  - all calls share the array and it keeps the previous call's contents, so two
 //    calls whose GPU work overlaps (different streams or host threads) race;
 //  - the first call on a device looks up the array's device address
@@ -101,6 +103,11 @@ extern "C" int ej_verify_noalloc(const ej_strings *S, const ej_params *p, const 
     NA_CK(cudaMemcpyAsync(&total, S->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
     if (total < 0) return EJ_ERR_INVALID_ARG;
+    // sizes far beyond the array are rejected before any size arithmetic that
+    // could wrap: at least 16 bytes per string, 9 per pair, 1/4 per byte
+    if (n > (int64_t)(kScratchBytes / 16) || n_pairs > (int64_t)(kScratchBytes / 9) ||
+        total > (int64_t)kScratchBytes * 4)
+        return EJ_ERR_TOO_LARGE;
 
     // carve the scratch array
     const int B = packed_bits_for(alpha);

@@ -341,6 +341,10 @@ CollectStatus slot_collect(Slot &sl, std::vector<uint64_t> *pairs, std::string *
         *why = "a query failed validation";
         return COLLECT_ERROR;
     }
+    if (err & DERR_TIMEOUT) {
+        *why = "the persistent verifier gave up after its bound of loop passes";
+        return COLLECT_ERROR;
+    }
     if (err & (DERR_PAIR | DERR_GUARD)) {
         *why = "internal verifier error";
         return COLLECT_ERROR;

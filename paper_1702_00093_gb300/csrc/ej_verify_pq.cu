@@ -28,7 +28,7 @@ namespace ej {
 
 namespace {
 
-constexpr int64_t kMaxIters = 1ll << 24;   // loop passes per warp before the kernel gives up
+constexpr int64_t kMaxIters = 1ll << 24;   // default bound on loop passes per warp (VerifyOut::max_passes)
 
 // 64/B symbols of a packed string starting at symbol o (any int64; symbols
 // outside [0, len) read as code 0), symbol t in bits [B*t, B*t + B).
@@ -157,7 +157,8 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     int32_t kp = K;          // the pair's threshold (<= K, the band)
     int sg = 0;              // the pair's join (merged launch)
     int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
-    int64_t iters = 0;       // loop passes of this warp (bounded, see kMaxIters)
+    int64_t iters = 0;       // loop passes of this warp (bounded by max_iters)
+    const int64_t max_iters = vo.max_passes > 0 ? vo.max_passes : kMaxIters;
     int base = 0;
     uint64_t Pv[W1], Mv[W1];
 #pragma unroll
@@ -170,8 +171,10 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     };
 
     while (true) {
-        if (++iters > kMaxIters) {
-            if (lane == 0) warp_err((uint32_t)DERR_GUARD);
+        if (++iters > max_iters) {
+            // every lane counts the same passes, so the whole warp leaves here
+            // (no block barrier follows); the call reports EJ_ERR_TIMEOUT
+            if (lane == 0) warp_err((uint32_t)DERR_TIMEOUT);
             break;
         }
         // refill free slots (both lanes of a slot agree on `have` and `exhausted`)

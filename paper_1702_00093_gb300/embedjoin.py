@@ -29,7 +29,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
-            "ej_set_schedule", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_set_schedule", "ej_set_loop_bound", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
             "ej_batch_verify_ms",
             "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
             "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
@@ -140,6 +140,8 @@ def lib():
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
+        L.ej_set_loop_bound.argtypes = [vp, C.c_int64]
+        L.ej_set_loop_bound.restype = C.c_int
         L.ej_set_schedule.argtypes = [vp, C.POINTER(_Schedule)]
         L.ej_set_schedule.restype = C.c_int
         L.ej_batch_create.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), C.c_int32, C.c_int32,
@@ -281,6 +283,11 @@ class Context:
         """ej_join's back-half schedule (ej_schedule); zeros = defaults. See the header."""
         sc = _Schedule(mode, slots_per_warp, warps_per_subpartition, order, buckets, chain)
         self._check(lib().ej_set_schedule(self._h, C.byref(sc)), "ej_set_schedule")
+
+    def set_loop_bound(self, passes: int = 0):
+        """Loop passes per warp of the persistent verifier before it gives up
+        (EJ_ERR_TIMEOUT); 0 = the default bound."""
+        self._check(lib().ej_set_loop_bound(self._h, passes), "ej_set_loop_bound")
 
     def set_timing(self, on: bool = True):
         self._check(lib().ej_set_timing(self._h, 1 if on else 0), "ej_set_timing")

@@ -3,11 +3,15 @@ allocate device memory (memory reserved up front by another allocator, or a
 request path where cudaMalloc/cudaFree must not run because they can
 synchronise the device). Its scratch is a fixed device array inside the
 library. The test calls it through the C ABI twice in a row and checks both
-results against ej_verify on the same pairs (integer work: identical output).
-This file is collected last on purpose."""
+results against ej_verify and against the CPU oracle on the same pairs
+(integer work: identical output), with the device's free memory unchanged
+across the two calls. The file is named so that pytest collects it after the
+other test files (a run that stops at the first failure has run them all);
+the tests themselves pass alone in a fresh process or after the others."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1702_00093_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -19,6 +23,7 @@ def test_verify_noalloc_matches_verify_twice():
         pytest.skip("no CUDA device")
     from paper_1702_00093_gb300 import build
     build.build()
+    oracle.build()
     from paper_1702_00093_gb300 import embedjoin as ej
 
     dev = "cuda:0"
@@ -46,12 +51,18 @@ def test_verify_noalloc_matches_verify_twice():
             k_ref = ctx.verify(s, params, pt, ref)
             want = ref[:k_ref].cpu().numpy()
             assert k_ref > 0
-            for _ in range(2):   # the fixed scratch keeps the last call's contents
-                out = torch.full_like(pt, -1)
+            flags = oracle.verify(ss.data, ss.offsets, arr, K)
+            assert np.array_equal(want.view(np.uint64), arr[flags == 1])
+            outs = [torch.full_like(pt, -1) for _ in range(3)]
+            ej.verify_noalloc(s, params, pt, outs[2])     # loads every module it uses
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            for out in outs[:2]:   # the fixed scratch keeps the last call's contents
                 k = ej.verify_noalloc(s, params, pt, out)
                 torch.cuda.synchronize()
                 assert k == k_ref
                 assert np.array_equal(out[:k].cpu().numpy(), want)
+            assert torch.cuda.mem_get_info()[0] == free0
     finally:
         ctx.close()
 
