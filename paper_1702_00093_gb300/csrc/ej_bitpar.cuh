@@ -230,14 +230,23 @@ __device__ __forceinline__ void bd_build(uint64_t *ring, int T_, int slot, const
     } else {
         for (uint32_t c = 0; c < alpha; c++) ring[(size_t)(c * R + slot) * T_] = 0ull;
         if (valid_m) {
+            // each 16-symbol chunk is read once; every symbol sets its bit with a
+            // shared-memory OR that returns nothing, so consecutive symbols (which
+            // may hit the same word) do not wait on one another
             const int64_t ks = k0 + t_lo, ke = k0 + (t_hi < 64 ? t_hi : 64);
-            for (int64_t kk = ks; kk < ke; kk++) {
-                const uint4 v = xc[kk >> 4];
-                const uint32_t sel = (uint32_t)(kk & 15);
-                const uint32_t wv = (sel < 8) ? ((sel < 4) ? v.x : v.y) : ((sel < 12) ? v.z : v.w);
-                const uint32_t c = (wv >> ((sel & 3u) * 8u)) & 0xFFu;
-                const uint32_t bit = rev ? (uint32_t)(63 - (kk - k0)) : (uint32_t)(kk - k0);
-                if (c < alpha) ring[(size_t)(c * R + slot) * T_] |= 1ull << bit;
+            for (int64_t ch = ks >> 4; ch <= ((ke - 1) >> 4); ch++) {
+                const uint4 v = xc[ch];
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const int64_t kk = ch * 16 + q;
+                    const uint32_t w = q < 4 ? v.x : q < 8 ? v.y : q < 12 ? v.z : v.w;
+                    const uint32_t c = (w >> ((q & 3) * 8)) & 0xFFu;
+                    if (kk >= ks && kk < ke && c < alpha) {
+                        const uint32_t bit = rev ? (uint32_t)(63 - (kk - k0)) : (uint32_t)(kk - k0);
+                        atomicOr(reinterpret_cast<unsigned long long *>(ring + (size_t)(c * R + slot) * T_),
+                                 1ull << bit);
+                    }
+                }
             }
         }
     }

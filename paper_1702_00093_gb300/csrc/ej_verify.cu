@@ -607,6 +607,7 @@ static cudaError_t launch_g1(const uint4 *packed, const uint64_t *pofs, const in
 // two halves run concurrently, halving the sequential chain of a pair.
 
 constexpr int VBD_THREADS = 128;
+constexpr int VBD_CHECK = 32;   // columns between the joint early-exit tests (a power of two)
 
 template <int W1, int B>
 __global__ void __launch_bounds__(VBD_THREADS)
@@ -689,6 +690,32 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             int32_t next_move = K + 1 + 64;   // first column whose window starts one word lower
             int32_t j = 1;
             for (; j <= ncols; j++) {
+                if ((j & (VBD_CHECK - 1)) == 0 && j <= n1) {
+                    // early exit, decided by both halves together: the minimum of each
+                    // half's window at its column j-1 (row 64*k0, value T, included).
+                    // A path of cost <= K crosses both columns inside the band, where
+                    // the values are exact, so the two minima add up to at most its
+                    // cost. Both lanes of the pair reach every such column (j <= n1 <=
+                    // n - n1), so they exchange and leave together.
+                    int32_t run = 0, mn = 0;
+#pragma unroll
+                    for (int v = 0; v < W1; v++) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
+                                                 ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
+                            const int32_t cand = run + s_nmin[idx];
+                            mn = cand < mn ? cand : mn;
+                            run += s_nsum[idx];
+                        }
+                    }
+                    const int32_t lb = T + mn;
+                    const int32_t lb_other = __shfl_xor_sync(pmask, lb, 1);
+                    if (lb + lb_other > K) {
+                        rejected = true;
+                        break;
+                    }
+                }
                 if (j == next_move) {
                     next_move += 64;
                     // drop the top word into T, shift the window down one word
@@ -705,26 +732,6 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                         soff[v] = (uint32_t)(sl >= R ? sl - R : sl) * T_;
                     }
                     bd_build<B, R>(ring, T_, (int)(soff[W1 - 1] / T_), xc, m, k0 + W1 - 1, rev, alpha);
-                    if ((k0 & 1) == 0) {
-                        // early exit: minimum over the window exceeds K. Row 64*k0 (value T)
-                        // is still the top of the band at column j-1, so it takes part.
-                        int32_t run = 0, mn = 0;
-#pragma unroll
-                        for (int v = 0; v < W1; v++) {
-#pragma unroll
-                            for (int q = 0; q < 16; q++) {
-                                const uint32_t idx = (uint32_t)((Pv[v] >> (4 * q)) & 15u) |
-                                                     ((uint32_t)((Mv[v] >> (4 * q)) & 15u) << 4);
-                                const int32_t cand = run + s_nmin[idx];
-                                mn = cand < mn ? cand : mn;
-                                run += s_nsum[idx];
-                            }
-                        }
-                        if (T + mn > K) {
-                            rejected = true;
-                            break;
-                        }
-                    }
                 }
                 uint32_t c;
                 if (rev) { c = yb.code(); yb.advance(); }

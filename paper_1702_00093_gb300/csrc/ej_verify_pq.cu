@@ -18,9 +18,10 @@
 // so that a batch larger than the slots keeps every slot busy until the queue
 // runs dry.
 //
-// Early exit. At every window move each half computes the minimum value m_h of
-// its window (including the row above it). A path of cost <= K crosses both
-// halves' current columns inside their bands, where the values are exact, so
+// Early exit. Once per chunk, at the chunk position of the window moves, each
+// half that is still running computes the minimum value m_h of its window
+// (including the row above it). A path of cost <= K crosses both halves'
+// current columns inside their bands, where the values are exact, so
 // m_fwd + m_bwd > K proves ED > K; both lanes of the pair stop.
 #include "ej_bitpar.cuh"
 
@@ -60,7 +61,7 @@ __device__ __forceinline__ uint64_t sym_reverse(uint64_t u) {
 }
 
 template <int W1, int B, int TPB>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, 1)
 verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
                  const uint64_t *__restrict__ pairs, int64_t np, int32_t K, int32_t nsm, int32_t spw_force,
@@ -300,7 +301,10 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         {
             // window move before column j = jbase + smove, then the joint bound
             const int32_t j = jbase + smove;
-            const bool moving = have && !rejected && j == next_move && j <= ncols;
+            // every pair still running takes part in the joint bound, also before
+            // its first window move (short pairs have none)
+            const bool active = have && !rejected && j <= ncols;
+            const bool moving = active && j == next_move;
             int32_t lb = 0;
             if (moving) {
                 next_move += 64;
@@ -315,6 +319,8 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                     const int sl = base + W1 - 1;
                     build_word(sl >= R ? sl - R : sl, k0 + W1 - 1);
                 }
+            }
+            if (active) {
                 // minimum over the window at column j-1; row 64*k0 (value T) takes part
                 int32_t run = 0, mn = 0;
 #pragma unroll
@@ -331,7 +337,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 lb = Tacc + (j - 1) + mn;
             }
             const int32_t lb_other = __shfl_xor_sync(FULL, lb, 1);
-            if (moving && lb + lb_other > kp) {
+            if (active && lb + lb_other > kp) {
                 rejected = true;
                 rej_col = j;
                 lim = -1;

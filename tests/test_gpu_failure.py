@@ -29,9 +29,10 @@ def ej():
 
 
 def _case():
-    ss = synth.long_dna(n_clusters=3, seed=41)     # 30 strings of ~5000 symbols
-    p = synth.long_dna_params(150)
-    return ss, p
+    # 3 clusters of 8 DNA strings of 2500-3000 symbols, ~12 edits per member:
+    # every pair of a cluster is a candidate and most pass K = 60
+    ss = synth.dna_clusters(41, 3, 8, 2500, 3000, edits_mean=12.0)
+    return ss, dict(K=60, r=4, m=8, z=10, seed=3, L=2500)
 
 
 def test_loop_bound_runs_out_then_context_still_exact(ej):
@@ -44,7 +45,7 @@ def test_loop_bound_runs_out_then_context_still_exact(ej):
         s = ej.Strings.from_set(ss, DEV)
         params = ej.Params(alphabet=ss.alphabet, **p)
         c.set_schedule(mode=1)                     # the persistent verifier
-        c.set_loop_bound(2)                        # a pair of ~5000 columns needs ~80 passes
+        c.set_loop_bound(2)                        # a pair of ~2700 columns needs ~22 passes
         with pytest.raises(ej.EJError) as e:
             c.join(s, params, device=DEV)
         assert e.value.status == ej.EJ_ERR_TIMEOUT
@@ -69,7 +70,7 @@ def test_loop_bound_in_a_batch(ej):
     stream = torch.cuda.Stream()
     try:
         s = ej.Strings.from_set(ss, DEV)
-        params = [ej.Params(alphabet=ss.alphabet, **synth.long_dna_params(K)) for K in (50, 150)]
+        params = [ej.Params(alphabet=ss.alphabet, **dict(p, K=K)) for K in (20, 60)]
         c.set_schedule(mode=1)
         c.set_loop_bound(2)
         with torch.cuda.stream(stream):

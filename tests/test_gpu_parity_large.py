@@ -56,21 +56,19 @@ def _u64(t):
     return t.cpu().numpy().view(np.uint64) if hasattr(t, "cpu") else np.asarray(t, dtype=np.uint64)
 
 
-def _short_dna(n, seed, lo=8, hi=13):
-    rng = np.random.default_rng(seed)
-    lut = np.frombuffer(b"ACGT", np.uint8)
-    return synth.pack([lut[rng.integers(0, 4, size=int(rng.integers(lo, hi)))].tobytes() for _ in range(n)],
-                      b"ACGT")
-
-
 N_LARGE = 30000
+
+
+LARGE = dict(r=2, m=3, seed=9, L=40)
+LARGE_KZ = ((2, 8), (3, 7))
 
 
 @pytest.fixture(scope="module")
 def large_set():
-    ss = _short_dna(N_LARGE, 30)
-    ref = {K: oracle.join(ss.data, ss.offsets, b"ACGT", K=K, r=2, m=3, z=z, seed=9)
-           for K, z in ((1, 4), (2, 3))}
+    # 3000 clusters of 10 DNA strings of 20-28 symbols (~1.5 edits per member):
+    # buckets of a few to hundreds of records, ~2-3M candidates per join
+    ss = synth.dna_clusters(30, 3000, 10, 20, 28, edits_mean=1.5)
+    ref = {K: oracle.join(ss.data, ss.offsets, b"ACGT", K=K, z=z, **LARGE) for K, z in LARGE_KZ}
     return ss, ref
 
 
@@ -81,15 +79,16 @@ def test_join_global_and_radix_bucket_paths_equal_oracle(ej, ctx, large_set, buc
     sorted path whose per-table sort is the segmented radix sort (buckets 2),
     with the persistent (mode 1) and grid-strided (mode 2) verifiers."""
     ss, ref = large_set
+    assert ss.n == N_LARGE
     s = ej.Strings.from_set(ss, DEV)
-    params = ej.Params(K=1, r=2, m=3, z=4, seed=9, alphabet=b"ACGT")
+    params = ej.Params(K=2, z=8, alphabet=b"ACGT", **LARGE)
     try:
         ctx.set_schedule(mode=mode, buckets=buckets)
         pairs, st = ctx.join(s, params, device=DEV, capacity=1 << 20)
     finally:
         ctx.set_schedule()
-    want = ref[1]
-    assert want.n_candidates > 10000 and st.max_bucket > 20
+    want = ref[2]
+    assert want.n_candidates > 100000 and st.max_bucket > 20
     assert st.n_candidates == want.n_candidates
     assert np.array_equal(_u64(pairs), want.pairs)
 
@@ -100,31 +99,29 @@ def test_lsh_candidates_radix_path_equals_oracle(ej, ctx, large_set):
     sort, windows, pair sort-unique), then ej_verify."""
     ss, ref = large_set
     s = ej.Strings.from_set(ss, DEV)
-    params = ej.Params(K=1, r=2, m=3, z=4, seed=9, alphabet=b"ACGT")
+    params = ej.Params(K=2, z=8, alphabet=b"ACGT", **LARGE)
     keys = torch.zeros(params.r * params.m * ss.n, dtype=torch.int64, device=DEV)
     ctx.embed_sign(s, params, keys)
-    L = 3 * int(ss.lengths().max())
-    want_keys = oracle.keys(ss.data, ss.offsets, b"ACGT", 2, 3, 4, L, 9)
+    want_keys = oracle.keys(ss.data, ss.offsets, b"ACGT", params.r, params.m, params.z, params.L, params.seed)
     assert np.array_equal(_u64(keys).reshape(6, ss.n), want_keys)
-    cand_ref = oracle.candidates(ss.data, ss.offsets, want_keys, 1)
+    cand_ref = oracle.candidates(ss.data, ss.offsets, want_keys, 2)
     out = torch.empty(cand_ref.shape[0] + 16, dtype=torch.int64, device=DEV)
     n, mb = ctx.lsh_candidates(s, params, keys, out)
-    assert n == cand_ref.shape[0] == ref[1].n_candidates
+    assert n == cand_ref.shape[0] == ref[2].n_candidates
     assert np.array_equal(_u64(out[:n]), cand_ref)
     vout = torch.empty(n, dtype=torch.int64, device=DEV)
     k = ctx.verify(s, params, out[:n], vout)
-    assert np.array_equal(_u64(vout[:k]), ref[1].pairs)
+    assert np.array_equal(_u64(vout[:k]), ref[2].pairs)
 
 
 @pytest.mark.parametrize("buckets", [0, 2])
 def test_batch_large_tables_equals_oracle(ej, ctx, large_set, stream, buckets):
-    """A two-join batch at n = 30000 (K = 1 with z = 4, K = 2 with z = 3; same
-    seed, r, m): shared walks and shared global buckets (buckets 0) or the
+    """A two-join batch at n = 30000 (K = 2 with z = 8, K = 3 with z = 7; same
+    seed, L, r, m): shared walks and shared global buckets (buckets 0) or the
     sorted path (buckets 2), replayed as a graph; each join equals the oracle."""
     ss, ref = large_set
     s = ej.Strings.from_set(ss, DEV)
-    params = [ej.Params(K=1, r=2, m=3, z=4, seed=9, alphabet=b"ACGT"),
-              ej.Params(K=2, r=2, m=3, z=3, seed=9, alphabet=b"ACGT")]
+    params = [ej.Params(K=K, z=z, alphabet=b"ACGT", **LARGE) for K, z in LARGE_KZ]
     try:
         ctx.set_schedule(buckets=buckets)
         with torch.cuda.stream(stream):
