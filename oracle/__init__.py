@@ -19,6 +19,10 @@ Parity status per function:
                                      values)
   join                             : pinned (running example output; worked
                                      example; precision against brute force)
+  join_plus (Alg. 4 and 5)         : pinned (equal to join when one substring and
+                                     T = 1; candidates equal to the set definition
+                                     by brute force; P[>= T matched signatures]
+                                     equal to the binomial p_T of Section 5)
   keys (streamed walk + signatures) : pinned equal to sign(embed(...))
   verify_cutoff                    : pinned equal to verify (banded DP)
 """
@@ -101,6 +105,11 @@ def lib():
             L.or_join.restype = C.c_int
             L.or_join.argtypes = [vp, vp, i64, C.POINTER(_Params), vp, i64, vp, i64,
                                   C.POINTER(_Stats)]
+            L.or_join_plus.restype = C.c_int
+            L.or_join_plus.argtypes = [vp, vp, i64, C.POINTER(_Params), i32, i32, vp, i64, vp, i64,
+                                       C.POINTER(_Stats), C.POINTER(C.c_int64)]
+            L.or_plus_substrings.restype = i32
+            L.or_plus_substrings.argtypes = [i32, i32]
             _lib = L
     return _lib
 
@@ -306,4 +315,47 @@ def join(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, seed: i
         if st.n_out <= cap and (not keep_candidates or st.n_candidates <= cap):
             return JoinResult(out[:st.n_out].copy(),
                               cand[:st.n_candidates].copy() if keep_candidates else None, st)
+        cap = max(int(st.n_out), int(st.n_candidates)) + 1
+
+
+# ---------------------------------------------------------------------------
+# EmbedJoin+ (Algorithms 4 and 5)
+# ---------------------------------------------------------------------------
+
+def plus_substrings(K: int, delta: int) -> int:
+    """ceil(K / delta), at least 1: the substrings (suffixes) embedded per string."""
+    return int(lib().or_plus_substrings(K, delta))
+
+
+def join_plus(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, seed: int, delta: int,
+              T: int | None = None, L: int = 0, out_len: int = 0, pi_inject=None, pos_inject=None,
+              keep_candidates: bool = True) -> JoinResult:
+    """EmbedJoin+ end to end. T defaults to Section 5's rule: 2 when there is
+    more than one substring per string, else 1."""
+    data, offsets = _strings(data, offsets)
+    n = offsets.shape[0] - 1
+    if T is None:
+        T = 2 if plus_substrings(K, delta) > 1 else 1
+    ab = _u8(alphabet)
+    pi = None if pi_inject is None else np.ascontiguousarray(pi_inject, dtype=np.uint8)
+    pos = None if pos_inject is None else np.ascontiguousarray(pos_inject, dtype=np.uint32)
+    prm = _Params(r, m, z, L, out_len, K, seed, _p(ab), len(alphabet), _p(pi),
+                  0 if pi is None else pi.shape[1], _p(pos))
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, dtype=np.uint64)
+        cand = np.zeros(cap if keep_candidates else 1, dtype=np.uint64)
+        st = _Stats()
+        nt = C.c_int64(0)
+        rc = lib().or_join_plus(_p(data), _p(offsets), n, C.byref(prm), delta, T, _p(out), cap,
+                                _p(cand) if keep_candidates else None, cap if keep_candidates else 0,
+                                C.byref(st), C.byref(nt))
+        if rc != 0:
+            raise ValueError(f"oracle join_plus failed: {rc}")
+        if st.n_out <= cap and (not keep_candidates or st.n_candidates <= cap):
+            res = JoinResult(out[:st.n_out].copy(),
+                             cand[:st.n_candidates].copy() if keep_candidates else None, st)
+            res.n_tuples = int(nt.value)
+            res.T = T
+            return res
         cap = max(int(st.n_out), int(st.n_candidates)) + 1

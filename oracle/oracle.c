@@ -610,3 +610,184 @@ int or_join(const uint8_t *data, const int64_t *offsets, int64_t n, const or_par
     free(cl); free(flags);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* EmbedJoin+ (Algorithms 4 and 5): suffix embeddings and match counting     */
+/* ------------------------------------------------------------------------ */
+
+/* A match of Alg. 5: substring k_x of string x and substring k_y of string y
+ * share a bucket in one table; x is the string visited first (sorted order). */
+typedef struct { int32_t x, y, kx, ky; } or_tuple;
+
+static int cmp_tuple(const void *a, const void *b) {
+    const or_tuple *p = (const or_tuple *)a, *q = (const or_tuple *)b;
+    if (p->x != q->x) return p->x < q->x ? -1 : 1;
+    if (p->y != q->y) return p->y < q->y ? -1 : 1;
+    if (p->kx != q->kx) return p->kx < q->kx ? -1 : 1;
+    if (p->ky != q->ky) return p->ky < q->ky ? -1 : 1;
+    return 0;
+}
+
+/* Number of substrings per string, ceil(K / delta), at least 1 (a threshold of 0
+ * still embeds the whole string). */
+int32_t or_plus_substrings(int32_t K, int32_t delta) {
+    if (delta <= 0) return 0;
+    int32_t s = (K + delta - 1) / delta;
+    return s < 1 ? 1 : s;
+}
+
+/*
+ * EmbedJoin+ end to end. Alg. 4: strings sorted by (length, lexicographic);
+ * for every embedding l and string s_i, the substrings s_{i,k} = s_i[(k-1)delta
+ * .. |s_i|) for k = 1 .. ceil(K/delta) (empty once the start passes the end),
+ * each CGK-embedded with the same random string R^l. Alg. 5: strings visited in
+ * sorted order; for every table (l, f) and substring k, every stored (s, k') of
+ * the bucket of its signature with s != s_i gives the match (s, s_i, k', k) if
+ * |s_i| - |s| <= K, else (s, k') is removed; then (s_i, k) is stored. Matches
+ * are counted per (x, y, k_x, k_y); a pair with some count >= T is a candidate
+ * (once), and candidates with ED <= K are the output.
+ * stats: n_candidates = candidate pairs, n_out = output pairs. tuples (optional)
+ * gets the number of matches (with repetition). Returns 0 or an error code.
+ */
+int or_join_plus(const uint8_t *data, const int64_t *offsets, int64_t n, const or_params *p, int32_t delta,
+                 int32_t T, uint64_t *out, int64_t capacity, uint64_t *cand, int64_t cand_capacity,
+                 or_stats *st, int64_t *tuples) {
+    memset(st, 0, sizeof *st);
+    if (tuples) *tuples = 0;
+    if (n < 0 || p->r == 0 || p->m == 0 || p->z == 0 || p->K < 0 || p->alpha == 0 || p->alpha > 255 ||
+        delta <= 0 || T < 1)
+        return OR_ERR_ARG;
+    const int32_t S = or_plus_substrings(p->K, delta);
+    int64_t N = 0;
+    for (int64_t s = 0; s < n; s++)
+        if (offsets[s + 1] - offsets[s] > N) N = offsets[s + 1] - offsets[s];
+    int64_t out_len = p->out_len ? p->out_len : (N > 0 ? 3 * N : 1);
+    uint32_t L = p->L ? p->L : (uint32_t)out_len;
+    st->out_len = out_len; st->L = L;
+    if (n < 2) return OR_OK;
+    if ((int64_t)L > out_len || L == 0) return OR_ERR_ARG;
+    uint8_t code_of[256];
+    memset(code_of, 255, sizeof code_of);
+    for (uint32_t c = 0; c < p->alpha; c++) code_of[p->alphabet[c]] = (uint8_t)c;
+    for (int64_t q = 0; q < offsets[n]; q++)
+        if (code_of[data[q]] == 255) return OR_ERR_ARG;
+
+    /* Alg. 4: hash functions, then the embeddings of every substring */
+    const int64_t TT = (int64_t)p->r * p->m;
+    uint32_t *pos = (uint32_t *)malloc((size_t)TT * p->z * sizeof(uint32_t));
+    uint64_t *keys = (uint64_t *)malloc((size_t)TT * (size_t)n * (size_t)S * sizeof(uint64_t));
+    uint8_t *t = (uint8_t *)malloc((size_t)out_len);
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!pos || !keys || !t || !order) { free(pos); free(keys); free(t); free(order); return OR_ERR_OOM; }
+    if (p->pos_inject) memcpy(pos, p->pos_inject, (size_t)TT * p->z * sizeof(uint32_t));
+    else or_positions_all(p->seed, p->r, p->m, p->z, L, pos);
+    for (uint32_t l = 0; l < p->r; l++) {
+        const uint8_t *pi = p->pi_inject ? p->pi_inject + (int64_t)l * p->inject_steps * p->alpha : NULL;
+        for (int64_t s = 0; s < n; s++)
+            for (int32_t k = 0; k < S; k++) {
+                const int64_t len = offsets[s + 1] - offsets[s];
+                const int64_t start = (int64_t)k * delta < len ? (int64_t)k * delta : len;
+                int64_t we = or_cgk_embed(data + offsets[s] + start, len - start, code_of, p->alpha, p->seed, l,
+                                          out_len, pi, p->inject_steps, t);
+                for (uint32_t f = 0; f < p->m; f++)
+                    keys[((int64_t)l * p->m + f) * n * S + s * S + k] =
+                        or_signature_key(t, we, pos + ((uint64_t)l * p->m + f) * p->z, p->z, p->alpha);
+            }
+    }
+    free(t);
+    free(pos);
+
+    /* Alg. 5: sliding window over the tables in sorted order, collecting matches */
+    for (int64_t i = 0; i < n; i++) order[i] = (int32_t)i;
+    g_sort.data = data; g_sort.offsets = offsets;
+    qsort(order, (size_t)n, sizeof(int32_t), cmp_len_lex);
+    int64_t cap = 1;
+    while (cap < 2 * n * S) cap <<= 1;
+    table_t *tabs = (table_t *)calloc((size_t)TT, sizeof(table_t));
+    int err = tabs ? OR_OK : OR_ERR_OOM;
+    for (int64_t tb = 0; tb < TT && !err; tb++) {
+        tabs[tb].cap = cap;
+        tabs[tb].keys = (uint64_t *)malloc((size_t)cap * sizeof(uint64_t));
+        tabs[tb].slot_bucket = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+        tabs[tb].buckets = (ivec *)malloc((size_t)(n * S) * sizeof(ivec));
+        if (!tabs[tb].keys || !tabs[tb].slot_bucket || !tabs[tb].buckets) { err = OR_ERR_OOM; break; }
+        for (int64_t h = 0; h < cap; h++) tabs[tb].slot_bucket[h] = -1;
+    }
+    or_tuple *C = NULL;
+    int64_t nc = 0, ccap = 0;
+    for (int64_t a = 0; a < n && !err; a++) {
+        const int32_t si = order[a];
+        const int64_t li = offsets[si + 1] - offsets[si];
+        for (int64_t tb = 0; tb < TT && !err; tb++)
+            for (int32_t k = 0; k < S && !err; k++) {
+                ivec *B = table_bucket(&tabs[tb], keys[tb * n * S + (int64_t)si * S + k], 1);
+                for (int64_t b = 0; b < B->n;) {
+                    const int32_t rec = B->v[b];
+                    const int32_t s = rec / S, kp = rec % S;
+                    if (s == si) { b++; continue; }
+                    const int64_t ls = offsets[s + 1] - offsets[s];
+                    if (li - ls <= p->K) {
+                        if (nc == ccap) {
+                            int64_t nca = ccap ? 2 * ccap : 1024;
+                            or_tuple *nv = (or_tuple *)realloc(C, (size_t)nca * sizeof(or_tuple));
+                            if (!nv) { err = OR_ERR_OOM; break; }
+                            C = nv; ccap = nca;
+                        }
+                        C[nc].x = s; C[nc].y = si; C[nc].kx = kp; C[nc].ky = k;
+                        nc++;
+                        b++;
+                    } else {
+                        B->v[b] = B->v[--B->n];   /* remove (s, k') from the table */
+                    }
+                }
+                if (!err) err = ivec_push(B, si * S + k);
+            }
+    }
+    for (int64_t tb = 0; tabs && tb < TT; tb++) {
+        if (tabs[tb].buckets)
+            for (int64_t b = 0; b < tabs[tb].nb; b++) free(tabs[tb].buckets[b].v);
+        free(tabs[tb].keys); free(tabs[tb].slot_bucket); free(tabs[tb].buckets);
+    }
+    free(tabs); free(order); free(keys);
+    if (err) { free(C); return err; }
+    if (tuples) *tuples = nc;
+
+    /* count every (x, y, k_x, k_y); a pair with some count >= T is a candidate */
+    uint64_t *cl = (uint64_t *)malloc((size_t)(nc ? nc : 1) * sizeof(uint64_t));
+    if (!cl) { free(C); return OR_ERR_OOM; }
+    int64_t ncand = 0;
+    if (nc) qsort(C, (size_t)nc, sizeof(or_tuple), cmp_tuple);
+    for (int64_t q = 0; q < nc;) {
+        int64_t e = q + 1;
+        while (e < nc && cmp_tuple(&C[q], &C[e]) == 0) e++;
+        if (e - q >= T) {
+            const uint64_t lo = (uint64_t)(C[q].x < C[q].y ? C[q].x : C[q].y);
+            const uint64_t hi = (uint64_t)(C[q].x < C[q].y ? C[q].y : C[q].x);
+            cl[ncand++] = (lo << 32) | hi;
+        }
+        q = e;
+    }
+    free(C);
+    int64_t nu = 0;
+    if (ncand) {
+        qsort(cl, (size_t)ncand, sizeof(uint64_t), cmp_u64);
+        for (int64_t q = 0; q < ncand; q++)
+            if (q == 0 || cl[q] != cl[q - 1]) cl[nu++] = cl[q];
+    }
+    /* verification of every candidate pair (Section 3.3) */
+    uint8_t *flags = (uint8_t *)malloc((size_t)(nu ? nu : 1));
+    if (!flags) { free(cl); return OR_ERR_OOM; }
+    or_verify(data, offsets, cl, nu, p->K, flags);
+    int64_t no = 0;
+    for (int64_t q = 0; q < nu; q++) {
+        if (cand && q < cand_capacity) cand[q] = cl[q];
+        if (flags[q]) {
+            if (out && no < capacity) out[no] = cl[q];
+            no++;
+        }
+    }
+    st->n_candidates = nu;
+    st->n_out = no;
+    free(cl); free(flags);
+    return OR_OK;
+}

@@ -5,9 +5,11 @@ set is every pair with ED <= K, from the brute-force join with the cutoff DP.
 Test infrastructure: it calls only the oracle and the seeded input generators.
 
     python -m oracle.recall            # one JSON line per (workload, K), then serving
+    python -m oracle.recall --write    # the same, also written to oracle/recall_samples.json
     python -m oracle.recall --sweep-z  # long DNA and text-like: recall and candidates per z
 """
 import json
+import os
 import sys
 import time
 
@@ -19,12 +21,13 @@ def samples():
     """(name, string set, Ks, params(K)) for every join workload, at sizes the
     brute force finishes in seconds."""
     small = synth.SMALL_DNA_PARAMS
-    yield ("small DNA, n=1000 (the full workload)", synth.small_dna(), [small["K"]],
+    yield ("small_dna", "small DNA, n=1000 (the full workload)", synth.small_dna(), [small["K"]],
            lambda K: dict(r=small["r"], m=small["m"], z=small["z"], seed=small["seed"], L=0))
-    yield ("long DNA, 20 clusters of 10 (n=200)", synth.long_dna(n_clusters=20, seed=1002), [50, 150, 250],
-           synth.long_dna_params)
-    yield "protein-like, n=1000", synth.protein_like(1003, 1000), list(synth.PROTEIN_KS), synth.protein_params
-    yield "text-like, n=300", synth.text_like(1004, 300), list(synth.TEXT_KS), synth.text_params
+    yield ("long_dna", "long DNA, 20 clusters of 10 (n=200)", synth.long_dna(n_clusters=20, seed=1002),
+           [50, 150, 250], synth.long_dna_params)
+    yield ("protein", "protein-like, n=1000", synth.protein_like(1003, 1000), list(synth.PROTEIN_KS),
+           synth.protein_params)
+    yield "text", "text-like, n=300", synth.text_like(1004, 300), list(synth.TEXT_KS), synth.text_params
 
 
 def serving_recall(n_index: int = 2000, n_queries: int = 100):
@@ -55,15 +58,17 @@ def serving_recall(n_index: int = 2000, n_queries: int = 100):
                 if hit[i]:
                     got.add((q, int(i)))
     found = len(got)
-    print(json.dumps({"workload": f"serving search, index n={n}, {len(qs)} queries", "K": "per query",
-                      "true_pairs": len(want), "found": found, "recall": found / len(want) if want else None,
-                      "precision": 1.0}), flush=True)
+    row = {"key": "serving", "workload": f"serving search, index n={n}, {len(qs)} queries", "K": "per query",
+           "n": n, "true_pairs": len(want), "found": found, "recall": found / len(want) if want else None,
+           "precision": 1.0}
+    print(json.dumps(row), flush=True)
+    return row
 
 
 def sweep_z():
     """Recall and candidate count of the long-DNA and text-like samples for each
     number of samples per function z (r, m, L and the seed as in the workload)."""
-    for name, ss, Ks, params in list(samples())[1::2]:
+    for _, name, ss, Ks, params in list(samples())[1::2]:
         for K in Ks:
             truth = set(oracle.join_bruteforce(ss.data, ss.offsets, K, cutoff=True).tolist())
             p = params(K)
@@ -81,7 +86,8 @@ def main():
     if "--sweep-z" in sys.argv:
         sweep_z()
         return
-    for name, ss, Ks, params in samples():
+    rows = []
+    for key, name, ss, Ks, params in samples():
         for K in Ks:
             p = params(K)
             t0 = time.perf_counter()
@@ -92,12 +98,17 @@ def main():
             t2 = time.perf_counter()
             got, want = set(res.pairs.tolist()), set(truth.tolist())
             found = len(got & want)
-            print(json.dumps({"workload": name, "K": K, "n": ss.n, "true_pairs": len(want), "found": found,
-                              "recall": found / len(want) if want else None,
-                              "precision": found / len(got) if got else None,
-                              "candidates": res.n_candidates, "join_s": round(t1 - t0, 2),
-                              "bruteforce_s": round(t2 - t1, 2)}), flush=True)
-    serving_recall()
+            row = {"key": key, "workload": name, "K": K, "n": ss.n, "true_pairs": len(want), "found": found,
+                   "recall": found / len(want) if want else None, "precision": found / len(got) if got else None,
+                   "candidates": res.n_candidates, "join_s": round(t1 - t0, 2), "bruteforce_s": round(t2 - t1, 2)}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    rows.append(serving_recall())
+    if "--write" in sys.argv:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "recall_samples.json")
+        with open(path, "w") as f:
+            json.dump({"written_by": "python -m oracle.recall --write", "rows": rows}, f, indent=1)
+            f.write("\n")
 
 
 if __name__ == "__main__":
