@@ -1,29 +1,35 @@
 #!/usr/bin/env python3
 """Benchmark of the EmbedJoin hot path on one GPU (or N independent replicas).
 
-Default workload (long DNA-like strings): n = 20000 strings over {A,C,G,T}, 2000
-clusters of 10, base length uniform in [4500, 5500], each member carrying
+Headline workload (long DNA-like strings): n = 20000 strings over {A,C,G,T},
+2000 clusters of 10, base length uniform in [4500, 5500], each member carrying
 Poisson(rate * length) random edits with rate uniform in [1%, 8%]. One step =
 the whole join (validate -> pack -> random tables -> CGK walk + signatures ->
 buckets -> pairs -> dedup -> verify -> sorted output) at K = 50, 150 and 250
 (r = 7, m = 20 functions, z = 15/14/13 positions, L = 5000), inputs resident in
-HBM. --workload protein / text select the protein-like (n=200000, K=40,60) and
-text-like (n=350000, K=100,200,300) sets instead.
+HBM. It heads the line as the plain method on long strings on the GPU, the
+configuration the metric is quoted on; the protein-like (n = 200000, K = 40/60),
+text-like (n = 350000, K = 100/200/300) and serving (index of 10^6 strings)
+workloads are measured at their full sizes in the same run, under "workloads".
+--workload protein / text / serving puts one of them at the head instead.
 
 The headline runs the step through ej_batch: the joins of a step captured once
 as a CUDA graph (each join on its own stream, one merged verifier launch over
-all joins' candidates) and replayed every step, outputs read back sorted; the
-roofline is that merged launch's, timed with CUDA events inside the batch.
-Beside it the same step is timed through one ej_join call per K (whose
-per-stage events give the stage breakdown and a per-launch verify roofline)
-and through the plain per-stage calls ej_embed -> ej_sign -> ej_lsh_candidates
--> ej_verify; all three must return the same pair sets. --batch-eager issues
-the batch's work without a graph (the same work, for per-kernel profilers).
+all joins' candidates where they use the persistent verifier) and replayed
+every step, outputs read back sorted. Beside it the same step is timed through
+one ej_join call per K (whose per-stage CUDA events give the stage breakdown,
+the per-stage HBM fractions and a per-launch verify roofline) and through the
+plain per-stage calls ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify;
+all paths must return the same pair sets.
 
 Metric: candidate pairs verified per second of whole-step wall time (the
 "verified pairs/s" of the headline metric; join wall time and band cells/s are
 reported beside it). The L2 cache is flushed (256 MiB write) before every timed
 step, outside the timed events.
+
+Rooflines: the verifier against the measured 32-bit integer instruction rate
+of this GPU (ej_measure_int_peak, lop3/add mix), the other stages against the
+measured HBM copy bandwidth (MEASURED_PEAKS.json, else the 6.8 TB/s fallback).
 
 --impl reference times the CPU oracle (plain single-threaded C) on a bounded
 sample of the same workload, the same metric.
@@ -46,16 +52,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "verified pairs/s (candidate pairs verified per second of whole-join wall time)"
-# GB300: 152 SMs; the integer ALU pipe (add, logic, shift) retires 16 lanes per clock
-# per SM sub-partition, 64 per SM, at up to 2070 MHz
+# GB300: 152 SMs; the derived figure assumes 64 integer ALU lanes per SM per clock
+# at the maximum SM clock (kept beside the measured rate for context)
 SMS, ALU_LANES_PER_SM, MAX_SM_MHZ = 152, 64, 2070.0
 INT_OPS_PER_WORD_COLUMN = 26   # 32-bit ops of one 64-bit word of the bit-parallel step
+HBM_FALLBACK_GBS = 6800.0
 VERIFY_SOURCE = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify_pq.cu")
 # DRAM bytes per verify launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the long-DNA workload: "merged" = the batch's merged launch,
 # "join" = mean over the K=50/150/250 launches of ej_join; valid only while the
 # verify source is the one that was captured
 VERIFY_TRAFFIC = {"source_sha256_prefix": "543eb403d5eb9127", "bytes_per_launch": {"merged": 11593472, "join": None}}
+RECALL_SAMPLES = os.path.join(ROOT, "oracle", "recall_samples.json")
 
 
 def workloads():
@@ -65,16 +73,19 @@ def workloads():
             make=lambda seed, args: synth.long_dna(n_clusters=args.clusters, seed=seed),
             seed=1002, params=synth.long_dna_params, Ks=(50, 150, 250),
             sample=lambda args: synth.long_dna(n_clusters=args.sample_clusters, seed=1002),
+            cluster_truth=True,
             desc=lambda ss, args: (f"long DNA-like self-join: n={ss.n} over ACGT, {args.clusters} clusters of 10, "
                                    f"length U[4500,5500], member edit rate U[1%,8%]")),
         "protein": dict(
             make=lambda seed, args: synth.protein_like(seed, args.n or 200000), seed=1003, params=synth.protein_params,
             Ks=synth.PROTEIN_KS, sample=lambda args: synth.protein_like(1003, 20 * args.sample_clusters),
+            cluster_truth=False,
             desc=lambda ss, args: (f"protein-like self-join: n={ss.n} over 25 letters (Zipf 1), log-normal "
                                    f"length (median 400) in [100,2000], 20% near-duplicates")),
         "text": dict(
             make=lambda seed, args: synth.text_like(seed, args.n or 350000), seed=1004, params=synth.text_params,
             Ks=synth.TEXT_KS, sample=lambda args: synth.text_like(1004, 3 * args.sample_clusters),
+            cluster_truth=True,
             desc=lambda ss, args: (f"text-like self-join: n={ss.n} over 37 symbols, length U[800,3000], "
                                    f"clusters of 2-20 at edit rate U[2%,20%]")),
     }
@@ -88,7 +99,17 @@ def verify_traffic(kind):
     return None
 
 
-def parse():
+def hbm_peak() -> tuple[float, str]:
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -109,9 +130,13 @@ def parse():
     ap.add_argument("--paths", type=str, default="batch,join,plain",
                     help="paths to time (batch = the graph-captured headline; without it the ej_join path heads "
                          "the line, e.g. for profilers that do not follow stream capture)")
+    ap.add_argument("--full-size", type=str, default="protein,text,serving",
+                    help="workloads measured at full size beside the headline ('' = none)")
+    ap.add_argument("--full-steps", type=int, default=2, help="timed steps of each full-size join workload")
+    ap.add_argument("--no-recall", action="store_true", help="skip the recall measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-clusters", type=int, default=100)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_init():
@@ -185,7 +210,8 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self) -> dict:
+    def summary(self, windows=None) -> dict:
+        windows = self.windows if windows is None else windows
         sm, mx, reasons, inside = [], MAX_SM_MHZ, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -197,7 +223,7 @@ class ClockSampler:
                 clk, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            if not any(t0 - 0.025 <= ts <= t1 + 0.025 for t0, t1 in self.windows):
+            if not any(t0 - 0.025 <= ts <= t1 + 0.025 for t0, t1 in windows):
                 continue
             inside += 1
             sm.append(clk)
@@ -207,6 +233,10 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": inside}
 
+
+# ---------------------------------------------------------------------------
+# CPU baseline and the reference arm (the oracle)
+# ---------------------------------------------------------------------------
 
 def cpu_baseline(wl: dict, args, Ks) -> dict:
     """The oracle as it stands (single-threaded C) on a bounded sample."""
@@ -229,6 +259,30 @@ def cpu_baseline(wl: dict, args, Ks) -> dict:
             "sample": f"{ss.n} strings of the same recipe, K={','.join(map(str, Ks))}, one join each; "
                       f"{t:.1f} s single-threaded",
             "per_K": per_k}
+
+
+def cpu_all_cores(ss, params, gpu_pairs) -> dict:
+    """The oracle on every host core over the benchmark's own input: keys of all
+    strings split by string ranges, Alg. 3's candidates in one process, the
+    banded-DP verification split over candidate chunks (the same pair sets as
+    the single-threaded oracle). Its output is compared with the GPU's."""
+    import oracle
+    from oracle import parallel
+    oracle.build()
+    per_k, cand, t, same = {}, 0, 0.0, True
+    for p, got in zip(params, gpu_pairs):
+        t0 = time.perf_counter()
+        pairs, nc = parallel.join(ss.data, ss.offsets, ss.alphabet, K=p.K, r=p.r, m=p.m, z=p.z, seed=p.seed, L=p.L)
+        dt = time.perf_counter() - t0
+        ok = bool(pairs.shape[0] == got.shape[0] and (pairs == got).all())
+        same &= ok
+        cand += nc
+        t += dt
+        per_k[str(p.K)] = {"s": round(dt, 2), "candidates": nc, "out": int(pairs.shape[0]), "equal_to_gpu": ok}
+    return {"value": cand / t, "unit": "pairs/s", "cores": parallel.cores(), "kind": "oracle",
+            "sample": f"the benchmark's own input ({ss.n} strings, every K); oracle pieces on all host cores "
+                      f"(string ranges for the walks, candidate chunks for the verification)",
+            "seconds": round(t, 2), "same_config": True, "identical_to_gpu": same, "per_K": per_k}
 
 
 def run_reference(args, rank, world):
@@ -256,19 +310,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, rank, world, local):
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+
+def serving_summary(args, rank, local, clk) -> dict:
     """Search against a resident index: the query stream as one offline batch,
     then as Poisson arrivals at each offered rate through the continuous-batching
     server (p50/p99 latency and achieved queries/s per rate)."""
     import random
 
     import numpy as np
-    import torch
 
     from paper_1702_00093_gb300 import embedjoin as ej
     from paper_1702_00093_gb300 import synth
 
-    torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     idx_ss = synth.serving_index(args.index_size, seed=1005 + rank)
     qs, ks = synth.serving_queries(idx_ss, args.queries, seed=1006 + rank)
@@ -286,60 +342,487 @@ def run_serving(args, rank, world, local):
         per_q.setdefault(int(v) >> 32, []).append(int(v) & 0xFFFFFFFF)
     rates = []
     identical = True
-    with ClockSampler(local) as clk:
-        for rate in [float(x) for x in args.rates.split(",") if x]:
-            n = min(len(qs), max(200, int(rate * 4.0)))
-            srv = ej.Server(index, max_batch=256, inflight=4)
-            rnd = random.Random(7)
-            done = {}
-            sub = {}
+    windows = []
+    for rate in [float(x) for x in args.rates.split(",") if x]:
+        n = min(len(qs), max(200, int(rate * 4.0)))
+        srv = ej.Server(index, max_batch=256, inflight=4)
+        rnd = random.Random(7)
+        done = {}
+        sub = {}
 
-            def submitter():
-                t = time.perf_counter()
-                for q in range(n):
-                    t += rnd.expovariate(rate)
-                    d = t - time.perf_counter()
-                    if d > 0:
-                        time.sleep(d)
-                    sub[srv.submit(qs[q], int(ks[q]))] = q
+        def submitter():
+            t = time.perf_counter()
+            for q in range(n):
+                t += rnd.expovariate(rate)
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                sub[srv.submit(qs[q], int(ks[q]))] = q
 
-            th = threading.Thread(target=submitter)
-            w0 = time.time()
-            th.start()
-            deadline = time.time() + 120
-            while len(done) < n and time.time() < deadline:
-                for rid, status, matches, lat, queue in srv.poll(1024, 2000):
-                    done[rid] = (status, matches, lat, queue)
-            th.join()
-            clk.mark(w0, time.time())
-            st = srv.stats()
-            srv.close()
-            lats = [v[2] for v in done.values()]
-            for rid, (status, matches, _, _) in done.items():
-                identical &= status == 0 and list(matches) == per_q.get(sub[rid], [])
-            rates.append({"offered_qps": rate, "queries": n, "completed": len(done),
-                          "achieved_qps": st["queries_per_s"], "p50_ms": float(np.percentile(lats, 50)),
-                          "p99_ms": float(np.percentile(lats, 99)), "mean_batch": st["mean_batch"],
-                          "batches": st["batches"], "deferred": st["deferred"], "retries": st["retries"]})
-    if rank == 0:
-        best = max(rates, key=lambda r: r["achieved_qps"]) if rates else None
-        line = {
-            "metric": "queries/s (edit-similarity search against a resident index, continuous batching)",
-            "value": best["achieved_qps"] if best else None, "unit": "queries/s", "n_gpus": world,
-            "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"serving: index of {idx_ss.n} ACGT strings, length U[900,1100], 10% planted "
-                                   f"near-duplicates; {len(qs)} queries, half mutated index strings (rate "
-                                   f"U[1%,10%]), half random of length U[200,5000], K = U[1%,10%] of the length; "
-                                   f"r=7, m=7, z=8, L=1000; Poisson arrivals",
-                       "index_build_s": build_s, "parallelism": "single GPU"},
-            "offline_batch": {"queries": len(qs), "seconds": offline_s, "queries_per_s": len(qs) / offline_s,
-                              "matches": int(offline.shape[0])},
-            "rates": rates, "identical_to_offline": bool(identical), "clocks": clk.summary(),
-        }
-        print(json.dumps(line), flush=True)
+        th = threading.Thread(target=submitter)
+        w0 = time.time()
+        th.start()
+        deadline = time.time() + 120
+        while len(done) < n and time.time() < deadline:
+            for rid, status, matches, lat, queue in srv.poll(1024, 2000):
+                done[rid] = (status, matches, lat, queue)
+        th.join()
+        windows.append((w0, time.time()))
+        clk.mark(w0, time.time())
+        st = srv.stats()
+        srv.close()
+        lats = [v[2] for v in done.values()]
+        for rid, (status, matches, _, _) in done.items():
+            identical &= status == 0 and list(matches) == per_q.get(sub[rid], [])
+        rates.append({"offered_qps": rate, "queries": n, "completed": len(done),
+                      "achieved_qps": st["queries_per_s"], "p50_ms": float(np.percentile(lats, 50)),
+                      "p99_ms": float(np.percentile(lats, 99)), "mean_batch": st["mean_batch"],
+                      "batches": st["batches"], "deferred": st["deferred"], "retries": st["retries"]})
     index.close()
     ctx.close()
+    best = max(rates, key=lambda r: r["achieved_qps"]) if rates else None
+    return {
+        "metric": "queries/s (edit-similarity search against a resident index, continuous batching)",
+        "value": best["achieved_qps"] if best else None, "unit": "queries/s",
+        "workload": (f"serving: index of {idx_ss.n} ACGT strings, length U[900,1100], 10% planted near-duplicates; "
+                     f"{len(qs)} queries, half mutated index strings (rate U[1%,10%]), half random of length "
+                     f"U[200,5000], K = U[1%,10%] of the length; r=7, m=7, z=8, L=1000; Poisson arrivals"),
+        "index_build_s": build_s,
+        "offline_batch": {"queries": len(qs), "seconds": offline_s, "queries_per_s": len(qs) / offline_s,
+                          "matches": int(offline.shape[0])},
+        "rates": rates, "identical_to_offline": bool(identical), "clocks": clk.summary(windows),
+    }
+
+
+def run_serving(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        s = serving_summary(args, rank, local, clk)
+    if rank == 0:
+        line = {"metric": s["metric"], "value": s["value"], "unit": s["unit"], "n_gpus": world,
+                "steps": len(s["rates"]), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": s["workload"], "index_build_s": s["index_build_s"],
+                           "parallelism": "single GPU"},
+                "offline_batch": s["offline_batch"], "rates": s["rates"],
+                "identical_to_offline": s["identical_to_offline"], "clocks": s["clocks"]}
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Joins: the batch (graph), ej_join per K, the plain per-stage calls
+# ---------------------------------------------------------------------------
+
+def packed_bytes(lengths, alphabet_size: int) -> int:
+    """Bytes of the packed codes: every string on its own 16-byte chunks, 2-bit
+    codes for alphabets of at most 4 symbols, else 8-bit."""
+    import numpy as np
+    b = 2 if alphabet_size <= 4 else 8
+    return int((((np.asarray(lengths, dtype=np.int64) * b + 127) // 128) * 16).sum())
+
+
+def stage_rooflines(ss, params, jstats, steps, hbm_gbs, hbm_src) -> dict:
+    """HBM fractions of the stages of ej_join, from its per-stage CUDA events
+    (means over the timed steps, summed over the step's joins). Algorithmic
+    bytes per stage, all counted once:
+      pack     strings read + offsets + packed codes and lengths written
+      walk     packed codes read + r*m*n signature keys written (8 B each)
+      buckets  r*m*n keys read + raw pairs written (8 B each)
+      dedup    raw pairs read + candidates written (8 B each)"""
+    n = ss.n
+    total = int(ss.offsets[-1])
+    pk = packed_bytes(ss.lengths(), len(ss.alphabet))
+    acc = {"pack": [0.0, 0], "walk": [0.0, 0], "buckets": [0.0, 0], "dedup": [0.0, 0]}
+    by_k = {}
+    for K, _, s in jstats:
+        by_k.setdefault(K, []).append(s)
+    for p in params:
+        rows = by_k.get(p.K, [])
+        if not rows:
+            continue
+        keys = 8 * p.r * p.m * n
+        raw, cand = rows[0]["n_raw_pairs"], rows[0]["n_candidates"]
+        stage_bytes = {"pack": total + 8 * (n + 1) + pk + 4 * n, "walk": pk + keys,
+                       "buckets": keys + 8 * raw, "dedup": 8 * raw + 8 * cand}
+        stage_ms = {"pack": "ms_pack", "walk": "ms_embed_sign", "buckets": "ms_buckets", "dedup": "ms_dedup"}
+        for k in acc:
+            acc[k][0] += statistics.mean(r[stage_ms[k]] for r in rows)
+            acc[k][1] += stage_bytes[k]
+    out = {}
+    for k, (ms, by) in acc.items():
+        if ms <= 0:
+            continue
+        gbs = by / (ms * 1e-3) / 1e9
+        out[k] = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                  "bytes_per_step": by, "ms_per_step": ms}
+    out["peak_source"] = hbm_src + " (of measured)" if hbm_src.startswith("measured") else hbm_src
+    out["kernels"] = {"pack": "validate_offsets_kernel, chunk counts, scan, pack_kernel",
+                      "walk": "embed_sign_kernel (fused CGK walk + signatures; bound by instruction issue, "
+                              "not by HBM: see profiles/embed_sign_long_dna.md)",
+                      "buckets": "bucket_table_kernel (shared-memory tables) or bucket_insert/emit (global) or "
+                                 "the sorted path",
+                      "dedup": "dedup/ordering kernels (device hash set, order bins, scatter)"}
+    out["timing"] = "CUDA events on ej_join's stream around each stage, inputs resident, L2 flushed before each step"
+    return out
+
+
+def verify_roofline(word_cols, ms, launches, int_peak, kernel, measured_in, traffic=None) -> dict:
+    ops = word_cols * INT_OPS_PER_WORD_COLUMN / (ms / 1e3) if ms else 0.0
+    derived = SMS * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
+    peak = int_peak["ops_per_s"] if int_peak else derived
+    return {"kernel": kernel, "bound": "alu", "achieved": ops / 1e12, "peak": peak / 1e12,
+            "unit": "Tops/s (32-bit integer ops)", "frac": ops / peak if peak else None, "traffic": traffic,
+            "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+            "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": word_cols,
+            "word_columns_basis": "columns advanced x 64-bit words of each join's own band",
+            "measured_in": measured_in,
+            "peak_basis": (int_peak["basis"] if int_peak else "derived: 152 SMs x 64 lanes/clock x 2070 MHz"),
+            "derived_alu_peak": derived / 1e12}
+
+
+def cluster_recall(ej, ctx, ss, params, result_pairs, dev, stream, n_cross=100000) -> dict:
+    """Recall of the GPU output at full size against the exact truth of a set whose
+    only close pairs are cluster mates: every pair of a cluster is verified
+    exactly (ej_verify, parity-tested against the oracle's banded DP), and a
+    sample of pairs of different clusters checks that none of them is within K."""
+    import numpy as np
+    import torch
+    cl = ss.cluster
+    order = np.argsort(cl, kind="stable")
+    bounds = np.flatnonzero(np.diff(cl[order])) + 1
+    groups = np.split(order, bounds)
+    pa, pb = [], []
+    for g in groups:
+        if g.shape[0] < 2:
+            continue
+        i, j = np.triu_indices(g.shape[0], 1)
+        a, b = g[i], g[j]
+        pa.append(np.minimum(a, b))
+        pb.append(np.maximum(a, b))
+    intra = np.unique((np.concatenate(pa).astype(np.uint64) << np.uint64(32)) | np.concatenate(pb).astype(np.uint64))
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, ss.n, size=n_cross)
+    b = rng.integers(0, ss.n, size=n_cross)
+    keep = (cl[a] != cl[b]) & (a != b)
+    cross = np.unique((np.minimum(a, b)[keep].astype(np.uint64) << np.uint64(32)) |
+                      np.maximum(a, b)[keep].astype(np.uint64))
+    s = ej.Strings.from_set(ss, dev)
+    out = {}
+    for p, got in zip(params, result_pairs):
+        res = {}
+        for name, arr in (("intra", intra), ("cross", cross)):
+            pt = torch.from_numpy(arr.view(np.int64).copy()).to(dev)
+            o = torch.empty_like(pt)
+            k = ctx.verify(s, p, pt, o, stream)
+            res[name] = o[:k].cpu().numpy().view(np.uint64)
+        got = got.cpu().numpy().view(np.uint64)
+        truth = res["intra"]
+        found = int(np.isin(truth, got).sum())
+        out[str(p.K)] = {"true_pairs": int(truth.shape[0]), "found": found,
+                         "recall": found / truth.shape[0] if truth.shape[0] else None,
+                         "cross_pairs_checked": int(cross.shape[0]), "cross_pairs_within_K": int(res["cross"].shape[0]),
+                         "output_pairs_outside_clusters": int((~np.isin(got, truth)).sum())}
+    return {"per_K": out, "basis": "the full GPU output against every cluster pair verified exactly (ej_verify) "
+                                   "plus a sample of cross-cluster pairs (none within K means the cluster pairs "
+                                   "are the truth)"}
+
+
+def sample_recall(workload: str):
+    """Recall measured by the oracle on seeded samples of the recipe
+    (oracle/recall.py writes the file; the GPU output equals the oracle's)."""
+    try:
+        with open(RECALL_SAMPLES) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    rows = [r for r in d.get("rows", []) if r.get("key") == workload]
+    return {"per_K": {str(r["K"]): {k: r[k] for k in ("n", "true_pairs", "found", "recall")} for r in rows},
+            "basis": "the oracle's join on a seeded sample of the same recipe against the brute-force join "
+                     "(oracle/recall.py; the GPU output is identical to the oracle's)"} if rows else None
+
+
+def run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps, warm, paths, plain_steps,
+                      e2e_steps, autotune, batch_eager, int_peak, hbm, timed_windows):
+    """Times the step (one join per parameter set) through the batch, ej_join and
+    the plain per-stage calls; returns the pieces of a result line."""
+    import torch
+    strings = ej.Strings.from_set(ss, dev)
+    res = {"paths": {}}
+
+    def timed(step, n_steps, mark=True):
+        total = 0.0
+        for _ in range(n_steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0 = time.time()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if mark:
+                clk.mark(w0, time.time())
+                timed_windows.append((w0, time.time()))
+            total += e0.elapsed_time(e1)
+        return total
+
+    use_batch = "batch" in paths
+    batch_ms, cand_step, launches_step, result_pairs, e2e = None, 0, 0, None, None
+    merged_ms, merged_word_cols, eager_ms, same_eager = [], 0, None, None
+    bstats = {}
+    if use_batch:
+        batch = ctx.batch(strings, params, autotune=autotune, stream=stream, eager=batch_eager)
+        outs = [torch.empty(1 << 16, dtype=torch.int64, device=dev) for _ in params]
+
+        def batch_step(b=None):
+            b = b or batch
+            b.run(stream)
+            for i in range(len(params)):
+                while True:
+                    try:
+                        bstats[i] = b.result_into(i, outs[i], stream)
+                        break
+                    except ej.EJError as e:
+                        if getattr(e, "needed", None) is None:
+                            raise
+                        outs[i] = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+
+        for _ in range(warm):
+            batch_step()
+        batch_ms = timed(batch_step, steps)
+        cand_step = sum(st.n_candidates for _, st in bstats.values())
+        launches_step = batch.kernel_count + sum(st.kernel_launches for _, st in bstats.values())
+        result_pairs = [outs[i][:bstats[i][0]].clone() for i in range(len(params))]
+
+        if e2e_steps > 0:
+            # end to end through the public API: strings copied from pinned host
+            # memory every step, results read into host memory
+            h_data = torch.from_numpy(ss.data).pin_memory()
+            h_off = torch.from_numpy(ss.offsets).pin_memory()
+            h_outs = [torch.empty(max(int(o.shape[0]), 1), dtype=torch.int64).pin_memory().numpy() for o in outs]
+            h_t, h_cand, d2h = 0.0, 0, 0
+            for it in range(e2e_steps + 1):
+                torch.cuda.synchronize()
+                barrier(world)
+                t0 = time.perf_counter()
+                strings.data.copy_(h_data, non_blocking=True)
+                strings.offsets.copy_(h_off, non_blocking=True)
+                batch.run(stream)
+                step_c, step_out = 0, 0
+                for i in range(len(params)):
+                    n, st = batch.result_into(i, h_outs[i], stream)
+                    step_c += st.n_candidates
+                    step_out += n
+                dt = time.perf_counter() - t0
+                if it > 0:   # the first pass warms the host staging
+                    h_t += dt
+                    h_cand += step_c
+                    d2h += step_out * 8
+            h_t = allreduce(h_t, world, "max")
+            h_cand = allreduce(h_cand, world, "sum")
+            e2e = {"value": h_cand / h_t, "unit": "pairs/s",
+                   "h2d_bytes_per_step": int(ss.data.nbytes + ss.offsets.nbytes),
+                   "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps,
+                   "ms_per_step": 1e3 * h_t / e2e_steps, "api": "ej_batch_run + ej_batch_result, host buffers"}
+        batch.close()   # its scratch is not needed by the other paths
+
+        # the same batch issued without a graph: times its merged verifier launch
+        # with CUDA events on its stream (a graph replay cannot be timed per kernel)
+        if not batch_eager and "eager" in paths:
+            eb = ctx.batch(strings, params, autotune=autotune, stream=stream, eager=True)
+
+            def eager_step():
+                batch_step(eb)
+                try:
+                    merged_ms.append(eb.verify_ms())
+                except ej.EJError:
+                    pass
+
+            for _ in range(warm):
+                eager_step()
+            merged_ms.clear()
+            eager_ms = timed(eager_step, steps, mark=False)
+            merged_word_cols = sum(st.verify_word_columns for _, st in bstats.values())
+            same_eager = all(torch.equal(outs[i][:bstats[i][0]], result_pairs[i]) for i in range(len(params)))
+            eb.close()
+
+    # the same step through ej_join (stage timings, verify roofline)
+    ctx.set_timing(True)
+    jout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+    jstats = []
+    join_steps = steps if "join" in paths or not use_batch else 0
+
+    def join_step():
+        nonlocal jout
+        for p in params:
+            while True:
+                try:
+                    n, st = ctx.join_into(strings, p, jout, stream)
+                    break
+                except ej.EJError as e:
+                    if e.status != ej.EJ_ERR_CAPACITY:
+                        raise
+                    jout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+            jstats.append((p.K, n, st.as_dict()))
+
+    join_ms, same_join = None, None
+    if join_steps > 0:
+        for _ in range(min(warm, 1) if use_batch else warm):
+            join_step()
+        jstats.clear()
+        join_ms = timed(join_step, join_steps, mark=not use_batch)
+        join_pairs = []
+        for p in params:
+            n, _ = ctx.join_into(strings, p, jout, stream)
+            join_pairs.append(jout[:n].clone())
+        if use_batch:
+            same_join = all(torch.equal(a, b) for a, b in zip(join_pairs, result_pairs))
+        else:
+            result_pairs = join_pairs
+            batch_ms = join_ms
+            cand_step = sum(s_["n_candidates"] for _, _, s_ in jstats) // join_steps
+            launches_step = sum(s_["kernel_launches"] for _, _, s_ in jstats) // join_steps
+            steps = join_steps
+    ctx.set_timing(False)
+
+    plain_ms, same_plain, cand_plain = None, None, 0
+    if "plain" in paths and plain_steps > 0:
+        pctx = ej.Context(ctx.device)
+        plain = [dataclasses.replace(p, out_len=p.L) for p in params]   # the walk is causal: prefix L
+        infos = [pctx.plan(strings, p, stream) for p in plain]
+        emb = torch.empty(max(i.embedding_bytes for i in infos) // 4 + 1, dtype=torch.int32, device=dev)
+        we = torch.empty(max(i.walk_end_count for i in infos) + 1, dtype=torch.int32, device=dev)
+        keys = torch.empty(max(i.key_count for i in infos) + 1, dtype=torch.int64, device=dev)
+        cand_buf = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+        pout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+        plain_res = {}
+
+        def plain_step():
+            nonlocal cand_buf, pout
+            for i, p in enumerate(plain):
+                pctx.embed(strings, p, emb, we, stream)
+                pctx.sign(strings, p, emb, we, keys, stream)
+                while True:
+                    try:
+                        nc, _ = pctx.lsh_candidates(strings, p, keys, cand_buf, stream)
+                        break
+                    except ej.EJError as e:
+                        if e.status != ej.EJ_ERR_CAPACITY:
+                            raise
+                        cand_buf = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+                        pout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
+                k = pctx.verify(strings, p, cand_buf[:nc], pout, stream)
+                plain_res[i] = (nc, pout[:k].clone())
+
+        if plain_steps > 1:
+            plain_step()
+        plain_ms = timed(plain_step, plain_steps, mark=False)
+        same_plain = all(torch.equal(plain_res[i][1], result_pairs[i]) for i in range(len(params)))
+        cand_plain = sum(plain_res[i][0] for i in range(len(params)))
+        del emb, we, keys, cand_buf, pout
+        pctx.close()
+
+    # verify rooflines
+    res["int_peak"] = int_peak
+    if jstats:
+        verify_ms = sum(s["ms_verify"] for _, _, s in jstats)
+        word_cols = sum(s["verify_word_columns"] for _, _, s in jstats)
+        n_verify = sum(1 for _, _, s in jstats if s["n_candidates"] > 0)
+        res["join_roofline"] = verify_roofline(
+            word_cols, verify_ms, n_verify, int_peak,
+            "the verifier of ej_join, one launch per join (persistent verify_pq_kernel for mean string length "
+            ">= 2048, else grid-strided verify_bd_kernel)",
+            "the ej_join pass (CUDA events around each verify launch, its stream)", verify_traffic("join"))
+        res["stage_roofline"] = stage_rooflines(ss, params, jstats, join_steps, hbm[0], hbm[1])
+        per_k = {}
+        for p in params:
+            rows = [s for k, _, s in jstats if k == p.K]
+            per_k[str(p.K)] = {
+                "join_ms": statistics.mean(s["ms_total"] for s in rows),
+                "prepare_ms": statistics.mean(s["ms_prepare"] for s in rows),
+                "pack_ms": statistics.mean(s["ms_pack"] for s in rows),
+                "embed_sign_ms": statistics.mean(s["ms_embed_sign"] for s in rows),
+                "candidates_ms": statistics.mean(s["ms_candidates"] for s in rows),
+                "buckets_ms": statistics.mean(s["ms_buckets"] for s in rows),
+                "dedup_ms": statistics.mean(s["ms_dedup"] for s in rows),
+                "verify_ms": statistics.mean(s["ms_verify"] for s in rows),
+                "candidates": rows[0]["n_candidates"], "raw_pairs": rows[0]["n_raw_pairs"],
+                "out_pairs": rows[0]["n_out"], "max_bucket": rows[0]["max_bucket"],
+                "band_cells": rows[0]["band_cells"],
+                "verify_word_columns": rows[0]["verify_word_columns"],
+            }
+        res["per_K"] = per_k
+    if merged_ms:
+        m_ms = statistics.mean(merged_ms)
+        res["merged_roofline"] = verify_roofline(
+            merged_word_cols, m_ms * len(merged_ms), len(merged_ms), int_peak,
+            "verify_pq_kernel (the batch's merged launch over all joins' candidates)",
+            "the batch issued without a graph (same kernels), timed steps: CUDA events around the merged launch, "
+            "on its stream", verify_traffic("merged"))
+        res["merged_roofline"]["word_columns"] = merged_word_cols
+        res["merged_roofline"]["avg_launch_ms"] = m_ms
+        m_ops = merged_word_cols * INT_OPS_PER_WORD_COLUMN / (m_ms / 1e3)
+        res["merged_roofline"]["achieved"] = m_ops / 1e12
+        res["merged_roofline"]["frac"] = m_ops / (res["merged_roofline"]["peak"] * 1e12)
+    res.update(batch_ms=batch_ms, steps=steps, cand_step=cand_step, launches_step=launches_step,
+               result_pairs=result_pairs, e2e=e2e, use_batch=use_batch)
+    if join_ms is not None:
+        res["paths"]["join_path"] = {"value": sum(s["n_candidates"] for _, _, s in jstats) / (join_ms / 1e3),
+                                     "ms_per_step": join_ms / join_steps, "steps": join_steps,
+                                     "api": "ej_join per K", "identical_output": same_join}
+    if plain_ms is not None:
+        res["paths"]["plain_path"] = {
+            "value": cand_plain * plain_steps / (plain_ms / 1e3), "ms_per_step": plain_ms / plain_steps,
+            "steps": plain_steps, "api": "ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify per K",
+            "identical_output": bool(same_plain)}
+    if eager_ms is not None:
+        res["paths"]["eager_batch_path"] = {
+            "ms_per_step": eager_ms / steps, "value": cand_step * steps / (eager_ms / 1e3),
+            "api": "ej_batch with EJ_BATCH_EAGER (the same work issued every step without a graph)",
+            "identical_output": bool(same_eager)}
+    return res
+
+
+def measure_int_peak(ej, device) -> dict:
+    got = {}
+    for mix, name in ((0, "lop3+add"), (1, "lop3"), (2, "add")):
+        ops, ms = ej.measure_int_peak(device, mix, 4096)
+        got[name] = ops / 1e12
+    return {"ops_per_s": got["lop3+add"] * 1e12, "by_mix_tops": got,
+            "basis": "measured: ej_measure_int_peak, independent lop3.b32/add.u32 chains on every SM "
+                     "(best of 3 launches, CUDA events); the lop3+add mix (of measured)"}
+
+
+def full_size_join(ej, name, args, rank, dev, stream, flush, world, clk, int_peak, hbm, windows) -> dict:
+    wl = workloads()[name]
+    fargs = argparse.Namespace(**vars(args))
+    fargs.n = 0
+    t0 = time.perf_counter()
+    ss = wl["make"](wl["seed"] + rank, fargs)
+    gen_s = time.perf_counter() - t0
+    params = [ej.Params(alphabet=ss.alphabet, **dict(wl["params"](K), K=K)) for K in wl["Ks"]]
+    ctx = ej.Context(int(dev.split(":")[1]))
+    try:
+        r = run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps=args.full_steps, warm=1,
+                              paths={"batch", "join", "plain"}, plain_steps=1, e2e_steps=0, autotune=args.autotune,
+                              batch_eager=False, int_peak=int_peak, hbm=hbm, timed_windows=windows)
+        out = {"workload": wl["desc"](ss, fargs) + f"; K={','.join(str(p.K) for p in params)}; r={params[0].r}, "
+                                                  f"m={params[0].m}, z={'/'.join(str(p.z) for p in params)}, "
+                                                  f"L={params[0].L}; one step = one join per K (ej_batch graph)",
+               "n": ss.n, "Ks": [p.K for p in params], "steps": r["steps"], "warmup": 1,
+               "ms_per_step": r["batch_ms"] / r["steps"],
+               "value": r["cand_step"] * r["steps"] / (r["batch_ms"] / 1e3), "unit": "pairs/s",
+               "band_cells_per_s": sum(v["band_cells"] for v in r["per_K"].values()) / (r["batch_ms"] / r["steps"] / 1e3),
+               "per_K": r["per_K"], "roofline": r["join_roofline"], "stage_roofline": r["stage_roofline"],
+               **r["paths"], "generate_s": round(gen_s, 1)}
+        if not args.no_recall:
+            out["recall"] = (cluster_recall(ej, ctx, ss, params, r["result_pairs"], dev, stream)
+                             if wl["cluster_truth"] else sample_recall(name))
+        return out
+    finally:
+        ctx.close()
 
 
 def main():
@@ -361,271 +844,78 @@ def main():
     wl = workloads()[args.workload]
     Ks = tuple(int(k) for k in args.Ks.split(",")) if args.Ks else wl["Ks"]
     ss = wl["make"](wl["seed"] + rank, args)   # an independent problem per rank
-    params = []
-    for K in Ks:
-        p = wl["params"](K)
-        params.append(ej.Params(K=K, r=p["r"], m=p["m"], z=p["z"], seed=p["seed"], L=p["L"], alphabet=ss.alphabet))
-    strings = ej.Strings.from_set(ss, dev)
+    params = [ej.Params(alphabet=ss.alphabet, **dict(wl["params"](K), K=K)) for K in Ks]
     ctx = ej.Context(local)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     warm = max(args.warmup, 3)
-
-    def timed(step, n_steps, clk):
-        """n_steps of step() on `stream`, L2 flushed before each, CUDA events."""
-        total = 0.0
-        for _ in range(n_steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            barrier(world)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            w0 = time.time()
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if clk is not None:
-                clk.mark(w0, time.time())
-            total += e0.elapsed_time(e1)
-        return total
-
+    int_peak = measure_int_peak(ej, local)
+    hbm = hbm_peak()
+    head_windows = []
     with torch.cuda.stream(stream), ClockSampler(local) as clk:
-        paths = set(args.paths.split(","))
-        use_batch = "batch" in paths
-        batch_ms, cand_step, launches_step, result_pairs, e2e = None, 0, 0, None, None
-        merged_ms, merged_word_cols, eager_ms, same_eager = [], 0, None, None
-        if use_batch:
-            # ---- headline: all joins of the step as one CUDA graph -------------------
-            batch = ctx.batch(strings, params, autotune=args.autotune, stream=stream, eager=args.batch_eager)
-            outs = [torch.empty(1 << 16, dtype=torch.int64, device=dev) for _ in params]
-            bstats = {}
+        paths = set(args.paths.split(",")) | {"eager"}
+        r = run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps=args.steps, warm=warm,
+                              paths=paths, plain_steps=args.plain_steps, e2e_steps=args.e2e_steps,
+                              autotune=args.autotune, batch_eager=args.batch_eager, int_peak=int_peak, hbm=hbm,
+                              timed_windows=head_windows)
+        head_clocks = clk.summary(head_windows)
+        recall = None
+        if not args.no_recall and rank == 0:
+            recall = (cluster_recall(ej, ctx, ss, params, r["result_pairs"], dev, stream)
+                      if wl["cluster_truth"] else sample_recall(args.workload))
+        full = {}
+        if world == 1:
+            for name in [x for x in args.full_size.split(",") if x and x != args.workload]:
+                fw = []
+                if name == "serving":
+                    full[name] = serving_summary(args, rank, local, clk)
+                else:
+                    full[name] = full_size_join(ej, name, args, rank, dev, stream, flush, world, clk, int_peak, hbm,
+                                                fw)
+                    full[name]["clocks"] = clk.summary(fw)
+    ctx.close()
 
-            def batch_step(b=None):
-                b = b or batch
-                b.run(stream)
-                for i in range(len(params)):
-                    while True:
-                        try:
-                            bstats[i] = b.result_into(i, outs[i], stream)
-                            break
-                        except ej.EJError as e:
-                            if getattr(e, "needed", None) is None:
-                                raise
-                            outs[i] = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-
-            for _ in range(warm):
-                batch_step()
-            batch_ms = timed(batch_step, args.steps, clk)
-            cand_step = sum(st.n_candidates for _, st in bstats.values())
-            launches_step = batch.kernel_count + sum(st.kernel_launches for _, st in bstats.values())
-            result_pairs = [outs[i][:bstats[i][0]].clone() for i in range(len(params))]
-
-            # ---- end to end through the public API with host buffers -------------------
-            e2e = None
-            if args.e2e_steps > 0:
-                h_data = torch.from_numpy(ss.data).pin_memory()
-                h_off = torch.from_numpy(ss.offsets).pin_memory()
-                h_outs = [torch.empty(max(int(o.shape[0]), 1), dtype=torch.int64).pin_memory().numpy() for o in outs]
-                h_t, h_cand, d2h = 0.0, 0, 0
-                for it in range(args.e2e_steps + 1):
-                    torch.cuda.synchronize()
-                    barrier(world)
-                    t0 = time.perf_counter()
-                    strings.data.copy_(h_data, non_blocking=True)
-                    strings.offsets.copy_(h_off, non_blocking=True)
-                    batch.run(stream)
-                    step_c, step_out = 0, 0
-                    for i in range(len(params)):
-                        n, st = batch.result_into(i, h_outs[i], stream)
-                        step_c += st.n_candidates
-                        step_out += n
-                    dt = time.perf_counter() - t0
-                    if it > 0:   # the first pass warms the host staging
-                        h_t += dt
-                        h_cand += step_c
-                        d2h += step_out * 8
-                h_t = allreduce(h_t, world, "max")
-                h_cand = allreduce(h_cand, world, "sum")
-                e2e = {"value": h_cand / h_t, "unit": "pairs/s",
-                       "h2d_bytes_per_step": int(ss.data.nbytes + ss.offsets.nbytes),
-                       "d2h_bytes_per_step": int(d2h / args.e2e_steps), "steps": args.e2e_steps,
-                       "ms_per_step": 1e3 * h_t / args.e2e_steps, "api": "ej_batch_run + ej_batch_result, host buffers"}
-            batch.close()   # its scratch is not needed by the other paths
-
-            # ---- the same batch issued without a graph: times the merged verifier ----
-            # launch with CUDA events on its stream (a graph replay cannot be timed
-            # per kernel), for the roofline of the step's dominant kernel
-            if not args.batch_eager:
-                eb = ctx.batch(strings, params, autotune=args.autotune, stream=stream, eager=True)
-
-                def eager_step():
-                    batch_step(eb)
-                    try:
-                        merged_ms.append(eb.verify_ms())
-                    except ej.EJError:
-                        pass
-
-                for _ in range(warm):
-                    eager_step()
-                merged_ms.clear()
-                eager_ms = timed(eager_step, args.steps, clk)
-                merged_word_cols = sum(st.verify_word_columns for _, st in bstats.values())
-                same_eager = all(torch.equal(outs[i][:bstats[i][0]], result_pairs[i]) for i in range(len(params)))
-                eb.close()
-
-        # ---- the same step through ej_join (stage timings, verify roofline) --------
-        ctx.set_timing(True)
-        jout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
-        jstats = []
-
-        def join_step():
-            nonlocal jout
-            for p in params:
-                while True:
-                    try:
-                        n, st = ctx.join_into(strings, p, jout, stream)
-                        break
-                    except ej.EJError as e:
-                        if e.status != ej.EJ_ERR_CAPACITY:
-                            raise
-                        jout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-                jstats.append((p.K, n, st.as_dict()))
-
-        for _ in range(warm):
-            join_step()
-        jstats.clear()
-        join_ms = timed(join_step, args.steps, None if use_batch else clk)
-        same_join = True
-        join_pairs = []
-        for i, p in enumerate(params):
-            n, _ = ctx.join_into(strings, p, jout, stream)
-            join_pairs.append(jout[:n].clone())
-        if use_batch:
-            same_join = all(torch.equal(a, b) for a, b in zip(join_pairs, result_pairs))
-        else:
-            # the ej_join path heads the line
-            result_pairs = join_pairs
-            batch_ms = join_ms
-            cand_step = sum(s_["n_candidates"] for _, _, s_ in jstats) // args.steps
-            launches_step = sum(s_["kernel_launches"] for _, _, s_ in jstats) // args.steps
-
-        plain_ms, same_plain, cand_plain = None, None, 0
-        if "plain" in paths:
-            # ---- the plain per-stage path (on a fresh context) --------------------------
-            ctx.close()
-            ctx = ej.Context(local)
-            plain = [dataclasses.replace(p, out_len=p.L) for p in params]   # the walk is causal: prefix L
-            infos = [ctx.plan(strings, p, stream) for p in plain]
-            emb = torch.empty(max(i.embedding_bytes for i in infos) // 4 + 1, dtype=torch.int32, device=dev)
-            we = torch.empty(max(i.walk_end_count for i in infos) + 1, dtype=torch.int32, device=dev)
-            keys = torch.empty(max(i.key_count for i in infos) + 1, dtype=torch.int64, device=dev)
-            cand_buf = torch.empty(1 << 16, dtype=torch.int64, device=dev)
-            pout = torch.empty(1 << 16, dtype=torch.int64, device=dev)
-            plain_res = {}
-
-            def plain_step():
-                nonlocal cand_buf, pout
-                for i, p in enumerate(plain):
-                    ctx.embed(strings, p, emb, we, stream)
-                    ctx.sign(strings, p, emb, we, keys, stream)
-                    while True:
-                        try:
-                            nc, _ = ctx.lsh_candidates(strings, p, keys, cand_buf, stream)
-                            break
-                        except ej.EJError as e:
-                            if e.status != ej.EJ_ERR_CAPACITY:
-                                raise
-                            cand_buf = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-                            pout = torch.empty(e.needed + 1024, dtype=torch.int64, device=dev)
-                    k = ctx.verify(strings, p, cand_buf[:nc], pout, stream)
-                    plain_res[i] = (nc, pout[:k].clone())
-
-            plain_step()
-            plain_ms = timed(plain_step, args.plain_steps, None)
-            same_plain = all(torch.equal(plain_res[i][1], result_pairs[i]) for i in range(len(params)))
-            cand_plain = sum(plain_res[i][0] for i in range(len(params)))
-    clocks = clk.summary()
-
-    batch_ms_max = allreduce(batch_ms, world, "max")
-    value = allreduce(cand_step * args.steps, world, "sum") / (batch_ms_max / 1e3)
-
-    # verify kernel roofline, from the ej_join pass (events around each verify launch)
-    verify_ms = sum(s["ms_verify"] for _, _, s in jstats)
-    word_cols = sum(s["verify_word_columns"] for _, _, s in jstats)
-    n_verify = sum(1 for _, _, s in jstats if s["n_candidates"] > 0)
-    ach_ops = word_cols * INT_OPS_PER_WORD_COLUMN / (verify_ms / 1e3) if verify_ms else 0.0
-    peak_ops = SMS * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
-    per_k = {}
-    for K in Ks:
-        rows = [s for k, _, s in jstats if k == K]
-        per_k[str(K)] = {
-            "join_ms": statistics.mean(s["ms_total"] for s in rows),
-            "prepare_ms": statistics.mean(s["ms_prepare"] for s in rows),
-            "embed_sign_ms": statistics.mean(s["ms_embed_sign"] for s in rows),
-            "candidates_ms": statistics.mean(s["ms_candidates"] for s in rows),
-            "verify_ms": statistics.mean(s["ms_verify"] for s in rows),
-            "candidates": rows[0]["n_candidates"], "raw_pairs": rows[0]["n_raw_pairs"],
-            "out_pairs": rows[0]["n_out"], "max_bucket": rows[0]["max_bucket"],
-            "band_cells": rows[0]["band_cells"],
-        }
+    batch_ms_max = allreduce(r["batch_ms"], world, "max")
+    steps = r["steps"]
+    value = allreduce(r["cand_step"] * steps, world, "sum") / (batch_ms_max / 1e3)
+    per_k = r.get("per_K", {})
     cells_step = sum(v["band_cells"] for v in per_k.values())
-    join_roofline = {"kernel": "the verifier of ej_join, one launch per join (persistent verify_pq_kernel for "
-                               "mean string length >= 2048, else grid-strided verify_bd_kernel)", "bound": "alu",
-                     "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (32-bit integer ops)",
-                     "frac": ach_ops / peak_ops, "traffic": verify_traffic("join"),
-                     "launches": n_verify, "avg_launch_ms": verify_ms / max(n_verify, 1),
-                     "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": word_cols,
-                     "measured_in": "the ej_join pass (CUDA events around each verify launch, its stream)",
-                     "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"}
-    roofline = join_roofline
-    if merged_ms:
-        m_ms = statistics.mean(merged_ms)
-        m_ops = merged_word_cols * INT_OPS_PER_WORD_COLUMN / (m_ms / 1e3)
-        roofline = {"kernel": "verify_pq_kernel (the batch's merged launch over all joins' candidates)",
-                    "bound": "alu", "achieved": m_ops / 1e12, "peak": peak_ops / 1e12,
-                    "unit": "Tops/s (32-bit integer ops)", "frac": m_ops / peak_ops,
-                    "traffic": verify_traffic("merged"), "launches": len(merged_ms), "avg_launch_ms": m_ms,
-                    "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": merged_word_cols,
-                    "word_columns_basis": "columns advanced x 64-bit words of each join's own band",
-                    "measured_in": "the batch issued without a graph (same kernels), timed steps: CUDA events "
-                                   "around the merged launch, on its stream",
-                    "peak_basis": "integer ALU pipe: 152 SMs x 64 lanes/clock x 2070 MHz (derived)"}
+    roofline = r.get("merged_roofline") or r.get("join_roofline")
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": warm, "ms_per_step": batch_ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": batch_ms_max / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{wl['desc'](ss, args)}; K={','.join(map(str, Ks))}; "
                                    f"r={params[0].r}, m={params[0].m}, z={'/'.join(str(p.z) for p in params)}, "
                                    f"L={params[0].L}; one step = one join per K" +
-                                   (", the joins of a step captured as one CUDA graph (ej_batch)" if use_batch
+                                   (", the joins of a step captured as one CUDA graph (ej_batch)" if r["use_batch"]
                                     else ", one ej_join call per K"),
                        "n": ss.n, "Ks": list(Ks), "l2": "flushed before each timed step (256 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU", "autotune": args.autotune},
-            "join_wall_s_per_step": batch_ms_max / args.steps / 1e3,
-            "band_cells_per_s": allreduce(cells_step * args.steps, world, "sum") / (batch_ms_max / 1e3),
-            "join_path": {"value": cand_step * args.steps / (join_ms / 1e3), "ms_per_step": join_ms / args.steps,
-                          "api": "ej_join per K", "identical_output": bool(same_join)},
-            "plain_path": None if plain_ms is None else {
-                "value": cand_plain * args.plain_steps / (plain_ms / 1e3), "ms_per_step": plain_ms / args.plain_steps,
-                "steps": args.plain_steps, "api": "ej_embed -> ej_sign -> ej_lsh_candidates -> ej_verify per K",
-                "identical_output": bool(same_plain)},
-            "eager_batch_path": None if eager_ms is None else {
-                "ms_per_step": eager_ms / args.steps, "value": cand_step * args.steps / (eager_ms / 1e3),
-                "api": "ej_batch with EJ_BATCH_EAGER (the same work issued every step without a graph)",
-                "identical_output": bool(same_eager)},
+                       "parallelism": "replicas" if world > 1 else "single GPU", "autotune": args.autotune,
+                       "headline": ("the plain method on long strings on one GPU heads the line; the protein-like, "
+                                    "text-like and serving workloads are measured at full size under 'workloads'")},
+            "join_wall_s_per_step": batch_ms_max / steps / 1e3,
+            "band_cells_per_s": allreduce(cells_step * steps, world, "sum") / (batch_ms_max / 1e3),
+            **r["paths"],
             "per_K": per_k,
             "roofline": roofline,
-            "join_path_roofline": join_roofline,
-            "clocks": clocks,
-            "gpu_launches": int(launches_step * args.steps),
-            "e2e": e2e,
+            "join_path_roofline": r.get("join_roofline"),
+            "stage_roofline": r.get("stage_roofline"),
+            "int_peak": int_peak,
+            "clocks": head_clocks,
+            "gpu_launches": int(r["launches_step"] * steps),
+            "e2e": r["e2e"],
+            "recall": recall,
+            "workloads": full,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, args, Ks)
+            if args.workload == "long_dna" and args.clusters == 2000:
+                got = [p.cpu().numpy().view("uint64") for p in r["result_pairs"]]
+                line["cpu_baseline"]["all_cores"] = cpu_all_cores(ss, params, got)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -124,6 +124,14 @@ typedef struct {
                                 actually advanced (ceil((2K+1)/64) words per
                                 column, early exit included) */
     int64_t kernel_launches; /* CUDA kernels this call launched */
+    /* finer stage times (ms, only with ej_set_timing(ctx, 1)): the part of
+       ms_prepare spent validating and packing the strings, and ms_candidates
+       split into the bucket stage (signature sets, or sorted tables, and the
+       emission of raw pairs) and the deduplication with the candidate order */
+    float ms_pack;
+    float ms_buckets;
+    float ms_dedup;
+    float ms_reserved;       /* 0 */
 } ej_join_stats;
 
 /* Create a context bound to CUDA device `device`. *ctx is NULL on failure. */
@@ -168,6 +176,20 @@ int ej_set_verify_config(ej_ctx *ctx, int lanes_per_pair, int words_per_lane, in
  * passes < 0.
  */
 int ej_set_loop_bound(ej_ctx *ctx, int64_t passes);
+
+/*
+ * Measurement helper (the paper has no counterpart): the throughput of the
+ * GPU's 32-bit integer instructions, the roofline denominator of the verifier,
+ * whose inner step is 32-bit logic, adds with carry and shifts. Every thread of
+ * a full-occupancy grid runs independent chains (iters passes of 64
+ * instructions) of lop3.b32 and add.u32 alternating (mix 0), lop3.b32 only
+ * (mix 1) or add.u32 only (mix 2); the best of three timed launches (CUDA
+ * events) gives *ops_per_s, instructions per second over the whole GPU, and
+ * *ms its duration. Allocates 4 bytes and a stream of its own.
+ * Errors: EJ_ERR_INVALID_ARG (mix outside 0..2, iters <= 0, NULL ops_per_s),
+ * EJ_ERR_CUDA.
+ */
+int ej_measure_int_peak(int device, int32_t mix, int32_t iters, double *ops_per_s, double *ms);
 
 /*
  * Similarity search against a resident index (EmbedJoin's structure kept on the
@@ -312,9 +334,10 @@ void ej_batch_destroy(ej_batch *batch);
  *     (one pass over the pairs; a warp's slots start together and the warp ends
  *     with its slowest pair). 0 (default): 1 when the strings' mean length is at
  *     least 2048 (long pairs, where refilling pays), else 2.
- *   chain (batches): how the persistent verifiers of a batch's joins share the
- *     GPU (merged, chained or overlapping; the other stages always overlap);
- *     see the field.
+ *   chain (batches): how the verifiers of a batch's joins share the GPU: the
+ *     persistent ones merged, chained or overlapping, the grid-strided ones
+ *     chained unless chain is 1 (the other stages always overlap); see the
+ *     field.
  *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
  *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
  *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
@@ -335,7 +358,9 @@ void ej_batch_destroy(ej_batch *batch);
  *     (a signature of z samples is one of more samples modulo (|alphabet|+1)^z),
  *     each partner checked against the join's own signature and K; 1 keeps
  *     every join's own buckets. Tables of up to 21845 records are bucketed in
- *     shared memory, one block per table, which pays for small buckets only.
+ *     shared memory, one block per table, which pays for small buckets only;
+ *     a batch moves a join whose sizing pass finds a bucket of more than 256
+ *     records to the buckets in global memory.
  *     2: the tables are sorted by (signature, length) and each record pairs
  *     with the window after it (the ej_lsh_candidates path). It is much
  *     cheaper when a few signatures collect thousands of strings, e.g. short
@@ -348,7 +373,9 @@ typedef struct {
     int32_t warps_per_subpartition;
     int32_t order;
     int32_t buckets;
-    int32_t chain;   /* batches, joins that use the persistent verifier: 3: one merged launch
+    int32_t chain;   /* batches: joins on the grid-strided verifier are verified one after
+                        another unless chain is 1. Joins that use the persistent verifier:
+                        3: one merged launch
                         verifies them all, at the widest of their bands, each pair with its
                         own join's K, largest K first (the queue runs from one join's pairs
                         into the next, so no join waits for another's last pairs); 2: one
@@ -473,6 +500,30 @@ int ej_verify_noalloc(const ej_strings *strings, const ej_params *params, const 
  */
 int ej_join(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, uint64_t *out,
             int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream);
+
+/*
+ * EmbedJoin+ (Section 5, Algorithms 4 and 5): the join for strings whose
+ * alignments start with a long run of insertions (a shift), which plain
+ * EmbedJoin's walks do not absorb. Every string s_i is embedded S times, as
+ * its suffixes s_i[(k-1)*delta ..] for k = 1 .. S, S = ceil(K/delta) (at least
+ * 1), each with the same random strings and sampled positions as ej_join
+ * (out_len and L those of the whole strings). A match is a pair of substrings
+ * (x, k_x), (y, k_y) of two different strings x, y with ||x| - |y|| <= K whose
+ * signatures agree in one table; a pair (x, y) is a candidate when some
+ * substring pair of it matches in at least T tables (Section 5 uses T = 2 when
+ * S > 1, else 1, with which EmbedJoin+ is EmbedJoin). Candidates with
+ * ED <= K are the output, sorted ascending as for ej_join.
+ * stats: n_raw_pairs = matches (substring pairs, once per table), n_candidates,
+ * n_out, max_bucket (records of one signature in one table, a record being one
+ * substring), band_cells and verify_word_columns of the verification; stage
+ * times as ej_join's when timing is on (ms_candidates covers the buckets, the
+ * match counting and the dedup). Synchronises `stream`.
+ * Errors: EJ_ERR_INVALID_ARG (delta <= 0, T < 1, and those of ej_join),
+ * EJ_ERR_UNSUPPORTED (n * S * r * m records beyond 2^32), EJ_ERR_CAPACITY
+ * (*n_out = needed).
+ */
+int ej_join_plus(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, int32_t delta, int32_t T,
+                 uint64_t *out, int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream);
 
 /*
  * Test hook for the running example of Section 4 (Tables 2-4): replace the

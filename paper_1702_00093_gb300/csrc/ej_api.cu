@@ -29,6 +29,7 @@ enum BufId {
     B_PACKED, B_CHUNK_CNT, B_POFS, B_SCAN_TMP3, B_TSYM, B_SPOS, B_STAG,
     B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS, B_BKEYS, B_BHEADS, B_BNEXT, B_FBINS, B_FSTARTS,
     B_FSCAN,
+    B_PLUS_SUBLEN, B_PLUS_WHOLE, B_PLUS_SUBOFF, B_PLUS_BYTES, B_PLUS_SCAN, B_PLUS_CAND,
     B_NUM
 };
 
@@ -58,13 +59,15 @@ struct ej_ctx {
     uint32_t pos_m = 0, pos_z = 0, pos_r = 0;
     // pinned host counters
     int64_t *h_cnt = nullptr;
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[9] = {};   // ej_join stage timing: [0] start .. [5] end, [6]/[7] pack, [8] after buckets
     // raw-pair capacity remembered from the previous join (grows on overflow)
     uint64_t raw_cap_hint = 0;
     // verifier tiling override (0 = automatic)
     int vG = 0, vV = 0, vWarps = 0;
     ej_schedule sched{0, 0, 0, 0, 0, 0};   // ej_join's back-half schedule (ej_set_schedule)
     int64_t loop_bound = 0;   // persistent verifier: loop passes per warp (ej_set_loop_bound; 0 = default)
+    bool no_smem_buckets = false;   // a batch join with huge buckets: hashed buckets in global memory
+    ej_ctx *plus_sub = nullptr;     // ej_join_plus: the context of the suffix set
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -235,6 +238,7 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     CK(cudaMemsetAsync(derr, 0, 4 * sizeof(uint32_t), s));
     CKS(ensure_t(ctx, B_LENS, (size_t)(n > 0 ? n : 1), &pl->lens));
     unsigned long long *dmax = (unsigned long long *)(derr + 2);
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_validate(pl->st.bytes, pl->st.offsets, n, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->lens,
                        derr, dmax, s));
     // pack into B-bit codes: chunk counts -> offsets -> pack (flags bad symbols)
@@ -252,6 +256,7 @@ int make_plan(ej_ctx *ctx, const ej_strings *S, const ej_params *p, bool need_ls
     CK(exclusive_scan_u32(ccnt, pofs, n + 1, nullptr, stmp, s));
     CK(launch_pack(pl->st.bytes, pl->st.offsets, pl->lens, n, total, (const uint8_t *)ctx->bufs[B_CODEMAP].p, pl->B,
                    pofs, packed, derr, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[7], s));
     pl->packed = packed;
     pl->pofs = pofs;
     CK(cudaMemcpyAsync(ctx->h_cnt, derr, 16, cudaMemcpyDeviceToHost, s));
@@ -655,6 +660,11 @@ struct BackState {
     VerifyConfig vc{0, 0, 0};
 };
 
+// Largest bucket (records of one signature in one table) that a batch join
+// keeps in shared memory; its sizing pass moves joins with larger ones to the
+// hashed buckets in global memory.
+constexpr unsigned SMEM_BUCKET_MAX = 256;
+
 int back_buckets(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, BackState *bs,
                  cudaStream_t s) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
@@ -662,7 +672,7 @@ int back_buckets(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t
     CKS(ensure_t(ctx, B_DERR, 8, &derr));
     CK(cudaMemsetAsync(derr, 0, 4, s));
     bs->hashed = ctx->sched.buckets != 2 && n * T < (int64_t)0xFFFFFFFFll;
-    bs->table_smem = bs->hashed && bucket_table_smem(n) > 0;
+    bs->table_smem = bs->hashed && bucket_table_smem(n) > 0 && !ctx->no_smem_buckets;
     bs->keys = keys;
     if (bs->table_smem) {
         // built by the emitting kernel, one block per table
@@ -734,6 +744,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
         CK(launch_bucket_emit(pl.lens, n, T, p->K, bs.bnext, raw, cap, cnt, s));
     else
         CK(launch_emit_append(bs.srk, bs.srid, pl.lens, n, T, p->K, raw, cap, cnt, s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[8], s));
     // queue order: 0 follows the verifier (persistent: length classes; grid-
     // strided: by first string), measured best for each on the long-DNA and the
     // protein-like / text-like shapes
@@ -1199,10 +1210,10 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
             cst = batch_join_keys(b->joins, j, j.side, 2);
             if (cst == EJ_OK && cudaEventRecord(j.keyed, j.side) != cudaSuccess) cst = EJ_ERR_CUDA;
         }
-    // persistent verifiers run one after another unless chain == 1: two persistent
-    // grids sharing the SMs (each capping its working warps per SM) measured from
-    // slightly faster to 10x slower from one replay to the next; every other stage
-    // overlaps
+    // verifiers run one after another unless chain == 1: two persistent grids
+    // sharing the SMs (each capping its working warps per SM) measured from
+    // slightly faster to 10x slower from one replay to the next, and two grid-
+    // strided ones each fill the GPU; every other stage overlaps
     // shared buckets: each owner inserts and emits its members' pairs
     for (auto &j : b->joins)
         if (cst == EJ_OK && !j.bucket_members.empty()) cst = batch_shared_emit(b, j);
@@ -1222,8 +1233,10 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
             // verified by the merged launch below
             cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, nullptr, nullptr, &unused, shared);
         } else {
-            const int pt = pq_choice(j.sub, j.pl, &j.p, j.bs.vc);
-            const bool heavy = pt > 0 && ctx->sched.chain != 1;
+            // every verifier of a batch fills the GPU on its own: they run one
+            // after another (chain 1: free to overlap) while the other joins'
+            // walks, buckets and dedup overlap them
+            const bool heavy = ctx->sched.chain != 1;
             cst = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, j.side, heavy ? prev_verify : nullptr,
                                heavy ? j.verified : nullptr, nullptr, shared);
             if (heavy) prev_verify = j.verified;
@@ -1386,6 +1399,7 @@ void ej_destroy(ej_ctx *c) {
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    if (c->plus_sub) ej_destroy(c->plus_sub);
     delete c;
 }
 
@@ -1636,6 +1650,198 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
             cudaEventElapsedTime(&stats->ms_candidates, ctx->ev[2], ctx->ev[3]);
             cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
             cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[5]);
+            cudaEventElapsedTime(&stats->ms_pack, ctx->ev[6], ctx->ev[7]);
+            cudaEventElapsedTime(&stats->ms_buckets, ctx->ev[2], ctx->ev[8]);
+            cudaEventElapsedTime(&stats->ms_dedup, ctx->ev[8], ctx->ev[3]);
+        }
+    }
+    return EJ_OK;
+}
+
+
+// EmbedJoin+ (Section 5, Alg. 4 and 5). The suffixes become the strings of a
+// device set of their own (record q = i*S + k), signed by the ordinary fused
+// walk with the whole strings' out_len and L; the hashed buckets emit every
+// pair of records sharing a bucket once per table, filtered by the whole
+// strings' lengths; after a sort of those record pairs (Alg. 5's matches
+// (x, y, k_x, k_y)), runs of at least T of them between different strings give
+// the candidates, which are verified on the whole strings.
+int ej_join_plus(ej_ctx *ctx, const ej_strings *S, const ej_params *p, int32_t delta, int32_t T, uint64_t *out,
+                 int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream) {
+    if (!ctx || !n_out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_out");
+    *n_out = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (delta <= 0 || T < 1) return fail(ctx, EJ_ERR_INVALID_ARG, "delta must be > 0 and T >= 1");
+    const int64_t launches0 = launches_so_far();
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    const int64_t n = pl.st.n;
+    if (n < 2) return EJ_OK;
+    if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
+    const int32_t nsub = p->K > 0 ? (int32_t)(((int64_t)p->K + delta - 1) / delta) : 1;
+    const int64_t nq = n * (int64_t)nsub, TT = (int64_t)p->r * p->m;
+    if (nq >= (1ll << 31) || nq * TT >= 0xFFFFFFFFll)
+        return fail(ctx, EJ_ERR_UNSUPPORTED, "strings x substrings x tables beyond the 32-bit record ids");
+    // the suffix set
+    uint32_t *sub_len = nullptr;
+    int32_t *whole = nullptr;
+    uint64_t *sub_off = nullptr;
+    void *scan = nullptr;
+    CKS(ensure_t(ctx, B_PLUS_SUBLEN, (size_t)nq + 1, &sub_len));
+    CKS(ensure_t(ctx, B_PLUS_WHOLE, (size_t)nq, &whole));
+    CKS(ensure_t(ctx, B_PLUS_SUBOFF, (size_t)nq + 1, &sub_off));
+    CKS(ensure(ctx, B_PLUS_SCAN, scan_temp_bytes(nq + 1), &scan));
+    CK(cudaMemsetAsync(sub_len + nq, 0, sizeof(uint32_t), s));
+    CK(launch_suffix_lengths(pl.lens, n, nsub, delta, sub_len, whole, s));
+    CK(exclusive_scan_u32(sub_len, sub_off, nq + 1, nullptr, scan, s));
+    CK(cudaMemcpyAsync(ctx->h_cnt, sub_off + nq, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t sub_total = ctx->h_cnt[0];
+    uint8_t *sub_bytes = nullptr;
+    CKS(ensure_t(ctx, B_PLUS_BYTES, (size_t)(sub_total > 0 ? sub_total : 1), &sub_bytes));
+    CK(launch_suffix_copy(pl.st.bytes, pl.st.offsets, n, nsub, delta, sub_off, sub_bytes, s));
+    if (!ctx->plus_sub && ej_create(&ctx->plus_sub, ctx->device) != EJ_OK)
+        return fail(ctx, EJ_ERR_OOM, "suffix-set context");
+    ej_ctx *sub = ctx->plus_sub;
+    sub->sched = ctx->sched;
+    ej_strings sset{sub_bytes, (const int64_t *)sub_off, nq};
+    ej_params sp = *p;
+    sp.out_len = pl.out_len;   // the whole strings' embedding length and sampling range
+    sp.L = pl.L;
+    Plan spl;
+    auto sub_fail = [&](int st) { return fail(ctx, st, "suffix set: %s", sub->err.c_str()); };
+    int st = make_plan(sub, &sset, &sp, true, &spl, s);
+    if (st != EJ_OK) return sub_fail(st);
+    uint64_t *keys = nullptr;
+    if ((st = ensure_t(sub, B_KEYS, (size_t)(TT * nq), &keys)) != EJ_OK) return sub_fail(st);
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+    if ((st = keys_dev(sub, &sp, spl, keys, s)) != EJ_OK) return sub_fail(st);
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
+    // buckets of the suffix records, matches filtered by the whole strings' lengths
+    const uint64_t H = bucket_slots_per_table(nq);
+    uint64_t *bkeys = nullptr;
+    uint32_t *bheads = nullptr, *bnext = nullptr, *derr = nullptr;
+    unsigned long long *cnt = nullptr;
+    CKS(ensure_t(sub, B_BKEYS, (size_t)(H * TT), &bkeys));
+    CKS(ensure_t(sub, B_BHEADS, (size_t)(H * TT), &bheads));
+    CKS(ensure_t(sub, B_BNEXT, (size_t)(nq * TT), &bnext));
+    CKS(ensure_t(sub, B_DERR, 8, &derr));
+    CKS(ensure_t(sub, B_JCOUNT, 8, &cnt));
+    CK(cudaMemsetAsync(derr, 0, 4, s));
+    CK(cudaMemsetAsync(bkeys, 0xFF, H * TT * sizeof(uint64_t), s));
+    CK(cudaMemsetAsync(bheads, 0xFF, H * TT * sizeof(uint32_t), s));
+    CK(launch_bucket_insert(keys, nq, TT, H, bkeys, bheads, bnext, derr, s));
+    uint64_t cap = (uint64_t)(nq * 4 > 65536 ? nq * 4 : 65536);
+    uint64_t *raw = nullptr, *raw2 = nullptr;
+    int64_t nraw = 0;
+    for (int attempt = 0;; attempt++) {
+        CKS(ensure_t(sub, B_RAW, (size_t)cap, &raw));
+        CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+        CK(launch_bucket_emit(whole, nq, TT, p->K, bnext, raw, cap, cnt, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        nraw = ctx->h_cnt[0];
+        if ((uint64_t)nraw <= cap) break;
+        if (attempt > 2) return fail(ctx, EJ_ERR_CUDA, "match count changed between attempts");
+        cap = (uint64_t)nraw + (uint64_t)nraw / 8 + 1024;
+    }
+    const int64_t max_bucket = ctx->h_cnt[1];
+    // count the matches of every record pair (sorted), keep runs of >= T
+    const int nb = bits_for((uint64_t)(nq > 1 ? nq - 1 : 1));
+    int shifts[16];
+    int np = 0;
+    for (int b = 0; b < nb; b += 8) shifts[np++] = b;
+    for (int b = 0; b < nb; b += 8) shifts[np++] = 32 + b;
+    int64_t ncp = 0;
+    uint64_t *cp = nullptr, *cp2 = nullptr;
+    const uint64_t *sorted = raw;
+    bool alt = false;
+    if (nraw > 0) {
+        const size_t rs = radix_counts_len(nraw, 1);
+        uint32_t *rsc = nullptr;
+        uint64_t *rso = nullptr;
+        void *stmp = nullptr;
+        CKS(ensure_t(sub, B_RAW_ALT, (size_t)nraw, &raw2));
+        CKS(ensure_t(sub, B_RS_COUNTS, rs, &rsc));
+        CKS(ensure_t(sub, B_RS_OFFS, rs, &rso));
+        CKS(ensure(sub, B_SCAN_TMP, scan_temp_bytes((int64_t)rs), &stmp));
+        CK(radix_sort_segmented(raw, nullptr, raw2, nullptr, nraw, 1, shifts, np, RadixTemp{rsc, rso, stmp}, &alt, s));
+        sorted = alt ? raw2 : raw;
+        CKS(ensure_t(sub, B_CAND, (size_t)nraw, &cp));
+        CK(launch_plus_runs(sorted, nraw, nsub, T, cp, (uint64_t)nraw, cnt + 2, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, cnt + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ncp = ctx->h_cnt[0];
+    }
+    // candidate string pairs: sorted, unique
+    int64_t ncand = 0;
+    uint64_t *cand = nullptr;
+    if (ncp > 0) {
+        const int nbs = bits_for((uint64_t)(n - 1));
+        np = 0;
+        for (int b = 0; b < nbs; b += 8) shifts[np++] = b;
+        for (int b = 0; b < nbs; b += 8) shifts[np++] = 32 + b;
+        const size_t rs = radix_counts_len(ncp, 1);
+        uint32_t *rsc = nullptr;
+        uint64_t *rso = nullptr;
+        void *stmp = nullptr;
+        CKS(ensure_t(sub, B_APP, (size_t)ncp, &cp2));
+        CKS(ensure_t(sub, B_RS_COUNTS, rs, &rsc));
+        CKS(ensure_t(sub, B_RS_OFFS, rs, &rso));
+        CKS(ensure(sub, B_SCAN_TMP, scan_temp_bytes((int64_t)rs), &stmp));
+        CK(radix_sort_segmented(cp, nullptr, cp2, nullptr, ncp, 1, shifts, np, RadixTemp{rsc, rso, stmp}, &alt, s));
+        const uint64_t *sp_ = alt ? cp2 : cp;
+        uint8_t *fl = nullptr;
+        uint64_t *fo = nullptr;
+        void *stmp2 = nullptr;
+        CKS(ensure_t(sub, B_FLAGS, (size_t)ncp, &fl));
+        CKS(ensure_t(sub, B_FLAG_OFFS, (size_t)ncp, &fo));
+        CKS(ensure(sub, B_SCAN_TMP2, scan_temp_bytes(ncp), &stmp2));
+        CK(launch_unique_flags(sp_, ncp, fl, s));
+        CK(exclusive_scan_u8(fl, fo, ncp, (uint64_t *)(cnt + 3), stmp2, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, cnt + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ncand = ctx->h_cnt[0];
+        CKS(ensure_t(ctx, B_PLUS_CAND, (size_t)(ncand > 0 ? ncand : 1), &cand));
+        CK(launch_compact_u64(sp_, fl, fo, ncp, cand, s));
+    }
+    // verification on the whole strings (Section 3.3)
+    int64_t cntout = 0;
+    uint64_t work[2] = {0, 0};
+    CKS(verify_dev(ctx, pl, p, cand, ncand, nullptr, 0, &cntout, s, work));
+    *n_out = cntout;
+    if (stats) {
+        stats->n_raw_pairs = nraw;
+        stats->n_candidates = ncand;
+        stats->n_out = cntout;
+        stats->max_bucket = max_bucket;
+        stats->band_cells = work[0];
+        stats->verify_word_columns = work[1];
+    }
+    if (cntout > capacity)
+        return fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cntout,
+                    (long long)capacity);
+    if (cntout > 0) {
+        void *d_out = nullptr;
+        bool h_out = false;
+        CKS(out_target(ctx, B_OUT_STAGE, out, (size_t)cntout * sizeof(uint64_t), &d_out, &h_out));
+        CK(launch_compact_u64(cand, (const uint8_t *)ctx->bufs[B_FLAGS].p, (const uint64_t *)ctx->bufs[B_FLAG_OFFS].p,
+                              ncand, (uint64_t *)d_out, s));
+        if (h_out) CK(cudaMemcpyAsync(out, d_out, (size_t)cntout * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    }
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[5], s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->kernel_launches = launches_so_far() - launches0;
+        if (ctx->timing) {
+            cudaEventElapsedTime(&stats->ms_prepare, ctx->ev[0], ctx->ev[1]);
+            cudaEventElapsedTime(&stats->ms_embed_sign, ctx->ev[1], ctx->ev[2]);
+            cudaEventElapsedTime(&stats->ms_candidates, ctx->ev[2], ctx->ev[3]);
+            cudaEventElapsedTime(&stats->ms_verify, ctx->ev[3], ctx->ev[4]);
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[5]);
         }
     }
     return EJ_OK;
@@ -1711,6 +1917,15 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         for (int attempt = 0;; attempt++) {
             if ((st = back_attempt(j.sub, j.pl, &j.p, j.bs, cap, s)) != EJ_OK) return bail(st);
             if ((st = back_read(j.sub, hc, s)) != EJ_OK) return bail(st);
+            if (j.bs.table_smem && hc[1] > (unsigned long long)SMEM_BUCKET_MAX) {
+                // a table in one block's shared memory walks a bucket of b records
+                // in b(b-1)/2 steps on one SM: huge buckets go to global memory,
+                // where every SM takes part
+                j.sub->no_smem_buckets = true;
+                if ((st = back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s)) != EJ_OK) return bail(st);
+                attempt = -1;
+                continue;
+            }
             if (hc[0] <= cap) break;
             if (attempt > 2) return bail(fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts"));
             cap = hc[0] + hc[0] / 4 + 1024;

@@ -225,6 +225,14 @@ cudaError_t launch_compact_u64(const uint64_t *in, const uint8_t *flags, const u
 cudaError_t launch_emit_append(const uint64_t *rec_keys, const uint32_t *rec_ids, const int32_t *lens, int64_t n,
                                int64_t T, int32_t K, uint64_t *raw, uint64_t cap, unsigned long long *counters,
                                cudaStream_t s);
+// EmbedJoin+ (ej_plus.cu): the suffix set of every string (record q = i*S + k)
+// and the candidate pairs from the sorted record-pair matches.
+cudaError_t launch_suffix_lengths(const int32_t *lens, int64_t n, int32_t S, int32_t delta, uint32_t *sub_len,
+                                  int32_t *whole_len, cudaStream_t s);
+cudaError_t launch_suffix_copy(const uint8_t *bytes, const int64_t *offsets, int64_t n, int32_t S, int32_t delta,
+                               const uint64_t *sub_off, uint8_t *out, cudaStream_t s);
+cudaError_t launch_plus_runs(const uint64_t *sorted, int64_t nraw, int32_t S, int32_t T, uint64_t *out,
+                             uint64_t cap, unsigned long long *count, cudaStream_t s);
 // Buckets by hashing (ej_join): per-table signature sets of H slots
 // (bucket_slots_per_table(n)); slot_keys filled with ~0, heads with 0xFF bytes.
 uint64_t bucket_slots_per_table(int64_t n);

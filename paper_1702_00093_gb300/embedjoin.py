@@ -29,7 +29,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
-            "ej_set_schedule", "ej_set_loop_bound", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_set_schedule", "ej_set_loop_bound", "ej_measure_int_peak", "ej_join_plus", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
             "ej_batch_verify_ms",
             "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
             "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
@@ -88,7 +88,8 @@ class JoinStats(C.Structure):
                 ("max_bucket", C.c_int64), ("ms_prepare", C.c_float), ("ms_embed_sign", C.c_float),
                 ("ms_candidates", C.c_float), ("ms_verify", C.c_float), ("ms_total", C.c_float),
                 ("band_cells", C.c_uint64), ("verify_word_columns", C.c_uint64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("ms_pack", C.c_float), ("ms_buckets", C.c_float),
+                ("ms_dedup", C.c_float), ("ms_reserved", C.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -140,8 +141,13 @@ def lib():
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
+        L.ej_join_plus.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64), vp, vp]
+        L.ej_join_plus.restype = C.c_int
         L.ej_set_loop_bound.argtypes = [vp, C.c_int64]
         L.ej_set_loop_bound.restype = C.c_int
+        L.ej_measure_int_peak.argtypes = [C.c_int, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]
+        L.ej_measure_int_peak.restype = C.c_int
         L.ej_set_schedule.argtypes = [vp, C.POINTER(_Schedule)]
         L.ej_set_schedule.restype = C.c_int
         L.ej_batch_create.argtypes = [vp, C.POINTER(_Strings), C.POINTER(_Params), C.c_int32, C.c_int32,
@@ -376,6 +382,41 @@ class Context:
                     raise
                 capacity = e.needed
 
+    def join_plus_into(self, s: Strings, p: Params, delta: int, T: int, out, stream=None) -> tuple[int, JoinStats]:
+        """ej_join_plus into a caller buffer. Raises EJError with .needed on overflow."""
+        cs, (cp, _keep) = s._c(), p._c()
+        n = C.c_int64(0)
+        stats = JoinStats()
+        cap = 0 if out is None else int(out.shape[0])
+        st = lib().ej_join_plus(self._h, C.byref(cs), C.byref(cp), delta, T, _ptr(out), cap, C.byref(n),
+                                C.byref(stats), _stream(stream))
+        if st == EJ_ERR_CAPACITY:
+            e = EJError(st, "ej_join_plus: capacity")
+            e.needed = n.value
+            raise e
+        self._check(st, "ej_join_plus")
+        return n.value, stats
+
+    def join_plus(self, s: Strings, p: Params, delta: int, T: int | None = None, device=None,
+                  capacity: int = 1 << 16, stream=None):
+        """EmbedJoin+ (Section 5): (pairs, stats) as join(); T defaults to 2 when
+        ceil(K/delta) > 1, else 1."""
+        if T is None:
+            T = 2 if max(1, -(-p.K // delta)) > 1 else 1
+        while True:
+            if device is None:
+                out = np.zeros(max(capacity, 1), dtype=np.uint64)
+            else:
+                import torch
+                out = torch.empty(max(capacity, 1), dtype=torch.int64, device=device)
+            try:
+                n, stats = self.join_plus_into(s, p, delta, T, out, stream)
+                return out[:n], stats
+            except EJError as e:
+                if e.status != EJ_ERR_CAPACITY:
+                    raise
+                capacity = e.needed
+
     def set_test_tables(self, pi=None, positions=None):
         """Inject explicit pi tables [r][steps][alphabet] (0/1) and/or positions
         [r][m][z] (the running example's Tables 2-3). No arguments restores RNG."""
@@ -387,6 +428,16 @@ class Context:
             0 if pi_a is None else pi_a.shape[2], _ptr(pos_a),
             0 if pos_a is None else pos_a.shape[1], 0 if pos_a is None else pos_a.shape[2])
         self._check(st, "ej_set_test_tables")
+
+
+def measure_int_peak(device: int = 0, mix: int = 0, iters: int = 4096) -> tuple[float, float]:
+    """ej_measure_int_peak: (32-bit integer instructions/s over the GPU, ms of the
+    timed launch) for mix 0 (lop3 + add), 1 (lop3) or 2 (add)."""
+    ops, ms = C.c_double(0.0), C.c_double(0.0)
+    st = lib().ej_measure_int_peak(device, mix, iters, C.byref(ops), C.byref(ms))
+    if st != EJ_OK:
+        raise EJError(st, f"ej_measure_int_peak: {lib().ej_status_string(st).decode()}")
+    return ops.value, ms.value
 
 
 def verify_noalloc(s: Strings, p: Params, pairs, out, stream=None) -> int:

@@ -82,7 +82,7 @@ int main(void) {{
   printf("ej_server_stats %zu\\n", sizeof(ej_server_stats));
   F(ej_params, seed) F(ej_params, alphabet) F(ej_params, alphabet_size) F(ej_params, K)
   F(ej_plan_info, embedding_bytes) F(ej_plan_info, key_count)
-  F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total)
+  F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total) F(ej_join_stats, ms_pack) F(ej_join_stats, ms_dedup)
   F(ej_schedule, warps_per_subpartition) F(ej_schedule, order) F(ej_schedule, buckets) F(ej_schedule, chain)
   F(ej_server_config, max_batch_bytes) F(ej_server_config, hbm_reserve) F(ej_server_config, hbm_budget)
   F(ej_search_result, status) F(ej_search_result, matches) F(ej_search_result, queue_ms)

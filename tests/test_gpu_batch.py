@@ -266,3 +266,29 @@ def test_batch_misuse_is_reported(ej, ctx, stream):
             b.result(0, device=DEV, stream=stream)
         assert e.value.status == ej.EJ_ERR_INVALID_ARG
         b.close()
+
+
+def test_batch_moves_huge_buckets_to_global_memory_and_chains_verifiers(ej, ctx, stream):
+    """Short protein-like strings whose walks end early share signatures made of
+    the bottom symbol: buckets of hundreds of records. The batch's sizing pass
+    moves such joins from one block's shared memory to the buckets in global
+    memory, and its grid-strided verifiers run one after another; every join
+    still equals ej_join and the oracle."""
+    ss = synth.protein_like(7, 3000, median=120, lo=20, hi=400)
+    s = ej.Strings.from_set(ss, DEV)
+    params = [ej.Params(K=K, r=3, m=4, z=8, seed=1, L=600, alphabet=ss.alphabet) for K in (12, 16)]
+    with torch.cuda.stream(stream):
+        b = ctx.batch(s, params, stream=stream)
+        for rep in range(2):
+            b.run(stream)
+            for i, p in enumerate(params):
+                got, st = b.result(i, device=DEV, stream=stream)
+                want, st_j = ctx.join(s, p, device=DEV, stream=stream)
+                assert np.array_equal(_u64(got), _u64(want))
+                assert st.n_candidates == st_j.n_candidates and st.max_bucket > 256
+                if rep == 0:
+                    ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=p.K, r=p.r, m=p.m, z=p.z, seed=p.seed,
+                                      L=p.L)
+                    assert st.n_candidates == ref.n_candidates
+                    assert np.array_equal(_u64(got), ref.pairs)
+        b.close()
