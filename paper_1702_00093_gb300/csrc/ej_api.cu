@@ -1771,10 +1771,11 @@ int ej_join_plus(ej_ctx *ctx, const ej_strings *S, const ej_params *p, int32_t d
         CK(radix_sort_segmented(raw, nullptr, raw2, nullptr, nraw, 1, shifts, np, RadixTemp{rsc, rso, stmp}, &alt, s));
         sorted = alt ? raw2 : raw;
         CKS(ensure_t(sub, B_CAND, (size_t)nraw, &cp));
-        CK(launch_plus_runs(sorted, nraw, nsub, T, cp, (uint64_t)nraw, cnt + 2, s));
-        CK(cudaMemcpyAsync(ctx->h_cnt, cnt + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(launch_plus_runs(sorted, nraw, nsub, T, cp, (uint64_t)nraw, cnt + 2, cnt + 4, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, cnt + 2, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         ncp = ctx->h_cnt[0];
+        nraw -= ctx->h_cnt[2];   // record pairs of one string's substrings are not matches
     }
     // candidate string pairs: sorted, unique
     int64_t ncand = 0;

@@ -232,7 +232,7 @@ cudaError_t launch_suffix_lengths(const int32_t *lens, int64_t n, int32_t S, int
 cudaError_t launch_suffix_copy(const uint8_t *bytes, const int64_t *offsets, int64_t n, int32_t S, int32_t delta,
                                const uint64_t *sub_off, uint8_t *out, cudaStream_t s);
 cudaError_t launch_plus_runs(const uint64_t *sorted, int64_t nraw, int32_t S, int32_t T, uint64_t *out,
-                             uint64_t cap, unsigned long long *count, cudaStream_t s);
+                             uint64_t cap, unsigned long long *count, unsigned long long *same, cudaStream_t s);
 // Buckets by hashing (ej_join): per-table signature sets of H slots
 // (bucket_slots_per_table(n)); slot_keys filled with ~0, heads with 0xFF bytes.
 uint64_t bucket_slots_per_table(int64_t n);

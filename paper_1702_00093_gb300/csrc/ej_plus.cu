@@ -9,7 +9,8 @@
 // table once per table: a record pair (q_a, q_b) is exactly Alg. 5's match
 // (x, y, k_x, k_y). After a sort of the record pairs, a run of equal pairs is
 // the count of that tuple over the tables; a pair of different strings with a
-// count of at least T becomes a candidate.
+// count of at least T becomes a candidate (pairs of two substrings of one
+// string share buckets too; they are counted apart and dropped).
 #include "ej_internal.cuh"
 
 namespace ej {
@@ -52,15 +53,18 @@ __global__ void suffix_copy_kernel(const uint8_t *__restrict__ bytes, const int6
 // pair may come from several tuples, duplicates are removed afterwards).
 __global__ void plus_runs_kernel(const uint64_t *__restrict__ sorted, int64_t nraw, int32_t S, int32_t T,
                                  uint64_t *__restrict__ out, unsigned long long cap,
-                                 unsigned long long *__restrict__ count) {
+                                 unsigned long long *__restrict__ count, unsigned long long *__restrict__ same) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t v = sorted[e];
         if (e > 0 && sorted[e - 1] == v) continue;   // not the first of its run
         int64_t run = 1;
-        while (e + run < nraw && sorted[e + run] == v && run < T) run++;
-        if (run < T) continue;
+        while (e + run < nraw && sorted[e + run] == v) run++;   // at most one per table
         const uint64_t a = (v >> 32) / (uint64_t)S, b = (v & 0xFFFFFFFFull) / (uint64_t)S;
-        if (a == b) continue;
+        if (a == b) {   // two substrings of one string: not a match of Alg. 5
+            atomicAdd(same, (unsigned long long)run);
+            continue;
+        }
+        if (run < T) continue;
         const unsigned long long idx = atomicAdd(count, 1ull);
         if (idx < cap) out[idx] = a < b ? (a << 32 | b) : (b << 32 | a);
     }
@@ -92,9 +96,10 @@ cudaError_t launch_suffix_copy(const uint8_t *bytes, const int64_t *offsets, int
 }
 
 cudaError_t launch_plus_runs(const uint64_t *sorted, int64_t nraw, int32_t S, int32_t T, uint64_t *out,
-                             uint64_t cap, unsigned long long *count, cudaStream_t s) {
+                             uint64_t cap, unsigned long long *count, unsigned long long *same, cudaStream_t s) {
     if (nraw == 0) return cudaSuccess;
-    plus_runs_kernel<<<grid_for(nraw, 256), 256, 0, s>>>(sorted, nraw, S, T, out, (unsigned long long)cap, count);
+    plus_runs_kernel<<<grid_for(nraw, 256), 256, 0, s>>>(sorted, nraw, S, T, out, (unsigned long long)cap, count,
+                                                          same);
     note_launches(1);
     return cudaGetLastError();
 }
