@@ -332,8 +332,14 @@ void ej_batch_destroy(ej_batch *batch);
  *     device work queue and refill a pair slot as soon as its pair is decided;
  *     otherwise the grid-strided verifier. 2: always the grid-strided verifier
  *     (one pass over the pairs; a warp's slots start together and the warp ends
- *     with its slowest pair). 0 (default): 1 when the strings' mean length is at
- *     least 2048 (long pairs, where refilling pays), else 2.
+ *     with its slowest pair). 3: the shared-string verifier: the candidates are
+ *     grouped by their longer string x into warp tasks of up to 16 pairs, and
+ *     the warp keeps one ring of x's match masks per direction for all of them
+ *     (built cooperatively, once per task), instead of one per lane (two lanes
+ *     per pair, up to 12 words per lane). 0 (default): 1 when the strings' mean
+ *     length is at least 2048 (long pairs, where refilling pays); else 3 for
+ *     alphabets of more than 4 symbols (whose per-lane rings leave the
+ *     grid-strided verifier one or two warps per SM) and 2 for the rest.
  *   chain (batches): how the verifiers of a batch's joins share the GPU: the
  *     persistent ones merged, chained or overlapping, the grid-strided ones
  *     chained unless chain is 1 (the other stages always overlap); see the
@@ -344,11 +350,14 @@ void ej_batch_destroy(ej_batch *batch);
  *   order: the order in which candidates enter the verifier. 4: by length
  *     class, longest first (the shorter string's length in 256 classes), so
  *     that the pairs a warp takes have similar lengths and the longest start
- *     first; 3: by the pair's first string (a counting sort: the pairs a warp
+ *     first; 5: by the pair's longer string (the one whose match masks the
+ *     verifier builds; always used with mode 3); 3: by the pair's first string
+ *     (a counting sort: the pairs a warp
  *     takes share their first string, so they read the same memory and, through
  *     the length filter, have similar lengths); 1: by decreasing number of tables
  *     in which the two strings collided; 2: hash-table order. 0 (default): 4
- *     with the persistent verifier, 3 with the grid-strided one.
+ *     with the persistent verifier, 3 with the grid-strided one, 5 with the
+ *     shared-string one.
  *   buckets: 0 (default) or 1: equal signatures are grouped by hashing (per
  *     table an open-addressing set whose slots head lists of records); a
  *     record pairs with the later records of its list, so a bucket of b strings

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libembedjoin.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ej_embed.cu", "ej_sort.cu", "ej_verify.cu", "ej_api.cu", "ej_noalloc.cu", "ej_pipeline.cu", "ej_verify_pq.cu", "ej_serve.cu", "ej_peak.cu", "ej_plus.cu"]
+SOURCES = ["ej_embed.cu", "ej_sort.cu", "ej_verify.cu", "ej_api.cu", "ej_noalloc.cu", "ej_pipeline.cu", "ej_verify_pq.cu", "ej_serve.cu", "ej_peak.cu", "ej_plus.cu", "ej_verify_sx.cu"]
 
 
 def nvcc() -> str:

@@ -30,6 +30,7 @@ enum BufId {
     B_HASH, B_APP, B_JCOUNT, B_NEXT, B_HCOUNT, B_BINS, B_TICKETS, B_BKEYS, B_BHEADS, B_BNEXT, B_FBINS, B_FSTARTS,
     B_FSCAN,
     B_PLUS_SUBLEN, B_PLUS_WHOLE, B_PLUS_SUBOFF, B_PLUS_BYTES, B_PLUS_SCAN, B_PLUS_CAND,
+    B_SX_TCOUNT, B_SX_TSTART, B_SX_TASKS, B_SX_SCAN,
     B_NUM
 };
 
@@ -708,6 +709,16 @@ int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const Verif
     return (vc.G == 2 && want_pq) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
 }
 
+// The shared-string verifier (mode 3; mode 0 for short strings over more than
+// four symbols, where the per-lane match-mask rings of the grid-strided
+// verifier leave one or two warps per SM): two lanes per pair, the band within
+// 12 words per lane, the warp's shared area within the block's budget.
+bool sx_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const VerifyConfig &vc) {
+    if (vc.G != 2 || vc.V > 12 || sx_smem_bytes(vc.V, p->alphabet_size) > 220 * 1024) return false;
+    const bool long_pairs = pl.st.n > 0 && pl.st.total / pl.st.n >= 2048;
+    return ctx->sched.mode == 3 || (ctx->sched.mode == 0 && !long_pairs && p->alphabet_size > 4);
+}
+
 // verify_after / verify_done (optional): the verifier launch waits for the
 // first event and records the second (a batch chains its joins' verifiers, so
 // that persistent verifiers never run concurrently). defer (optional): no
@@ -748,12 +759,16 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     // queue order: 0 follows the verifier (persistent: length classes; grid-
     // strided: by first string), measured best for each on the long-DNA and the
     // protein-like / text-like shapes
-    const int pq_threads = pq_choice(ctx, pl, p, bs.vc);
-    const int order = ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
-    if (order == 3) {
-        // candidates ordered by their first string (a warp's pairs share it)
-        uint32_t *hcount = nullptr, *fbins = nullptr;
-        uint64_t *fstarts = nullptr;
+    const bool sx = !defer && sx_choice(ctx, pl, p, bs.vc);
+    const int pq_threads = sx ? 0 : pq_choice(ctx, pl, p, bs.vc);
+    // the shared-string verifier needs its pairs grouped by their longer string
+    const int order = sx ? 5 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
+    uint32_t *fbins = nullptr;
+    uint64_t *fstarts = nullptr;
+    if (order == 3 || order == 5) {
+        // candidates ordered by their first string (a warp's pairs share it), or
+        // by their longer string (the string whose match masks are built)
+        uint32_t *hcount = nullptr;
         void *fscan = nullptr;
         CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
         CKS(ensure_t(ctx, B_FBINS, (size_t)n + 1, &fbins));
@@ -761,7 +776,8 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
         CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(n + 1), &fscan));
         CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
         CK(cudaMemsetAsync(fbins, 0, (size_t)(n + 1) * sizeof(uint32_t), s));
-        CK(launch_dedup_by_first(raw, cap, table, hcount, hsize, n, fbins, fstarts, fscan, cand, cnt, s));
+        CK(launch_dedup_by_first(raw, cap, table, hcount, hsize, n, fbins, fstarts, fscan, cand, cnt, s,
+                                 order == 5 ? pl.lens : nullptr));
     } else if (order != 2) {
         // candidates handed to the verifier longest first (order 4: length classes,
         // so that the pairs a warp takes have similar lengths) or most-collided
@@ -788,6 +804,21 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     VerifyOut vo{nullptr, app, cnt + 3, cap, cnt + 2, derr, cnt + 4, cnt + 6, tickets};
     vo.max_passes = ctx->loop_bound;
     const VerifyConfig &vc = bs.vc;
+    if (sx) {
+        // warp tasks of up to 16 candidates sharing their longer string
+        const int64_t tcap = (int64_t)(cap / 16) + n + 1;
+        uint32_t *tcount = nullptr;
+        uint64_t *tstart = nullptr, *tasks = nullptr;
+        void *tscan = nullptr;
+        CKS(ensure_t(ctx, B_SX_TCOUNT, (size_t)n + 1, &tcount));
+        CKS(ensure_t(ctx, B_SX_TSTART, (size_t)n + 1, &tstart));
+        CKS(ensure_t(ctx, B_SX_TASKS, (size_t)tcap, &tasks));
+        CKS(ensure(ctx, B_SX_SCAN, scan_temp_bytes(n + 1), &tscan));
+        CK(launch_sx_tasks(fbins, fstarts, n, tcount, tstart, cnt + 7, tscan, tasks, s));
+        if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
+        CK(launch_verify_sx(vc.V, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, tasks, cnt + 7, tcap,
+                            p->K, vo, s));
+    } else {
     if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
     if (pq_threads > 0)
         // defaults: 16 slots per warp, one working warp per SM sub-partition (the
@@ -799,6 +830,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     else
         CK(launch_verify(vc, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K,
                          pl.max_len, vo, s));
+    }
     if (verify_done) CK(cudaEventRecord(verify_done, s));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], s));
     return EJ_OK;
@@ -1439,8 +1471,8 @@ int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
         ctx->sched = ej_schedule{0, 0, 0, 0, 0, 0};
         return EJ_OK;
     }
-    if (sc->mode < 0 || sc->mode > 2 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
-        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 4 ||
+    if (sc->mode < 0 || sc->mode > 3 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
+        sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 5 ||
         sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 3)
         return fail(ctx, EJ_ERR_INVALID_ARG,
                     "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",

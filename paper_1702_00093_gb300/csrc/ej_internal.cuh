@@ -303,9 +303,19 @@ cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *ta
                                  unsigned long long *counters, cudaStream_t s);
 // Dedup ordered by the pair's first string (counting sort over n bins): bins
 // (n + 1 uint32) and hcount start at zero; starts holds n + 2 uint64.
+// With longer_lens, the bins are the pairs' longer strings (the grouping of the
+// shared-string verifier); after the call starts[x] is the end of bin x.
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
-                                  unsigned long long *counters, cudaStream_t s);
+                                  unsigned long long *counters, cudaStream_t s,
+                                  const int32_t *longer_lens = nullptr);
+// Shared-string verifier (ej_verify_sx.cu): warp tasks of up to 16 candidates
+// that share their longer string, from the bins of launch_dedup_by_first with
+// longer_lens (tcount n+1 uint32, tstart n+1 uint64, tasks up to
+// candidates/16 + n entries; *ntasks_dev = their number), and the verifier.
+size_t sx_smem_bytes(int W1, uint32_t alpha);
+cudaError_t launch_sx_tasks(const uint32_t *bins, const uint64_t *ends, int64_t n, uint32_t *tcount, uint64_t *tstart,
+                            unsigned long long *ntasks_dev, void *scan_tmp, uint64_t *tasks, cudaStream_t s);
 int small_sort_max();
 cudaError_t launch_small_sort(uint64_t *a, const unsigned long long *count_dev, uint64_t n_cap, cudaStream_t s);
 
@@ -390,5 +400,11 @@ int pq_threads_for(int W1, uint32_t alpha);   // 0 if no block size fits
 cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,
                              const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
                              int32_t K, VerifyOut vo, cudaStream_t s);
+// Shared-string verifier (W1 = 2..12): the pairs of tasks[0 .. *ntasks_dev)
+// (at most ntasks_cap), each task up to 16 pairs sharing their longer string.
+cudaError_t launch_verify_sx(int W1, const uint4 *packed, const uint64_t *pofs, int B, const int32_t *lens, int64_t n,
+                             uint32_t alpha, const uint64_t *pairs, const uint64_t *tasks,
+                             const unsigned long long *ntasks_dev, int64_t ntasks_cap, int32_t K, VerifyOut vo,
+                             cudaStream_t s);
 
 }  // namespace ej

@@ -647,13 +647,22 @@ __global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const u
 // Order by the pair's first string (a counting sort on i of (i << 32 | j)):
 // consecutive candidates share their first string, so a warp's pairs read the
 // same string and, through the length filter, have similar lengths.
-__global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, uint32_t *__restrict__ bins,
-                                  unsigned long long *__restrict__ counters) {
+// With lens, the bin is the pair's longer string instead (the first one on a
+// tie), which groups the pairs that share the string whose match masks the
+// verifier builds.
+__device__ __forceinline__ uint64_t first_bin(uint64_t key, const int32_t *__restrict__ lens) {
+    const uint64_t a = key >> 32, b = key & 0xFFFFFFFFull;
+    if (!lens) return a;
+    return lens[a] >= lens[b] ? a : b;
+}
+
+__global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
+                                  uint32_t *__restrict__ bins, unsigned long long *__restrict__ counters) {
     unsigned int mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
-            atomicAdd(&bins[key >> 32], 1u);
+            atomicAdd(&bins[first_bin(key, lens)], 1u);
             mine++;
         }
     }
@@ -661,26 +670,26 @@ __global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t h
     if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&counters[2], (unsigned long long)mine);
 }
 
-__global__ void first_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize,
+__global__ void first_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
                                      unsigned long long *__restrict__ cursor, uint64_t *__restrict__ cand) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
-        if (key != ~0ull) cand[atomicAdd(&cursor[key >> 32], 1ull)] = key;
+        if (key != ~0ull) cand[atomicAdd(&cursor[first_bin(key, lens)], 1ull)] = key;
     }
 }
 
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
-                                  unsigned long long *counters, cudaStream_t s) {
+                                  unsigned long long *counters, cudaStream_t s, const int32_t *longer_lens) {
     int64_t g = ((int64_t)cap + 255) / 256;
     dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
     int64_t gh = ((int64_t)hsize + 255) / 256;
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
-    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, bins, counters);
+    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, bins, counters);
     note_launches(2);
     cudaError_t e = exclusive_scan_u32(bins, starts, n + 1, nullptr, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, (unsigned long long *)starts, cand);
+    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, (unsigned long long *)starts, cand);
     note_launches(1);
     return cudaGetLastError();
 }

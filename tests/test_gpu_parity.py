@@ -390,9 +390,9 @@ def _near_pair_set(rng, K, alphabet, n_base=20, max_len=700):
                                         (90, synth.TEXT)])
 def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
     """ej_join's back half under every schedule (persistent work queue with 1..16
-    slots per warp and capped warps, grid-strided; collision-count or hash order;
-    hashed or sorted buckets) and every two-lane window width gives the oracle's
-    pair set."""
+    slots per warp and capped warps, grid-strided, shared-string; collision-count,
+    hash, first-string, length-class or longer-string order; hashed or sorted
+    buckets) and every two-lane window width gives the oracle's pair set."""
     rng = np.random.default_rng(1000 + K)
     ss = _near_pair_set(rng, K, alphabet)
     z = 3 if len(alphabet) == 4 else 2
@@ -405,18 +405,20 @@ def test_join_every_schedule_and_window_is_exact(ej, ctx, K, alphabet):
     try:
         for sched in [(0, 0, 0, 0, 0), (2, 0, 0, 0, 0), (1, 0, 0, 0, 0), (1, 1, 0, 0, 2), (1, 2, 0, 2, 0),
                       (1, 5, 1, 0, 2), (1, 16, 1, 1, 1), (1, 16, 2, 2, 0), (1, 3, 1, 0, 0), (2, 0, 0, 2, 2),
-                      (2, 0, 0, 3, 0), (1, 16, 1, 3, 0), (0, 0, 0, 3, 2), (1, 16, 1, 4, 0), (2, 0, 0, 4, 2)]:
+                      (2, 0, 0, 3, 0), (1, 16, 1, 3, 0), (0, 0, 0, 3, 2), (1, 16, 1, 4, 0), (2, 0, 0, 4, 2),
+                      (3, 0, 0, 0, 0), (3, 0, 0, 0, 2), (3, 0, 0, 0, 1), (2, 0, 0, 5, 0), (1, 16, 1, 5, 0)]:
             ctx.set_schedule(*sched)
             pairs, stats = ctx.join(s, params, device=DEV)
             assert stats.n_candidates == ref.n_candidates
             assert np.array_equal(_np_u64(pairs), ref.pairs), sched
             runs += 1
-        ctx.set_schedule(1, 0)   # the persistent verifier at every window width
-        for V in range(W + 1, 13):
-            ctx.set_verify_config(2, V, 0)
-            pairs, _ = ctx.join(s, params, device=DEV)
-            assert np.array_equal(_np_u64(pairs), ref.pairs), V
-            runs += 1
+        for mode in (1, 3):   # the persistent and shared-string verifiers at every window width
+            ctx.set_schedule(mode, 0)
+            for V in range(W + 1, 13):
+                ctx.set_verify_config(2, V, 0)
+                pairs, _ = ctx.join(s, params, device=DEV)
+                assert np.array_equal(_np_u64(pairs), ref.pairs), (mode, V)
+                runs += 1
     finally:
         ctx.set_schedule(0, 0)
         ctx.set_verify_config(0, 0, 0)
@@ -449,3 +451,29 @@ def test_buckets_in_shared_memory_and_global(ej, ctx, n):
         ref = oracle.join(ss.data, ss.offsets, b"ACGT", K=1, r=2, m=3, z=4, seed=9)
         assert ref.n_candidates == st_h.n_candidates
         assert np.array_equal(_np_u64(hashed), ref.pairs)
+
+
+@pytest.mark.parametrize("maker,K", [
+    (lambda: synth.protein_like(21, 2000, median=150, lo=30, hi=600), 40),
+    (lambda: synth.text_like(22, 600, len_lo=200, len_hi=900, rate_lo=0.02, rate_hi=0.2), 150),
+    (lambda: synth.dna_clusters(23, 40, 10, 200, 400, edits_mean=10.0), 30),
+])
+def test_shared_string_verifier_tasks(ej, ctx, maker, K):
+    """The shared-string verifier on candidate sets whose longer strings have from
+    one to hundreds of pairs (tasks of 1..16 pairs), ragged lengths, and 2-bit
+    and 8-bit codes: the oracle's pair set, also through the plain ej_verify of
+    the same candidates."""
+    ss = maker()
+    L = int(2 * ss.lengths().mean())
+    params = ej.Params(K=K, r=4, m=6, z=4, seed=8, L=L, alphabet=ss.alphabet)
+    ref = oracle.join(ss.data, ss.offsets, ss.alphabet, K=K, r=4, m=6, z=4, seed=8, L=L)
+    assert ref.n_candidates > 200 and len(ref.pairs) > 0
+    s = ej.Strings.from_set(ss, DEV)
+    try:
+        for mode in (3, 0):
+            ctx.set_schedule(mode, 0)
+            pairs, st = ctx.join(s, params, device=DEV)
+            assert st.n_candidates == ref.n_candidates
+            assert np.array_equal(_np_u64(pairs), ref.pairs), mode
+    finally:
+        ctx.set_schedule()
