@@ -51,6 +51,7 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
         np = dn < np ? dn : np;
     }
     if (vo.pairs_off_dev) pairs += *vo.pairs_off_dev;
+    unsigned long long loc_cells = 0, loc_cols = 0;
     constexpr int GPW = 32 / G;
     const int32_t w_min = (2 * K + 1 + 63) / 64;
     extern __shared__ uint64_t smem[];
@@ -332,12 +333,23 @@ verify_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pof
         }
         if (valid && gl == 0) {
             emit_result(vo, p, pairs, pass);
-            if (work) {
-                atomicAdd(&work[0], band_cells(mlen, nlen, kp));
-                atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
-            }
+            loc_cells += band_cells(mlen, nlen, kp);
+            loc_cols += (unsigned long long)cols_run * (unsigned long long)w_min;
         }
         __syncwarp();
+    }
+    // work counters: one atomic per warp (per-pair atomics on two addresses
+    // serialise in the memory system)
+    if (work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loc_cells += __shfl_xor_sync(FULL, loc_cells, o);
+            loc_cols += __shfl_xor_sync(FULL, loc_cols, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (loc_cells) atomicAdd(&work[0], loc_cells);
+            if (loc_cols) atomicAdd(&work[1], loc_cols);
+        }
     }
 }
 
@@ -367,6 +379,7 @@ verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         np = dn < np ? dn : np;
     }
     constexpr int R = W + 2;
+    unsigned long long loc_cells = 0, loc_cols = 0;
     extern __shared__ uint64_t smem[];
     __shared__ int8_t s_nsum[256];
     __shared__ int8_t s_nmin[256];
@@ -550,9 +563,20 @@ verify_g1_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             }
         }
         emit_result(vo, p, pairs, pass);
-        if (work) {
-            atomicAdd(&work[0], band_cells(mrows, ncols, K));
-            atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+        loc_cells += band_cells(mrows, ncols, K);
+        loc_cols += (unsigned long long)cols_run * (unsigned long long)w_min;
+    }
+    // work counters: one atomic per warp (per-pair atomics on two addresses
+    // serialise in the memory system)
+    if (work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loc_cells += __shfl_xor_sync(FULL, loc_cells, o);
+            loc_cols += __shfl_xor_sync(FULL, loc_cols, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (loc_cells) atomicAdd(&work[0], loc_cells);
+            if (loc_cols) atomicAdd(&work[1], loc_cols);
         }
     }
 }
@@ -643,7 +667,8 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const unsigned pmask = 3u << (lane & ~1);
     const int32_t w_min = (2 * K + 1 + 63) / 64;
     const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 1);
-    const int64_t niter = (np + stride - 1) / stride;   // same for both lanes of a pair
+    const int64_t niter = (np + stride - 1) / stride;   // the same on every lane: the warp ends together
+    unsigned long long loc_cells = 0, loc_cols = 0;
 
     for (int64_t it = 0; it < niter; it++) {
         const int64_t p = it * stride + (int64_t)blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1);
@@ -828,11 +853,24 @@ verify_bd_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             }
         }
         if (valid && !rev) emit_result(vo, p, pairs, pass);
-        if (valid && work) {
-            if (!rev) atomicAdd(&work[0], band_cells(m, n, K));
-            atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+        if (valid) {
+            if (!rev) loc_cells += band_cells(m, n, K);
+            loc_cols += (unsigned long long)cols_run * (unsigned long long)w_min;
         }
         __syncwarp(pmask);
+    }
+    // work counters: one atomic per warp (per-pair atomics on two addresses
+    // serialise in the memory system)
+    if (work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loc_cells += __shfl_xor_sync(FULL, loc_cells, o);
+            loc_cols += __shfl_xor_sync(FULL, loc_cols, o);
+        }
+        if (lane == 0) {
+            if (loc_cells) atomicAdd(&work[0], loc_cells);
+            if (loc_cols) atomicAdd(&work[1], loc_cols);
+        }
     }
 }
 

@@ -36,27 +36,37 @@ __device__ __forceinline__ uint32_t sym_at(const uint4 *__restrict__ xc, int64_t
 
 // Word k (rows 64k+1 .. 64k+64) of x, or of reversed x, built by the whole warp
 // into ring slot `slot` (entry c * RS + slot for symbol c): lane t reads rows t
-// and t + 32; the lanes holding the same symbol find one another with
-// __match_any_sync, which is that symbol's mask of the 32 rows.
+// and t + 32 (coop_load), and the lanes holding the same symbol find one
+// another with __match_any_sync, which is that symbol's mask of the 32 rows
+// (coop_store). The loads of several words are issued before any of them is
+// stored, so that their latencies overlap.
+struct WordSyms {
+    uint32_t s0, s1;
+};
+
 template <int B>
-__device__ __forceinline__ void coop_build(uint64_t *ring, int RS, int slot, const uint4 *__restrict__ xc,
-                                           int64_t m, int64_t k, bool rev, uint32_t alpha, int lane) {
+__device__ __forceinline__ WordSyms coop_load(const uint4 *__restrict__ xc, int64_t m, int64_t k, bool rev, int lane) {
     const int64_t i0 = rev ? m - 1 - 64 * k - lane : 64 * k + lane;
     const int64_t i1 = rev ? i0 - 32 : i0 + 32;
-    const uint32_t s0 = (i0 >= 0 && i0 < m) ? sym_at<B>(xc, i0) : 0xFFFFu;
-    const uint32_t s1 = (i1 >= 0 && i1 < m) ? sym_at<B>(xc, i1) : 0xFFFFu;
-    const unsigned m0 = __match_any_sync(FULL, s0);
-    const unsigned m1 = __match_any_sync(FULL, s1);
+    WordSyms w;
+    w.s0 = (i0 >= 0 && i0 < m) ? sym_at<B>(xc, i0) : 0xFFFFu;
+    w.s1 = (i1 >= 0 && i1 < m) ? sym_at<B>(xc, i1) : 0xFFFFu;
+    return w;
+}
+
+__device__ __forceinline__ void coop_store(uint64_t *ring, int RS, int slot, WordSyms w, uint32_t alpha, int lane) {
+    const unsigned m0 = __match_any_sync(FULL, w.s0);
+    const unsigned m1 = __match_any_sync(FULL, w.s1);
     for (uint32_t c = lane; c < alpha; c += 32) ring[(size_t)c * RS + slot] = 0ull;
     __syncwarp();
     // lanes with the same symbol write the same value
-    if (s0 < alpha) reinterpret_cast<uint32_t *>(ring + (size_t)s0 * RS + slot)[0] = m0;
-    if (s1 < alpha) reinterpret_cast<uint32_t *>(ring + (size_t)s1 * RS + slot)[1] = m1;
+    if (w.s0 < alpha) reinterpret_cast<uint32_t *>(ring + (size_t)w.s0 * RS + slot)[0] = m0;
+    if (w.s1 < alpha) reinterpret_cast<uint32_t *>(ring + (size_t)w.s1 * RS + slot)[1] = m1;
     __syncwarp();
 }
 
 template <int W1, int B>
-__global__ void __launch_bounds__(SX_WARPS * 32)
+__global__ void __launch_bounds__(SX_WARPS * 32, 4)
 verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
                  const uint64_t *__restrict__ pairs, const uint64_t *__restrict__ tasks,
@@ -93,14 +103,26 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const int64_t ntasks = cap_t < ntasks_cap ? cap_t : ntasks_cap;
     const int64_t nw = (int64_t)gridDim.x * SX_WARPS;
 
-    for (int64_t t = (int64_t)blockIdx.x * SX_WARPS + wib; t < ntasks; t += nw) {   // warp-uniform
-        const uint64_t tk = tasks[t];
+    unsigned long long loc_cells = 0, loc_cols = 0;
+    // a task's descriptor and this lane's pair are loaded during the task before
+    int64_t t = (int64_t)blockIdx.x * SX_WARPS + wib;
+    uint64_t tk_next = 0, pr_next = 0;
+    if (t < ntasks) {
+        tk_next = tasks[t];
+        if (slot_pair < (int)(tk_next & 31u)) pr_next = pairs[(int64_t)(tk_next >> 5) + slot_pair];
+    }
+    for (; t < ntasks; t += nw) {   // warp-uniform
+        const uint64_t tk = tk_next;
+        const uint64_t pr = pr_next;
+        if (t + nw < ntasks) {
+            tk_next = tasks[t + nw];
+            if (slot_pair < (int)(tk_next & 31u)) pr_next = pairs[(int64_t)(tk_next >> 5) + slot_pair];
+        }
         const int64_t first = (int64_t)(tk >> 5);
         const int cnt = (int)(tk & 31u);
         bool valid = slot_pair < cnt;
         int64_t a = 0, b = 0;
         if (valid) {
-            const uint64_t pr = pairs[first + slot_pair];
             a = (int64_t)(pr >> 32);
             b = (int64_t)(pr & 0xFFFFFFFFull);
             if (a >= n_str || b >= n_str) {
@@ -134,9 +156,24 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         if (maxcols > 0) {
             const int32_t mx = xs >= 0 ? lens[xs] : 0;
             const uint4 *xc = packed + pofs[xs >= 0 ? xs : 0];
-            for (int w = 0; w < W1; w++) {
-                coop_build<B>(ringF, RS, w, xc, mx, w, false, alpha, lane);
-                coop_build<B>(ringB, RS, w, xc, mx, w, true, alpha, lane);
+            // the first W1 words of both directions, loaded four words at a time
+#pragma unroll
+            for (int w0 = 0; w0 < W1; w0 += 2) {
+                WordSyms f[2], r[2];
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    if (w0 + d < W1) {
+                        f[d] = coop_load<B>(xc, mx, w0 + d, false, lane);
+                        r[d] = coop_load<B>(xc, mx, w0 + d, true, lane);
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    if (w0 + d < W1) {
+                        coop_store(ringF, RS, w0 + d, f[d], alpha, lane);
+                        coop_store(ringB, RS, w0 + d, r[d], alpha, lane);
+                    }
+                }
             }
             SymReader<B> yf;
             SymReaderRev<B> yb;
@@ -192,8 +229,10 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                     kr++;
                     const int freed = base;   // the dropped top word's slot takes the new bottom word
                     base = (base + 1 == R) ? 0 : base + 1;
-                    coop_build<B>(ringF, RS, freed, xc, mx, kr + W1 - 1, false, alpha, lane);
-                    coop_build<B>(ringB, RS, freed, xc, mx, kr + W1 - 1, true, alpha, lane);
+                    const WordSyms f = coop_load<B>(xc, mx, kr + W1 - 1, false, lane);
+                    const WordSyms r = coop_load<B>(xc, mx, kr + W1 - 1, true, lane);
+                    coop_store(ringF, RS, freed, f, alpha, lane);
+                    coop_store(ringB, RS, freed, r, alpha, lane);
                 }
                 if (running) {
                     uint32_t c;
@@ -291,11 +330,24 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             }
         }
         if (valid && !rev) emit_result(vo, first + slot_pair, pairs, pass);
-        if (valid && work) {
-            if (!rev) atomicAdd(&work[0], band_cells(m, n, K));
-            atomicAdd(&work[1], (unsigned long long)cols_run * (unsigned long long)w_min);
+        if (valid) {
+            if (!rev) loc_cells += band_cells(m, n, K);
+            loc_cols += (unsigned long long)cols_run * (unsigned long long)w_min;
         }
         __syncwarp();   // the shared area is rebuilt by the next task
+    }
+    // work counters: one atomic per warp (per-pair atomics on two addresses
+    // serialise in the memory system)
+    if (work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loc_cells += __shfl_xor_sync(FULL, loc_cells, o);
+            loc_cols += __shfl_xor_sync(FULL, loc_cols, o);
+        }
+        if (lane == 0) {
+            if (loc_cells) atomicAdd(&work[0], loc_cells);
+            if (loc_cols) atomicAdd(&work[1], loc_cols);
+        }
     }
 }
 
