@@ -62,7 +62,7 @@ VERIFY_SOURCE = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify_
 # one ncu capture of the long-DNA workload: "merged" = the batch's merged launch,
 # "join" = mean over the K=50/150/250 launches of ej_join; valid only while the
 # verify source is the one that was captured
-VERIFY_TRAFFIC = {"source_sha256_prefix": "543eb403d5eb9127", "bytes_per_launch": {"merged": 11593472, "join": None}}
+VERIFY_TRAFFIC = {"source_sha256_prefix": "c91d305b64729406", "bytes_per_launch": {"merged": 8611584, "join": None}}
 RECALL_SAMPLES = os.path.join(ROOT, "oracle", "recall_samples.json")
 
 
@@ -785,6 +785,43 @@ def run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps
     return res
 
 
+def plus_summary(ej, ctx, ss, params, dev, stream, flush, steps=3) -> dict:
+    """EmbedJoin+ (Section 5) on the headline strings: ej_join_plus per K with
+    delta = 70 (about the square root of the mean length), T = 2 and 16
+    functions where there are several substrings (else T = 1 and the
+    workload's functions: EmbedJoin itself); time per call (CUDA events, L2
+    flushed, after one warm call) and recall against the cluster truth."""
+    import torch
+    delta = 70
+    s = ej.Strings.from_set(ss, dev)
+    rows, outs, plist = {}, [], []
+    for p in params:
+        nsub = max(1, -(-p.K // delta))
+        T = 2 if nsub > 1 else 1
+        q = dataclasses.replace(p, m=16) if T == 2 else p
+        ctx.join_plus(s, q, delta, T, device=dev, stream=stream)          # warm
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pairs, st = ctx.join_plus(s, q, delta, T, device=dev, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        rows[str(p.K)] = {"delta": delta, "substrings": nsub, "T": T, "r": q.r, "m": q.m, "z": q.z, "L": q.L,
+                          "ms": total / steps, "matches": st.n_raw_pairs, "candidates": st.n_candidates,
+                          "out_pairs": st.n_out}
+        outs.append(pairs)
+        plist.append(q)
+    rec = cluster_recall(ej, ctx, ss, plist, outs, dev, stream)
+    for k, v in rec["per_K"].items():
+        rows[k]["recall"] = v["recall"]
+        rows[k]["output_pairs_outside_clusters"] = v["output_pairs_outside_clusters"]
+    return {"per_K": rows, "api": "ej_join_plus", "recall_basis": rec["basis"]}
+
+
 def measure_int_peak(ej, device) -> dict:
     got = {}
     for mix, name in ((0, "lop3+add"), (1, "lop3"), (2, "add")):
@@ -863,6 +900,9 @@ def main():
         if not args.no_recall and rank == 0:
             recall = (cluster_recall(ej, ctx, ss, params, r["result_pairs"], dev, stream)
                       if wl["cluster_truth"] else sample_recall(args.workload))
+        plus = None
+        if args.workload == "long_dna" and world == 1 and not args.no_recall:
+            plus = plus_summary(ej, ctx, ss, params, dev, stream, flush)
         full = {}
         if world == 1:
             for name in [x for x in args.full_size.split(",") if x and x != args.workload]:
@@ -908,6 +948,7 @@ def main():
             "gpu_launches": int(r["launches_step"] * steps),
             "e2e": r["e2e"],
             "recall": recall,
+            "embedjoin_plus": plus,
             "workloads": full,
         }
         if world == 1 and not args.no_cpu_baseline:
