@@ -19,6 +19,11 @@ Parity status per function:
                                      values)
   join                             : pinned (running example output; worked
                                      example; precision against brute force)
+  join(key_P) (<u,v> mod P keys)   : pinned (one sample per function reduces to
+                                     the exact key; candidates contain the exact
+                                     key's; distinct signatures collide at 1/P)
+  join_grouped (Section 4.1)       : pinned (one group is EmbedJoin; every pair
+                                     within K in length shares a group)
   join_plus (Alg. 4 and 5)         : pinned (equal to join when one substring and
                                      T = 1; candidates equal to the set definition
                                      by brute force; P[>= T matched signatures]
@@ -105,6 +110,19 @@ def lib():
             L.or_join.restype = C.c_int
             L.or_join.argtypes = [vp, vp, i64, C.POINTER(_Params), vp, i64, vp, i64,
                                   C.POINTER(_Stats)]
+            L.or_join_ext.restype = C.c_int
+            L.or_join_ext.argtypes = [vp, vp, i64, C.POINTER(_Params), u64, vp, i64, vp, i64, C.POINTER(_Stats)]
+            L.or_join_grouped.restype = C.c_int
+            L.or_join_grouped.argtypes = [vp, vp, i64, C.POINTER(_Params), u64, vp, i64,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.or_group_count.restype = i64
+            L.or_group_count.argtypes = [i64, i32]
+            L.or_in_group.restype = C.c_int
+            L.or_in_group.argtypes = [i64, i64, i32]
+            L.or_sign_all_modp.restype = None
+            L.or_sign_all_modp.argtypes = [vp, vp, i64, u32, u32, u32, i64, vp, u32, u64, u64, vp]
+            L.or_hash_coefficient.restype = u32
+            L.or_hash_coefficient.argtypes = [u64, u32, u32, u32, u64]
             L.or_join_plus.restype = C.c_int
             L.or_join_plus.argtypes = [vp, vp, i64, C.POINTER(_Params), i32, i32, vp, i64, vp, i64,
                                        C.POINTER(_Stats), C.POINTER(C.c_int64)]
@@ -293,8 +311,9 @@ class JoinResult:
 
 def join(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, seed: int,
          L: int = 0, out_len: int = 0, pi_inject=None, pos_inject=None,
-         keep_candidates: bool = True) -> JoinResult:
-    """EmbedJoin (Alg. 3 with Alg. 2) end to end."""
+         keep_candidates: bool = True, key_P: int = 0) -> JoinResult:
+    """EmbedJoin (Alg. 3 with Alg. 2) end to end. key_P > 0 buckets by the
+    two-level hash <u, v> mod key_P of Section 4 instead of the exact key."""
     data, offsets = _strings(data, offsets)
     n = offsets.shape[0] - 1
     ab = _u8(alphabet)
@@ -307,9 +326,9 @@ def join(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, seed: i
         out = np.zeros(cap, dtype=np.uint64)
         cand = np.zeros(cap if keep_candidates else 1, dtype=np.uint64)
         st = _Stats()
-        rc = lib().or_join(_p(data), _p(offsets), n, C.byref(prm), _p(out), cap,
-                           _p(cand) if keep_candidates else None, cap if keep_candidates else 0,
-                           C.byref(st))
+        rc = lib().or_join_ext(_p(data), _p(offsets), n, C.byref(prm), key_P, _p(out), cap,
+                               _p(cand) if keep_candidates else None, cap if keep_candidates else 0,
+                               C.byref(st))
         if rc != 0:
             raise ValueError(f"oracle join failed: {rc}")
         if st.n_out <= cap and (not keep_candidates or st.n_candidates <= cap):
@@ -359,3 +378,52 @@ def join_plus(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, se
             res.T = T
             return res
         cap = max(int(st.n_out), int(st.n_candidates)) + 1
+
+
+# ---------------------------------------------------------------------------
+# Two-level hashing and grouping (Section 4)
+# ---------------------------------------------------------------------------
+
+def hash_coefficient(seed: int, l: int, f: int, q: int, P: int) -> int:
+    return int(lib().or_hash_coefficient(seed, l, f, q, P))
+
+
+def sign_modp(emb: np.ndarray, walk_end: np.ndarray, pos: np.ndarray, alpha: int, seed: int, P: int) -> np.ndarray:
+    """Hashed keys uint64 [r*m][n]: <u, v> mod P of every signature."""
+    emb = np.ascontiguousarray(emb, dtype=np.uint8)
+    walk_end = np.ascontiguousarray(walk_end, dtype=np.int64)
+    pos = np.ascontiguousarray(pos, dtype=np.uint32)
+    r, n, out_len = emb.shape
+    _, m, z = pos.shape
+    keys = np.zeros((r * m, n), dtype=np.uint64)
+    lib().or_sign_all_modp(_p(emb), _p(walk_end), n, r, m, z, out_len, _p(pos), alpha, seed, P, _p(keys))
+    return keys
+
+
+def group_count(N: int, K: int) -> int:
+    return int(lib().or_group_count(N, K))
+
+
+def in_group(length: int, g: int, K: int) -> bool:
+    return bool(lib().or_in_group(length, g, K))
+
+
+def join_grouped(data, offsets, alphabet: bytes, K: int, r: int, m: int, z: int, seed: int, L: int = 0,
+                 key_P: int = 0):
+    """EmbedJoin with grouping (Section 4.1): (sorted output pairs, candidates
+    verified over all groups)."""
+    data, offsets = _strings(data, offsets)
+    n = offsets.shape[0] - 1
+    ab = _u8(alphabet)
+    prm = _Params(r, m, z, L, 0, K, seed, _p(ab), len(alphabet), None, 0, None)
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, dtype=np.uint64)
+        no, nc = C.c_int64(0), C.c_int64(0)
+        rc = lib().or_join_grouped(_p(data), _p(offsets), n, C.byref(prm), key_P, _p(out), cap, C.byref(no),
+                                   C.byref(nc))
+        if rc != 0:
+            raise ValueError(f"oracle join_grouped failed: {rc}")
+        if no.value <= cap:
+            return out[:no.value].copy(), int(nc.value)
+        cap = int(no.value)

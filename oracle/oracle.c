@@ -155,6 +155,40 @@ uint64_t or_signature_key(const uint8_t *t, int64_t walk_end, const uint32_t *po
     return key;
 }
 
+/* The paper's two-level hashing of a signature (Section 4): the z sampled
+ * symbols as a vector u with entries 1..|S| (and |S|+1 for the padding symbol),
+ * a random vector v in [0, P)^z per function, key = <u, v> mod P.
+ *   v[l][f][q] = mulhi64(splitmix64(splitmix64(seed) ^ (3<<56 | l<<48 | f<<32 | q)), P)
+ * (a counter-based reading of "a random vector"). Equal signatures get equal
+ * keys; different ones collide with probability 1/P over v. */
+uint32_t or_hash_coefficient(uint64_t seed, uint32_t l, uint32_t f, uint32_t q, uint64_t P) {
+    uint64_t base = or_splitmix64(seed);
+    uint64_t ctr = (3ull << 56) | ((uint64_t)l << 48) | ((uint64_t)f << 32) | (uint64_t)q;
+    return (uint32_t)(((unsigned __int128)or_splitmix64(base ^ ctr) * (unsigned __int128)P) >> 64);
+}
+
+uint64_t or_signature_key_modp(const uint8_t *t, int64_t walk_end, const uint32_t *pos, uint32_t z, uint32_t alpha,
+                               uint64_t seed, uint32_t l, uint32_t f, uint64_t P) {
+    uint64_t acc = 0;
+    for (uint32_t q = 0; q < z; q++) {
+        uint64_t u = 1 + (((int64_t)pos[q] < walk_end) ? t[pos[q]] : alpha);
+        acc = (acc + u * (uint64_t)or_hash_coefficient(seed, l, f, q, P)) % P;
+    }
+    return acc;
+}
+
+/* Hashed keys of every (table, string): keys[(l*m+f)*n + s] = <u, v> mod P. */
+void or_sign_all_modp(const uint8_t *emb, const int64_t *walk_end, int64_t n, uint32_t r, uint32_t m, uint32_t z,
+                      int64_t out_len, const uint32_t *pos, uint32_t alpha, uint64_t seed, uint64_t P,
+                      uint64_t *keys) {
+    for (uint32_t l = 0; l < r; l++)
+        for (uint32_t f = 0; f < m; f++)
+            for (int64_t s = 0; s < n; s++)
+                keys[((int64_t)l * m + f) * n + s] = or_signature_key_modp(
+                    emb + ((int64_t)l * n + s) * out_len, walk_end[(int64_t)l * n + s],
+                    pos + ((uint64_t)l * m + f) * z, z, alpha, seed, l, f, P);
+}
+
 /* keys is [r*m][n]: keys[(l*m+f)*n + s]. */
 void or_sign_all(const uint8_t *emb, const int64_t *walk_end, int64_t n, uint32_t r, uint32_t m,
                  uint32_t z, int64_t out_len, const uint32_t *pos, uint32_t alpha, uint64_t *keys) {
@@ -550,8 +584,18 @@ static double now_s(void) {
 
 /* Runs the whole method. out gets up to `capacity` output pairs; cand (optional)
  * gets up to cand_capacity candidate pairs. Returns 0 or an error code. */
+int or_join_ext(const uint8_t *data, const int64_t *offsets, int64_t n, const or_params *p, uint64_t key_P,
+                uint64_t *out, int64_t capacity, uint64_t *cand, int64_t cand_capacity, or_stats *st);
+
 int or_join(const uint8_t *data, const int64_t *offsets, int64_t n, const or_params *p,
             uint64_t *out, int64_t capacity, uint64_t *cand, int64_t cand_capacity, or_stats *st) {
+    return or_join_ext(data, offsets, n, p, 0, out, capacity, cand, cand_capacity, st);
+}
+
+/* or_join with the bucket key chosen by key_P: 0 = the exact mixed-radix key,
+ * else the two-level hash <u, v> mod key_P of Section 4. */
+int or_join_ext(const uint8_t *data, const int64_t *offsets, int64_t n, const or_params *p, uint64_t key_P,
+                uint64_t *out, int64_t capacity, uint64_t *cand, int64_t cand_capacity, or_stats *st) {
     memset(st, 0, sizeof *st);
     if (n < 0 || p->r == 0 || p->m == 0 || p->z == 0 || p->K < 0 || p->alpha == 0 || p->alpha > 255)
         return OR_ERR_ARG;
@@ -578,7 +622,16 @@ int or_join(const uint8_t *data, const int64_t *offsets, int64_t n, const or_par
     if (!err) {
         if (p->pos_inject) memcpy(pos, p->pos_inject, (size_t)T * p->z * sizeof(uint32_t));
         else or_positions_all(p->seed, p->r, p->m, p->z, L, pos);
-        or_sign_all(emb, we, n, p->r, p->m, p->z, out_len, pos, p->alpha, keys);
+        if (key_P == 0) {
+            or_sign_all(emb, we, n, p->r, p->m, p->z, out_len, pos, p->alpha, keys);
+        } else {
+            for (uint32_t l = 0; l < p->r; l++)
+                for (uint32_t f = 0; f < p->m; f++)
+                    for (int64_t s = 0; s < n; s++)
+                        keys[((int64_t)l * p->m + f) * n + s] = or_signature_key_modp(
+                            emb + ((int64_t)l * n + s) * out_len, we[(int64_t)l * n + s],
+                            pos + ((uint64_t)l * p->m + f) * p->z, p->z, p->alpha, p->seed, l, f, key_P);
+        }
     }
     free(emb); free(we); free(pos);
     if (err) { free(keys); return err; }
@@ -789,5 +842,95 @@ int or_join_plus(const uint8_t *data, const int64_t *offsets, int64_t n, const o
     st->n_candidates = nu;
     st->n_out = no;
     free(cl); free(flags);
+    return OR_OK;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Grouping (Section 4.1)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Number of length groups: N' = ceil(N/K)*K, groups 1 .. N'/K - 1 (at least
+ * one); group g (1-based) holds the strings of length in ((g-1)K, (g+1)K], the
+ * first also the empty strings. K >= 1. */
+int64_t or_group_count(int64_t N, int32_t K) {
+    int64_t Np = ((N + K - 1) / K) * K;
+    int64_t g = Np / K - 1;
+    return g < 1 ? 1 : g;
+}
+
+int or_in_group(int64_t len, int64_t g, int32_t K) {
+    if (g == 1 && len == 0) return 1;
+    return len > (g - 1) * (int64_t)K && len <= (g + 1) * (int64_t)K;
+}
+
+/*
+ * EmbedJoin with grouping: the strings are split into the length groups above
+ * (every string in up to two of them, every pair within K in length in a
+ * common one), EmbedJoin runs on each group on its own (its own N and 3N, the
+ * caller's r, m, z, L, K and seed) and the outputs are united. out gets the
+ * sorted unique union; *n_cand the candidates verified over all groups (with
+ * the repeats the redundancy causes). key_P as for or_join_ext.
+ */
+int or_join_grouped(const uint8_t *data, const int64_t *offsets, int64_t n, const or_params *p, uint64_t key_P,
+                    uint64_t *out, int64_t capacity, int64_t *n_out, int64_t *n_cand) {
+    *n_out = 0; *n_cand = 0;
+    if (p->K < 1) return OR_ERR_ARG;
+    int64_t N = 0;
+    for (int64_t s = 0; s < n; s++)
+        if (offsets[s + 1] - offsets[s] > N) N = offsets[s + 1] - offsets[s];
+    const int64_t G = or_group_count(N, p->K);
+    int32_t *idx = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    int64_t *goff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    uint8_t *gdata = (uint8_t *)malloc((size_t)(offsets[n] ? offsets[n] : 1));
+    uint64_t *all = NULL;
+    int64_t nall = 0, cap_all = 0;
+    int err = (idx && goff && gdata) ? OR_OK : OR_ERR_OOM;
+    for (int64_t g = 1; g <= G && !err; g++) {
+        int64_t gn = 0;
+        goff[0] = 0;
+        for (int64_t s = 0; s < n; s++) {
+            const int64_t len = offsets[s + 1] - offsets[s];
+            if (!or_in_group(len, g, p->K)) continue;
+            memcpy(gdata + goff[gn], data + offsets[s], (size_t)len);
+            goff[gn + 1] = goff[gn] + len;
+            idx[gn++] = (int32_t)s;
+        }
+        if (gn < 2) continue;
+        or_stats st;
+        int64_t gcap = 1024;
+        uint64_t *gout = NULL;
+        for (;;) {
+            gout = (uint64_t *)malloc((size_t)gcap * sizeof(uint64_t));
+            if (!gout) { err = OR_ERR_OOM; break; }
+            err = or_join_ext(gdata, goff, gn, p, key_P, gout, gcap, NULL, 0, &st);
+            if (err || st.n_out <= gcap) break;
+            gcap = st.n_out;
+            free(gout);
+        }
+        if (err) { free(gout); break; }
+        *n_cand += st.n_candidates;
+        if (nall + st.n_out > cap_all) {
+            int64_t nc = 2 * (nall + st.n_out) + 1024;
+            uint64_t *nv = (uint64_t *)realloc(all, (size_t)nc * sizeof(uint64_t));
+            if (!nv) { free(gout); err = OR_ERR_OOM; break; }
+            all = nv; cap_all = nc;
+        }
+        /* group-local ids are increasing in the global order */
+        for (int64_t q = 0; q < st.n_out; q++)
+            all[nall++] = ((uint64_t)idx[gout[q] >> 32] << 32) | (uint64_t)idx[gout[q] & 0xffffffffu];
+        free(gout);
+    }
+    free(idx); free(goff); free(gdata);
+    if (err) { free(all); return err; }
+    int64_t nu = 0;
+    if (nall) {
+        qsort(all, (size_t)nall, sizeof(uint64_t), cmp_u64);
+        for (int64_t q = 0; q < nall; q++)
+            if (q == 0 || all[q] != all[q - 1]) all[nu++] = all[q];
+    }
+    for (int64_t q = 0; q < nu && q < capacity && out; q++) out[q] = all[q];
+    *n_out = nu;
+    free(all);
     return OR_OK;
 }
