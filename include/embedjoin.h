@@ -535,6 +535,35 @@ int ej_join_plus(ej_ctx *ctx, const ej_strings *strings, const ej_params *params
                  uint64_t *out, int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream);
 
 /*
+ * Fidelity options of Section 4 (the paper's own choices where this library
+ * defaults to others).
+ *
+ * ej_set_key_hash: bucket keys by the paper's two-level hashing instead of the
+ * exact key: the signature's z symbols as a vector u with entries 1..|alphabet|
+ * (|alphabet|+1 for the padding symbol), a random vector v in [0, P)^z per
+ * function (v[l][f][q] = mulhi64(splitmix64(splitmix64(seed) ^ (3<<56 | l<<48 |
+ * f<<32 | q)), P)), key = <u, v> mod P. Equal signatures share a bucket as
+ * before; different ones also share it with probability 1/P (extra candidates,
+ * removed by the verification). Applies to ej_sign, ej_embed_sign, ej_join,
+ * ej_join_plus and ej_join_grouped on this context; ej_batch_create rejects it
+ * (EJ_ERR_UNSUPPORTED). P = 0 restores the exact keys; otherwise P must be a
+ * prime in [2, 2^32) (EJ_ERR_INVALID_ARG), e.g. 1000003.
+ *
+ * ej_join_grouped: EmbedJoin with grouping instead of one embedding length for
+ * all strings (Section 4.1): with N' = ceil(N/K) K, the strings fall into the
+ * groups g = 1 .. N'/K - 1 (at least one) of lengths ((g-1)K, (g+1)K] (the
+ * first group also holds the empty strings), so every pair within K in length
+ * shares a group; each group is joined on its own (out_len = 3 N of the group,
+ * the caller's r, m, z, L, K and seed) and the outputs are united (sorted,
+ * unique, as for ej_join). stats: candidates, raw pairs and band work summed
+ * over the groups (a pair in two groups counts twice), n_out of the union.
+ * Needs K >= 1 (EJ_ERR_INVALID_ARG); other errors as for ej_join.
+ */
+int ej_set_key_hash(ej_ctx *ctx, uint64_t P);
+int ej_join_grouped(ej_ctx *ctx, const ej_strings *strings, const ej_params *params, uint64_t *out,
+                    int64_t capacity, int64_t *n_out, ej_join_stats *stats, void *stream);
+
+/*
  * Test hook for the running example of Section 4 (Tables 2-4): replace the
  * random bits and positions with explicit tables (host pointers, copied).
  *   pi: [r][steps][alphabet_size] bytes in {0,1}, code-indexed; steps at or

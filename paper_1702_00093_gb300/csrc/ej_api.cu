@@ -31,6 +31,7 @@ enum BufId {
     B_FSCAN,
     B_PLUS_SUBLEN, B_PLUS_WHOLE, B_PLUS_SUBOFF, B_PLUS_BYTES, B_PLUS_SCAN, B_PLUS_CAND,
     B_SX_TCOUNT, B_SX_TSTART, B_SX_TASKS, B_SX_SCAN,
+    B_GROUP_IDX, B_GROUP_OFF, B_GROUP_BYTES, B_GROUP_OUT,
     B_NUM
 };
 
@@ -69,6 +70,8 @@ struct ej_ctx {
     int64_t loop_bound = 0;   // persistent verifier: loop passes per warp (ej_set_loop_bound; 0 = default)
     bool no_smem_buckets = false;   // a batch join with huge buckets: hashed buckets in global memory
     ej_ctx *plus_sub = nullptr;     // ej_join_plus: the context of the suffix set
+    ej_ctx *group_sub = nullptr;    // ej_join_grouped: the context of one length group
+    uint64_t key_P = 0;             // ej_set_key_hash: 0 = exact keys, else <u, v> mod key_P
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -416,11 +419,16 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
             CK(launch_derive_keys(keys, p->m, n, p->r, p->m, prefix->z[e] < p->z ? mod : 0, prefix->keys[e], s));
         }
     }
+    if (ctx->key_P && walk)
+        CK(launch_keys_modp(keys, n, p->r, p->m, p->z, p->alphabet_size, p->seed, ctx->key_P, s));
     if (pi_dev || pos_inj) CK(cudaStreamSynchronize(s));
     return EJ_OK;
 }
 
-int key_bits(const ej_params *p) {
+int bits_for(uint64_t maxval);
+
+int key_bits(const ej_ctx *ctx, const ej_params *p) {
+    if (ctx->key_P) return bits_for(ctx->key_P - 1);   // hashed keys are < P
     unsigned __int128 v = 1;
     for (uint32_t q = 0; q < p->z; q++) v *= (unsigned __int128)(p->alphabet_size + 1);
     uint64_t maxkey = (uint64_t)(v - 1);
@@ -441,7 +449,7 @@ int sorted_records(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
                    const uint64_t **out_rk, const uint32_t **out_rid, cudaStream_t s) {
     const int64_t n = pl.st.n, T = (int64_t)p->r * p->m;
     const int idb = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
-    if (n <= table_sort_max() && idb + key_bits(p) <= 64 && idb + bits_for((uint64_t)pl.max_len) <= 64) {
+    if (n <= table_sort_max() && idb + key_bits(ctx, p) <= 64 && idb + bits_for((uint64_t)pl.max_len) <= 64) {
         // every table fits one block: length order, then all tables, one block each
         uint64_t *lk = nullptr, *lsorted = nullptr;
         uint32_t *perm = nullptr;
@@ -454,7 +462,7 @@ int sorted_records(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
         uint32_t *rid = nullptr;
         CKS(ensure_t(ctx, B_RK, (size_t)(n * T), &rk));
         CKS(ensure_t(ctx, B_RID, (size_t)(n * T), &rid));
-        CK(launch_table_sort(keys, perm, n, T, idb, key_bits(p), rk, rid, s));
+        CK(launch_table_sort(keys, perm, n, T, idb, key_bits(ctx, p), rk, rid, s));
         *out_rk = rk;
         *out_rid = rid;
         return EJ_OK;
@@ -492,7 +500,7 @@ int sorted_records(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64
     CK(launch_len_order_gather(keys, order, n, T, rk, rid, s));
     // 3. stable sort by key within each table
     np = 0;
-    for (int b = 0; b < key_bits(p); b += 8) shifts[np++] = b;
+    for (int b = 0; b < key_bits(ctx, p); b += 8) shifts[np++] = b;
     CK(radix_sort_segmented(rk, rid, rk2, rid2, n, T, shifts, np, rt, &alt, s));
     *out_rk = alt ? rk2 : rk;
     *out_rid = alt ? rid2 : rid;
@@ -1432,6 +1440,7 @@ void ej_destroy(ej_ctx *c) {
         if (e) cudaEventDestroy(e);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->plus_sub) ej_destroy(c->plus_sub);
+    if (c->group_sub) ej_destroy(c->group_sub);
     delete c;
 }
 
@@ -1440,6 +1449,17 @@ const char *ej_last_error(ej_ctx *c) { return c ? c->err.c_str() : ""; }
 int ej_set_timing(ej_ctx *c, int enable) {
     if (!c) return EJ_ERR_INVALID_ARG;
     c->timing = enable != 0;
+    return EJ_OK;
+}
+
+int ej_set_key_hash(ej_ctx *c, uint64_t P) {
+    if (!c) return EJ_ERR_INVALID_ARG;
+    if (P != 0 && (P < 2 || P >= (1ull << 32)))
+        return fail(c, EJ_ERR_INVALID_ARG, "the hash modulus must be 0 or in [2, 2^32)");
+    if (P > 3)
+        for (uint64_t d = 2; d * d <= P; d++)
+            if (P % d == 0) return fail(c, EJ_ERR_INVALID_ARG, "the hash modulus %llu is not prime", (unsigned long long)P);
+    c->key_P = P;
     return EJ_OK;
 }
 
@@ -1567,6 +1587,8 @@ int ej_sign(ej_ctx *ctx, const ej_strings *S, const ej_params *p, const void *em
     CKS(out_target(ctx, B_KEYS, keys, kb, &d_keys, &h_keys));
     CK(launch_sign((const uint32_t *)d_emb, (const int32_t *)d_we, pl.st.n, p->r, p->m, p->z, pl.out_len,
                    pl.planes, p->alphabet_size, pos, (uint64_t *)d_keys, s));
+    if (ctx->key_P)
+        CK(launch_keys_modp((uint64_t *)d_keys, pl.st.n, p->r, p->m, p->z, p->alphabet_size, p->seed, ctx->key_P, s));
     if (h_keys) {
         CK(cudaMemcpyAsync(keys, d_keys, kb, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1881,6 +1903,163 @@ int ej_join_plus(ej_ctx *ctx, const ej_strings *S, const ej_params *p, int32_t d
 }
 
 
+// EmbedJoin with grouping (Section 4.1): every length group runs as a join of
+// its own (its strings gathered into a buffer of their own, on a private
+// context with this context's schedule and key choice), the group-local output
+// pairs are mapped back to the set's ids, and the union is sorted and made
+// unique. The groups are chosen on the host from the strings' lengths.
+int ej_join_grouped(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out, int64_t capacity,
+                    int64_t *n_out, ej_join_stats *stats, void *stream) {
+    if (!ctx || !n_out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/n_out");
+    *n_out = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (p && p->K < 1) return fail(ctx, EJ_ERR_INVALID_ARG, "grouping needs K >= 1");
+    const int64_t launches0 = launches_so_far();
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Plan pl;
+    CKS(make_plan(ctx, S, p, true, &pl, s));
+    const int64_t n = pl.st.n;
+    if (n < 2) return EJ_OK;
+    if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
+    std::vector<int32_t> lens((size_t)n);
+    CK(cudaMemcpyAsync(lens.data(), pl.lens, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t K = p->K, N = pl.max_len;
+    int64_t G = ((N + K - 1) / K) * K / K - 1;
+    if (G < 1) G = 1;
+    if (!ctx->group_sub && ej_create(&ctx->group_sub, ctx->device) != EJ_OK)
+        return fail(ctx, EJ_ERR_OOM, "group context");
+    ej_ctx *sub = ctx->group_sub;
+    sub->sched = ctx->sched;
+    sub->key_P = ctx->key_P;
+    sub->vG = ctx->vG;
+    sub->vV = ctx->vV;
+    sub->vWarps = ctx->vWarps;
+    std::vector<int32_t> idx;
+    std::vector<int64_t> goff;
+    struct DevBuf {   // the union of the groups' outputs, freed on every return
+        uint64_t *p = nullptr;
+        ~DevBuf() { if (p) cudaFree(p); }
+    } allbuf;
+    uint64_t *&all = allbuf.p;
+    int64_t nall = 0, cap_all = 0, cand_total = 0, raw_total = 0, maxb = 0;
+    uint64_t cells = 0, wcols = 0;
+    for (int64_t g = 1; g <= G; g++) {
+        idx.clear();
+        goff.assign(1, 0);
+        for (int64_t i = 0; i < n; i++) {
+            const int64_t len = lens[(size_t)i];
+            if ((g == 1 && len == 0) || (len > (g - 1) * K && len <= (g + 1) * K)) {
+                idx.push_back((int32_t)i);
+                goff.push_back(goff.back() + len);
+            }
+        }
+        const int64_t gn = (int64_t)idx.size();
+        if (gn < 2) continue;
+        int32_t *d_idx = nullptr;
+        int64_t *d_goff = nullptr;
+        uint8_t *d_gbytes = nullptr;
+        CKS(ensure_t(ctx, B_GROUP_IDX, (size_t)gn, &d_idx));
+        CKS(ensure_t(ctx, B_GROUP_OFF, (size_t)gn + 1, &d_goff));
+        CKS(ensure_t(ctx, B_GROUP_BYTES, (size_t)(goff.back() > 0 ? goff.back() : 1), &d_gbytes));
+        CK(cudaMemcpyAsync(d_idx, idx.data(), (size_t)gn * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_goff, goff.data(), (size_t)(gn + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        CK(launch_gather_strings(pl.st.bytes, pl.st.offsets, d_idx, gn, d_goff, d_gbytes, s));
+        ej_strings gs{d_gbytes, d_goff, gn};
+        ej_params gp = *p;
+        gp.out_len = 0;   // the group's own 3N
+        ej_join_stats gst;
+        int64_t gcount = 0;
+        uint64_t *gout = nullptr;
+        int64_t gcap = 1 << 16;
+        int st = EJ_OK;
+        for (;;) {
+            CKS(ensure_t(ctx, B_GROUP_OUT, (size_t)gcap, &gout));
+            st = ej_join(sub, &gs, &gp, gout, gcap, &gcount, &gst, s);
+            if (st != EJ_ERR_CAPACITY) break;
+            gcap = gcount;
+        }
+        if (st != EJ_OK) return fail(ctx, st, "group %lld: %s", (long long)g, sub->err.c_str());
+        cand_total += gst.n_candidates;
+        raw_total += gst.n_raw_pairs;
+        maxb = std::max<int64_t>(maxb, gst.max_bucket);
+        cells += gst.band_cells;
+        wcols += gst.verify_word_columns;
+        if (gcount == 0) continue;
+        if (nall + gcount > cap_all) {
+            // grow the union buffer (keeping what it holds)
+            const int64_t nc = 2 * (nall + gcount) + 1024;
+            uint64_t *nb = nullptr;
+            if (cudaMalloc(&nb, (size_t)nc * sizeof(uint64_t)) != cudaSuccess)
+                return fail(ctx, EJ_ERR_OOM, "grouped output");
+            if (nall) CK(cudaMemcpyAsync(nb, all, (size_t)nall * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+            CK(cudaStreamSynchronize(s));
+            if (all) cudaFree(all);
+            all = nb;
+            cap_all = nc;
+        }
+        CK(launch_remap_pairs(gout, gcount, d_idx, all + nall, s));
+        nall += gcount;
+    }
+    // the union: sorted, unique
+    int64_t cnt = 0;
+    int st = EJ_OK;
+    if (nall > 0) {
+        uint64_t *alt = nullptr;
+        CKS(ensure_t(ctx, B_RAW_ALT, (size_t)nall, &alt));
+        const int nb = bits_for((uint64_t)(n - 1));
+        int shifts[16], np = 0;
+        for (int b = 0; b < nb; b += 8) shifts[np++] = b;
+        for (int b = 0; b < nb; b += 8) shifts[np++] = 32 + b;
+        const size_t rs = radix_counts_len(nall, 1);
+        uint32_t *rsc = nullptr;
+        uint64_t *rso = nullptr, *fo = nullptr, *dcnt = nullptr;
+        void *stmp = nullptr, *stmp2 = nullptr;
+        uint8_t *fl = nullptr;
+        CKS(ensure_t(ctx, B_RS_COUNTS, rs, &rsc));
+        CKS(ensure_t(ctx, B_RS_OFFS, rs, &rso));
+        CKS(ensure(ctx, B_SCAN_TMP, scan_temp_bytes((int64_t)rs), &stmp));
+        bool alt_out = false;
+        CK(radix_sort_segmented(all, nullptr, alt, nullptr, nall, 1, shifts, np, RadixTemp{rsc, rso, stmp}, &alt_out, s));
+        const uint64_t *sorted = alt_out ? alt : all;
+        CKS(ensure_t(ctx, B_FLAGS, (size_t)nall, &fl));
+        CKS(ensure_t(ctx, B_FLAG_OFFS, (size_t)nall, &fo));
+        CKS(ensure(ctx, B_SCAN_TMP2, scan_temp_bytes(nall), &stmp2));
+        CKS(ensure_t(ctx, B_COUNTERS, 8, &dcnt));
+        CK(launch_unique_flags(sorted, nall, fl, s));
+        CK(exclusive_scan_u8(fl, fo, nall, dcnt, stmp2, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt, dcnt, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cnt = ctx->h_cnt[0];
+        if (cnt > capacity) {
+            st = fail(ctx, EJ_ERR_CAPACITY, "output needs %lld pairs, capacity %lld", (long long)cnt,
+                      (long long)capacity);
+        } else {
+            void *d_out = nullptr;
+            bool h_out = false;
+            st = out_target(ctx, B_OUT_STAGE, out, (size_t)cnt * sizeof(uint64_t), &d_out, &h_out);
+            if (st == EJ_OK) {
+                CK(launch_compact_u64(sorted, fl, fo, nall, (uint64_t *)d_out, s));
+                if (h_out) CK(cudaMemcpyAsync(out, d_out, (size_t)cnt * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+            }
+        }
+    }
+    *n_out = cnt;
+    if (stats) {
+        stats->n_raw_pairs = raw_total;
+        stats->n_candidates = cand_total;
+        stats->n_out = cnt;
+        stats->max_bucket = maxb;
+        stats->band_cells = cells;
+        stats->verify_word_columns = wcols;
+        stats->kernel_launches = launches_so_far() - launches0;
+    }
+    return st;
+}
+
+
 int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, int32_t n_params, int32_t flags,
                     ej_batch **out, void *stream) {
     if (!ctx || !out) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL ctx/out");
@@ -1893,6 +2072,8 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         return fail(ctx, EJ_ERR_INVALID_ARG, "a batch needs n >= 2 strings in device memory");
     if (ctx->pi.size() || ctx->posinj.size())
         return fail(ctx, EJ_ERR_INVALID_ARG, "injected test tables are not supported in a batch");
+    if (ctx->key_P)
+        return fail(ctx, EJ_ERR_UNSUPPORTED, "hashed bucket keys (ej_set_key_hash) are not supported in a batch");
     for (int32_t i = 1; i < n_params; i++)
         if (params[i].alphabet_size != params[0].alphabet_size ||
             memcmp(params[i].alphabet, params[0].alphabet, params[0].alphabet_size) != 0)

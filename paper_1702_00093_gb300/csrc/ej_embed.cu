@@ -850,4 +850,79 @@ cudaError_t launch_derive_keys(const uint64_t *src, uint32_t m_src, int64_t n, u
     return cudaGetLastError();
 }
 
+// The two-level hash of Section 4 in place of the exact keys [r*m][n]: the
+// exact key sum_q c_q (alpha+1)^q is decoded into the signature's codes c_q,
+// and the key becomes <u, v> mod P with u_q = c_q + 1 and v[l][f][q] =
+// mulhi64(splitmix64(splitmix64(seed) ^ (3<<56 | l<<48 | f<<32 | q)), P).
+__global__ void keys_modp_kernel(uint64_t *__restrict__ keys, int64_t n, uint32_t r, uint32_t m, uint32_t z,
+                                 uint32_t alpha, uint64_t seed, uint64_t P) {
+    const int64_t total = (int64_t)r * m * n;
+    const uint64_t base = mix64(seed), radix = (uint64_t)alpha + 1;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = g / n;
+        const uint32_t l = (uint32_t)(t / m), f = (uint32_t)(t - (int64_t)l * m);
+        uint64_t key = keys[g], acc = 0;
+        for (uint32_t q = 0; q < z; q++) {
+            const uint64_t c = key % radix;
+            key /= radix;
+            const uint64_t ctr = (3ull << 56) | ((uint64_t)l << 48) | ((uint64_t)f << 32) | (uint64_t)q;
+            const uint64_t v = __umul64hi(mix64(base ^ ctr), P);
+            acc = (acc + (c + 1) * v) % P;
+        }
+        keys[g] = acc;
+    }
+}
+
+cudaError_t launch_keys_modp(uint64_t *keys, int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t alpha,
+                             uint64_t seed, uint64_t P, cudaStream_t s) {
+    const int64_t total = (int64_t)r * m * n;
+    if (total == 0) return cudaGetLastError();
+    const int64_t g = (total + 255) / 256;
+    keys_modp_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, s>>>(keys, n, r, m, z, alpha, seed, P);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Strings idx[0 .. gn) of a set gathered into one buffer (goff: their offsets
+// there), one warp per string.
+__global__ void gather_strings_kernel(const uint8_t *__restrict__ bytes, const int64_t *__restrict__ offsets,
+                                      const int32_t *__restrict__ idx, int64_t gn, const int64_t *__restrict__ goff,
+                                      uint8_t *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < gn; q += warps) {
+        const int64_t i = idx[q];
+        const int64_t len = goff[q + 1] - goff[q];
+        const uint8_t *src = bytes + offsets[i];
+        for (int64_t t = lane; t < len; t += 32) out[goff[q] + t] = src[t];
+    }
+}
+
+// Group-local pairs (a << 32 | b) mapped to the ids idx[a], idx[b] (increasing
+// in a group, so the order a < b is kept), appended at out[base ..).
+__global__ void remap_pairs_kernel(const uint64_t *__restrict__ pairs, int64_t cnt, const int32_t *__restrict__ idx,
+                                   uint64_t *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = pairs[e];
+        out[e] = ((uint64_t)(uint32_t)idx[v >> 32] << 32) | (uint64_t)(uint32_t)idx[v & 0xFFFFFFFFull];
+    }
+}
+
+cudaError_t launch_gather_strings(const uint8_t *bytes, const int64_t *offsets, const int32_t *idx, int64_t gn,
+                                  const int64_t *goff, uint8_t *out, cudaStream_t s) {
+    if (gn == 0) return cudaGetLastError();
+    int64_t g = (gn * 32 + 255) / 256;
+    gather_strings_kernel<<<(unsigned)(g > 152 * 32 ? 152 * 32 : g), 256, 0, s>>>(bytes, offsets, idx, gn, goff, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap_pairs(const uint64_t *pairs, int64_t cnt, const int32_t *idx, uint64_t *out, cudaStream_t s) {
+    if (cnt == 0) return cudaGetLastError();
+    int64_t g = (cnt + 255) / 256;
+    remap_pairs_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, s>>>(pairs, cnt, idx, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace ej

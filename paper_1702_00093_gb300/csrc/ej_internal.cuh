@@ -171,6 +171,15 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
 cudaError_t launch_derive_keys(const uint64_t *src, uint32_t m_src, int64_t n, uint32_t r, uint32_t m,
                                uint64_t modulus, uint64_t *dst, cudaStream_t s);
 
+// The two-level hash <u, v> mod P of Section 4 in place of exact keys [r*m][n].
+cudaError_t launch_keys_modp(uint64_t *keys, int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t alpha,
+                             uint64_t seed, uint64_t P, cudaStream_t s);
+// Grouping (Section 4.1): strings idx[0..gn) gathered at offsets goff, and
+// group-local output pairs mapped back to the set's ids.
+cudaError_t launch_gather_strings(const uint8_t *bytes, const int64_t *offsets, const int32_t *idx, int64_t gn,
+                                  const int64_t *goff, uint8_t *out, cudaStream_t s);
+cudaError_t launch_remap_pairs(const uint64_t *pairs, int64_t cnt, const int32_t *idx, uint64_t *out, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Scan and sort primitives (ej_sort.cu)
 // ---------------------------------------------------------------------------

@@ -29,7 +29,8 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_set_timing",
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
-            "ej_set_schedule", "ej_set_loop_bound", "ej_measure_int_peak", "ej_join_plus", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_set_schedule", "ej_set_loop_bound", "ej_measure_int_peak", "ej_join_plus",
+            "ej_set_key_hash", "ej_join_grouped", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
             "ej_batch_verify_ms",
             "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
             "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
@@ -141,6 +142,10 @@ def lib():
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
+        L.ej_set_key_hash.argtypes = [vp, C.c_uint64]
+        L.ej_set_key_hash.restype = C.c_int
+        L.ej_join_grouped.argtypes = [vp, vp, vp, vp, C.c_int64, C.POINTER(C.c_int64), vp, vp]
+        L.ej_join_grouped.restype = C.c_int
         L.ej_join_plus.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64), vp, vp]
         L.ej_join_plus.restype = C.c_int
         L.ej_set_loop_bound.argtypes = [vp, C.c_int64]
@@ -416,6 +421,29 @@ class Context:
                 if e.status != EJ_ERR_CAPACITY:
                     raise
                 capacity = e.needed
+
+    def set_key_hash(self, P: int = 0):
+        """Bucket keys by the two-level hash <u, v> mod P of Section 4 (0 = exact keys)."""
+        self._check(lib().ej_set_key_hash(self._h, P), "ej_set_key_hash")
+
+    def join_grouped(self, s: Strings, p: Params, device=None, capacity: int = 1 << 16, stream=None):
+        """EmbedJoin with grouping by length (Section 4.1): (pairs, stats) as join()."""
+        while True:
+            if device is None:
+                out = np.zeros(max(capacity, 1), dtype=np.uint64)
+            else:
+                import torch
+                out = torch.empty(max(capacity, 1), dtype=torch.int64, device=device)
+            cs, (cp, _keep) = s._c(), p._c()
+            n = C.c_int64(0)
+            stats = JoinStats()
+            st = lib().ej_join_grouped(self._h, C.byref(cs), C.byref(cp), _ptr(out), int(out.shape[0]), C.byref(n),
+                                       C.byref(stats), _stream(stream))
+            if st == EJ_ERR_CAPACITY and n.value > out.shape[0]:
+                capacity = n.value
+                continue
+            self._check(st, "ej_join_grouped")
+            return out[:n.value], stats
 
     def set_test_tables(self, pi=None, positions=None):
         """Inject explicit pi tables [r][steps][alphabet] (0/1) and/or positions
