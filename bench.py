@@ -124,7 +124,9 @@ def parse(argv=None):
     ap.add_argument("--Ks", type=str, default="", help="comma-separated K values (default: the workload's)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-stage path")
-    ap.add_argument("--autotune", action="store_true", help="autotune each join of the batch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the headline batch without the autotuner (by default each of its joins is tuned per "
+                         "length class and K on its own data; the full-size workloads use the defaults)")
     ap.add_argument("--batch-eager", action="store_true",
                     help="issue the batch's work without a CUDA graph (same work; for per-kernel profilers)")
     ap.add_argument("--paths", type=str, default="batch,join,plain",
@@ -861,7 +863,7 @@ def full_size_join(ej, name, args, rank, dev, stream, flush, world, clk, int_pea
     ctx = ej.Context(int(dev.split(":")[1]))
     try:
         r = run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps=args.full_steps, warm=1,
-                              paths={"batch", "join", "plain"}, plain_steps=1, e2e_steps=0, autotune=args.autotune,
+                              paths={"batch", "join", "plain"}, plain_steps=1, e2e_steps=0, autotune=False,
                               batch_eager=False, int_peak=int_peak, hbm=hbm, timed_windows=windows)
         out = {"workload": wl["desc"](ss, fargs) + f"; K={','.join(str(p.K) for p in params)}; r={params[0].r}, "
                                                   f"m={params[0].m}, z={'/'.join(str(p.z) for p in params)}, "
@@ -911,8 +913,9 @@ def main():
         paths = set(args.paths.split(",")) | {"eager"}
         r = run_join_workload(ej, ctx, ss, params, dev, stream, flush, world, clk, steps=args.steps, warm=warm,
                               paths=paths, plain_steps=args.plain_steps, e2e_steps=args.e2e_steps,
-                              autotune=args.autotune, batch_eager=args.batch_eager, int_peak=int_peak, hbm=hbm,
+                              autotune=not args.no_autotune, batch_eager=args.batch_eager, int_peak=int_peak, hbm=hbm,
                               timed_windows=head_windows)
+        tune_table = ctx.autotune_table()
         head_clocks = clk.summary(head_windows)
         recall = None
         if not args.no_recall and rank == 0:
@@ -952,7 +955,7 @@ def main():
                                    (", the joins of a step captured as one CUDA graph (ej_batch)" if r["use_batch"]
                                     else ", one ej_join call per K"),
                        "n": ss.n, "Ks": list(Ks), "l2": "flushed before each timed step (256 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU", "autotune": args.autotune,
+                       "parallelism": "replicas" if world > 1 else "single GPU", "autotune": not args.no_autotune,
                        "headline": ("the plain method on long strings on one GPU heads the line; the protein-like, "
                                     "text-like and serving workloads are measured at full size under 'workloads'")},
             "join_wall_s_per_step": batch_ms_max / steps / 1e3,
@@ -963,6 +966,7 @@ def main():
             "join_path_roofline": r.get("join_roofline"),
             "stage_roofline": r.get("stage_roofline"),
             "int_peak": int_peak,
+            "autotune_table": tune_table,
             "clocks": head_clocks,
             "gpu_launches": int(r["launches_step"] * steps),
             "e2e": r["e2e"],

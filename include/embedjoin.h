@@ -275,7 +275,9 @@ void ej_server_destroy(ej_server *server);
  * no counterpart). ej_batch_create plans the strings once (validate, pack),
  * runs every parameter set once eagerly to size all buffers (the raw-pair
  * capacity gets a margin of 1/8), optionally autotunes each join's back half on
- * its own data (EJ_BATCH_AUTOTUNE: the verifier schedule of ej_set_schedule),
+ * its own data (EJ_BATCH_AUTOTUNE: the verifier choice of the autotuner, see
+ * ej_set_autotune; an entry of the context's table for the join's length class
+ * and K is used as it is),
  * and captures the whole device path of all joins into one graph: validate and
  * pack once, then per parameter set, on its own stream so that the joins
  * overlap, the walk and signatures, buckets, pairs, dedup and verification.
@@ -398,6 +400,39 @@ typedef struct {
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside
  * the ranges above. */
 int ej_set_schedule(ej_ctx *ctx, const ej_schedule *schedule);
+
+/*
+ * Autotuner (a performance choice; the output never depends on it). With
+ * ej_set_autotune(ctx, 1), ej_join looks up its (length class, K) in the
+ * context's table, where the length class is floor(log2(mean string length));
+ * on a miss it tunes on the call's own strings and candidates before the join:
+ *  - the fused walk's walks (strings) per block: 256, 512 or 1024;
+ *  - the verifier and its tiling: the persistent verifier with 16 or 8 pair
+ *    slots per warp and one or two working warps per SM sub-partition, the
+ *    shared-string verifier, the grid-strided two-lane verifier in
+ *    first-string or length-class order, one lane per pair with the band in
+ *    registers (bands of up to 8 words), and four lanes per pair (up to 4 words
+ *    each); every choice is timed twice (CUDA events) after a warm-up run, on
+ *    the join's own candidates, and the fastest is kept in the table.
+ * Later joins of the same class and K use the entry without tuning. A batch
+ * created with EJ_BATCH_AUTOTUNE tunes each join's back half the same way (or
+ * uses the context's entry) and records it in the table. ej_autotune_table
+ * copies up to `max` entries, *n = the table's size. ej_set_autotune(ctx, 0)
+ * stops using the table; ej_set_autotune(ctx, -1) also clears it.
+ */
+typedef struct {
+    int32_t length_class;    /* floor(log2(mean string length)) */
+    int32_t K;
+    int32_t walk_threads;    /* walks (strings) per block of the fused walk (0: not tuned) */
+    int32_t lanes_per_pair;  /* verifier tiling as for ej_set_verify_config (0 = automatic) */
+    int32_t words_per_lane;
+    int32_t configs_tried;
+    ej_schedule schedule;    /* mode, slots_per_warp, warps_per_subpartition, order chosen */
+    float walk_ms;           /* the chosen walk on the tuning join (0: not tuned) */
+    float back_ms;           /* the chosen back half: buckets, pairs, dedup, verification */
+} ej_tune_entry;
+int ej_set_autotune(ej_ctx *ctx, int enable);
+int ej_autotune_table(ej_ctx *ctx, ej_tune_entry *out, int32_t max, int32_t *n);
 
 /*
  * Validate the strings against the parameters and report the derived sizes

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "ej_internal.cuh"
@@ -72,6 +73,9 @@ struct ej_ctx {
     ej_ctx *plus_sub = nullptr;     // ej_join_plus: the context of the suffix set
     ej_ctx *group_sub = nullptr;    // ej_join_grouped: the context of one length group
     uint64_t key_P = 0;             // ej_set_key_hash: 0 = exact keys, else <u, v> mod key_P
+    int walk_tpb = 0;               // walks (strings) per block of the fused walk (0 = 512)
+    bool autotune = false;          // ej_set_autotune: joins consult / fill tune_table
+    std::map<uint64_t, ej_tune_entry> tune_table;   // (length class << 32 | K) -> choice
     // cached alphabet
     uint8_t alpha_cache[256];
     uint32_t alpha_cache_n = 0;
@@ -369,7 +373,8 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         pos_inj = d;
     }
     if (tables) CK(launch_positions(p->seed, p->r, p->m, p->z, pl.L, pos_inj, pos, s));
-    if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z) > 0) {
+    if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z, ctx->walk_tpb) > 0 ||
+        embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z) > 0) {
         uint32_t *tsym = nullptr, *spos = nullptr, *stag = nullptr;
         CKS(ensure_t(ctx, B_TSYM, symbol_table_words(p->r, p->alphabet_size, pl.L), &tsym));
         CKS(ensure_t(ctx, B_SPOS, (size_t)p->r * p->m * p->z, &spos));
@@ -387,7 +392,7 @@ int keys_dev(ej_ctx *ctx, const ej_params *p, const Plan &pl, uint64_t *keys, cu
         if (walk) {
             if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
             CK(launch_embed_sign(pl.packed, pl.pofs, pl.lens, n, p->r, p->m, p->z, pl.L, p->alphabet_size, pl.B,
-                                 tsym, next, spos, stag, keys, s, prefix));
+                                 tsym, next, spos, stag, keys, s, prefix, ctx->walk_tpb));
             if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s));
         }
         prefix = nullptr;   // written by the walk
@@ -931,6 +936,150 @@ int join_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *k
     return back_finish(ctx, pl, p, hc, out, capacity, n_out, stats, s);
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: per (length class, K), the walk's block size and the verifier's
+// kind and tiling, timed on the join's own strings and candidates
+// ---------------------------------------------------------------------------
+
+struct TuneCand {
+    ej_schedule sc;   // mode, slots_per_warp, warps_per_subpartition, order (buckets, chain kept)
+    int G, V;         // verifier tiling (0 = automatic)
+};
+
+std::vector<TuneCand> tune_candidates(const ej_params *p) {
+    const int W = (2 * p->K + 1 + 63) / 64;
+    std::vector<TuneCand> c = {
+        {{1, 16, 1, 0, 0, 0}, 0, 0}, {{1, 16, 2, 0, 0, 0}, 0, 0}, {{1, 8, 1, 0, 0, 0}, 0, 0},
+        {{3, 0, 0, 0, 0, 0}, 0, 0},  {{2, 0, 0, 3, 0, 0}, 0, 0},  {{2, 0, 0, 4, 0, 0}, 0, 0},
+    };
+    if (W <= 8) c.push_back({{2, 0, 0, 3, 0, 0}, 1, W});
+    if ((W + 3) / 4 <= 4) c.push_back({{2, 0, 0, 3, 0, 0}, 4, (W + 3) / 4});
+    return c;
+}
+
+uint64_t tune_key(const Plan &pl, const ej_params *p) {
+    const int64_t mean = pl.st.n > 0 ? pl.st.total / pl.st.n : 0;
+    int cls = 0;
+    while (cls < 62 && (mean >> (cls + 1)) > 0) cls++;
+    return ((uint64_t)(uint32_t)cls << 32) | (uint32_t)p->K;
+}
+
+void apply_tune(ej_ctx *ctx, const ej_tune_entry &e) {
+    ctx->sched.mode = e.schedule.mode;
+    ctx->sched.slots_per_warp = e.schedule.slots_per_warp;
+    ctx->sched.warps_per_subpartition = e.schedule.warps_per_subpartition;
+    ctx->sched.order = e.schedule.order;
+    ctx->vG = e.lanes_per_pair;
+    ctx->vV = e.words_per_lane;
+    if (e.walk_threads) ctx->walk_tpb = e.walk_threads;
+}
+
+// Times the back half (buckets .. verification, raw capacity cap) under every
+// candidate and leaves the fastest in *best (the context's own settings are
+// restored). Candidates that fail to launch are skipped.
+int tune_back(ej_ctx *ctx, const Plan &pl, const ej_params *p, const uint64_t *keys, uint64_t cap, cudaStream_t s,
+              ej_tune_entry *best) {
+    const ej_schedule sc0 = ctx->sched;
+    const int vG0 = ctx->vG, vV0 = ctx->vV;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int tried = 0;
+    for (const TuneCand &c : tune_candidates(p)) {
+        ctx->sched = sc0;
+        ctx->sched.mode = c.sc.mode;
+        ctx->sched.slots_per_warp = c.sc.slots_per_warp;
+        ctx->sched.warps_per_subpartition = c.sc.warps_per_subpartition;
+        ctx->sched.order = c.sc.order;
+        ctx->vG = c.G;
+        ctx->vV = c.V;
+        float t = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; rep++) {
+            BackState bs;
+            ok = cudaEventRecord(e0, s) == cudaSuccess && back_buckets(ctx, pl, p, keys, &bs, s) == EJ_OK &&
+                 back_attempt(ctx, pl, p, bs, cap, s) == EJ_OK && cudaEventRecord(e1, s) == cudaSuccess &&
+                 cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.f;
+            if (ok) cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t += ms;   // the first run warms the choice up
+        }
+        if (!ok) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s);
+            continue;
+        }
+        tried++;
+        if (t < best_ms) {
+            best_ms = t;
+            best->schedule = ctx->sched;
+            best->lanes_per_pair = c.G;
+            best->words_per_lane = c.V;
+        }
+    }
+    ctx->sched = sc0;
+    ctx->vG = vG0;
+    ctx->vV = vV0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best->back_ms = best_ms / 2.f;
+    best->configs_tried += tried;
+    return tried ? EJ_OK : fail(ctx, EJ_ERR_CUDA, "no verifier choice ran");
+}
+
+// The whole tuning of one join: the walk's block size, then the back half.
+int tune_join(ej_ctx *ctx, const Plan &pl, const ej_params *p, uint64_t *keys, cudaStream_t s, ej_tune_entry *out) {
+    const uint64_t key = tune_key(pl, p);
+    memset(out, 0, sizeof *out);
+    out->length_class = (int32_t)(key >> 32);
+    out->K = p->K;
+    const int tpb0 = ctx->walk_tpb;
+    ctx->walk_tpb = 0;
+    CKS(keys_dev(ctx, p, pl, keys, s));   // tables and a first walk
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int tpb : {256, 512, 1024}) {
+        if (embed_sign_smem(p->alphabet_size, pl.L, p->m, p->z, tpb) == 0) continue;
+        ctx->walk_tpb = tpb;
+        float t = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            CK(cudaEventRecord(e0, s));
+            CKS(keys_dev(ctx, p, pl, keys, s, nullptr, 2));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) t += ms;
+        }
+        out->configs_tried++;
+        if (t < best) {
+            best = t;
+            out->walk_threads = tpb;
+            out->walk_ms = t / 2.f;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->walk_tpb = tpb0;
+    // the back half with a raw-pair capacity sized by one ordinary run
+    BackState bs;
+    CKS(back_buckets(ctx, pl, p, keys, &bs, s));
+    uint64_t cap = raw_cap_start(ctx, pl.st.n);
+    unsigned long long hc[8];
+    for (int attempt = 0;; attempt++) {
+        CKS(back_attempt(ctx, pl, p, bs, cap, s));
+        CKS(back_read(ctx, hc, s));
+        if (hc[0] <= cap) break;
+        if (attempt > 0) return fail(ctx, EJ_ERR_CUDA, "raw pair count changed between attempts");
+        cap = hc[0] + hc[0] / 4 + 1024;
+    }
+    ctx->raw_cap_hint = cap;
+    return tune_back(ctx, pl, p, keys, cap, s, out);
+}
+
 // Output array: device pointer or a staging buffer to copy to host after.
 int out_target(ej_ctx *ctx, BufId id, void *user, size_t bytes, void **dev, bool *is_host) {
     if (is_device_ptr(user)) {
@@ -1083,13 +1232,6 @@ void batch_sources(std::vector<BatchJoin> &joins) {
         }
     }
 }
-
-// Schedules the autotuner tries for the back half of one join (verifier slots
-// per warp, working warps per SM sub-partition, queue order); the fastest on
-// the join's own data wins.
-const ej_schedule kTuneSet[] = {
-    {1, 16, 1, 4, 0}, {1, 16, 2, 4, 0}, {1, 16, 1, 3, 0}, {1, 16, 1, 1, 0}, {2, 0, 0, 3, 0}, {2, 0, 0, 4, 0},
-};
 
 // Merged verification (ej_schedule.chain 0 or 3): the joins that use the
 // persistent verifier are verified by one launch at the widest of their bands,
@@ -1315,38 +1457,21 @@ int batch_issue(ej_batch *b, cudaStream_t s) {
     return cst;
 }
 
-int batch_autotune(BatchJoin &j, cudaStream_t s, float *best_ms) {
-    ej_ctx *ctx = j.sub;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    ej_schedule best_sc = j.sub->sched;
-    for (const ej_schedule &sc : kTuneSet) {
-        j.sub->sched = sc;
-        float t = 0.f;
-        for (int rep = 0; rep < 3; rep++) {
-            CK(cudaEventRecord(e0, s));
-            CKS(back_buckets(j.sub, j.pl, &j.p, j.keys, &j.bs, s));
-            CKS(back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s));
-            CK(cudaEventRecord(e1, s));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) t += ms;   // the first repetition warms the schedule up
-        }
-        if (t < best) {
-            best = t;
-            best_sc = sc;
-        }
+int batch_autotune(ej_ctx *parent, BatchJoin &j, cudaStream_t s, float *best_ms) {
+    const uint64_t key = tune_key(j.pl, &j.p);
+    auto it = parent->tune_table.find(key);
+    if (it == parent->tune_table.end()) {
+        ej_tune_entry e;
+        memset(&e, 0, sizeof e);
+        e.length_class = (int32_t)(key >> 32);
+        e.K = j.p.K;
+        CKS(tune_back(j.sub, j.pl, &j.p, j.keys, j.cap, s, &e));
+        it = parent->tune_table.emplace(key, e).first;
     }
-    j.sub->sched = best_sc;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *best_ms = best / 2.f;
+    apply_tune(j.sub, it->second);
+    *best_ms = it->second.back_ms;
     return EJ_OK;
 }
-
 
 }  // namespace
 
@@ -1460,6 +1585,24 @@ int ej_set_key_hash(ej_ctx *c, uint64_t P) {
         for (uint64_t d = 2; d * d <= P; d++)
             if (P % d == 0) return fail(c, EJ_ERR_INVALID_ARG, "the hash modulus %llu is not prime", (unsigned long long)P);
     c->key_P = P;
+    return EJ_OK;
+}
+
+int ej_set_autotune(ej_ctx *c, int enable) {
+    if (!c) return EJ_ERR_INVALID_ARG;
+    if (enable < 0) c->tune_table.clear();
+    c->autotune = enable > 0;
+    return EJ_OK;
+}
+
+int ej_autotune_table(ej_ctx *c, ej_tune_entry *out, int32_t max, int32_t *n) {
+    if (!c || !n || max < 0 || (max > 0 && !out)) return EJ_ERR_INVALID_ARG;
+    *n = (int32_t)c->tune_table.size();
+    int32_t k = 0;
+    for (const auto &kv : c->tune_table) {
+        if (k >= max) break;
+        out[k++] = kv.second;
+    }
     return EJ_OK;
 }
 
@@ -1682,6 +1825,24 @@ int ej_join(ej_ctx *ctx, const ej_strings *S, const ej_params *p, uint64_t *out,
     if (pl.st.n < 2) return EJ_OK;
     uint64_t *keys = nullptr;
     CKS(ensure_t(ctx, B_KEYS, (size_t)p->r * p->m * pl.st.n, &keys));
+    // autotuner: this call runs with its (length class, K) entry, tuned now if missing
+    const ej_schedule sc0 = ctx->sched;
+    const int vG0 = ctx->vG, vV0 = ctx->vV, tpb0 = ctx->walk_tpb;
+    struct Restore {
+        ej_ctx *c; ej_schedule sc; int g, v, t; bool on;
+        ~Restore() { if (on) { c->sched = sc; c->vG = g; c->vV = v; c->walk_tpb = t; } }
+    } restore{ctx, sc0, vG0, vV0, tpb0, ctx->autotune && !ctx->pi.size() && !ctx->posinj.size()};
+    if (restore.on) {
+        const uint64_t key = tune_key(pl, p);
+        auto it = ctx->tune_table.find(key);
+        if (it == ctx->tune_table.end()) {
+            ej_tune_entry e;
+            CKS(tune_join(ctx, pl, p, keys, s, &e));
+            it = ctx->tune_table.emplace(key, e).first;
+        }
+        apply_tune(ctx, it->second);
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
+    }
     CKS(keys_dev(ctx, p, pl, keys, s));
     if (!out && capacity > 0) return fail(ctx, EJ_ERR_INVALID_ARG, "NULL out");
     ej_join_stats st_local;
@@ -2149,7 +2310,7 @@ int ej_batch_create(ej_ctx *ctx, const ej_strings *S, const ej_params *params, i
         if ((st = back_attempt(j.sub, j.pl, &j.p, j.bs, j.cap, s)) != EJ_OK) return bail(st);
         if (flags & EJ_BATCH_AUTOTUNE) {
             float ms = 0.f;
-            if ((st = batch_autotune(j, s, &ms)) != EJ_OK) return bail(st);
+            if ((st = batch_autotune(ctx, j, s, &ms)) != EJ_OK) return bail(st);
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, EJ_ERR_CUDA, "eager pass failed"));
     }

@@ -489,7 +489,7 @@ cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uin
     return cudaGetLastError();
 }
 
-constexpr int ES_THREADS = 512;
+constexpr int ES_THREADS = 512;   // default walks (strings) per block
 constexpr size_t ES_TABLE_MAX = 48 * 1024;   // next-step table kept in shared memory up to this size
 
 // Per-embedding stride of the next-step table, even so that every table starts
@@ -550,12 +550,13 @@ static size_t es_code_words(uint32_t alpha, uint32_t M) {
     return (M + per - 1) / per;
 }
 
-size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z) {
+size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z, int tpb) {
+    if (tpb <= 0) tpb = ES_THREADS;
     const size_t M = (size_t)m * z;
     if (M > 16384 || z > 65535 || m > 65535) return 0;
     const size_t table = embed_sign_uses_table(alpha, L) ? (size_t)alpha * next_row(L) * 2 : (size_t)alpha * sym_words(L) * 4;
     const size_t bytes = (size_t)z * 8 + (M + 1) * 4 + M * 4 + ((table + 7) & ~(size_t)7) +
-                         es_code_words(alpha, (uint32_t)M) * 4 * ES_THREADS;
+                         es_code_words(alpha, (uint32_t)M) * 4 * (size_t)tpb;
     return bytes <= 200 * 1024 ? bytes : 0;
 }
 
@@ -605,8 +606,8 @@ struct WordReader {
 
 // TABLE: next steps from the 16-bit table (one shared load per character);
 // otherwise a find-first-set over the step bitmaps. CB: bits per stored code.
-template <int B, bool TABLE, int CB>
-__global__ void __launch_bounds__(ES_THREADS)
+template <int B, bool TABLE, int CB, int TPB>
+__global__ void __launch_bounds__(TPB)
 embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                   const int32_t *__restrict__ lens, int64_t n, uint32_t m, uint32_t z, uint32_t L,
                   uint32_t alpha, const uint32_t *__restrict__ tsym, const uint16_t *__restrict__ next,
@@ -622,7 +623,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     const uint32_t NR = next_row(L);
     const size_t tab_bytes = TABLE ? (size_t)alpha * NR * 2 : (size_t)alpha * LW * 4;
     uint16_t *s_next = (uint16_t *)s_tab;
-    uint32_t *s_code = (uint32_t *)((char *)s_tab + ((tab_bytes + 7) & ~(size_t)7));  // [words][ES_THREADS]
+    uint32_t *s_code = (uint32_t *)((char *)s_tab + ((tab_bytes + 7) & ~(size_t)7));  // [words][TPB]
     for (uint32_t i = threadIdx.x; i <= M; i += blockDim.x) {
         s_pos[i] = i < M ? spos[(size_t)l * M + i] : 0xFFFFFFFFu;
         if (i < M) {
@@ -647,7 +648,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     }
     __syncthreads();
 
-    const int64_t s = (int64_t)blockIdx.x * ES_THREADS + threadIdx.x;
+    const int64_t s = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const int32_t len = s < n ? lens[s] : 0;
     uint32_t *my = s_code + threadIdx.x;
     if (TABLE) {
@@ -680,12 +681,12 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                 const bool hit = live && ps < a_next;   // a sample inside this character's steps
                 acc = hit ? ((acc >> CB) | (c << (32 - CB))) : acc;
                 k += hit ? 1u : 0u;
-                if (hit && k % PER == 0) my[(size_t)(k / PER - 1) * ES_THREADS] = acc;
+                if (hit && k % PER == 0) my[(size_t)(k / PER - 1) * TPB] = acc;
                 ps = s_pos[k];
                 while (live && ps < a_next) {   // rare: another sample in the same character
                     acc = (acc >> CB) | (c << (32 - CB));
                     k++;
-                    if (k % PER == 0) my[(size_t)(k / PER - 1) * ES_THREADS] = acc;
+                    if (k % PER == 0) my[(size_t)(k / PER - 1) * TPB] = acc;
                     ps = s_pos[k];
                 }
                 a = a_next;
@@ -693,7 +694,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
 #pragma unroll
             for (int w = 0; w < WPB; w++) cur[w] = nxt[w];
         }
-        if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc >> (CB * (PER - k % PER));
+        if (k % PER) my[(size_t)(k / PER) * TPB] = acc >> (CB * (PER - k % PER));
         if (s < n) {
             for (uint32_t f = 0; f < m; f++) {
                 uint64_t key = 0;
@@ -703,7 +704,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                     for (; q < qe; q++) {
                         const uint32_t rk = s_rank[f * z + q];
                         const uint32_t c = (rk < k)
-                                               ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                               ? ((my[(size_t)(rk / PER) * TPB] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
                                                : alpha;
                         key += (uint64_t)c * s_pow[q];
                     }
@@ -745,7 +746,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
         const bool hit = ps < a_next;
         acc |= hit ? (c << ((k % PER) * CB)) : 0u;
         if (hit && (k % PER == PER - 1)) {
-            my[(size_t)(k / PER) * ES_THREADS] = acc;
+            my[(size_t)(k / PER) * TPB] = acc;
             acc = 0;
         }
         k += hit ? 1u : 0u;
@@ -753,7 +754,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
         while (ps < a_next) {            // rare: another sample in the same character
             acc |= c << ((k % PER) * CB);
             if (k % PER == PER - 1) {
-                my[(size_t)(k / PER) * ES_THREADS] = acc;
+                my[(size_t)(k / PER) * TPB] = acc;
                 acc = 0;
             }
             ps = s_pos[++k];
@@ -763,7 +764,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
         rd.advance();
     }
     const uint32_t k_end = k;            // samples from k_end on lie after the walk: bottom
-    if (k % PER) my[(size_t)(k / PER) * ES_THREADS] = acc;
+    if (k % PER) my[(size_t)(k / PER) * TPB] = acc;
     if (s < n) {
         for (uint32_t f = 0; f < m; f++) {
             uint64_t key = 0;
@@ -773,7 +774,7 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
                 for (; q < qe; q++) {
                     const uint32_t rk = s_rank[f * z + q];
                     const uint32_t c = (rk < k_end)
-                                           ? ((my[(size_t)(rk / PER) * ES_THREADS] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
+                                           ? ((my[(size_t)(rk / PER) * TPB] >> ((rk % PER) * CB)) & ((1u << CB) - 1u))
                                            : alpha;
                     key += (uint64_t)c * s_pow[q];
                 }
@@ -784,21 +785,38 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     }
 }
 
+template <int B, bool TABLE, int CB, int TPB>
+static void es_launch_t(size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs, const int32_t *lens,
+                        int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, const uint32_t *tsym,
+                        const uint16_t *next, const uint32_t *spos, const uint32_t *stag, uint64_t *keys,
+                        const PrefixKeys &pk) {
+    cudaFuncSetAttribute(embed_sign_kernel<B, TABLE, CB, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((n + TPB - 1) / TPB), r);
+    embed_sign_kernel<B, TABLE, CB, TPB><<<grid, TPB, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym, next,
+                                                                 spos, stag, keys, pk);
+}
+
+// The walk with tpb walks (strings) per block: 256, 512 (default) or 1024.
 template <int B, bool TABLE, int CB>
-static void es_launch(dim3 grid, size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs,
-                      const int32_t *lens, int64_t n, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha,
+static void es_launch(int tpb, size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs,
+                      const int32_t *lens, int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha,
                       const uint32_t *tsym, const uint16_t *next, const uint32_t *spos, const uint32_t *stag,
                       uint64_t *keys, const PrefixKeys &pk) {
-    cudaFuncSetAttribute(embed_sign_kernel<B, TABLE, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    embed_sign_kernel<B, TABLE, CB><<<grid, ES_THREADS, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, tsym,
-                                                                   next, spos, stag, keys, pk);
+    if (tpb == 256)
+        es_launch_t<B, TABLE, CB, 256>(smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+    else if (tpb == 1024)
+        es_launch_t<B, TABLE, CB, 1024>(smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+    else
+        es_launch_t<B, TABLE, CB, 512>(smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
 }
 
 cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n,
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
                               const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
-                              const uint32_t *stag, uint64_t *keys, cudaStream_t s, const PrefixKeys *prefix) {
+                              const uint32_t *stag, uint64_t *keys, cudaStream_t s, const PrefixKeys *prefix,
+                              int tpb) {
     if (n == 0) return cudaGetLastError();
+    if (tpb != 256 && tpb != 1024) tpb = ES_THREADS;
     PrefixKeys pk{};
     if (prefix) pk = *prefix;
     if (pk.n < 0 || pk.n > MAX_PREFIX_KEYS) return cudaErrorInvalidValue;
@@ -809,16 +827,16 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
             std::swap(pk.z[f], pk.z[f - 1]);
             std::swap(pk.keys[f], pk.keys[f - 1]);
         }
-    const size_t smem = embed_sign_smem(alpha, L, m, z);
+    size_t smem = embed_sign_smem(alpha, L, m, z, tpb);
+    if (smem == 0 && tpb != ES_THREADS) smem = embed_sign_smem(alpha, L, m, z, tpb = ES_THREADS);
     if (smem == 0) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((n + ES_THREADS - 1) / ES_THREADS), r);
     const bool table = embed_sign_uses_table(alpha, L) && next != nullptr;
     if (B == 2) {
-        if (table) es_launch<2, true, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
-        else es_launch<2, false, 2>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        if (table) es_launch<2, true, 2>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        else es_launch<2, false, 2>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
     } else {
-        if (table) es_launch<8, true, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
-        else es_launch<8, false, 8>(grid, smem, s, packed, pofs, lens, n, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        if (table) es_launch<8, true, 8>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
+        else es_launch<8, false, 8>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
     }
     note_launches(1);
     return cudaGetLastError();

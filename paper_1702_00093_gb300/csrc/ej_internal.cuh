@@ -146,7 +146,9 @@ size_t symbol_table_words(uint32_t r, uint32_t alpha, uint32_t L);
 cudaError_t launch_sort_samples(const uint32_t *pos, uint32_t r, uint32_t m, uint32_t z, uint32_t *spos,
                                 uint32_t *stag, cudaStream_t s);
 // Shared memory the fused kernel needs (0 if it does not fit: use embed + sign).
-size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z);
+// Shared memory of the fused walk with tpb walks per block (0 = the default 512);
+// 0 if it does not fit.
+size_t embed_sign_smem(uint32_t alpha, uint32_t L, uint32_t m, uint32_t z, int tpb = 0);
 // next[l][c][a] = next1_c(a) + 1 (16-bit) when embed_sign_uses_table(alpha, L).
 bool embed_sign_uses_table(uint32_t alpha, uint32_t L);
 size_t next_table_elems(uint32_t r, uint32_t alpha, uint32_t L);
@@ -164,7 +166,7 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
                               uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, int B,
                               const uint32_t *tsym, const uint16_t *next, const uint32_t *spos,
                               const uint32_t *stag, uint64_t *keys, cudaStream_t s,
-                              const PrefixKeys *prefix = nullptr);
+                              const PrefixKeys *prefix = nullptr, int tpb = 0);
 // Keys [r][m][n] of (r, m, z) from keys [r_src][m_src][n] of a set with the same
 // seed and L and r_src >= r, m_src >= m, z_src >= z: dst = src mod modulus
 // ((alpha+1)^z; 0 = plain copy when z = z_src).

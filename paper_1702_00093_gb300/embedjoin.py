@@ -30,7 +30,7 @@ EXPORTED = ["ej_create", "ej_destroy", "ej_status_string", "ej_last_error", "ej_
             "ej_plan", "ej_embed", "ej_sign", "ej_lsh_candidates", "ej_verify", "ej_join",
             "ej_set_test_tables", "ej_set_verify_config", "ej_embed_sign", "ej_verify_noalloc",
             "ej_set_schedule", "ej_set_loop_bound", "ej_measure_int_peak", "ej_join_plus",
-            "ej_set_key_hash", "ej_join_grouped", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
+            "ej_set_key_hash", "ej_join_grouped", "ej_set_autotune", "ej_autotune_table", "ej_batch_create", "ej_batch_run", "ej_batch_result", "ej_batch_kernel_count",
             "ej_batch_verify_ms",
             "ej_batch_destroy", "ej_index_create", "ej_index_size", "ej_index_search", "ej_index_destroy",
             "ej_server_create", "ej_server_submit", "ej_server_poll", "ej_server_release", "ej_server_get_stats",
@@ -65,6 +65,22 @@ class ServerStats(C.Structure):
 class _Schedule(C.Structure):
     _fields_ = [("mode", C.c_int32), ("slots_per_warp", C.c_int32), ("warps_per_subpartition", C.c_int32),
                 ("order", C.c_int32), ("buckets", C.c_int32), ("chain", C.c_int32)]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("length_class", C.c_int32), ("K", C.c_int32), ("walk_threads", C.c_int32),
+                ("lanes_per_pair", C.c_int32), ("words_per_lane", C.c_int32), ("configs_tried", C.c_int32),
+                ("schedule", _Schedule), ("walk_ms", C.c_float), ("back_ms", C.c_float)]
+
+    def as_dict(self) -> dict:
+        sc = self.schedule
+        return {"length_class": self.length_class, "mean_length_range": [1 << self.length_class,
+                                                                          (2 << self.length_class) - 1],
+                "K": self.K, "walk_threads_per_block": self.walk_threads,
+                "verifier": {0: "automatic", 1: "persistent", 2: "grid-strided", 3: "shared-string"}.get(sc.mode),
+                "slots_per_warp": sc.slots_per_warp, "warps_per_subpartition": sc.warps_per_subpartition,
+                "order": sc.order, "lanes_per_pair": self.lanes_per_pair, "words_per_lane": self.words_per_lane,
+                "configs_tried": self.configs_tried, "walk_ms": self.walk_ms, "back_ms": self.back_ms}
 
 
 class _Params(C.Structure):
@@ -142,6 +158,10 @@ def lib():
         L.ej_embed_sign.restype = C.c_int
         L.ej_set_verify_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ej_set_verify_config.restype = C.c_int
+        L.ej_set_autotune.argtypes = [vp, C.c_int]
+        L.ej_set_autotune.restype = C.c_int
+        L.ej_autotune_table.argtypes = [vp, vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.ej_autotune_table.restype = C.c_int
         L.ej_set_key_hash.argtypes = [vp, C.c_uint64]
         L.ej_set_key_hash.restype = C.c_int
         L.ej_join_grouped.argtypes = [vp, vp, vp, vp, C.c_int64, C.POINTER(C.c_int64), vp, vp]
@@ -421,6 +441,17 @@ class Context:
                 if e.status != EJ_ERR_CAPACITY:
                     raise
                 capacity = e.needed
+
+    def set_autotune(self, enable: int = 1):
+        """Autotuner on (1) / off (0) / off and table cleared (-1); see the header."""
+        self._check(lib().ej_set_autotune(self._h, enable), "ej_set_autotune")
+
+    def autotune_table(self) -> list:
+        n = C.c_int32(0)
+        self._check(lib().ej_autotune_table(self._h, None, 0, C.byref(n)), "ej_autotune_table")
+        arr = (TuneEntry * max(n.value, 1))()
+        self._check(lib().ej_autotune_table(self._h, arr, n.value, C.byref(n)), "ej_autotune_table")
+        return [arr[i].as_dict() for i in range(n.value)]
 
     def set_key_hash(self, P: int = 0):
         """Bucket keys by the two-level hash <u, v> mod P of Section 4 (0 = exact keys)."""

@@ -84,6 +84,8 @@ int main(void) {{
   F(ej_plan_info, embedding_bytes) F(ej_plan_info, key_count)
   F(ej_join_stats, ms_prepare) F(ej_join_stats, ms_total) F(ej_join_stats, ms_pack) F(ej_join_stats, ms_dedup)
   F(ej_schedule, warps_per_subpartition) F(ej_schedule, order) F(ej_schedule, buckets) F(ej_schedule, chain)
+  F(ej_tune_entry, schedule) F(ej_tune_entry, back_ms)
+  printf("ej_tune_entry %zu\\n", sizeof(ej_tune_entry));
   F(ej_server_config, max_batch_bytes) F(ej_server_config, hbm_reserve) F(ej_server_config, hbm_budget)
   F(ej_search_result, status) F(ej_search_result, matches) F(ej_search_result, queue_ms)
   F(ej_server_stats, deferred) F(ej_server_stats, p99_ms) F(ej_server_stats, device_bytes)
@@ -97,13 +99,14 @@ int main(void) {{
     assert int(got["ej_strings"]) == C.sizeof(ej._Strings)
     assert int(got["ej_plan_info"]) == C.sizeof(ej.PlanInfo)
     assert int(got["ej_join_stats"]) == C.sizeof(ej.JoinStats)
+    assert int(got["ej_tune_entry"]) == C.sizeof(ej.TuneEntry)
     assert int(got["ej_schedule"]) == C.sizeof(ej._Schedule)
     assert int(got["ej_server_config"]) == C.sizeof(ej.ServerConfig)
     assert int(got["ej_search_result"]) == C.sizeof(ej.SearchResult)
     assert int(got["ej_server_stats"]) == C.sizeof(ej.ServerStats)
     pairs = {"ej_params": ej._Params, "ej_plan_info": ej.PlanInfo, "ej_join_stats": ej.JoinStats,
              "ej_schedule": ej._Schedule, "ej_server_config": ej.ServerConfig,
-             "ej_search_result": ej.SearchResult, "ej_server_stats": ej.ServerStats}
+             "ej_search_result": ej.SearchResult, "ej_server_stats": ej.ServerStats, "ej_tune_entry": ej.TuneEntry}
     for key, val in got.items():
         if "." not in key:
             continue
