@@ -477,7 +477,8 @@ def verify_roofline(word_cols, ms, launches, int_peak, kernel, measured_in, traf
             "unit": "Tops/s (32-bit integer ops)", "frac": ops / peak if peak else None, "traffic": traffic,
             "launches": launches, "avg_launch_ms": ms / max(launches, 1),
             "ops_per_word_column": INT_OPS_PER_WORD_COLUMN, "word_columns": word_cols,
-            "word_columns_basis": "columns advanced x 64-bit words of each join's own band",
+            "word_columns_basis": ("columns advanced x 64-bit words of each pair's band (K_lo + K_hi + 1 <= K + 1 "
+                                   "diagonals for the persistent verifier, 2K + 1 for the others)"),
             "measured_in": measured_in,
             "peak_basis": (int_peak["basis"] if int_peak else "derived: 152 SMs x 64 lanes/clock x 2070 MHz"),
             "derived_alu_peak": derived / 1e12}

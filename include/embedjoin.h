@@ -120,9 +120,14 @@ typedef struct {
     uint64_t band_cells;     /* sum over candidates of the Ukkonen band size
                                 |{(a,b): a<|x|, b<|y|, |a-b|<=K}| (work of the
                                 verification, counted algorithmically) */
-    uint64_t verify_word_columns; /* 64-bit band words times columns the verifier
-                                actually advanced (ceil((2K+1)/64) words per
-                                column, early exit included) */
+    uint64_t verify_word_columns; /* 64-bit words of the band the verifier runs
+                                times the columns it actually advanced (early
+                                exit included): the persistent verifier runs the
+                                diagonals a cost-K alignment can use given the
+                                pair's length difference d, K_lo + K_hi + 1 <= K + 1
+                                (K_lo = floor((K-d)/2), K_hi = floor((K+d)/2)),
+                                ceil((K_lo + K_hi + 1)/64) words; the others run
+                                Ukkonen's 2K+1 diagonals, ceil((2K+1)/64) words */
     int64_t kernel_launches; /* CUDA kernels this call launched */
     /* finer stage times (ms, only with ej_set_timing(ctx, 1)): the part of
        ms_prepare spent validating and packing the strings, and ms_candidates
@@ -286,9 +291,9 @@ void ej_server_destroy(ej_server *server);
  * set's walks (the key of fewer samples is the wider key modulo
  * (|alphabet|+1)^z). Sets with the same seed, L, r and m take their raw pairs
  * from the buckets of the one with the smallest z (ej_schedule.buckets). The
- * sets on the persistent verifier are verified by one merged launch, each pair
- * with its own set's K (ej_schedule.chain). Every set still gets exactly
- * ej_join's candidates and output.
+ * sets on the persistent verifier are verified by one merged launch, a pair
+ * that several sets list once, at the largest of their K (ej_schedule.chain).
+ * Every set still gets exactly ej_join's candidates and output.
  * ej_batch_run replays the graph on `stream` without any host synchronisation;
  * the run itself sorts every join's output (up to 8192 pairs) and stages the
  * counters in pinned host memory. ej_batch_result(i) waits for the run and
@@ -347,8 +352,11 @@ void ej_batch_destroy(ej_batch *batch);
  *     chained unless chain is 1 (the other stages always overlap); see the
  *     field.
  *   slots_per_warp: 0 = 16, else 1..16 pair slots per warp.
- *   warps_per_subpartition: 0 = 1, else 1..16: at most that many working warps
- *     per SM sub-partition (4 per SM); slots beyond the batch refill from the queue.
+ *   warps_per_subpartition: 1..16: at most that many working warps per SM
+ *     sub-partition (4 per SM); slots beyond the batch refill from the queue.
+ *     0 (default): from the pair count, 1 while one warp's slots would take
+ *     fewer than 8 pairs each (more warps only start every pair at once, and a
+ *     launch ends with its slowest pairs), 2 below 32, else 4.
  *   order: the order in which candidates enter the verifier. 4: by length
  *     class, longest first (the shorter string's length in 256 classes), so
  *     that the pairs a warp takes have similar lengths and the longest start
@@ -386,15 +394,20 @@ typedef struct {
     int32_t buckets;
     int32_t chain;   /* batches: joins on the grid-strided verifier are verified one after
                         another unless chain is 1. Joins that use the persistent verifier:
-                        3: one merged launch
-                        verifies them all, at the widest of their bands, each pair with its
-                        own join's K, largest K first (the queue runs from one join's pairs
-                        into the next, so no join waits for another's last pairs); 2: one
-                        launch per join, one after another; 1: one launch per join, free to
-                        overlap (two persistent grids sharing the SMs were measured up to
-                        10x slower at times); 0 (default): 3 when the wider band adds at
-                        most half the word-columns of the joins' own bands (candidate counts
-                        of the sizing pass), else 2 */
+                        4: one merged launch over the union of their candidates: every
+                        distinct pair once, at the largest K of the joins that list it, in
+                        the widest of their bands; its distance (exact up to that K) decides
+                        it for each of them (joins whose signatures nest, e.g. the prefix
+                        keys of a batch, share most candidates); pairs listed by more joins
+                        enter the queue first; 3: one merged launch over the joins'
+                        candidates in turn, largest K first, each pair with its own join's
+                        K (the queue runs from one join's pairs into the next, so no join
+                        waits for another's last pairs); 2: one launch per join, one after
+                        another; 1: one launch per join, free to overlap (two persistent
+                        grids sharing the SMs were measured up to 10x slower at times);
+                        0 (default): 4 when the wider band adds at most half the
+                        word-columns of the joins' own bands (candidate counts of the
+                        sizing pass), else 2 */
 } ej_schedule;
 
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside

@@ -73,7 +73,7 @@ struct ej_ctx {
     ej_ctx *plus_sub = nullptr;     // ej_join_plus: the context of the suffix set
     ej_ctx *group_sub = nullptr;    // ej_join_grouped: the context of one length group
     uint64_t key_P = 0;             // ej_set_key_hash: 0 = exact keys, else <u, v> mod key_P
-    int walk_tpb = 0;               // walks (strings) per block of the fused walk (0 = 512)
+    int walk_tpb = 0;               // walks (strings) per block of the fused walk (0: 1024 for at most 4 symbols, else 512)
     bool autotune = false;          // ej_set_autotune: joins consult / fill tune_table
     std::map<uint64_t, ej_tune_entry> tune_table;   // (length class << 32 | K) -> choice
     // cached alphabet
@@ -719,7 +719,7 @@ uint64_t raw_cap_start(ej_ctx *ctx, int64_t n) {
 int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const VerifyConfig &vc) {
     const bool long_pairs = pl.st.n > 0 && pl.st.total / pl.st.n >= 2048;
     const bool want_pq = ctx->sched.mode == 1 || (ctx->sched.mode == 0 && long_pairs);
-    return (vc.G == 2 && want_pq) ? pq_threads_for(vc.V, p->alphabet_size) : 0;
+    return (vc.G == 2 && want_pq) ? pq_threads_for(pq_words(p->K), p->alphabet_size) : 0;
 }
 
 // The shared-string verifier (mode 3; mode 0 for short strings over more than
@@ -834,10 +834,10 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     } else {
     if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
     if (pq_threads > 0)
-        // defaults: 16 slots per warp, one working warp per SM sub-partition (the
-        // slots refill from the queue); measured best on the long-DNA shapes
-        CK(launch_verify_pq(vc.V, pq_threads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
-                            ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1,
+        // defaults: 16 slots per warp (they refill from the queue); working warps
+        // per SM sub-partition from the pair count (the kernel's automatic rule)
+        CK(launch_verify_pq(pq_words(p->K), pq_threads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
+                            ctx->sched.warps_per_subpartition,
                             pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, (int64_t)cap, p->K, vo,
                             s));
     else
@@ -949,7 +949,8 @@ struct TuneCand {
 std::vector<TuneCand> tune_candidates(const ej_params *p) {
     const int W = (2 * p->K + 1 + 63) / 64;
     std::vector<TuneCand> c = {
-        {{1, 16, 1, 0, 0, 0}, 0, 0}, {{1, 16, 2, 0, 0, 0}, 0, 0}, {{1, 8, 1, 0, 0, 0}, 0, 0},
+        {{1, 16, 1, 0, 0, 0}, 0, 0}, {{1, 16, 2, 0, 0, 0}, 0, 0}, {{1, 16, 4, 0, 0, 0}, 0, 0},
+        {{1, 8, 1, 0, 0, 0}, 0, 0},
         {{3, 0, 0, 0, 0, 0}, 0, 0},  {{2, 0, 0, 3, 0, 0}, 0, 0},  {{2, 0, 0, 4, 0, 0}, 0, 0},
     };
     if (W <= 8) c.push_back({{2, 0, 0, 3, 0, 0}, 1, W});
@@ -1141,6 +1142,12 @@ struct ej_batch {
     VerifySeg *segs_dev = nullptr;
     unsigned long long *mqueue = nullptr;
     unsigned int *mtickets = nullptr;
+    // ... over the union of their candidates (chain 4): each distinct pair once
+    bool munion = false;
+    uint64_t ucap = 0, uhsize = 0;
+    uint64_t *utable = nullptr, *upairs = nullptr;
+    uint32_t *utmask = nullptr, *umask = nullptr;
+    unsigned long long *ubins = nullptr;      // count_bins() + 1: the bins, then the pair count
     cudaEvent_t v0 = nullptr, v1 = nullptr;   // around the merged launch
     bool eager = false;                       // no graph: every run issues the work
     // results staged by the run itself: per join 8 counters + the error word, and
@@ -1164,6 +1171,11 @@ void batch_free(ej_batch *b) {
     if (b->segs_dev) cudaFree(b->segs_dev);
     if (b->mqueue) cudaFree(b->mqueue);
     if (b->mtickets) cudaFree(b->mtickets);
+    if (b->utable) cudaFree(b->utable);
+    if (b->upairs) cudaFree(b->upairs);
+    if (b->utmask) cudaFree(b->utmask);
+    if (b->umask) cudaFree(b->umask);
+    if (b->ubins) cudaFree(b->ubins);
     for (auto &j : b->joins) {
         if (j.done) cudaEventDestroy(j.done);
         if (j.verified) cudaEventDestroy(j.verified);
@@ -1233,13 +1245,17 @@ void batch_sources(std::vector<BatchJoin> &joins) {
     }
 }
 
-// Merged verification (ej_schedule.chain 0 or 3): the joins that use the
+// Merged verification (ej_schedule.chain 0, 3 or 4): the joins that use the
 // persistent verifier are verified by one launch at the widest of their bands,
-// each pair with its own join's K, largest K first. The work queue then runs
-// from one join's candidates into the next, so no launch waits for another
-// launch's last pairs. Mode 0 merges when the wider band adds at most half of
-// the word-columns the joins' own bands would run (estimated from the eager
-// pass's candidate counts); otherwise, as mode 2, the launches are chained.
+// each pair with its own join's K. Mode 3: the work queue runs over the joins'
+// candidates in turn, largest K first, so no launch waits for another launch's
+// last pairs. Mode 4: it runs over the union of their candidates, each distinct
+// pair once at the largest K of the joins that list it (its distance, exact up
+// to that K, decides it for every one of them): joins over the same strings
+// whose signatures nest share most of their candidates. Mode 0 merges (as 4)
+// when the wider band adds at most half of the word-columns the joins' own
+// bands would run (estimated from the eager pass's candidate counts);
+// otherwise, as mode 2, the launches are chained.
 int batch_plan_merge(ej_batch *b) {
     ej_ctx *ctx = b->ctx;
     const int mode = ctx->sched.chain;
@@ -1256,17 +1272,17 @@ int batch_plan_merge(ej_batch *b) {
     double own = 0.0, wide = 0.0;
     for (int i : pq) {
         const BatchJoin &j = b->joins[(size_t)i];
-        W1 = std::max(W1, j.bs.vc.V);
+        W1 = std::max(W1, pq_words(j.p.K));
         K = std::max(K, (int)j.p.K);
     }
     for (int i : pq) {
         const BatchJoin &j = b->joins[(size_t)i];
-        own += (double)j.ncand * j.bs.vc.V;
+        own += (double)j.ncand * pq_words(j.p.K);
         wide += (double)j.ncand * W1;
     }
     if (mode == 0 && wide > 1.5 * own) return EJ_OK;
     const int threads = pq_threads_for(W1, b->joins[0].p.alphabet_size);
-    if (threads == 0 || W1 < (2 * K + 1 + 63) / 64 + 1) return EJ_OK;
+    if (threads == 0 || W1 < pq_words(K)) return EJ_OK;
     CK(cudaMalloc(&b->segs_dev, pq.size() * sizeof(VerifySeg)));
     CK(cudaMalloc(&b->mqueue, sizeof(unsigned long long)));
     CK(cudaMalloc(&b->mtickets, SM_TICKETS * sizeof(unsigned int)));
@@ -1274,6 +1290,17 @@ int batch_plan_merge(ej_batch *b) {
     b->mW1 = W1;
     b->mK = K;
     b->mthreads = threads;
+    if (mode == 0 || mode == 4) {
+        b->munion = true;
+        for (int i : pq) b->ucap += b->joins[(size_t)i].cap;
+        b->uhsize = 1;
+        while (b->uhsize < 2 * b->ucap) b->uhsize <<= 1;
+        CK(cudaMalloc(&b->utable, b->uhsize * sizeof(uint64_t)));
+        CK(cudaMalloc(&b->utmask, b->uhsize * sizeof(uint32_t)));
+        CK(cudaMalloc(&b->upairs, b->ucap * sizeof(uint64_t)));
+        CK(cudaMalloc(&b->umask, b->ucap * sizeof(uint32_t)));
+        CK(cudaMalloc(&b->ubins, ((size_t)count_bins() + 1) * sizeof(unsigned long long)));
+    }
     for (size_t k = 0; k < pq.size(); k++) b->joins[(size_t)pq[k]].seg = (int)k;
     return EJ_OK;
 }
@@ -1292,8 +1319,18 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
     vo.nseg = (int32_t)b->merged.size();
     vo.max_passes = ctx->loop_bound;
     const Plan &pl = b->pl;
+    if (b->munion) {
+        unsigned long long *ucount = b->ubins + count_bins();
+        CK(launch_union_candidates(b->segs_dev, vo.nseg, b->utable, b->utmask, b->uhsize, b->ubins, b->upairs,
+                                   b->umask, ucount, pl.lens, pl.max_len, s));
+        vo.upairs = b->upairs;
+        vo.umask = b->umask;
+        vo.unp_dev = ucount;
+        vo.ucap = b->ucap;
+        total_cap = b->ucap;
+    }
     CK(launch_verify_pq(b->mW1, b->mthreads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
-                        ctx->sched.warps_per_subpartition ? ctx->sched.warps_per_subpartition : 1, pl.packed, pl.pofs,
+                        ctx->sched.warps_per_subpartition, pl.packed, pl.pofs,
                         pl.B, pl.lens, pl.st.n, b->joins[0].p.alphabet_size, nullptr, (int64_t)total_cap, b->mK, vo, s));
     return EJ_OK;
 }
@@ -1636,7 +1673,7 @@ int ej_set_schedule(ej_ctx *ctx, const ej_schedule *sc) {
     }
     if (sc->mode < 0 || sc->mode > 3 || sc->slots_per_warp < 0 || sc->slots_per_warp > 16 ||
         sc->warps_per_subpartition < 0 || sc->warps_per_subpartition > 16 || sc->order < 0 || sc->order > 5 ||
-        sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 3)
+        sc->buckets < 0 || sc->buckets > 2 || sc->chain < 0 || sc->chain > 4)
         return fail(ctx, EJ_ERR_INVALID_ARG,
                     "schedule mode=%d slots_per_warp=%d warps_per_subpartition=%d order=%d buckets=%d not supported",
                     sc->mode, sc->slots_per_warp, sc->warps_per_subpartition, sc->order, sc->buckets);

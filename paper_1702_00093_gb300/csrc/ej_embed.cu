@@ -785,6 +785,157 @@ embed_sign_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__
     }
 }
 
+// Walk + signatures for alphabets of at most four symbols (2-bit codes), with
+// the next-step table extended by sample counts. Entry (a, c) of the block's
+// table is e = a' << 16 | 2 cnt(a'), where a' = next1_c(a) + 1 is the arrival
+// step of the character after a c that arrived at step a (L + 1 past the
+// sampling range) and cnt(x) is the number of sampled steps below x. The c read
+// at step a covers the samples cnt(a) .. cnt(a') - 1 (in step order), so with e
+// the entry of the current arrival, one character is: the next entry
+// e' = T[a'][c] (its row offset is e >> 12, the low half being below 4096), and
+// 2 (cnt(a') - cnt(a)) = e' - e in its low five bits: that many bits of copies
+// of c enter a 64-bit shift register from below (two funnel shifts). After 16
+// characters the block's count e_end - e_start decides: below 16 samples the
+// register holds every code of the block and at most one 32-bit record word has
+// filled, which is written; otherwise (or in a partial last block) the block is
+// walked again one character and one sample at a time. The record holds the
+// code of sample k (step order) at bits 30 - 2(k mod 16) of word k / 16.
+constexpr int ESD_MAX_M = 2047;   // 2 M < 4096: the count fits the entry's low 12 bits
+
+__host__ __device__ __forceinline__ size_t esd_words(uint32_t M) { return (M + 15) / 16 + 1; }
+
+size_t embed_sign_dna_smem(uint32_t L, uint32_t m, uint32_t z, int tpb) {
+    const size_t M = (size_t)m * z;
+    if (M == 0 || M > ESD_MAX_M || L + 1 >= 65536u) return 0;
+    const size_t bytes = (size_t)next_row(L) * 16 + esd_words((uint32_t)M) * 4 * (size_t)tpb + (size_t)z * 8 + M * 8;
+    return bytes <= 220 * 1024 ? bytes : 0;
+}
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1)
+embed_sign_dna_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
+                      const int32_t *__restrict__ lens, int64_t n, uint32_t m, uint32_t z, uint32_t L,
+                      uint32_t alpha, const uint16_t *__restrict__ next, const uint32_t *__restrict__ spos,
+                      const uint32_t *__restrict__ stag, uint64_t *__restrict__ keys, PrefixKeys pk) {
+    extern __shared__ uint64_t esd_smem[];
+    const uint32_t l = blockIdx.y, M = m * z, NR = next_row(L);
+    // the table first, at a fixed shared-memory address (its loads take the base
+    // as an immediate), then the record, powers, sample steps and ranks
+    uint32_t *s_tab = (uint32_t *)esd_smem;                        // [NR][4]
+    uint32_t *s_rec = s_tab + (size_t)NR * 4;                      // [esd_words(M)][TPB]
+    uint64_t *s_pow = (uint64_t *)(s_rec + esd_words(M) * TPB);    // [z] (8-byte aligned: NR*4 + words*TPB is even)
+    uint32_t *s_pos = (uint32_t *)(s_pow + z);                     // [M] sample steps, ascending
+    uint32_t *s_rank = s_pos + M;                                  // [M] step-order index of sample f*z+q
+    for (uint32_t i = threadIdx.x; i < M; i += TPB) {
+        s_pos[i] = spos[(size_t)l * M + i];
+        const uint32_t tag = stag[(size_t)l * M + i];
+        s_rank[(tag >> 16) * z + (tag & 0xFFFFu)] = i;
+    }
+    if (threadIdx.x == 0) {
+        uint64_t pw = 1;
+        for (uint32_t q = 0; q < z; q++) {
+            s_pow[q] = pw;
+            pw *= (uint64_t)alpha + 1;
+        }
+    }
+    __syncthreads();
+    const uint16_t *nx = next + (size_t)l * next_stride(alpha, L);
+    for (uint32_t idx = threadIdx.x; idx < NR * 4; idx += TPB) {
+        const uint32_t a = idx >> 2, c = idx & 3u;
+        const uint32_t an = c < alpha ? (uint32_t)nx[c * NR + a] : L + 1;   // codes >= alpha never occur
+        uint32_t lo = 0, hi = M;                                            // cnt(an): samples below an
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pos[mid] < an) lo = mid + 1;
+            else hi = mid;
+        }
+        s_tab[idx] = (an << 16) | (2u * lo);
+    }
+    __syncthreads();
+
+    const int64_t s = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const int32_t len = s < n ? lens[s] : 0;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(packed + (s < n ? pofs[s] : 0));
+    const char *tab = reinterpret_cast<const char *>(s_tab);
+    uint32_t *rec = s_rec + threadIdx.x;
+    const uint32_t KB = 2u * M;   // record bits when every sample is taken
+    uint32_t e = 0, hi = 0, lo = 0, kb = 0;
+    // exact walk of one character and its samples, one sample at a time
+    auto slow_char = [&](uint32_t c) {
+        const uint32_t en = *reinterpret_cast<const uint32_t *>(tab + (e >> 12) + 4u * c);
+        for (uint32_t d = (en - e) & 0xFFFFu; d > 0; d -= 2) {
+            hi = (hi << 2) | (lo >> 30);
+            lo = (lo << 2) | c;
+            kb += 2;
+            if ((kb & 31u) == 0) rec[(size_t)((kb >> 5) - 1) * TPB] = lo;
+        }
+        e = en;
+    };
+    const int32_t nfull = len >> 4, nw = (len + 15) >> 4;   // full blocks; words holding codes
+    uint32_t w = nw > 0 ? src[0] : 0u;
+    int32_t b = 0;
+    for (; b < nfull && kb < KB; b++) {
+        const uint32_t wn = b + 1 < nw ? src[b + 1] : 0u;   // the next block's codes, a block ahead
+        const uint32_t e0 = e, hi0 = hi, lo0 = lo;
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+            const uint32_t c4 = (t == 0 ? (w << 2) : (w >> (2 * t - 2))) & 0xCu;   // 4 x code
+            const uint32_t en = *reinterpret_cast<const uint32_t *>(tab + (e >> 12) + c4);
+            const uint32_t d = en - e;                      // 2 x samples of this character (low bits)
+            const uint32_t rep = c4 * 0x15555555u;          // the code in every 2-bit field but the lowest
+            hi = __funnelshift_l(lo, hi, d);                // (hi:lo) << d, the top d bits of rep below
+            lo = __funnelshift_l(rep, lo, d);
+            e = en;
+        }
+        const uint32_t dk = (e - e0) & 0xFFFFu;
+        if (dk < 32) {
+            const uint32_t kn = kb + dk;
+            if ((kn >> 5) != (kb >> 5))   // record word kn/32 - 1 has filled: its last code kn - ((kn>>5)<<5) bits up
+                rec[(size_t)((kn >> 5) - 1) * TPB] = __funnelshift_r(lo, hi, kn & 31u);
+            kb = kn;
+        } else {
+            // 16 or more samples in the block: again, exactly
+            e = e0;
+            hi = hi0;
+            lo = lo0;
+#pragma unroll 1
+            for (int t = 0; t < 16; t++) slow_char((w >> (2 * t)) & 3u);
+        }
+        w = wn;
+    }
+    if (b == nfull && kb < KB) {   // the partial last block
+        for (int32_t t = 0; t < (len & 15); t++) slow_char((w >> (2 * t)) & 3u);
+    }
+    const uint32_t k_end = kb >> 1;   // samples from k_end on lie after the walk: bottom
+    if (kb & 31u) rec[(size_t)(kb >> 5) * TPB] = lo << (32u - (kb & 31u));
+    if (s < n) {
+        for (uint32_t f = 0; f < m; f++) {
+            uint64_t key = 0;
+            uint32_t q = 0;
+            for (int ei = 0; ei <= pk.n; ei++) {   // the prefix keys (ascending z) on the way
+                const uint32_t qe = ei < pk.n ? pk.z[ei] : z;
+                for (; q < qe; q++) {
+                    const uint32_t rk = s_rank[f * z + q];
+                    const uint32_t c = (rk < k_end) ? ((rec[(size_t)(rk >> 4) * TPB] >> (30u - 2u * (rk & 15u))) & 3u) : alpha;
+                    key += (uint64_t)c * s_pow[q];
+                }
+                if (ei < pk.n) pk.keys[ei][((size_t)l * m + f) * n + s] = key;
+            }
+            keys[((size_t)l * m + f) * n + s] = key;
+        }
+    }
+}
+
+template <int TPB>
+static void esd_launch_t(size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs, const int32_t *lens,
+                         int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha,
+                         const uint16_t *next, const uint32_t *spos, const uint32_t *stag, uint64_t *keys,
+                         const PrefixKeys &pk) {
+    cudaFuncSetAttribute(embed_sign_dna_kernel<TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((n + TPB - 1) / TPB), r);
+    embed_sign_dna_kernel<TPB><<<grid, TPB, smem, s>>>(packed, pofs, lens, n, m, z, L, alpha, next, spos, stag, keys, pk);
+}
+
 template <int B, bool TABLE, int CB, int TPB>
 static void es_launch_t(size_t smem, cudaStream_t s, const uint4 *packed, const uint64_t *pofs, const int32_t *lens,
                         int64_t n, uint32_t r, uint32_t m, uint32_t z, uint32_t L, uint32_t alpha, const uint32_t *tsym,
@@ -816,6 +967,7 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
                               const uint32_t *stag, uint64_t *keys, cudaStream_t s, const PrefixKeys *prefix,
                               int tpb) {
     if (n == 0) return cudaGetLastError();
+    const int tpb_req = tpb;
     if (tpb != 256 && tpb != 1024) tpb = ES_THREADS;
     PrefixKeys pk{};
     if (prefix) pk = *prefix;
@@ -827,10 +979,22 @@ cudaError_t launch_embed_sign(const uint4 *packed, const uint64_t *pofs, const i
             std::swap(pk.z[f], pk.z[f - 1]);
             std::swap(pk.keys[f], pk.keys[f - 1]);
         }
+    const bool table = embed_sign_uses_table(alpha, L) && next != nullptr;
+    if (B == 2 && table) {
+        // four symbols or fewer: the walk with sample counts in the table, 1024
+        // walks per block (one block per SM holds the table), else 512
+        const int t2 = tpb_req == 512 ? 512 : 1024;
+        const size_t sm2 = embed_sign_dna_smem(L, m, z, t2);
+        if (sm2 > 0) {
+            if (t2 == 512) esd_launch_t<512>(sm2, s, packed, pofs, lens, n, r, m, z, L, alpha, next, spos, stag, keys, pk);
+            else esd_launch_t<1024>(sm2, s, packed, pofs, lens, n, r, m, z, L, alpha, next, spos, stag, keys, pk);
+            note_launches(1);
+            return cudaGetLastError();
+        }
+    }
     size_t smem = embed_sign_smem(alpha, L, m, z, tpb);
     if (smem == 0 && tpb != ES_THREADS) smem = embed_sign_smem(alpha, L, m, z, tpb = ES_THREADS);
     if (smem == 0) return cudaErrorInvalidValue;
-    const bool table = embed_sign_uses_table(alpha, L) && next != nullptr;
     if (B == 2) {
         if (table) es_launch<2, true, 2>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);
         else es_launch<2, false, 2>(tpb, smem, s, packed, pofs, lens, n, r, m, z, L, alpha, tsym, next, spos, stag, keys, pk);

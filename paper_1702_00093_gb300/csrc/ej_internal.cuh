@@ -276,6 +276,16 @@ cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uin
 // max_len to 256 classes). hcount (hsize uint32) and bins (count_bins() uint64)
 // start at zero.
 int count_bins();
+struct VerifySeg;
+// Union of the candidate lists of a merged launch's joins (segs[0 .. nseg)):
+// every distinct pair once in upairs, with the mask of the joins that list it
+// in umask, ordered by the number of joins (more first), then by the length
+// class of the shorter string (longer first). table/tmask: hsize slots (a power
+// of two >= 2 x the pairs, cleared here); bins: count_bins() entries;
+// *ucount = the number of distinct pairs (device).
+cudaError_t launch_union_candidates(const VerifySeg *segs, int nseg, uint64_t *table, uint32_t *tmask, uint64_t hsize,
+                                    unsigned long long *bins, uint64_t *upairs, uint32_t *umask,
+                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len, cudaStream_t s);
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
                                  const int32_t *lens, int64_t max_len, cudaStream_t s);
@@ -383,6 +393,15 @@ struct VerifyOut {
     // Persistent verifier: loop passes per warp before it gives up and sets
     // DERR_TIMEOUT (0 = the default bound, 2^24).
     int64_t max_passes;
+    // Merged launch over the union of the joins' candidates: when umask is set
+    // (with segs), the queue runs over upairs[0 .. min(*unp_dev, ucap)), pair q
+    // listed by the joins whose bits are set in umask[q]; it is verified once at
+    // the largest of their K and written to each of them whose K its distance
+    // meets (band cells counted per join, word columns to the largest K's join).
+    const uint64_t *upairs;
+    const uint32_t *umask;
+    const unsigned long long *unp_dev;
+    uint64_t ucap;
 };
 
 constexpr int SM_TICKETS = 1024;
@@ -406,6 +425,13 @@ cudaError_t launch_verify(VerifyConfig c, const uint4 *packed, const uint64_t *p
 // Persistent verifier (two lanes per pair, W1 = 2..12 words per lane, pairs
 // pulled from vo.queue). spw_force > 0 fixes the pair slots per warp (1..16);
 // wps > 0 caps the working warps at wps per SM sub-partition (slots refill).
+// Words per lane the persistent verifier needs for threshold K: its band has at
+// most K + 1 diagonals (the length difference narrows Ukkonen's 2K + 1), so
+// 1 + ceil(K / 64), at least 2.
+inline int pq_words(int32_t K) {
+    const int w = 1 + (K + 63) / 64;
+    return w < 2 ? 2 : w;
+}
 size_t pq_smem_bytes(int W1, uint32_t alpha, int threads);
 int pq_threads_for(int W1, uint32_t alpha);   // 0 if no block size fits
 cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,

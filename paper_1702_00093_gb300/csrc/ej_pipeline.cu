@@ -696,6 +696,104 @@ cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *t
 
 int count_bins() { return COUNT_BINS; }
 
+// ---------------------------------------------------------------------------
+// Union of the candidate lists of a merged verifier launch
+// ---------------------------------------------------------------------------
+
+// Every candidate of every join into one pair set; tmask[slot] collects the
+// bits of the joins that list the pair.
+__global__ void union_insert_kernel(const VerifySeg *__restrict__ segs, int nseg, uint64_t *__restrict__ table,
+                                    uint32_t *__restrict__ tmask, uint64_t hsize) {
+    const uint64_t EMPTY = ~0ull;
+    for (int g = 0; g < nseg; g++) {
+        const unsigned long long c = *segs[g].np_dev;
+        const int64_t cnt = (int64_t)(c < segs[g].cap ? c : segs[g].cap);
+        const uint64_t *pairs = segs[g].pairs;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+            const uint64_t key = pairs[i];
+            uint64_t h = pair_hash(key) & (hsize - 1);
+            for (uint64_t probe = 0; probe < hsize; probe++) {
+                const unsigned long long old = atomicCAS((unsigned long long *)&table[h], EMPTY, key);
+                if (old == EMPTY || old == key) {
+                    atomicOr(&tmask[h], 1u << g);
+                    break;
+                }
+                h = (h + 1) & (hsize - 1);
+            }
+        }
+    }
+}
+
+// Queue bin of a union pair: 32 bins per number of listing joins (more joins
+// first: a pair that passed the stricter signatures of several joins is the
+// more likely to be similar, and a similar pair runs its full length), then the
+// shorter string's length class (longer first).
+__device__ __forceinline__ uint32_t union_bin(uint64_t key, uint32_t mask, const int32_t *__restrict__ lens,
+                                              uint32_t len_scale) {
+    const int32_t a = lens[key >> 32], b = lens[key & 0xFFFFFFFFull];
+    const uint32_t sh = (uint32_t)(a < b ? a : b);
+    const uint64_t c = ((uint64_t)sh * 32) / ((uint64_t)len_scale + 1);
+    const uint32_t cls = c < 32 ? (uint32_t)c : 31u;
+    const uint32_t j = (uint32_t)__popc(mask);
+    return ((j > 8 ? 8u : j) - 1u) * 32u + cls;   // mask != 0 for an occupied slot
+}
+
+__global__ void union_hist_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ tmask,
+                                  uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
+                                  unsigned long long *__restrict__ bins, unsigned long long *__restrict__ ucount) {
+    __shared__ unsigned int sb[COUNT_BINS];
+    for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x) sb[t] = 0;
+    __syncthreads();
+    unsigned int mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) {
+            atomicAdd(&sb[union_bin(key, tmask[i], lens, len_scale)], 1u);
+            mine++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(ucount, (unsigned long long)mine);
+    __syncthreads();
+    for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x)
+        if (sb[t]) atomicAdd(&bins[t], (unsigned long long)sb[t]);
+}
+
+__global__ void union_scatter_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ tmask,
+                                     uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
+                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ upairs,
+                                     uint32_t *__restrict__ umask) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = table[i];
+        if (key != ~0ull) {
+            const uint32_t mk = tmask[i];
+            const unsigned long long at = atomicAdd(&cursor[union_bin(key, mk, lens, len_scale)], 1ull);
+            upairs[at] = key;
+            umask[at] = mk;
+        }
+    }
+}
+
+cudaError_t launch_union_candidates(const VerifySeg *segs, int nseg, uint64_t *table, uint32_t *tmask, uint64_t hsize,
+                                    unsigned long long *bins, uint64_t *upairs, uint32_t *umask,
+                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len, cudaStream_t s) {
+    if (nseg < 1 || nseg > MAX_VERIFY_SEGS || (hsize & (hsize - 1)) != 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tmask, 0, hsize * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bins, 0, COUNT_BINS * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ucount, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    const int64_t gh = ((int64_t)hsize + 255) / 256;
+    const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
+    const uint32_t scale = (uint32_t)(max_len > 0x7fffffff ? 0x7fffffff : max_len);
+    union_insert_kernel<<<gs, 256, 0, s>>>(segs, nseg, table, tmask, hsize);
+    union_hist_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, bins, ucount);
+    count_scan_kernel<<<1, COUNT_BINS, 0, s>>>(bins);
+    union_scatter_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, bins, upairs, umask);
+    note_launches(4);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
                                  const int32_t *lens, int64_t max_len, cudaStream_t s) {

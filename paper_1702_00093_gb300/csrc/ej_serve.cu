@@ -309,7 +309,7 @@ cudaError_t slot_launch(Slot &sl, const ej_index &x, const std::vector<Query> &q
         vo.n_b = x.set.n;
         vo.thr = qK;
         vo.pairs_off_dev = bins + nc + c;
-        const int W1 = cls_w1[c];
+        const int W1 = pq_words(kband[c]);   // the persistent verifier's narrower band
         const int threads = W1 <= 12 ? pq_threads_for(W1, alpha) : 0;
         if (threads > 0) {
             SV(launch_verify_pq(W1, threads, 16, 1, P<uint4>(sl.qpacked), P<uint64_t>(sl.qpofs), x.set.B,

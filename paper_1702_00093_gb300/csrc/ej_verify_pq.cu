@@ -9,20 +9,30 @@
 // ED(x, y) = min_i D(i, n1) + ED(x[i:], y[n1:]) joins them (the argument and the
 // boundary conditions are the ones of the block-aligned two-lane verifier).
 //
-// Scheduling. A warp advances its 16 pair slots in chunks of 64 columns and a
-// slot starts a new pair only at a chunk boundary, so that column j of every
-// pair falls on chunk position (j - 1) mod 64: the window moves, which happen at
-// columns j = K + 1 + 64t, all fall on the same chunk position K mod 64 and run
-// once per chunk for the whole warp. A finished slot waits at most one chunk.
-// The number of working warps is capped (by default one per SM sub-partition),
-// so that a batch larger than the slots keeps every slot busy until the queue
-// runs dry.
+// Band. With x the longer string (m rows), y the shorter (n columns) and
+// d = m - n, a path of cost c through cell (i, j) has c >= |i - j| + |d - (i - j)|
+// (the distances to the diagonals of both corners), so a path of cost <= K
+// stays on the diagonals i - j in [-K_lo, K_hi], K_lo = floor((K - d) / 2),
+// K_hi = floor((K + d) / 2): at most K + 1 diagonals, where Ukkonen's band has
+// 2K + 1 (the same argument as his cutoff). Both halves use it (reversing both
+// strings keeps d). The window of W1 words covers it when W1 >= 1 + K/64
+// rounded up, moving down one word before the columns K_lo + 1 + 64t, t >= 1.
+//
+// Scheduling. A warp advances its 16 pair slots in chunks of 64 columns. A slot
+// starts a new pair at a chunk boundary, its column 1 at chunk position s0 =
+// (smove - K_lo) mod 64 (the positions before it idle), so that every window
+// move of every pair falls on the same chunk position smove and runs once per
+// chunk for the whole warp. A finished slot waits at most one chunk. The number
+// of working warps is capped (by default one per SM sub-partition), so that a
+// batch larger than the slots keeps every slot busy until the queue runs dry.
 //
 // Early exit. Once per chunk, at the chunk position of the window moves, each
 // half that is still running computes the minimum value m_h of its window
 // (including the row above it). A path of cost <= K crosses both halves'
 // current columns inside their bands, where the values are exact, so
 // m_fwd + m_bwd > K proves ED > K; both lanes of the pair stop.
+#include <climits>
+
 #include "ej_bitpar.cuh"
 
 namespace ej {
@@ -31,17 +41,28 @@ namespace {
 
 constexpr int64_t kMaxIters = 1ll << 24;   // default bound on loop passes per warp (VerifyOut::max_passes)
 
-// 64/B symbols of a packed string starting at symbol o (any int64; symbols
-// outside [0, len) read as code 0), symbol t in bits [B*t, B*t + B).
+// The two words under 64/B symbols of a packed string starting at symbol o
+// (any int64; words outside the string read as 0) and the bit offset of symbol
+// o in the first: loads only, combined by sym_join when the symbols are needed
+// (so that the load's latency passes while the previous word is consumed).
+struct SymRaw {
+    uint64_t a, b;
+    uint32_t sh;
+};
 template <int B>
-__device__ __forceinline__ uint64_t sym_u64(const uint64_t *__restrict__ y64, int64_t nwords, int64_t o) {
+__device__ __forceinline__ SymRaw sym_fetch(const uint64_t *__restrict__ y64, int64_t nwords, int64_t o) {
     const int64_t bit = o * B;
     const int64_t w0 = bit >= 0 ? (bit >> 6) : -((-bit + 63) >> 6);
-    const uint32_t sh = (uint32_t)(bit - 64 * w0);
-    const uint64_t a = (w0 >= 0 && w0 < nwords) ? y64[w0] : 0ull;
-    const uint64_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? y64[w0 + 1] : 0ull;
-    return sh ? ((a >> sh) | (b << (64u - sh))) : a;
+    SymRaw r;
+    r.sh = (uint32_t)(bit - 64 * w0);
+    r.a = (w0 >= 0 && w0 < nwords) ? y64[w0] : 0ull;
+    r.b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? y64[w0 + 1] : 0ull;
+    return r;
 }
+__device__ __forceinline__ uint64_t sym_join(const SymRaw &r) {
+    return r.sh ? ((r.a >> r.sh) | (r.b << (64u - r.sh))) : r.a;
+}
+
 
 __device__ __forceinline__ unsigned sm_id() {
     unsigned r;
@@ -69,6 +90,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     uint32_t *__restrict__ err = vo.err;
     const VerifySeg *__restrict__ segs = vo.segs;   // merged launch: the joins' candidates in turn
     const int nseg = segs ? vo.nseg : 0;
+    const bool uni = segs && vo.umask;              // ... or their union, each pair once
     __shared__ long long s_cum[MAX_VERIFY_SEGS + 1];
     if (segs) {
         if (threadIdx.x == 0) {
@@ -77,6 +99,10 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 s_cum[g] = acc;
                 const long long c = (long long)*segs[g].np_dev;
                 acc += c < (long long)segs[g].cap ? c : (long long)segs[g].cap;
+            }
+            if (uni) {
+                const unsigned long long c = *vo.unp_dev;
+                acc = (long long)(c < vo.ucap ? c : vo.ucap);
             }
             s_cum[nseg] = acc;
         }
@@ -93,6 +119,15 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         if (!segs) atomicOr(err, bits);
         else
             for (int g = 0; g < nseg; g++) atomicOr(segs[g].err, bits);
+    };
+    // union pair q (listed by the joins of mask mk) with edit distance ed (or
+    // INT_MAX when above the band's K): to every listing join whose K it meets
+    auto emit_union = [&](int64_t q, uint32_t mk, int32_t ed) {
+        for (int g = 0; g < nseg; g++) {
+            if (!((mk >> g) & 1u) || ed > segs[g].K) continue;
+            const unsigned long long idx = atomicAdd(segs[g].app_count, 1ull);
+            if (idx < segs[g].app_cap) segs[g].app[idx] = vo.upairs[q];
+        }
     };
     // a finished pair's result: to its join's outputs in a merged launch
     auto emit = [&](int g, int64_t q, bool pass) {
@@ -130,7 +165,6 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const int lane = threadIdx.x & 31;
     const bool rev = lane & 1;
     const int slot = lane >> 1;
-    const int32_t w_min = (2 * K + 1 + 63) / 64;
     const int32_t smove = K & 63;             // chunk position of every window move
     const uint32_t cmax = alpha - 1u;
 
@@ -141,12 +175,27 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const int64_t spw = spw_force > 0 ? (spw_force > 16 ? 16 : spw_force) : 16;
     const int64_t warps_needed = (np + spw - 1) / spw;
     int64_t per_sm = (warps_needed + nsm - 1) / (nsm > 0 ? nsm : 1);
-    if (wps > 0 && per_sm > 4ll * wps) per_sm = 4ll * wps;
+    if (wps <= 0) {
+        // automatic: one working warp per sub-partition while the pairs are few
+        // (more warps would only start them all at once, and the launch ends
+        // with its slowest pairs); 2 or 4 when every slot of one warp per
+        // sub-partition would take at least 8 or 32 pairs (the second and third
+        // warps then hide the step's fixed latencies)
+        const int64_t per_slot = np / ((int64_t)(nsm > 0 ? nsm : 1) * 4 * spw);
+        wps = per_slot >= 32 ? 4 : per_slot >= 8 ? 2 : 1;
+    }
+    if (per_sm > 4ll * wps) per_sm = 4ll * wps;
     unsigned ticket = 0;
     if (lane == 0) ticket = atomicAdd(&vo.sm_tickets[sm_id() & (SM_TICKETS - 1)], 1u);
     ticket = __shfl_sync(FULL, ticket, 0);
     bool exhausted = (slot >= spw) || ((int64_t)ticket >= per_sm);
     if (__all_sync(FULL, exhausted)) return;
+    // merged launch: the warp's work counters per join, in shared memory (added
+    // to the joins' global counters once, when the warp ends)
+    __shared__ unsigned long long s_wk[TPB / 32][MAX_VERIFY_SEGS][2];
+    unsigned long long *wk = &s_wk[threadIdx.x >> 5][0][0];
+    if (lane < 2 * MAX_VERIFY_SEGS) wk[lane] = 0ull;
+    __syncwarp();
 
     unsigned long long loc_cells = 0, loc_cols = 0;
     bool have = false, rejected = false;
@@ -155,8 +204,15 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const uint64_t *y64 = reinterpret_cast<const uint64_t *>(packed);
     int64_t ywords = 0;
     int32_t m = 0, n = 0, ncols = 0, Tacc = 0, jbase = 1, next_move = 0, rej_col = 0;
+    int32_t wpair = 1;       // words of the pair's band, ceil((K_lo + K_hi + 1) / 64) (work counter)
+    // the raw word of y's (or reversed y's) symbols from symbol index sidx on
+    auto sym_word = [&](int64_t sidx) -> SymRaw {
+        return sym_fetch<B>(y64, ywords, rev ? (int64_t)n - SPW - sidx : sidx);
+    };
+    SymRaw snext{0ull, 0ull, 0u};   // the next word of the stream, already requested
     int32_t kp = K;          // the pair's threshold (<= K, the band)
-    int sg = 0;              // the pair's join (merged launch)
+    int sg = 0;              // the pair's join (merged launch; of the union: the largest K's)
+    uint32_t umk = 0;        // union pair: the mask of the joins that list it
     int32_t budget = 0;      // chunks this pair may still take (ncols/64 + 2 suffice)
     int64_t iters = 0;       // loop passes of this warp (bounded by max_iters)
     const int64_t max_iters = vo.max_passes > 0 ? vo.max_passes : kMaxIters;
@@ -195,7 +251,14 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 } else {
                     p = idx;
                     const uint64_t *pp = pairs;
-                    if (segs) {
+                    if (uni) {
+                        pp = vo.upairs;
+                        umk = vo.umask[idx];
+                        sg = -1;
+                        for (int g = 0; g < nseg; g++)
+                            if (((umk >> g) & 1u) && (sg < 0 || segs[g].K > segs[sg].K)) sg = g;
+                        if (sg < 0) sg = 0;   // an empty mask cannot occur; its pair reaches no join
+                    } else if (segs) {
                         sg = 0;
                         while (sg + 1 < nseg && idx >= s_cum[sg + 1]) sg++;
                         p = idx - s_cum[sg];
@@ -215,11 +278,20 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                         n = a_long ? lb : la;
                         kp = segs ? segs[sg].K : (vo.thr ? vo.thr[a] : K);
                         if (!rev) {
-                            if (segs) atomicAdd(&segs[sg].work[0], band_cells(m, n, kp));
-                            else loc_cells += band_cells(m, n, kp);
+                            if (uni) {
+                                for (int g = 0; g < nseg; g++)
+                                    if ((umk >> g) & 1u) atomicAdd(&wk[2 * g], band_cells(m, n, segs[g].K));
+                            } else if (segs) {
+                                atomicAdd(&wk[2 * sg], band_cells(m, n, kp));
+                            } else {
+                                loc_cells += band_cells(m, n, kp);
+                            }
                         }
                         if (m - n > kp || n == 0) {
-                            if (!rev) emit(sg, p, n == 0 && m <= kp);
+                            if (!rev) {
+                                if (uni) emit_union(p, umk, n == 0 ? m : INT_MAX);
+                                else emit(sg, p, n == 0 && m <= kp);
+                            }
                         } else {
                             const int32_t n1 = n / 2;
                             ncols = rev ? n - n1 : n1;
@@ -232,13 +304,17 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                                 Pv[v] = ~0ull;
                                 Mv[v] = 0ull;
                             }
+                            // the pair's band (see the head of this file); m - n <= kp here
+                            const int32_t klo = (kp - (m - n)) >> 1, khi = (kp + (m - n)) >> 1;
+                            wpair = (klo + khi + 64) >> 6;
                             base = 0;
                             k0 = 0;
                             Tacc = 0;
-                            jbase = 1;
-                            next_move = K + 1 + 64;
+                            jbase = 1 - ((smove - klo) & 63);   // column 1 at chunk position s0
+                            snext = sym_word((int64_t)jbase - 1);
+                            next_move = klo + 1 + 64;
                             rejected = false;
-                            budget = (ncols >> 6) + 3;
+                            budget = (ncols >> 6) + 4;
                             have = true;
                         }
                     }
@@ -249,23 +325,23 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
 
         // one chunk: columns jbase .. jbase+63 of every active slot
         int32_t lim = (have && !rejected) ? ncols - jbase : -1;   // steps s <= lim are columns of the pair
+        const int32_t slo = 1 - jbase;                             // and steps s >= slo (first chunk)
         // symbols of y (forward) or of reversed y, 64/B per word; the word after
-        // the current one is requested one word ahead
-        auto sym_word = [&](int64_t sidx) -> uint64_t {
-            return sym_u64<B>(y64, ywords, rev ? (int64_t)n - SPW - sidx : sidx);
-        };
-        uint64_t sreg = 0, snext = sym_word((int64_t)jbase - 1);
+        // the current one is requested one word ahead (snext: requested at the
+        // previous chunk's last word, or at the pair's start)
+        uint64_t sreg = 0;
         auto run_cols = [&](int s_begin, int s_end) {
 #pragma unroll 2
             for (int s = s_begin; s < s_end; s++) {
                 if ((s & (SPW - 1)) == 0) {
-                    sreg = rev ? sym_reverse<B>(snext) : snext;
+                    const uint64_t v = sym_join(snext);
+                    sreg = rev ? sym_reverse<B>(v) : v;
                     snext = sym_word((int64_t)jbase - 1 + s + SPW);
                 }
                 uint32_t c = (uint32_t)(sreg & CMASK);
                 sreg >>= B;
                 c = c < cmax ? c : cmax;
-                if (s <= lim) {
+                if (s <= lim && s >= slo) {
                     const uint64_t *row = ring + ((size_t)c * R2 + base) * T_;   // the window's words
                     uint64_t Eq[W1], A[W1], S[W1];
 #pragma unroll
@@ -303,7 +379,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             const int32_t j = jbase + smove;
             // every pair still running takes part in the joint bound, also before
             // its first window move (short pairs have none)
-            const bool active = have && !rejected && j <= ncols;
+            const bool active = have && !rejected && j >= 1 && j <= ncols;
             const bool moving = active && j == next_move;
             int32_t lb = 0;
             if (moving) {
@@ -362,8 +438,8 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             const int32_t T = Tacc + (rejected ? rej_col - 1 : ncols);
             if (pair_done) {
                 const unsigned long long cols = (unsigned long long)(rejected ? rej_col - 1 : ncols);
-                if (segs) atomicAdd(&segs[sg].work[1], cols * (unsigned long long)((2 * kp + 1 + 63) / 64));
-                else loc_cols += cols * (unsigned long long)w_min;
+                if (segs) atomicAdd(&wk[2 * sg + 1], cols * (unsigned long long)wpair);
+                else loc_cols += cols * (unsigned long long)wpair;
 #pragma unroll
                 for (int v = 0; v < W1; v++) {
                     ring[(size_t)(2 * v) * T_] = Pv[v];
@@ -375,6 +451,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             __syncwarp();
             if (pair_done && !rev) {
                 bool pass = false;
+                int32_t ed = INT_MAX;                           // the distance when <= kp
                 const uint64_t *rb = smem + threadIdx.x + 1;   // backward half's dump
                 const bool rej_b = rb[(size_t)(2 * W1 + 1) * T_] != 0ull;
                 if (!rejected && !rej_b) {
@@ -414,15 +491,21 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                             best = min(best, F + Bv);
                         }
                         pass = best <= kp;
+                        if (pass) ed = best;
                     }
                 }
-                emit(sg, p, pass);
+                if (uni) emit_union(p, umk, ed);
+                else emit(sg, p, pass);
             }
             __syncwarp();
             if (pair_done) have = false;
         }
     }
 
+    if (segs) {
+        __syncwarp();
+        if (lane < 2 * nseg && wk[lane]) atomicAdd(&segs[lane >> 1].work[lane & 1], wk[lane]);
+    }
     if (vo.work) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

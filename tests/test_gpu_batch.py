@@ -100,12 +100,14 @@ def test_batch_shares_walks_across_parameter_sets(ej, ctx, stream):
     assert np.array_equal(outs[0], ref.pairs)
 
 
-@pytest.mark.parametrize("chain", [0, 1, 2, 3])
+@pytest.mark.parametrize("chain", [0, 1, 2, 3, 4])
 def test_batch_persistent_verifiers_merged_chained_or_overlapping(ej, stream, chain):
-    """Joins on the persistent verifier with different bands (W1 = 2, 3, 5):
-    verified by one merged launch at the widest band (chain 3), one launch per
-    join in turn (2) or overlapping (1); every join returns ej_join's pairs and
-    counts its band cells at its own K."""
+    """Joins on the persistent verifier with different K (4, 40, 100, 20; the
+    same signatures, so their candidate sets nest): verified by one merged
+    launch over the union of their candidates, each pair once at the largest K
+    of the joins that list it (chain 4), one merged launch over the joins in
+    turn (3), one launch per join in turn (2) or overlapping (1); every join
+    returns ej_join's pairs and counts its band cells at its own K."""
     c = ej.Context(0)
     try:
         c.set_schedule(mode=1, chain=chain)
@@ -132,7 +134,7 @@ def test_batch_persistent_verifiers_merged_chained_or_overlapping(ej, stream, ch
                 got, _ = e.result(i, device=DEV, stream=stream)
                 want, _ = b.result(i, device=DEV, stream=stream)
                 assert np.array_equal(_u64(got), _u64(want)), (chain, i)
-            if chain == 3:
+            if chain in (3, 4):
                 assert e.verify_ms() > 0
             elif chain in (1, 2):
                 with pytest.raises(ej.EJError):
@@ -266,6 +268,33 @@ def test_batch_misuse_is_reported(ej, ctx, stream):
             b.result(0, device=DEV, stream=stream)
         assert e.value.status == ej.EJ_ERR_INVALID_ARG
         b.close()
+
+
+@pytest.mark.parametrize("chain", [3, 4])
+def test_batch_union_of_overlapping_candidate_sets_equals_oracle(ej, stream, chain):
+    """Persistent-verifier joins whose candidate sets overlap only in part (two
+    seeds, different z and K): the union launch verifies a pair listed by
+    several joins once, at the largest of their K, and each join still gets
+    exactly the oracle's pairs."""
+    c = ej.Context(0)
+    try:
+        c.set_schedule(mode=1, chain=chain)
+        ss = synth.small_dna(0.5)
+        s = ej.Strings.from_set(ss, DEV)
+        a = ss.alphabet
+        cfg = [(6, 12, 1), (12, 10, 2), (9, 11, 1), (3, 9, 2)]   # (K, z, seed)
+        params = [ej.Params(alphabet=a, K=K, r=3, m=8, z=z, seed=sd) for K, z, sd in cfg]
+        with torch.cuda.stream(stream):
+            b = c.batch(s, params, stream=stream)
+            b.run(stream)
+            for i, (K, z, sd) in enumerate(cfg):
+                got, st = b.result(i, device=DEV, stream=stream)
+                ref = oracle.join(ss.data, ss.offsets, a, K=K, r=3, m=8, z=z, seed=sd)
+                assert np.array_equal(_u64(got), ref.pairs), (chain, i)
+                assert st.n_candidates == ref.n_candidates, (chain, i)
+            b.close()
+    finally:
+        c.close()
 
 
 def test_batch_moves_huge_buckets_to_global_memory_and_chains_verifiers(ej, ctx, stream):
