@@ -727,7 +727,8 @@ int pq_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const Verif
 // verifier leave one or two warps per SM): two lanes per pair, the band within
 // 12 words per lane, the warp's shared area within the block's budget.
 bool sx_choice(const ej_ctx *ctx, const Plan &pl, const ej_params *p, const VerifyConfig &vc) {
-    if (vc.G != 2 || vc.V > 12 || sx_smem_bytes(vc.V, p->alphabet_size) > 220 * 1024) return false;
+    const int W1 = sx_band(p->K).W1;
+    if (vc.G != 2 || W1 > 12 || sx_smem_bytes(W1, p->alphabet_size) > 220 * 1024) return false;
     const bool long_pairs = pl.st.n > 0 && pl.st.total / pl.st.n >= 2048;
     return ctx->sched.mode == 3 || (ctx->sched.mode == 0 && !long_pairs && p->alphabet_size > 4);
 }
@@ -778,19 +779,23 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     const int order = sx ? 5 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
     uint32_t *fbins = nullptr;
     uint64_t *fstarts = nullptr;
+    // the shared-string verifier's window and length-difference classes
+    const SxBand sb = sx ? sx_band(p->K) : SxBand{0, 1u, 1u};
+    const int64_t nb = n * (int64_t)sb.nclass;   // candidate bins of order 3 / 5
     if (order == 3 || order == 5) {
         // candidates ordered by their first string (a warp's pairs share it), or
-        // by their longer string (the string whose match masks are built)
+        // by their longer string (the string whose match masks are built), for
+        // the shared-string verifier also by the class of the length difference
         uint32_t *hcount = nullptr;
         void *fscan = nullptr;
         CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
-        CKS(ensure_t(ctx, B_FBINS, (size_t)n + 1, &fbins));
-        CKS(ensure_t(ctx, B_FSTARTS, (size_t)n + 2, &fstarts));
-        CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(n + 1), &fscan));
+        CKS(ensure_t(ctx, B_FBINS, (size_t)nb + 1, &fbins));
+        CKS(ensure_t(ctx, B_FSTARTS, (size_t)nb + 2, &fstarts));
+        CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(nb + 1), &fscan));
         CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
-        CK(cudaMemsetAsync(fbins, 0, (size_t)(n + 1) * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(fbins, 0, (size_t)(nb + 1) * sizeof(uint32_t), s));
         CK(launch_dedup_by_first(raw, cap, table, hcount, hsize, n, fbins, fstarts, fscan, cand, cnt, s,
-                                 order == 5 ? pl.lens : nullptr));
+                                 order == 5 ? pl.lens : nullptr, sb.nclass, sb.width));
     } else if (order != 2) {
         // candidates handed to the verifier longest first (order 4: length classes,
         // so that the pairs a warp takes have similar lengths) or most-collided
@@ -818,19 +823,20 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     vo.max_passes = ctx->loop_bound;
     const VerifyConfig &vc = bs.vc;
     if (sx) {
-        // warp tasks of up to 16 candidates sharing their longer string
-        const int64_t tcap = (int64_t)(cap / 16) + n + 1;
+        // warp tasks of up to 16 candidates sharing their longer string and the
+        // class of their length difference
+        const int64_t tcap = (int64_t)(cap / 16) + nb + 1;
         uint32_t *tcount = nullptr;
         uint64_t *tstart = nullptr, *tasks = nullptr;
         void *tscan = nullptr;
-        CKS(ensure_t(ctx, B_SX_TCOUNT, (size_t)n + 1, &tcount));
-        CKS(ensure_t(ctx, B_SX_TSTART, (size_t)n + 1, &tstart));
+        CKS(ensure_t(ctx, B_SX_TCOUNT, (size_t)nb + 1, &tcount));
+        CKS(ensure_t(ctx, B_SX_TSTART, (size_t)nb + 1, &tstart));
         CKS(ensure_t(ctx, B_SX_TASKS, (size_t)tcap, &tasks));
-        CKS(ensure(ctx, B_SX_SCAN, scan_temp_bytes(n + 1), &tscan));
-        CK(launch_sx_tasks(fbins, fstarts, n, tcount, tstart, cnt + 7, tscan, tasks, s));
+        CKS(ensure(ctx, B_SX_SCAN, scan_temp_bytes(nb + 1), &tscan));
+        CK(launch_sx_tasks(fbins, fstarts, nb, tcount, tstart, cnt + 7, tscan, tasks, s));
         if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
-        CK(launch_verify_sx(vc.V, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, tasks, cnt + 7, tcap,
-                            p->K, vo, s));
+        CK(launch_verify_sx(sb.W1, pl.packed, pl.pofs, pl.B, pl.lens, n, p->alphabet_size, cand, tasks, cnt + 7,
+                            tcap, p->K, vo, s));
     } else {
     if (verify_after) CK(cudaStreamWaitEvent(s, verify_after, 0));
     if (pq_threads > 0)
@@ -1322,7 +1328,7 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
     if (b->munion) {
         unsigned long long *ucount = b->ubins + count_bins();
         CK(launch_union_candidates(b->segs_dev, vo.nseg, b->utable, b->utmask, b->uhsize, b->ubins, b->upairs,
-                                   b->umask, ucount, pl.lens, pl.max_len, s));
+                                   b->umask, ucount, pl.lens, pl.max_len, ctx->sched.order != 1, s));
         vo.upairs = b->upairs;
         vo.umask = b->umask;
         vo.unp_dev = ucount;

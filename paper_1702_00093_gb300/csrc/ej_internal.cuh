@@ -280,12 +280,14 @@ struct VerifySeg;
 // Union of the candidate lists of a merged launch's joins (segs[0 .. nseg)):
 // every distinct pair once in upairs, with the mask of the joins that list it
 // in umask, ordered by the number of joins (more first), then by the length
-// class of the shorter string (longer first). table/tmask: hsize slots (a power
-// of two >= 2 x the pairs, cleared here); bins: count_bins() entries;
-// *ucount = the number of distinct pairs (device).
+// class of the shorter string (longer first), or (length_major) by length class
+// first. table/tmask: hsize slots (a power of two >= 2 x the pairs, cleared
+// here); bins: count_bins() entries; *ucount = the number of distinct pairs
+// (device).
 cudaError_t launch_union_candidates(const VerifySeg *segs, int nseg, uint64_t *table, uint32_t *tmask, uint64_t hsize,
                                     unsigned long long *bins, uint64_t *upairs, uint32_t *umask,
-                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len, cudaStream_t s);
+                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len,
+                                    bool length_major, cudaStream_t s);
 cudaError_t launch_dedup_ordered(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                  unsigned long long *bins, uint64_t *cand, unsigned long long *counters,
                                  const int32_t *lens, int64_t max_len, cudaStream_t s);
@@ -325,15 +327,29 @@ cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *ta
 // Dedup ordered by the pair's first string (counting sort over n bins): bins
 // (n + 1 uint32) and hcount start at zero; starts holds n + 2 uint64.
 // With longer_lens, the bins are the pairs' longer strings (the grouping of the
-// shared-string verifier); after the call starts[x] is the end of bin x.
+// shared-string verifier), each split into nclass bins by the length
+// difference d (class min(d / width, nclass - 1)): n * nclass bins (bins and
+// starts then hold n * nclass + 1 and + 2 entries); after the call starts[b]
+// is the end of bin b.
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
                                   unsigned long long *counters, cudaStream_t s,
-                                  const int32_t *longer_lens = nullptr);
+                                  const int32_t *longer_lens = nullptr, uint32_t nclass = 1, uint32_t width = 1);
 // Shared-string verifier (ej_verify_sx.cu): warp tasks of up to 16 candidates
-// that share their longer string, from the bins of launch_dedup_by_first with
-// longer_lens (tcount n+1 uint32, tstart n+1 uint64, tasks up to
-// candidates/16 + n entries; *ntasks_dev = their number), and the verifier.
+// that share their longer string and length-difference class, from the bins of
+// launch_dedup_by_first with longer_lens (nb = n * nclass bins; tcount nb+1
+// uint32, tstart nb+1 uint64, tasks up to candidates/16 + nb entries;
+// *ntasks_dev = their number), and the verifier.
+// sx_band(K): the verifier's window W1 and the class width and count that keep
+// a task's band within it: a task's length differences lie in one class of
+// width D, so its band (the diagonals a cost-K alignment of any of its pairs
+// can use) spans at most K + (D - 1)/2 + 1 diagonals; D uses the rows that
+// ceil((K + 1) / 64) words leave (at least 32, else one more word).
+struct SxBand {
+    int W1;
+    uint32_t width, nclass;
+};
+SxBand sx_band(int32_t K);
 size_t sx_smem_bytes(int W1, uint32_t alpha);
 cudaError_t launch_sx_tasks(const uint32_t *bins, const uint64_t *ends, int64_t n, uint32_t *tcount, uint64_t *tstart,
                             unsigned long long *ntasks_dev, void *scan_tmp, uint64_t *tasks, cudaStream_t s);

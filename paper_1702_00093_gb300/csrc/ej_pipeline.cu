@@ -649,20 +649,27 @@ __global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const u
 // same string and, through the length filter, have similar lengths.
 // With lens, the bin is the pair's longer string instead (the first one on a
 // tie), which groups the pairs that share the string whose match masks the
-// verifier builds.
-__device__ __forceinline__ uint64_t first_bin(uint64_t key, const int32_t *__restrict__ lens) {
+// verifier builds; with nclass > 1, that string's bin is split further by the
+// class of the length difference, x * nclass + min(d / width, nclass - 1).
+__device__ __forceinline__ uint64_t first_bin(uint64_t key, const int32_t *__restrict__ lens, uint32_t nclass,
+                                              uint32_t width) {
     const uint64_t a = key >> 32, b = key & 0xFFFFFFFFull;
     if (!lens) return a;
-    return lens[a] >= lens[b] ? a : b;
+    const int32_t la = lens[a], lb = lens[b];
+    const uint64_t x = la >= lb ? a : b;
+    if (nclass <= 1) return x;
+    const uint32_t c = (uint32_t)(la >= lb ? la - lb : lb - la) / width;
+    return x * nclass + (c < nclass ? c : nclass - 1u);
 }
 
 __global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
-                                  uint32_t *__restrict__ bins, unsigned long long *__restrict__ counters) {
+                                  uint32_t nclass, uint32_t width, uint32_t *__restrict__ bins,
+                                  unsigned long long *__restrict__ counters) {
     unsigned int mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
-            atomicAdd(&bins[first_bin(key, lens)], 1u);
+            atomicAdd(&bins[first_bin(key, lens, nclass, width)], 1u);
             mine++;
         }
     }
@@ -671,25 +678,29 @@ __global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t h
 }
 
 __global__ void first_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
-                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ cand) {
+                                     uint32_t nclass, uint32_t width, unsigned long long *__restrict__ cursor,
+                                     uint64_t *__restrict__ cand) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
-        if (key != ~0ull) cand[atomicAdd(&cursor[first_bin(key, lens)], 1ull)] = key;
+        if (key != ~0ull) cand[atomicAdd(&cursor[first_bin(key, lens, nclass, width)], 1ull)] = key;
     }
 }
 
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
-                                  unsigned long long *counters, cudaStream_t s, const int32_t *longer_lens) {
+                                  unsigned long long *counters, cudaStream_t s, const int32_t *longer_lens,
+                                  uint32_t nclass, uint32_t width) {
+    if (nclass < 1 || width < 1) return cudaErrorInvalidValue;
+    const int64_t nb = n * (int64_t)nclass;   // bins (the scan covers nb + 1 entries)
     int64_t g = ((int64_t)cap + 255) / 256;
     dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
     int64_t gh = ((int64_t)hsize + 255) / 256;
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
-    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, bins, counters);
+    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, nclass, width, bins, counters);
     note_launches(2);
-    cudaError_t e = exclusive_scan_u32(bins, starts, n + 1, nullptr, scan_tmp, s);
+    cudaError_t e = exclusive_scan_u32(bins, starts, nb + 1, nullptr, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, (unsigned long long *)starts, cand);
+    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, nclass, width, (unsigned long long *)starts, cand);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -727,20 +738,23 @@ __global__ void union_insert_kernel(const VerifySeg *__restrict__ segs, int nseg
 // Queue bin of a union pair: 32 bins per number of listing joins (more joins
 // first: a pair that passed the stricter signatures of several joins is the
 // more likely to be similar, and a similar pair runs its full length), then the
-// shorter string's length class (longer first).
+// shorter string's length class (longer first); with length_major, the length
+// class first and the number of joins within it.
 __device__ __forceinline__ uint32_t union_bin(uint64_t key, uint32_t mask, const int32_t *__restrict__ lens,
-                                              uint32_t len_scale) {
+                                              uint32_t len_scale, bool length_major) {
     const int32_t a = lens[key >> 32], b = lens[key & 0xFFFFFFFFull];
     const uint32_t sh = (uint32_t)(a < b ? a : b);
     const uint64_t c = ((uint64_t)sh * 32) / ((uint64_t)len_scale + 1);
     const uint32_t cls = c < 32 ? (uint32_t)c : 31u;
     const uint32_t j = (uint32_t)__popc(mask);
-    return ((j > 8 ? 8u : j) - 1u) * 32u + cls;   // mask != 0 for an occupied slot
+    const uint32_t jb = (j > 8 ? 8u : j) - 1u;   // mask != 0 for an occupied slot
+    return length_major ? cls * 8u + jb : jb * 32u + cls;
 }
 
 __global__ void union_hist_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ tmask,
                                   uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
-                                  unsigned long long *__restrict__ bins, unsigned long long *__restrict__ ucount) {
+                                  bool length_major, unsigned long long *__restrict__ bins,
+                                  unsigned long long *__restrict__ ucount) {
     __shared__ unsigned int sb[COUNT_BINS];
     for (int t = threadIdx.x; t < COUNT_BINS; t += blockDim.x) sb[t] = 0;
     __syncthreads();
@@ -748,7 +762,7 @@ __global__ void union_hist_kernel(const uint64_t *__restrict__ table, const uint
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
-            atomicAdd(&sb[union_bin(key, tmask[i], lens, len_scale)], 1u);
+            atomicAdd(&sb[union_bin(key, tmask[i], lens, len_scale, length_major)], 1u);
             mine++;
         }
     }
@@ -761,13 +775,13 @@ __global__ void union_hist_kernel(const uint64_t *__restrict__ table, const uint
 
 __global__ void union_scatter_kernel(const uint64_t *__restrict__ table, const uint32_t *__restrict__ tmask,
                                      uint64_t hsize, const int32_t *__restrict__ lens, uint32_t len_scale,
-                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ upairs,
-                                     uint32_t *__restrict__ umask) {
+                                     bool length_major, unsigned long long *__restrict__ cursor,
+                                     uint64_t *__restrict__ upairs, uint32_t *__restrict__ umask) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
             const uint32_t mk = tmask[i];
-            const unsigned long long at = atomicAdd(&cursor[union_bin(key, mk, lens, len_scale)], 1ull);
+            const unsigned long long at = atomicAdd(&cursor[union_bin(key, mk, lens, len_scale, length_major)], 1ull);
             upairs[at] = key;
             umask[at] = mk;
         }
@@ -776,7 +790,8 @@ __global__ void union_scatter_kernel(const uint64_t *__restrict__ table, const u
 
 cudaError_t launch_union_candidates(const VerifySeg *segs, int nseg, uint64_t *table, uint32_t *tmask, uint64_t hsize,
                                     unsigned long long *bins, uint64_t *upairs, uint32_t *umask,
-                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len, cudaStream_t s) {
+                                    unsigned long long *ucount, const int32_t *lens, int64_t max_len,
+                                    bool length_major, cudaStream_t s) {
     if (nseg < 1 || nseg > MAX_VERIFY_SEGS || (hsize & (hsize - 1)) != 0) return cudaErrorInvalidValue;
     cudaError_t e;
     if ((e = cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s)) != cudaSuccess) return e;
@@ -787,9 +802,9 @@ cudaError_t launch_union_candidates(const VerifySeg *segs, int nseg, uint64_t *t
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
     const uint32_t scale = (uint32_t)(max_len > 0x7fffffff ? 0x7fffffff : max_len);
     union_insert_kernel<<<gs, 256, 0, s>>>(segs, nseg, table, tmask, hsize);
-    union_hist_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, bins, ucount);
+    union_hist_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, length_major, bins, ucount);
     count_scan_kernel<<<1, COUNT_BINS, 0, s>>>(bins);
-    union_scatter_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, bins, upairs, umask);
+    union_scatter_kernel<<<gs, 256, 0, s>>>(table, tmask, hsize, lens, scale, length_major, bins, upairs, umask);
     note_launches(4);
     return cudaGetLastError();
 }

@@ -2,13 +2,18 @@
 // of Algorithm 3): the same exact test ED(x, y) <= K as the two-lane
 // block-aligned verifier, with the match masks of x shared by a warp.
 //
-// The candidates arrive grouped by x, the longer string of each pair, in warp
-// tasks of up to 16 pairs that all share x. A warp runs its 16 pairs in two
-// lanes each (forward half and backward half, as in verify_bd_kernel). All
-// pairs of a task start together and the band window of every pair moves at
-// the same columns (K + 1 + 64t), so the windows of all forward halves cover
-// the same 64-row words of x, and those of all backward halves the same words
-// of reversed x: the warp keeps one ring of match masks per direction in
+// The candidates arrive grouped by x, the longer string of each pair, and by
+// the class of the length difference d = |x| - |y| (sx_band), in warp tasks of
+// up to 16 pairs that all share x and the class. A warp runs its 16 pairs in
+// two lanes each (forward half and backward half, as in verify_bd_kernel).
+// A path of cost <= K of a pair stays on the diagonals i - j in
+// [-floor((K - d)/2), floor((K + d)/2)] (the persistent verifier's band); the
+// task's band is the union of its pairs' bands, at most K + 1 + (D - 1)/2
+// diagonals for a class of width D. All pairs of a task start together and the
+// band window of every pair moves at the same columns (klo + 1 + 64t, klo the
+// task band's upper reach), so the windows of all forward halves cover the
+// same 64-row words of x, and those of all backward halves the same words of
+// reversed x: the warp keeps one ring of match masks per direction in
 // shared memory instead of one per lane. For large alphabets that is 16x less
 // shared memory per pair, which is what limited the per-lane verifier to one or
 // two warps per SM, and each word is built once per task, by the whole warp:
@@ -98,7 +103,6 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     const bool rev = lane & 1;
     const int slot_pair = lane >> 1;
     uint64_t *myring = rev ? ringB : ringF;
-    const int32_t w_min = (2 * K + 1 + 63) / 64;
     const int64_t cap_t = (int64_t)*ntasks_dev;
     const int64_t ntasks = cap_t < ntasks_cap ? cap_t : ntasks_cap;
     const int64_t nw = (int64_t)gridDim.x * SX_WARPS;
@@ -146,6 +150,10 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         const int32_t n1 = n / 2;
         const int32_t ncols = decided ? 0 : (rev ? n - n1 : n1);
         const int32_t maxcols = (int32_t)__reduce_max_sync(FULL, (unsigned)ncols);
+        // the task's band: the diagonals a cost-K alignment of any of its
+        // undecided pairs can use (their length differences lie in one class)
+        const unsigned nlo = __reduce_min_sync(FULL, decided ? 0xFFFFFFFFu : (unsigned)n);
+        const unsigned nhi = __reduce_max_sync(FULL, decided ? 0u : (unsigned)n);
 
         uint64_t Pv[W1], Mv[W1];
 #pragma unroll
@@ -184,7 +192,9 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
             const uint32_t cmax = alpha - 1u;
             int base = 0;              // ring slot of the window's top word (the same for the whole warp)
             int64_t kr = 0;            // window moves of the warp so far
-            int32_t next_move = K + 1 + 64;
+            const int32_t klo = (K - (mx - (int32_t)nhi)) >> 1, khi = (K + (mx - (int32_t)nlo)) >> 1;
+            if (klo + khi + 64 > 64 * W1 && lane == 0) atomicOr(err, (uint32_t)DERR_GUARD);   // not by construction
+            int32_t next_move = klo + 1 + 64;   // the window moves down before the columns klo + 1 + 64t
             bool done = decided;
             for (int32_t j = 1; j <= maxcols; j++) {
                 if ((j & (SX_CHECK - 1)) == 0) {
@@ -332,7 +342,8 @@ verify_sx_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         if (valid && !rev) emit_result(vo, first + slot_pair, pairs, pass);
         if (valid) {
             if (!rev) loc_cells += band_cells(m, n, K);
-            loc_cols += (unsigned long long)cols_run * (unsigned long long)w_min;
+            const int32_t d = m - n;   // the pair's own band: ((K - d) >> 1) + ((K + d) >> 1) + 1 diagonals
+            loc_cols += (unsigned long long)cols_run * (unsigned long long)((((K - d) >> 1) + ((K + d) >> 1) + 64) >> 6);
         }
         __syncwarp();   // the shared area is rebuilt by the next task
     }
@@ -399,6 +410,19 @@ cudaError_t launch_sx_t(const uint4 *packed, const uint64_t *pofs, const int32_t
 }
 
 }  // namespace
+
+SxBand sx_band(int32_t K) {
+    const int words = (K + 1 + 63) / 64;   // ceil((K + 1) / 64)
+    int W = words, slack = 64 * words - (K + 1);
+    if (2 * slack + 1 < 32) {   // classes narrower than 32 would split the strings' pairs too finely
+        W += 1;
+        slack += 64;
+    }
+    uint32_t D = 2u * (uint32_t)slack + 1u;
+    if (D > (uint32_t)K + 1u) D = (uint32_t)K + 1u;
+    return SxBand{W + 1, D, ((uint32_t)K + 1u + D - 1u) / D};
+}
+
 
 size_t sx_smem_bytes(int W1, uint32_t alpha) {
     const size_t RS = (W1 & 1) ? W1 : W1 + 1;
