@@ -344,7 +344,7 @@ cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *t
 // a task's band within it: a task's length differences lie in one class of
 // width D, so its band (the diagonals a cost-K alignment of any of its pairs
 // can use) spans at most K + (D - 1)/2 + 1 diagonals; D uses the rows that
-// ceil((K + 1) / 64) words leave (at least 32, else one more word).
+// ceil((K + 1) / 64) words leave (at least 7, else one more word).
 struct SxBand {
     int W1;
     uint32_t width, nclass;

@@ -414,7 +414,7 @@ cudaError_t launch_sx_t(const uint4 *packed, const uint64_t *pofs, const int32_t
 SxBand sx_band(int32_t K) {
     const int words = (K + 1 + 63) / 64;   // ceil((K + 1) / 64)
     int W = words, slack = 64 * words - (K + 1);
-    if (2 * slack + 1 < 32) {   // classes narrower than 32 would split the strings' pairs too finely
+    if (2 * slack + 1 < 7) {   // classes narrower than 7 would split the strings' pairs too finely
         W += 1;
         slack += 64;
     }
