@@ -379,7 +379,8 @@ void ej_batch_destroy(ej_batch *batch);
  *     every join's own buckets. Tables of up to 21845 records are bucketed in
  *     shared memory, one block per table, which pays for small buckets only;
  *     a batch moves a join whose sizing pass finds a bucket of more than 256
- *     records to the buckets in global memory.
+ *     records to the buckets in global memory, and one with a bucket of more
+ *     than 4096 records to the sorted tables (2), unshared.
  *     2: the tables are sorted by (signature, length) and each record pairs
  *     with the window after it (the ej_lsh_candidates path). It is much
  *     cheaper when a few signatures collect thousands of strings, e.g. short
