@@ -672,6 +672,7 @@ struct BackState {
     const uint32_t *srid = nullptr;
     uint32_t *bnext = nullptr;
     VerifyConfig vc{0, 0, 0};
+    bool any_order = false;            // the candidates feed a batch's union launch, which orders them itself
 };
 
 // Largest bucket (records of one signature in one table) that a batch join
@@ -779,7 +780,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     const bool sx = !defer && sx_choice(ctx, pl, p, bs.vc);
     const int pq_threads = sx ? 0 : pq_choice(ctx, pl, p, bs.vc);
     // the shared-string verifier needs its pairs grouped by their longer string
-    const int order = sx ? 5 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
+    const int order = sx ? 5 : bs.any_order ? 2 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
     uint32_t *fbins = nullptr;
     uint64_t *fstarts = nullptr;
     // the shared-string verifier's window and length-difference classes
@@ -1301,6 +1302,7 @@ int batch_plan_merge(ej_batch *b) {
     b->mthreads = threads;
     if (mode == 0 || mode == 4) {
         b->munion = true;
+        for (int i : pq) b->joins[(size_t)i].bs.any_order = true;   // the union orders the candidates
         for (int i : pq) b->ucap += b->joins[(size_t)i].cap;
         b->uhsize = 1;
         while (b->uhsize < 2 * b->ucap) b->uhsize <<= 1;
