@@ -370,29 +370,44 @@ constexpr uint16_t TB_OWNER = 0xFFFEu;  // s_next of an owner
 size_t bucket_table_smem(int64_t n) {
     if (n < 1 || n >= 0xFFFE) return 0;
     const uint64_t H = bucket_slots_per_table(n);
-    const size_t bytes = (size_t)H * 4 + (((size_t)n * 2 + 15) & ~(size_t)15);
-    return bytes <= 200 * 1024 ? bytes : 0;
+    const size_t bytes = (size_t)H * 5 + (((size_t)n * 2 + 15) & ~(size_t)15);
+    return bytes <= 220 * 1024 ? bytes : 0;
 }
+
+// 8-bit fingerprint of a signature (1..255; 0 marks a slot whose owner has not
+// written it yet): a probe that meets another signature's slot skips the
+// comparison of the keys in global memory unless the fingerprints agree.
+__device__ __forceinline__ uint8_t tb_fp(uint64_t kh) { return (uint8_t)((kh >> 56) | 1ull); }
 
 __global__ void __launch_bounds__(1024)
 bucket_table_kernel(const int32_t *__restrict__ lens, int64_t n, uint32_t H, SharedEmit se) {
     extern __shared__ uint32_t tb_smem[];
     uint32_t *slot = tb_smem;
     uint16_t *nxt = reinterpret_cast<uint16_t *>(tb_smem + H);
+    uint8_t *fp = reinterpret_cast<uint8_t *>(nxt) + (((size_t)n * 2 + 15) & ~(size_t)15);   // [H]
     const int64_t t = blockIdx.x;
     const uint64_t *bk = se.keys[0] + t * n;
     const int lane = threadIdx.x & 31;
     const int nj = se.njoins;
-    for (uint32_t h = threadIdx.x; h < H; h += blockDim.x) slot[h] = TB_EMPTY;
+    for (uint32_t h = threadIdx.x; h < H; h += blockDim.x) {
+        slot[h] = TB_EMPTY;
+        fp[h] = 0;
+    }
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const uint64_t k = bk[i];
+        const uint64_t kh = key_hash(k);
+        const uint8_t f = tb_fp(kh);
         nxt[i] = TB_OWNER;   // (kept if no slot were found, which H > n rules out)
-        uint32_t h = (uint32_t)(key_hash(k) & (uint64_t)(H - 1));
+        uint32_t h = (uint32_t)(kh & (uint64_t)(H - 1));
         for (uint32_t probe = 0; probe < H; probe++) {
             const uint32_t old = atomicCAS(&slot[h], TB_EMPTY, (uint32_t)i | ((uint32_t)TB_NONE << 16));
-            if (old == TB_EMPTY) break;
-            if (bk[old & 0xFFFFu] == k) {
+            if (old == TB_EMPTY) {
+                fp[h] = f;
+                break;
+            }
+            const uint8_t fo = fp[h];
+            if ((fo == 0 || fo == f) && bk[old & 0xFFFFu] == k) {
                 // a later record of this signature: push it onto the slot's list
                 uint32_t cur = old, seen;
                 while ((seen = atomicCAS(&slot[h], cur, (cur & 0xFFFFu) | ((uint32_t)i << 16))) != cur) cur = seen;
@@ -420,10 +435,12 @@ bucket_table_kernel(const int32_t *__restrict__ lens, int64_t n, uint32_t H, Sha
             if (nxt[i] != TB_OWNER) {
                 // a listed record: its owner (re-probe) and the list after it
                 const uint64_t k = bk[i];
-                uint32_t h = (uint32_t)(key_hash(k) & (uint64_t)(H - 1));
+                const uint64_t kh = key_hash(k);
+                const uint8_t f = tb_fp(kh);
+                uint32_t h = (uint32_t)(kh & (uint64_t)(H - 1));
                 for (uint32_t probe = 0; probe < H; probe++) {
                     const uint32_t v = slot[h];
-                    if (v != TB_EMPTY && bk[v & 0xFFFFu] == k) {
+                    if (v != TB_EMPTY && fp[h] == f && bk[v & 0xFFFFu] == k) {
                         owner = v & 0xFFFFu;
                         break;
                     }
@@ -1058,7 +1075,9 @@ cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *ta
 }
 
 // Sorts up to SMALL_SORT_MAX uint64 keys in one block (bitonic network in
-// shared memory); the count comes from the device.
+// shared memory); the count comes from the device. The stages whose compared
+// elements lie 2j apart with 2j within one warp's segment of the array run back
+// to back in that warp (warp syncs only); the others take the whole block.
 constexpr int SMALL_SORT_MAX = 8192;
 
 __global__ void __launch_bounds__(1024)
@@ -1067,25 +1086,39 @@ small_sort_kernel(uint64_t *__restrict__ a, const unsigned long long *__restrict
     const unsigned long long c = *count_dev;
     if (c > n_cap) return;   // left for a larger sort
     const int n = (int)c;
+    if (n < 2) return;
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < n ? a[i] : ~0ull;
     __syncthreads();
+    const int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int S = P / nwarp;   // elements of a warp's segment (a power of two)
+    if (S < 2) S = 2;
+    // compare-exchange of pair t of the stage (k, j): i has bit j clear, ixj = i + j
+    auto cx = [&](int t, int k, int j) {
+        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const int ixj = i + j;
+        const uint64_t x = s[i], y = s[ixj];
+        const bool up = (i & k) == 0;
+        if ((x > y) == up) {
+            s[i] = y;
+            s[ixj] = x;
+        }
+    };
     for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t x = s[i], y = s[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        s[i] = y;
-                        s[ixj] = x;
-                    }
-                }
-            }
+        int j = k >> 1;
+        for (; j >= S; j >>= 1) {   // across segments: the whole block
+            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) cx(t, k, j);
             __syncthreads();
         }
+        if (j > 0 && w * S < P) {   // within segments: each warp its own
+            const int seg_pairs = S >> 1, base_t = w * seg_pairs;
+            for (; j > 0; j >>= 1) {
+                for (int t = lane; t < seg_pairs; t += 32) cx(base_t + t, k, j);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = s[i];
 }
