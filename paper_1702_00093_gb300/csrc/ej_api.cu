@@ -33,6 +33,7 @@ enum BufId {
     B_PLUS_SUBLEN, B_PLUS_WHOLE, B_PLUS_SUBOFF, B_PLUS_BYTES, B_PLUS_SCAN, B_PLUS_CAND,
     B_SX_TCOUNT, B_SX_TSTART, B_SX_TASKS, B_SX_SCAN,
     B_GROUP_IDX, B_GROUP_OFF, B_GROUP_BYTES, B_GROUP_OUT,
+    B_DG_TEMP, B_GSTART,
     B_NUM
 };
 
@@ -754,11 +755,18 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     CKS(ensure_t(ctx, B_RAW, (size_t)cap, &raw));
     CKS(ensure_t(ctx, B_CAND, (size_t)cap, &cand));
     CKS(ensure_t(ctx, B_APP, (size_t)cap, &app));
-    CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
+    // the verifier and the candidate order it takes
+    const bool sx = !defer && sx_choice(ctx, pl, p, bs.vc);
+    const int pq_threads = sx ? 0 : pq_choice(ctx, pl, p, bs.vc);
+    // the shared-string verifier needs its pairs grouped by their longer string
+    const int order = sx ? 5 : bs.any_order ? 2 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
     // emitted: the raw pairs and counters [0], [1] are already written (shared
     // buckets of a batch)
     CK(cudaMemsetAsync(emitted ? cnt + 2 : cnt, 0, (emitted ? 6 : 8) * sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
+    if (!sx) {   // the shared-string verifier's candidates are deduplicated by sorting
+        CKS(ensure_t(ctx, B_HASH, (size_t)hsize, &table));
+        CK(cudaMemsetAsync(table, 0xFF, hsize * sizeof(uint64_t), s));
+    }
     if (emitted) {
     } else if (bs.table_smem) {
         SharedEmit se{};
@@ -777,19 +785,26 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     // queue order: 0 follows the verifier (persistent: length classes; grid-
     // strided: by first string), measured best for each on the long-DNA and the
     // protein-like / text-like shapes
-    const bool sx = !defer && sx_choice(ctx, pl, p, bs.vc);
-    const int pq_threads = sx ? 0 : pq_choice(ctx, pl, p, bs.vc);
-    // the shared-string verifier needs its pairs grouped by their longer string
-    const int order = sx ? 5 : bs.any_order ? 2 : ctx->sched.order != 0 ? ctx->sched.order : (pq_threads > 0 ? 4 : 3);
     uint32_t *fbins = nullptr;
     uint64_t *fstarts = nullptr;
     // the shared-string verifier's window and length-difference classes
     const SxBand sb = sx ? sx_band(p->K) : SxBand{0, 1u, 1u};
     const int64_t nb = n * (int64_t)sb.nclass;   // candidate bins of order 3 / 5
-    if (order == 3 || order == 5) {
+    if (sx) {
+        // the shared-string verifier's tasks: the distinct pairs sorted by their
+        // longer string and the class of their length difference
+        void *dgt = nullptr;
+        uint64_t *gstart = nullptr, *sorted_cand = nullptr;
+        CKS(ensure_t(ctx, B_FBINS, (size_t)nb + 1, &fbins));
+        CKS(ensure_t(ctx, B_FSTARTS, (size_t)nb + 2, &fstarts));
+        CKS(ensure_t(ctx, B_GSTART, (size_t)nb + 1, &gstart));
+        CKS(ensure(ctx, B_DG_TEMP, dedup_grouped_temp_bytes(cap), &dgt));
+        CK(launch_dedup_grouped(raw, cand, cap, n, pl.lens, sb.nclass, sb.width, cnt, dgt, fbins, fstarts, gstart,
+                                &sorted_cand, s));
+        cand = sorted_cand;
+    } else if (order == 3 || order == 5) {
         // candidates ordered by their first string (a warp's pairs share it), or
-        // by their longer string (the string whose match masks are built), for
-        // the shared-string verifier also by the class of the length difference
+        // by their longer string (the string whose match masks are built)
         uint32_t *hcount = nullptr;
         void *fscan = nullptr;
         CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));

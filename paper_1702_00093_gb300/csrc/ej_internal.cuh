@@ -276,6 +276,18 @@ cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uin
 // max_len to 256 classes). hcount (hsize uint32) and bins (count_bins() uint64)
 // start at zero.
 int count_bins();
+// Dedup by sorting, for the shared-string verifier: raw[0 .. counters[0]) (the
+// rest of cap is overwritten) is sorted by (longer string, class of the length
+// difference, other string) with the LSD radix sort (alt: cap entries), the
+// distinct pairs written in that order to *cand_out (raw or alt, the other
+// holding the sorted keys) and counted in counters[2]; per group g = x * nclass
+// + class: bins[g] (nb + 1 uint32, cleared here) its count, ends[g] its end
+// offset (nb uint64), gstart (nb uint64) scratch. temp: dedup_grouped_temp_bytes.
+size_t dedup_grouped_temp_bytes(uint64_t cap);
+cudaError_t launch_dedup_grouped(uint64_t *raw, uint64_t *alt, uint64_t cap, int64_t n, const int32_t *lens,
+                                 uint32_t nclass, uint32_t width, unsigned long long *counters, void *temp,
+                                 uint32_t *bins, uint64_t *ends, uint64_t *gstart, uint64_t **cand_out,
+                                 cudaStream_t s);
 struct VerifySeg;
 // Union of the candidate lists of a merged launch's joins (segs[0 .. nseg)):
 // every distinct pair once in upairs, with the mask of the joins that list it

@@ -725,6 +725,134 @@ cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *t
 int count_bins() { return COUNT_BINS; }
 
 // ---------------------------------------------------------------------------
+// Deduplication by sorting, grouped for the shared-string verifier
+// ---------------------------------------------------------------------------
+// Raw pair (i << 32 | j) -> key x << (cb + yb) | class << yb | y with x the
+// longer string (the first on a tie), y the other and class the length
+// difference's class; the capacity past the raw count gets the sentinel ~0.
+__global__ void group_key_kernel(uint64_t *__restrict__ a, uint64_t cap, const unsigned long long *__restrict__ counters,
+                                 const int32_t *__restrict__ lens, uint32_t yb, uint32_t cb, uint32_t nclass,
+                                 uint32_t width) {
+    const unsigned long long nraw_all = counters[0];
+    const uint64_t nraw = nraw_all < cap ? nraw_all : cap;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x) {
+        if (e >= nraw) {
+            a[e] = ~0ull;
+            continue;
+        }
+        const uint64_t v = a[e], i = v >> 32, j = v & 0xFFFFFFFFull;
+        const int32_t li = lens[i], lj = lens[j];
+        const bool i_long = li >= lj;
+        const uint64_t x = i_long ? i : j, y = i_long ? j : i;
+        uint32_t c = (uint32_t)(i_long ? li - lj : lj - li) / width;
+        c = c < nclass ? c : nclass - 1u;
+        a[e] = (x << (cb + yb)) | ((uint64_t)c << yb) | y;
+    }
+}
+
+// flags[e] = 1 for the first key of each run of equal keys (sentinels excluded)
+__global__ void group_unique_kernel(const uint64_t *__restrict__ k, uint64_t cap, uint8_t *__restrict__ flags) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = k[e];
+        flags[e] = (v != ~0ull && (e == 0 || k[e - 1] != v)) ? 1 : 0;
+    }
+}
+
+// The distinct keys back to pairs, in key order, at out[offs[e]]; per group
+// g = x * nclass + class (< n * nclass) its count (warp-aggregated: a warp's
+// keys are sorted, so its lanes of one group are consecutive) and, at the
+// group's first key, its start.
+__global__ void group_compact_kernel(const uint64_t *__restrict__ k, const uint8_t *__restrict__ flags,
+                                     const uint64_t *__restrict__ offs, uint64_t cap, uint32_t yb, uint32_t cb,
+                                     uint32_t nclass, uint64_t *__restrict__ out, uint32_t *__restrict__ bins,
+                                     uint64_t *__restrict__ gstart) {
+    const uint64_t ymask = (1ull << yb) - 1ull, cmask = (1ull << cb) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t base = e0 - (threadIdx.x & 31); base < cap; base += stride) {   // warp-uniform trip count
+        const uint64_t e = base + (threadIdx.x & 31);
+        const bool f = e < cap && flags[e];
+        uint64_t g = ~0ull;
+        if (f) {
+            const uint64_t v = k[e];
+            const uint64_t x = v >> (cb + yb), y = v & ymask;
+            out[offs[e]] = x < y ? (x << 32 | y) : (y << 32 | x);
+            g = x * nclass + ((v >> yb) & cmask);
+            // the group's first distinct key: the key before it is in another group
+            if (e == 0 || (k[e - 1] >> yb) != (v >> yb)) gstart[g] = offs[e];
+        }
+        const unsigned peers = __match_any_sync(FULL, g);
+        if (f && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&bins[g], (unsigned)__popc(peers));
+    }
+}
+
+// ends[g] = start + count of every group (read by the task builder where count > 0)
+__global__ void group_ends_kernel(const uint32_t *__restrict__ bins, const uint64_t *__restrict__ gstart, int64_t nb,
+                                  uint64_t *__restrict__ ends) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x)
+        ends[g] = bins[g] ? gstart[g] + bins[g] : 0ull;
+}
+
+size_t dedup_grouped_temp_bytes(uint64_t cap) {
+    const size_t counts = radix_counts_len((int64_t)cap, 1);
+    const size_t a = counts * 4, b = counts * 8;
+    const size_t scan = scan_temp_bytes((int64_t)(counts > cap + 1 ? counts : cap + 1));
+    const size_t flags = ((size_t)cap + 15) & ~(size_t)15;
+    const size_t offs = ((size_t)cap + 1) * 8;
+    return ((a + 15) & ~(size_t)15) + ((b + 15) & ~(size_t)15) + ((scan + 15) & ~(size_t)15) + flags + offs;
+}
+
+cudaError_t launch_dedup_grouped(uint64_t *raw, uint64_t *alt, uint64_t cap, int64_t n, const int32_t *lens,
+                                 uint32_t nclass, uint32_t width, unsigned long long *counters, void *temp,
+                                 uint32_t *bins, uint64_t *ends, uint64_t *gstart, uint64_t **cand_out,
+                                 cudaStream_t s) {
+    if (nclass < 1 || width < 1 || cap == 0) return cudaErrorInvalidValue;
+    uint32_t yb = 1;
+    while ((1ll << yb) < n) yb++;
+    uint32_t cb = 0;
+    while ((1u << cb) < nclass) cb++;
+    const uint32_t bits = 2 * yb + cb;
+    if (bits > 64) return cudaErrorInvalidValue;
+    const int64_t nb = n * (int64_t)nclass;
+    // carve the temporary area
+    char *t = (char *)temp;
+    const size_t counts = radix_counts_len((int64_t)cap, 1);
+    RadixTemp rt;
+    rt.counts = (uint32_t *)t;
+    t += (counts * 4 + 15) & ~(size_t)15;
+    rt.offsets = (uint64_t *)t;
+    t += (counts * 8 + 15) & ~(size_t)15;
+    rt.scan_temp = t;
+    t += (scan_temp_bytes((int64_t)(counts > cap + 1 ? counts : cap + 1)) + 15) & ~(size_t)15;
+    uint8_t *flags = (uint8_t *)t;
+    t += ((size_t)cap + 15) & ~(size_t)15;
+    uint64_t *offs = (uint64_t *)t;
+    const int64_t g = (int64_t)((cap + 255) / 256);
+    const unsigned gs = (unsigned)(g > 152 * 64 ? 152 * 64 : (g ? g : 1));
+    group_key_kernel<<<gs, 256, 0, s>>>(raw, cap, counters, lens, yb, cb, nclass, width);
+    note_launches(1);
+    int shifts[8];
+    int np = 0;
+    for (uint32_t b = 0; b < bits; b += 8) shifts[np++] = (int)b;
+    bool in_alt = false;
+    cudaError_t e = radix_sort_segmented(raw, nullptr, alt, nullptr, (int64_t)cap, 1, shifts, np, rt, &in_alt, s);
+    if (e != cudaSuccess) return e;
+    uint64_t *keys = in_alt ? alt : raw, *out = in_alt ? raw : alt;
+    group_unique_kernel<<<gs, 256, 0, s>>>(keys, cap, flags);
+    note_launches(1);
+    if ((e = exclusive_scan_u8(flags, offs, (int64_t)cap, (uint64_t *)&counters[2], rt.scan_temp, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(bins, 0, (size_t)(nb + 1) * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    group_compact_kernel<<<gs, 256, 0, s>>>(keys, flags, offs, cap, yb, cb, nclass, out, bins, gstart);
+    const int64_t gg = (nb + 255) / 256;
+    group_ends_kernel<<<(unsigned)(gg > 4096 ? 4096 : (gg ? gg : 1)), 256, 0, s>>>(bins, gstart, nb, ends);
+    note_launches(2);
+    *cand_out = out;
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
 // Union of the candidate lists of a merged verifier launch
 // ---------------------------------------------------------------------------
 
