@@ -205,9 +205,13 @@ struct RadixTemp {
     void *scan_temp;
 };
 size_t radix_counts_len(int64_t seg_len, int64_t nseg);
+// len_dev (nseg == 1 only, may be null): a device count; only the first
+// min(*len_dev, seg_len) records are sorted (the rest of both buffers is left
+// as it is).
 cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                                  int64_t seg_len, int64_t nseg, const int *shifts, int npasses,
-                                 RadixTemp tmp, bool *in_alt, cudaStream_t s);
+                                 RadixTemp tmp, bool *in_alt, cudaStream_t s,
+                                 const unsigned long long *len_dev = nullptr);
 
 // One block per table: stable sort of (key, id) records whose key has kb bits and
 // whose ids need idb bits (idb + kb <= 64, n <= table_sort_max()); records start
@@ -277,7 +281,7 @@ cudaError_t launch_dedup(const uint64_t *raw, uint64_t cap, uint64_t *table, uin
 // start at zero.
 int count_bins();
 // Dedup by sorting, for the shared-string verifier: raw[0 .. counters[0]) (the
-// rest of cap is overwritten) is sorted by (longer string, class of the length
+// rest of cap is not read) is sorted by (longer string, class of the length
 // difference, other string) with the LSD radix sort (alt: cap entries), the
 // distinct pairs written in that order to *cand_out (raw or alt, the other
 // holding the sorted keys) and counted in counters[2]; per group g = x * nclass

@@ -729,17 +729,13 @@ int count_bins() { return COUNT_BINS; }
 // ---------------------------------------------------------------------------
 // Raw pair (i << 32 | j) -> key x << (cb + yb) | class << yb | y with x the
 // longer string (the first on a tie), y the other and class the length
-// difference's class; the capacity past the raw count gets the sentinel ~0.
+// difference's class, for the raw pairs a[0 .. min(counters[0], cap)).
 __global__ void group_key_kernel(uint64_t *__restrict__ a, uint64_t cap, const unsigned long long *__restrict__ counters,
                                  const int32_t *__restrict__ lens, uint32_t yb, uint32_t cb, uint32_t nclass,
                                  uint32_t width) {
     const unsigned long long nraw_all = counters[0];
     const uint64_t nraw = nraw_all < cap ? nraw_all : cap;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x) {
-        if (e >= nraw) {
-            a[e] = ~0ull;
-            continue;
-        }
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = a[e], i = v >> 32, j = v & 0xFFFFFFFFull;
         const int32_t li = lens[i], lj = lens[j];
         const bool i_long = li >= lj;
@@ -750,12 +746,14 @@ __global__ void group_key_kernel(uint64_t *__restrict__ a, uint64_t cap, const u
     }
 }
 
-// flags[e] = 1 for the first key of each run of equal keys (sentinels excluded)
-__global__ void group_unique_kernel(const uint64_t *__restrict__ k, uint64_t cap, uint8_t *__restrict__ flags) {
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t v = k[e];
-        flags[e] = (v != ~0ull && (e == 0 || k[e - 1] != v)) ? 1 : 0;
-    }
+// flags[e] = 1 for the first key of each run of equal keys among the first
+// min(counters[0], cap) (0 past them)
+__global__ void group_unique_kernel(const uint64_t *__restrict__ k, uint64_t cap,
+                                    const unsigned long long *__restrict__ counters, uint8_t *__restrict__ flags) {
+    const unsigned long long nraw_all = counters[0];
+    const uint64_t nraw = nraw_all < cap ? nraw_all : cap;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x)
+        flags[e] = (e < nraw && (e == 0 || k[e - 1] != k[e])) ? 1 : 0;
 }
 
 // The distinct keys back to pairs, in key order, at out[offs[e]]; per group
@@ -835,10 +833,11 @@ cudaError_t launch_dedup_grouped(uint64_t *raw, uint64_t *alt, uint64_t cap, int
     int np = 0;
     for (uint32_t b = 0; b < bits; b += 8) shifts[np++] = (int)b;
     bool in_alt = false;
-    cudaError_t e = radix_sort_segmented(raw, nullptr, alt, nullptr, (int64_t)cap, 1, shifts, np, rt, &in_alt, s);
+    cudaError_t e = radix_sort_segmented(raw, nullptr, alt, nullptr, (int64_t)cap, 1, shifts, np, rt, &in_alt, s,
+                                         counters);   // the raw count, read on the device
     if (e != cudaSuccess) return e;
     uint64_t *keys = in_alt ? alt : raw, *out = in_alt ? raw : alt;
-    group_unique_kernel<<<gs, 256, 0, s>>>(keys, cap, flags);
+    group_unique_kernel<<<gs, 256, 0, s>>>(keys, cap, counters, flags);
     note_launches(1);
     if ((e = exclusive_scan_u8(flags, offs, (int64_t)cap, (uint64_t *)&counters[2], rt.scan_temp, s)) != cudaSuccess)
         return e;

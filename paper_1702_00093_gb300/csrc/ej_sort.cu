@@ -162,16 +162,18 @@ size_t radix_counts_len(int64_t seg_len, int64_t nseg) {
 
 __global__ void __launch_bounds__(RS_THREADS)
 radix_hist_kernel(const uint64_t *__restrict__ keys, int64_t seg_len, int tps, int shift,
-                  uint32_t *__restrict__ counts) {
+                  uint32_t *__restrict__ counts, const unsigned long long *__restrict__ len_dev) {
     __shared__ uint32_t h[256];
     const int tile = blockIdx.x;
     const int64_t seg = blockIdx.y;
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t seg_base = seg * seg_len, tile_base = (int64_t)tile * RS_TILE;
+    int64_t len = seg_len;   // records of the segment that take part
+    if (len_dev) len = (int64_t)*len_dev < seg_len ? (int64_t)*len_dev : seg_len;
     for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
         int64_t e = tile_base + i;
-        if (e < seg_len) atomicAdd(&h[(uint32_t)(keys[seg_base + e] >> shift) & 0xFFu], 1u);
+        if (e < len) atomicAdd(&h[(uint32_t)(keys[seg_base + e] >> shift) & 0xFFu], 1u);
     }
     __syncthreads();
     counts[(seg * 256 + threadIdx.x) * tps + tile] = h[threadIdx.x];
@@ -180,7 +182,8 @@ radix_hist_kernel(const uint64_t *__restrict__ keys, int64_t seg_len, int tps, i
 __global__ void __launch_bounds__(RS_THREADS)
 radix_scatter_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                      uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                     int64_t seg_len, int tps, int shift, const uint64_t *__restrict__ offsets) {
+                     int64_t seg_len, int tps, int shift, const uint64_t *__restrict__ offsets,
+                     const unsigned long long *__restrict__ len_dev) {
     __shared__ uint32_t wcnt[RS_WARPS][256];
     __shared__ uint64_t s_off[256];
     const int tile = blockIdx.x;
@@ -188,6 +191,8 @@ radix_scatter_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__res
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t seg_base = seg * seg_len;
     const int64_t sub_base = (int64_t)tile * RS_TILE + (int64_t)warp * (RS_ITEMS * 32);
+    int64_t len = seg_len;   // records of the segment that take part
+    if (len_dev) len = (int64_t)*len_dev < seg_len ? (int64_t)*len_dev : seg_len;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; w++) wcnt[w][threadIdx.x] = 0;
     s_off[threadIdx.x] = offsets[(seg * 256 + threadIdx.x) * tps + tile];
@@ -201,7 +206,7 @@ radix_scatter_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__res
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; it++) {
         const int64_t e = sub_base + it * 32 + lane;
-        const bool ok = e < seg_len;
+        const bool ok = e < len;
         k[it] = ok ? keys_in[seg_base + e] : 0ull;
         v[it] = (ok && vals_in) ? vals_in[seg_base + e] : 0u;
         const uint32_t d = ok ? ((uint32_t)(k[it] >> shift) & 0xFFu) : 256u;
@@ -241,7 +246,8 @@ radix_scatter_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__res
 
 cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                                  int64_t seg_len, int64_t nseg, const int *shifts, int npasses,
-                                 RadixTemp tmp, bool *in_alt, cudaStream_t s) {
+                                 RadixTemp tmp, bool *in_alt, cudaStream_t s, const unsigned long long *len_dev) {
+    if (len_dev && nseg != 1) return cudaErrorInvalidValue;
     *in_alt = false;
     if (seg_len == 0 || nseg == 0 || npasses == 0) return cudaGetLastError();
     const int tps = (int)((seg_len + RS_TILE - 1) / RS_TILE);
@@ -250,11 +256,11 @@ cudaError_t radix_sort_segmented(uint64_t *keys, uint32_t *vals, uint64_t *keys_
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < npasses; p++) {
-        radix_hist_kernel<<<grid, RS_THREADS, 0, s>>>(ki, seg_len, tps, shifts[p], tmp.counts);
+        radix_hist_kernel<<<grid, RS_THREADS, 0, s>>>(ki, seg_len, tps, shifts[p], tmp.counts, len_dev);
         cudaError_t e = exclusive_scan_u32(tmp.counts, tmp.offsets, ncounts, nullptr, tmp.scan_temp, s);
         if (e != cudaSuccess) return e;
         radix_scatter_kernel<<<grid, RS_THREADS, 0, s>>>(ki, vi, ko, vo, seg_len, tps, shifts[p],
-                                                         tmp.offsets);
+                                                         tmp.offsets, len_dev);
         note_launches(2);
         uint64_t *kt = ki; ki = ko; ko = kt;
         uint32_t *vt = vi; vi = vo; vo = vt;
