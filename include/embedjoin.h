@@ -361,13 +361,18 @@ void ej_batch_destroy(ej_batch *batch);
  *     class, longest first (the shorter string's length in 256 classes), so
  *     that the pairs a warp takes have similar lengths and the longest start
  *     first; 5: by the pair's longer string (the one whose match masks the
- *     verifier builds; always used with mode 3); 3: by the pair's first string
+ *     verifier builds) and, with mode 3 (which always uses it), by the class of
+ *     the length difference; 3: by the pair's first string
  *     (a counting sort: the pairs a warp
  *     takes share their first string, so they read the same memory and, through
  *     the length filter, have similar lengths); 1: by decreasing number of tables
  *     in which the two strings collided; 2: hash-table order. 0 (default): 4
  *     with the persistent verifier, 3 with the grid-strided one, 5 with the
- *     shared-string one.
+ *     shared-string one (whose candidates are grouped by a sort, not a hash
+ *     table). In a batch's union launch (chain 0 / 4) the joins' candidates
+ *     keep hash order and the union is ordered by the shorter string's length
+ *     class, then by the number of joins that list the pair (1: that number
+ *     first).
  *   buckets: 0 (default) or 1: equal signatures are grouped by hashing (per
  *     table an open-addressing set whose slots head lists of records); a
  *     record pairs with the later records of its list, so a bucket of b strings
