@@ -789,7 +789,7 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
     uint64_t *fstarts = nullptr;
     // the shared-string verifier's window and length-difference classes
     const SxBand sb = sx ? sx_band(p->K) : SxBand{0, 1u, 1u};
-    const int64_t nb = n * (int64_t)sb.nclass;   // candidate bins of order 3 / 5
+    const int64_t nb = n * (int64_t)sb.nclass;   // the shared-string verifier's candidate groups
     if (sx) {
         // the shared-string verifier's tasks: the distinct pairs sorted by their
         // longer string and the class of their length difference
@@ -804,17 +804,17 @@ int back_attempt(ej_ctx *ctx, const Plan &pl, const ej_params *p, const BackStat
         cand = sorted_cand;
     } else if (order == 3 || order == 5) {
         // candidates ordered by their first string (a warp's pairs share it), or
-        // by their longer string (the string whose match masks are built)
+        // by their longer string
         uint32_t *hcount = nullptr;
         void *fscan = nullptr;
         CKS(ensure_t(ctx, B_HCOUNT, (size_t)hsize, &hcount));
-        CKS(ensure_t(ctx, B_FBINS, (size_t)nb + 1, &fbins));
-        CKS(ensure_t(ctx, B_FSTARTS, (size_t)nb + 2, &fstarts));
-        CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(nb + 1), &fscan));
+        CKS(ensure_t(ctx, B_FBINS, (size_t)n + 1, &fbins));
+        CKS(ensure_t(ctx, B_FSTARTS, (size_t)n + 2, &fstarts));
+        CKS(ensure(ctx, B_FSCAN, scan_temp_bytes(n + 1), &fscan));
         CK(cudaMemsetAsync(hcount, 0, hsize * sizeof(uint32_t), s));
-        CK(cudaMemsetAsync(fbins, 0, (size_t)(nb + 1) * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(fbins, 0, (size_t)(n + 1) * sizeof(uint32_t), s));
         CK(launch_dedup_by_first(raw, cap, table, hcount, hsize, n, fbins, fstarts, fscan, cand, cnt, s,
-                                 order == 5 ? pl.lens : nullptr, sb.nclass, sb.width));
+                                 order == 5 ? pl.lens : nullptr));
     } else if (order != 2) {
         // candidates handed to the verifier longest first (order 4: length classes,
         // so that the pairs a warp takes have similar lengths) or most-collided

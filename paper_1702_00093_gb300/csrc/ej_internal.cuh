@@ -342,15 +342,12 @@ cudaError_t launch_dedup_classes(const uint64_t *raw, uint64_t cap, uint64_t *ta
                                  unsigned long long *counters, cudaStream_t s);
 // Dedup ordered by the pair's first string (counting sort over n bins): bins
 // (n + 1 uint32) and hcount start at zero; starts holds n + 2 uint64.
-// With longer_lens, the bins are the pairs' longer strings (the grouping of the
-// shared-string verifier), each split into nclass bins by the length
-// difference d (class min(d / width, nclass - 1)): n * nclass bins (bins and
-// starts then hold n * nclass + 1 and + 2 entries); after the call starts[b]
-// is the end of bin b.
+// With longer_lens, the bins are the pairs' longer strings; after the call
+// starts[x] is the end of bin x.
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
                                   unsigned long long *counters, cudaStream_t s,
-                                  const int32_t *longer_lens = nullptr, uint32_t nclass = 1, uint32_t width = 1);
+                                  const int32_t *longer_lens = nullptr);
 // Shared-string verifier (ej_verify_sx.cu): warp tasks of up to 16 candidates
 // that share their longer string and length-difference class, from the bins of
 // launch_dedup_by_first with longer_lens (nb = n * nclass bins; tcount nb+1

@@ -665,28 +665,20 @@ __global__ void count_scatter_kernel(const uint64_t *__restrict__ table, const u
 // consecutive candidates share their first string, so a warp's pairs read the
 // same string and, through the length filter, have similar lengths.
 // With lens, the bin is the pair's longer string instead (the first one on a
-// tie), which groups the pairs that share the string whose match masks the
-// verifier builds; with nclass > 1, that string's bin is split further by the
-// class of the length difference, x * nclass + min(d / width, nclass - 1).
-__device__ __forceinline__ uint64_t first_bin(uint64_t key, const int32_t *__restrict__ lens, uint32_t nclass,
-                                              uint32_t width) {
+// tie).
+__device__ __forceinline__ uint64_t first_bin(uint64_t key, const int32_t *__restrict__ lens) {
     const uint64_t a = key >> 32, b = key & 0xFFFFFFFFull;
     if (!lens) return a;
-    const int32_t la = lens[a], lb = lens[b];
-    const uint64_t x = la >= lb ? a : b;
-    if (nclass <= 1) return x;
-    const uint32_t c = (uint32_t)(la >= lb ? la - lb : lb - la) / width;
-    return x * nclass + (c < nclass ? c : nclass - 1u);
+    return lens[a] >= lens[b] ? a : b;
 }
 
 __global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
-                                  uint32_t nclass, uint32_t width, uint32_t *__restrict__ bins,
-                                  unsigned long long *__restrict__ counters) {
+                                  uint32_t *__restrict__ bins, unsigned long long *__restrict__ counters) {
     unsigned int mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
         if (key != ~0ull) {
-            atomicAdd(&bins[first_bin(key, lens, nclass, width)], 1u);
+            atomicAdd(&bins[first_bin(key, lens)], 1u);
             mine++;
         }
     }
@@ -695,29 +687,25 @@ __global__ void first_hist_kernel(const uint64_t *__restrict__ table, uint64_t h
 }
 
 __global__ void first_scatter_kernel(const uint64_t *__restrict__ table, uint64_t hsize, const int32_t *__restrict__ lens,
-                                     uint32_t nclass, uint32_t width, unsigned long long *__restrict__ cursor,
-                                     uint64_t *__restrict__ cand) {
+                                     unsigned long long *__restrict__ cursor, uint64_t *__restrict__ cand) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)hsize; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = table[i];
-        if (key != ~0ull) cand[atomicAdd(&cursor[first_bin(key, lens, nclass, width)], 1ull)] = key;
+        if (key != ~0ull) cand[atomicAdd(&cursor[first_bin(key, lens)], 1ull)] = key;
     }
 }
 
 cudaError_t launch_dedup_by_first(const uint64_t *raw, uint64_t cap, uint64_t *table, uint32_t *hcount, uint64_t hsize,
                                   int64_t n, uint32_t *bins, uint64_t *starts, void *scan_tmp, uint64_t *cand,
-                                  unsigned long long *counters, cudaStream_t s, const int32_t *longer_lens,
-                                  uint32_t nclass, uint32_t width) {
-    if (nclass < 1 || width < 1) return cudaErrorInvalidValue;
-    const int64_t nb = n * (int64_t)nclass;   // bins (the scan covers nb + 1 entries)
+                                  unsigned long long *counters, cudaStream_t s, const int32_t *longer_lens) {
     int64_t g = ((int64_t)cap + 255) / 256;
     dedup_count_kernel<<<(unsigned)(g > 8192 ? 8192 : (g ? g : 1)), 256, 0, s>>>(raw, cap, table, hcount, hsize, counters);
     int64_t gh = ((int64_t)hsize + 255) / 256;
     const unsigned gs = (unsigned)(gh > 2048 ? 2048 : (gh ? gh : 1));
-    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, nclass, width, bins, counters);
+    first_hist_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, bins, counters);
     note_launches(2);
-    cudaError_t e = exclusive_scan_u32(bins, starts, nb + 1, nullptr, scan_tmp, s);
+    cudaError_t e = exclusive_scan_u32(bins, starts, n + 1, nullptr, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, nclass, width, (unsigned long long *)starts, cand);
+    first_scatter_kernel<<<gs, 256, 0, s>>>(table, hsize, longer_lens, (unsigned long long *)starts, cand);
     note_launches(1);
     return cudaGetLastError();
 }
