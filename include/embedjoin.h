@@ -411,9 +411,11 @@ typedef struct {
                         waits for another's last pairs); 2: one launch per join, one after
                         another; 1: one launch per join, free to overlap (two persistent
                         grids sharing the SMs were measured up to 10x slower at times);
-                        0 (default): 4 when the wider band adds at most half the
+                        0 (default): when the wider band adds at most half the
                         word-columns of the joins' own bands (candidate counts of the
-                        sizing pass), else 2 */
+                        sizing pass), 4 while the joins' candidates come to fewer than
+                        32 per pair slot of one warp per SM sub-partition (the launch is
+                        then set by its longest pairs), else 3; otherwise 2 */
 } ej_schedule;
 
 /* NULL restores the defaults. Errors: EJ_ERR_INVALID_ARG for values outside

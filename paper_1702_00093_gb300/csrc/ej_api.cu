@@ -1277,10 +1277,11 @@ void batch_sources(std::vector<BatchJoin> &joins) {
 // last pairs. Mode 4: it runs over the union of their candidates, each distinct
 // pair once at the largest K of the joins that list it (its distance, exact up
 // to that K, decides it for every one of them): joins over the same strings
-// whose signatures nest share most of their candidates. Mode 0 merges (as 4)
-// when the wider band adds at most half of the word-columns the joins' own
-// bands would run (estimated from the eager pass's candidate counts);
-// otherwise, as mode 2, the launches are chained.
+// whose signatures nest share most of their candidates. Mode 0 merges when the
+// wider band adds at most half of the word-columns the joins' own bands would
+// run (estimated from the eager pass's candidate counts), as 4 while the
+// candidates are few for the slots, else as 3; otherwise, as mode 2, the
+// launches are chained.
 int batch_plan_merge(ej_batch *b) {
     ej_ctx *ctx = b->ctx;
     const int mode = ctx->sched.chain;
@@ -1315,12 +1316,24 @@ int batch_plan_merge(ej_batch *b) {
     b->mW1 = W1;
     b->mK = K;
     b->mthreads = threads;
-    if (mode == 0 || mode == 4) {
+    // mode 0: the union while the launch is set by its longest pairs (fewer than
+    // 32 pairs per slot of one warp per SM sub-partition, measured faster: 0.63 vs
+    // 0.67 ms on long DNA), the joins in turn when its total work sets it (29.6 vs
+    // 32.0 ms at 600 pairs per slot)
+    double total = 0.0;
+    for (int i : pq) total += (double)b->joins[(size_t)i].ncand;
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const bool tail_bound = total < 32.0 * (double)(dev_sms > 0 ? dev_sms : 1) * 4 * 16;
+    if (mode == 4 || (mode == 0 && tail_bound)) {
         b->munion = true;
         for (int i : pq) b->joins[(size_t)i].bs.any_order = true;   // the union orders the candidates
         for (int i : pq) b->ucap += b->joins[(size_t)i].cap;
+        // the union holds at most the joins' capacities together (each of which
+        // already has a margin over its candidates): a table of that many slots
+        // always has room, and is scanned whole by the union's order pass
         b->uhsize = 1;
-        while (b->uhsize < 2 * b->ucap) b->uhsize <<= 1;
+        while (b->uhsize < b->ucap + 1) b->uhsize <<= 1;
         CK(cudaMalloc(&b->utable, b->uhsize * sizeof(uint64_t)));
         CK(cudaMalloc(&b->utmask, b->uhsize * sizeof(uint32_t)));
         CK(cudaMalloc(&b->upairs, b->ucap * sizeof(uint64_t)));
