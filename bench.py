@@ -62,7 +62,7 @@ VERIFY_SOURCE = os.path.join(ROOT, "paper_1702_00093_gb300", "csrc", "ej_verify_
 # one ncu capture of the long-DNA workload: "merged" = the batch's merged launch,
 # "join" = mean over the K=50/150/250 launches of ej_join; valid only while the
 # verify source is the one that was captured
-VERIFY_TRAFFIC = {"source_sha256_prefix": "073febaed54b1ec6", "bytes_per_launch": {"merged": 13760768, "join": None}}
+VERIFY_TRAFFIC = {"source_sha256_prefix": "de1e03ec8e06edd5", "bytes_per_launch": {"merged": 13802496, "join": None}}
 RECALL_SAMPLES = os.path.join(ROOT, "oracle", "recall_samples.json")
 
 

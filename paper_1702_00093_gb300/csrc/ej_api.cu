@@ -1370,7 +1370,8 @@ int batch_merged_verify(ej_batch *b, cudaStream_t s) {
     }
     CK(launch_verify_pq(b->mW1, b->mthreads, ctx->sched.slots_per_warp ? ctx->sched.slots_per_warp : 16,
                         ctx->sched.warps_per_subpartition, pl.packed, pl.pofs,
-                        pl.B, pl.lens, pl.st.n, b->joins[0].p.alphabet_size, nullptr, (int64_t)total_cap, b->mK, vo, s));
+                        pl.B, pl.lens, pl.st.n, b->joins[0].p.alphabet_size, nullptr, (int64_t)total_cap, b->mK, vo, s,
+                        b->munion));   // the union launch runs only while its pairs are few
     return EJ_OK;
 }
 

@@ -463,9 +463,12 @@ inline int pq_words(int32_t K) {
 }
 size_t pq_smem_bytes(int W1, uint32_t alpha, int threads);
 int pq_threads_for(int W1, uint32_t alpha);   // 0 if no block size fits
+// lean: the variant for launches set by their longest pairs (few pairs per
+// slot): chunks in which every running pair has all its columns skip the
+// per-column guard (a second copy of the column loop)
 cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,
                              const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
-                             int32_t K, VerifyOut vo, cudaStream_t s);
+                             int32_t K, VerifyOut vo, cudaStream_t s, bool lean = false);
 // Shared-string verifier (W1 = 2..12): the pairs of tasks[0 .. *ntasks_dev)
 // (at most ntasks_cap), each task up to 16 pairs sharing their longer string.
 cudaError_t launch_verify_sx(int W1, const uint4 *packed, const uint64_t *pofs, int B, const int32_t *lens, int64_t n,

@@ -32,6 +32,7 @@
 // current columns inside their bands, where the values are exact, so
 // m_fwd + m_bwd > K proves ED > K; both lanes of the pair stop.
 #include <climits>
+#include <type_traits>
 
 #include "ej_bitpar.cuh"
 
@@ -81,7 +82,7 @@ __device__ __forceinline__ uint64_t sym_reverse(uint64_t u) {
     return ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
 }
 
-template <int W1, int B, int TPB>
+template <int W1, int B, int TPB, bool LEAN>
 __global__ void __launch_bounds__(TPB, 1)
 verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ pofs,
                  const int32_t *__restrict__ lens, int64_t n_str, uint32_t alpha,
@@ -330,7 +331,11 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
         // the current one is requested one word ahead (snext: requested at the
         // previous chunk's last word, or at the pair's start)
         uint64_t sreg = 0;
-        auto run_cols = [&](int s_begin, int s_end) {
+        // steps s_begin .. s_end-1; GUARD: only the steps that are columns of the
+        // lane's pair (without it every lane advances: lanes without a running
+        // pair compute values that nothing reads)
+        auto run_cols = [&](int s_begin, int s_end, auto guard) {
+            constexpr bool GUARD = decltype(guard)::value;
 #pragma unroll 2
             for (int s = s_begin; s < s_end; s++) {
                 if ((s & (SPW - 1)) == 0) {
@@ -341,7 +346,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 uint32_t c = (uint32_t)(sreg & CMASK);
                 sreg >>= B;
                 c = c < cmax ? c : cmax;
-                if (s <= lim && s >= slo) {
+                if (!GUARD || (s <= lim && s >= slo)) {
                     const uint64_t *row = ring + ((size_t)c * R2 + base) * T_;   // the window's words
                     uint64_t Eq[W1], A[W1], S[W1];
 #pragma unroll
@@ -373,7 +378,21 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 }
             }
         };
-        run_cols(0, smove);
+        // LEAN (launches set by their longest pairs): a range of steps runs
+        // unguarded when every lane with a running pair has all its columns in
+        // it (most chunks of long pairs); with many pairs per slot the second
+        // copy of the loop costs more in instruction fetch than the guard
+        auto run_range = [&](int a, int b) {
+            if constexpr (LEAN) {
+                const bool whole = !(have && !rejected) || (slo <= a && lim >= b - 1);
+                if (__all_sync(FULL, whole)) {
+                    run_cols(a, b, std::false_type{});
+                    return;
+                }
+            }
+            run_cols(a, b, std::true_type{});
+        };
+        run_range(0, smove);
         {
             // window move before column j = jbase + smove, then the joint bound
             const int32_t j = jbase + smove;
@@ -419,7 +438,7 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
                 lim = -1;
             }
         }
-        run_cols(smove, 64);
+        run_range(smove, 64);
         jbase += 64;
         if (have && --budget < 0 && !rejected && jbase <= ncols) {
             // cannot happen for a consistent state: stop this pair and report it
@@ -519,22 +538,22 @@ verify_pq_kernel(const uint4 *__restrict__ packed, const uint64_t *__restrict__ 
     }
 }
 
-template <int W1, int B, int TPB>
+template <int W1, int B, int TPB, bool LEAN>
 cudaError_t launch_pq_tt(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
                          const uint64_t *pairs, int64_t np, int32_t K, int spw_force, int wps, VerifyOut vo,
                          cudaStream_t s) {
     constexpr int threads = TPB;
     const size_t smem = pq_smem_bytes(W1, alpha, threads);
-    cudaError_t e = cudaFuncSetAttribute(verify_pq_kernel<W1, B, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(verify_pq_kernel<W1, B, TPB, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_pq_kernel<W1, B, TPB>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_pq_kernel<W1, B, TPB, LEAN>, threads, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t blocks = (int64_t)sms * per_sm;
-    verify_pq_kernel<W1, B, TPB><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
+    verify_pq_kernel<W1, B, TPB, LEAN><<<(unsigned)blocks, threads, smem, s>>>(packed, pofs, lens, n, alpha, pairs, np, K,
                                                                      sms, spw_force, wps, vo);
     note_launches(1);
     return cudaGetLastError();
@@ -543,11 +562,15 @@ cudaError_t launch_pq_tt(const uint4 *packed, const uint64_t *pofs, const int32_
 template <int W1, int B>
 cudaError_t launch_pq_t(const uint4 *packed, const uint64_t *pofs, const int32_t *lens, int64_t n, uint32_t alpha,
                         const uint64_t *pairs, int64_t np, int32_t K, int threads, int spw_force, int wps, VerifyOut vo,
-                        cudaStream_t s) {
+                        bool lean, cudaStream_t s) {
+    // the lean variant for 2-bit codes and 128 threads (the long-string shape);
+    // the other shapes keep the guarded loop only (build time)
+    if (threads == 128 && lean && B == 2)
+        return launch_pq_tt<W1, 2, 128, true>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
     if (threads == 128)
-        return launch_pq_tt<W1, B, 128>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
+        return launch_pq_tt<W1, B, 128, false>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
     if (threads == 32)
-        return launch_pq_tt<W1, B, 32>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
+        return launch_pq_tt<W1, B, 32, false>(packed, pofs, lens, n, alpha, pairs, np, K, spw_force, wps, vo, s);
     return cudaErrorInvalidValue;
 }
 
@@ -566,13 +589,13 @@ int pq_threads_for(int W1, uint32_t alpha) {
 
 cudaError_t launch_verify_pq(int W1, int threads, int spw_force, int wps, const uint4 *packed, const uint64_t *pofs, int B,
                              const int32_t *lens, int64_t n, uint32_t alpha, const uint64_t *pairs, int64_t np,
-                             int32_t K, VerifyOut vo, cudaStream_t s) {
+                             int32_t K, VerifyOut vo, cudaStream_t s, bool lean) {
     if (np == 0) return cudaGetLastError();
     if (!vo.queue || !vo.sm_tickets || (threads != 128 && threads != 32)) return cudaErrorInvalidValue;
 #define EJ_PQ(WW)                                                                                          \
     if (W1 == WW) {                                                                                        \
-        if (B == 2) return launch_pq_t<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, s); \
-        return launch_pq_t<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, s);   \
+        if (B == 2) return launch_pq_t<WW, 2>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, lean, s); \
+        return launch_pq_t<WW, 8>(packed, pofs, lens, n, alpha, pairs, np, K, threads, spw_force, wps, vo, lean, s);   \
     }
     EJ_PQ(2) EJ_PQ(3) EJ_PQ(4) EJ_PQ(5) EJ_PQ(6) EJ_PQ(7) EJ_PQ(8) EJ_PQ(9) EJ_PQ(10) EJ_PQ(11) EJ_PQ(12)
 #undef EJ_PQ
